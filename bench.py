@@ -1,0 +1,349 @@
+"""Benchmark: batched energy + gradient evaluations per second.
+
+Workload: 20-qubit 1D TFIM VQE, H = -sum Z_i Z_{i+1} - sum X_i, 10 layers of
+[RZZ(g_l) on all 19 bonds, RX(b_l) on all qubits] from |+>^20, a batch of 1024
+parameter sets per GPU with angles ~ N(0, 0.3^2), complex64 states (8 MiB
+each).  One step = energy and full gradient for every row of the batch
+(tc_expect_grad: forward sweep, Pauli-sum pass, adjoint sweep, reduction).
+
+Timed region: W untimed warm-up steps, then K steps bracketed by a barrier and
+torch.cuda.synchronize(), timed with CUDA events on the launch stream; the
+states (2 x 8 GiB) are larger than L2, so no flush is needed.  `value` is the
+whole-job rate: rows of all ranks / max-over-ranks time.  `e2e` repeats the
+measurement with the parameters in pinned host memory, copied in each step,
+and energies + gradients copied back each step.
+
+--impl reference times the FP64 oracle on the host cores (the reference arm of
+this benchmark; a deliberately slow restatement, not a target).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2205_10091_b300 import workloads as W  # noqa: E402
+
+METRIC = "batched energy+grad evals/s"
+UNIT = "evals/s"
+N_QUBITS, LAYERS, BATCH = 20, 10, 1024
+WORKLOAD = "tfim20_l10_b1024_c64_energy_grad"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) legs
+# ---------------------------------------------------------------------------
+def oracle_step_seconds(circ, theta_row, ham, n_fd_params: int):
+    """Time the FP64 oracle on one row: forward + energy, then central
+    differences on `n_fd_params` parameters; returns (t_forward, t_per_param)."""
+    from oracle import gradients as G
+    from oracle import statevector as sv
+
+    t0 = time.perf_counter()
+    sv.energy(sv.run_circuit(circ, theta_row), circ.n, ham)
+    t1 = time.perf_counter()
+    G.finite_difference(circ, theta_row, ham, h=1e-5, params=list(range(n_fd_params)))
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / max(n_fd_params, 1)
+
+
+def _limit_threads():
+    try:
+        from threadpoolctl import threadpool_limits
+
+        return threadpool_limits(1)
+    except Exception:  # pragma: no cover
+        import contextlib
+
+        return contextlib.nullcontext()
+
+
+def cpu_baseline(circ, theta, ham) -> dict:
+    with _limit_threads():
+        tf, tp = oracle_step_seconds(circ, theta[0], ham, n_fd_params=2)
+    per_eval = tf + tp * circ.n_params
+    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"1 row of the workload: FP64 numpy forward+energy ({tf:.2f} s) and central differences "
+                       f"on 2 of {circ.n_params} parameters ({tp:.2f} s each), extrapolated to all "
+                       f"{circ.n_params} parameters; 1 thread")}
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    circ, theta, ham = W.tfim_workload(N_QUBITS, LAYERS, BATCH)
+    with _limit_threads():
+        for w in range(args.warmup):
+            oracle_step_seconds(circ, theta[w % BATCH], ham, n_fd_params=1)
+        per = []
+        for k in range(args.steps):
+            tf, tp = oracle_step_seconds(circ, theta[k % BATCH], ham, n_fd_params=1)
+            per.append(tf + tp * circ.n_params)
+    per_eval = float(np.mean(per))
+    value = 1.0 / per_eval
+    sample = (f"per step 1 row: FP64 numpy forward+energy and central differences on 1 of {circ.n_params} "
+              f"parameters, extrapolated to all; 1 thread")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "layers": LAYERS, "batch_per_gpu": BATCH},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2205_10091_b300 import native as nt
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # each rank owns an independent batch of parameter sets (weak scaling)
+    circ, theta, ham = W.tfim_workload(N_QUBITS, LAYERS, BATCH, seed=W.SEED_TFIM20 + rank)
+    c = nt.Circuit(circ)
+    H = nt.Hamiltonian(ham)
+    B, P = theta.shape
+    stream = torch.cuda.current_stream()
+    d_theta = torch.as_tensor(theta, device="cuda")
+    energy = torch.empty(B, dtype=torch.float64, device="cuda")
+    grad = torch.empty((B, P), dtype=torch.float64, device="cuda")
+
+    for _ in range(args.warmup):
+        c.expect_grad(d_theta, H, energy=energy, grad=grad)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region --------------------------------------
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    nt.profile_begin()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        c.expect_grad(d_theta, H, energy=energy, grad=grad)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = nt.profile_end()
+    clk = clocks.stop()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * B / (ms / 1e3)
+
+    # ---- end to end through host buffers -------------------------------------
+    h_theta = torch.as_tensor(theta).pin_memory()
+    h_e = torch.empty(B, dtype=torch.float64).pin_memory()
+    h_g = torch.empty((B, P), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        d_theta.copy_(h_theta, non_blocking=True)
+        c.expect_grad(d_theta, H, energy=energy, grad=grad)
+        h_e.copy_(energy, non_blocking=True)
+        h_g.copy_(grad, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        d_theta.copy_(h_theta, non_blocking=True)
+        c.expect_grad(d_theta, H, energy=energy, grad=grad)
+        h_e.copy_(energy, non_blocking=True)
+        h_g.copy_(grad, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = {"value": world * B / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h_theta.numel() * 8),
+           "d2h_bytes_per_step": int((h_e.numel() + h_g.numel()) * 8)}
+
+    # ---- plain per-circuit path: one row, unfused sweeps, forward + energy ----
+    work = torch.empty((1, 1 << N_QUBITS), dtype=torch.complex64, device="cuda")
+    e_plain = torch.empty(1, dtype=torch.float64, device="cuda")
+    one = d_theta[:1].contiguous()
+    for _ in range(2):
+        c.expect_plain(one, H, work, energy=e_plain)
+    torch.cuda.synchronize()
+    n_plain = 20
+    e0.record(stream)
+    for _ in range(n_plain):
+        c.expect_plain(one, H, work, energy=e_plain)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / n_plain
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel --------------------------------------
+    peaks, peak_src = _peaks()
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    kname, kst = top
+    achieved = kst["algo_bytes"] / (kst["ms"] / 1e3) / 1e9
+    hbm = float(peaks["hbm_gbs"])
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        if tj.get("kernel") == kname and tj.get("source_hash") == _source_hash():
+            traffic = tj.get("bytes_per_launch")
+    launches = sum(v["launches"] for v in prof.values())
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "layers": LAYERS, "batch_per_gpu": B,
+                   "params_per_row": P, "hamiltonian_terms": int(H.T), "parallelism": f"dp{world}",
+                   "l2": "inputs larger than L2 (psi and lambda: 2 x 8 GiB per 1024 rows)"},
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "kernels": {k: {"launches": v["launches"], "ms_per_launch": v["ms"] / max(v["launches"], 1),
+                        "share": v["ms"] / max(sum(x["ms"] for x in prof.values()), 1e-9),
+                        "algo_gb_per_launch": v["algo_bytes"] / max(v["launches"], 1) / 1e9}
+                    for k, v in prof.items()},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_source": f"{peak_src} hbm_gbs",
+                     "traffic": traffic},
+        "plain_path": {"value": 1e3 / plain_ms, "unit": "forward+energy evals/s", "rows": 1,
+                       "ms_per_eval": plain_ms, "what": "unfused: one HBM sweep per gate, one per Pauli term"},
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(circ, theta, ham)
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def _source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2205_10091_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

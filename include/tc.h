@@ -1,0 +1,268 @@
+/*
+ * tc.h — C-ABI of libtc_b300.so, a B300 (sm_103a) engine for the batched
+ * circuit-expectation hot path of arXiv 2205.10091 ("TensorCircuit").
+ *
+ * What is computed (the paper's definitions; readings stated where the paper
+ * is silent):
+ *   |psi(theta)> = U_G ... U_1 |psi_0>          (Section "Circuits and gates")
+ *   E(theta)     = sum_j w_j <psi|P_j|psi>       (Eq. H-pauli; Section "Pauli
+ *                                                 structures and weights")
+ *   dE/dtheta_k  for every parameter, per batch row (Section "vmap and
+ *                vectorized_value_and_grad": argnums == vectorized_argnums)
+ *
+ * Conventions
+ *   - Qubit 0 is the most significant bit of the amplitude index (Section
+ *     "Preliminaries"); a state of n qubits is 2^n interleaved complex
+ *     numbers (re, im), complex64 (TC_C64) or complex128 (TC_C128).
+ *   - Rotations are exp(-i a G / 2) with a = scale * theta[param] and
+ *     G = X, Y, Z or Z(x)Z.  The paper's exp1 form exp(i t G) is scale = -2.
+ *   - CNOT(q0, q1): q0 is the control (Section "Basic circuits and outputs").
+ *   - A Pauli structure is n bytes over {0,1,2,3} = {I,X,Y,Z}; weights are
+ *     real doubles (Section "Pauli structures and weights").
+ *   - Batches: parameters are a row-major [B][n_params] array of doubles on
+ *     the device; states are [B][2^n] complex on the device.
+ *
+ * Ownership: the caller owns every device buffer it passes and every stream.
+ * The library owns only the opaque objects it returns (plans, networks,
+ * servers) and their internal scratch, which it allocates on the device
+ * within the memory budget of tc_options and frees in the destroy call.
+ * Host arrays passed to a create call are copied before it returns.
+ *
+ * Errors: every entry point returns a tc_status.  Argument errors are found
+ * on the host before any launch and leave device memory untouched.  A CUDA
+ * launch or runtime error returns TC_E_CUDA.  tc_last_error() returns a
+ * thread-local message for the last non-TC_OK status.  No exception crosses
+ * the ABI and no device code traps.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  Calls are asynchronous with respect to the host unless
+ * stated otherwise; results are valid after the stream is synchronised.
+ */
+#ifndef TC_B300_H
+#define TC_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TC_API __attribute__((visibility("default")))
+#else
+#define TC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TC_OK = 0,
+  TC_E_INVALID = 1,     /* bad argument (message in tc_last_error) */
+  TC_E_NOMEM = 2,       /* device allocation failed or budget exceeded */
+  TC_E_CUDA = 3,        /* CUDA runtime error */
+  TC_E_TIMEOUT = 4,     /* a bounded wait ran out */
+  TC_E_UNSUPPORTED = 5, /* valid request outside what the engine implements */
+  TC_E_BUSY = 6,        /* the server is full; retry later */
+  TC_E_CANCELLED = 7    /* the request was cancelled */
+} tc_status;
+
+typedef enum { TC_C64 = 0, TC_C128 = 1 } tc_dtype;
+typedef enum { TC_INIT_ZERO = 0, TC_INIT_PLUS = 1 } tc_init;
+
+/* Gate kinds.  Matrices (qubit 0 of a two-qubit matrix = row bit 1):
+ *   H, X                      standard
+ *   RX, RY, RZ (a)            exp(-i a X/2), exp(-i a Y/2), exp(-i a Z/2)
+ *   RZZ (a) on (q0, q1)       exp(-i a Z(x)Z / 2)
+ *   CNOT (q0 control, q1 target), CZ = diag(1, 1, 1, -1)
+ *   U1                        2x2 matrix from the pool (row-major)
+ *   U2                        4x4 matrix from the pool (row-major,
+ *                             row index 2*b(q0) + b(q1)) (Section "Arbitrary
+ *                             unitaries")
+ *   PAULI_NOISE (px,py,pz)    one Monte Carlo event of the Pauli channel
+ *                             with Kraus weights (1-px-py-pz, px, py, pz) in
+ *                             the order [I, X, Y, Z] (Section "Monte Carlo
+ *                             simulation with tc.Circuit"): the uniform
+ *                             number u of the event selects the outcome whose
+ *                             left-closed interval contains u (Section
+ *                             "Externalizing the randomness").
+ */
+typedef enum {
+  TC_OP_H = 0,
+  TC_OP_X = 1,
+  TC_OP_RX = 2,
+  TC_OP_RY = 3,
+  TC_OP_RZ = 4,
+  TC_OP_RZZ = 5,
+  TC_OP_CNOT = 6,
+  TC_OP_CZ = 7,
+  TC_OP_U1 = 8,
+  TC_OP_U2 = 9,
+  TC_OP_PAULI_NOISE = 10
+} tc_opkind;
+
+/* One gate.  56 bytes, naturally aligned (the Python binding mirrors it). */
+typedef struct {
+  int32_t kind;  /* tc_opkind */
+  int32_t q0;    /* first qubit */
+  int32_t q1;    /* second qubit of a two-qubit gate, else -1 */
+  int32_t param; /* parameter index for RX/RY/RZ/RZZ, -1 = none (angle 0) */
+  double scale;  /* angle = scale * theta[param] */
+  int32_t mat;   /* U1/U2: offset (complex entries) into the matrix pool */
+  int32_t pad;
+  double px, py, pz; /* PAULI_NOISE probabilities */
+} tc_op;
+
+typedef struct {
+  int32_t tile_qubits_fwd;  /* qubits per shared-memory tile, forward (0 = default) */
+  int32_t tile_qubits_bwd;  /* same for adjoint passes (0 = default) */
+  int64_t mem_budget_bytes; /* scratch cap for tc_expect_grad (0 = 60% of free memory) */
+  int32_t reserved[8];
+} tc_options;
+
+/* Plan statistics, filled by tc_circuit_info. */
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_qubits_internal; /* >= 9: narrower circuits run with idle low qubits */
+  int32_t n_ops;
+  int32_t n_params;
+  int32_t n_noise;
+  int32_t fwd_passes;  /* HBM sweeps of the forward plan */
+  int32_t bwd_passes;  /* HBM sweeps of the adjoint plan */
+  int32_t fwd_stages;  /* register stages summed over forward passes */
+  int32_t bwd_stages;
+  int32_t tile_qubits_fwd;
+  int32_t tile_qubits_bwd;
+  int32_t reserved[5];
+} tc_plan_info;
+
+typedef struct tc_circuit tc_circuit;
+
+/*
+ * tc_circuit_create — compile an op list into a fused-pass plan.
+ *   n_qubits  1..30
+ *   ops       host array of n_ops gates (copied)
+ *   n_params  columns of the parameter matrix; every op.param < n_params
+ *   pool      host array of 2*n_pool doubles (interleaved re, im) holding the
+ *             U1/U2 matrices (copied; may be NULL when n_pool == 0)
+ *   opt       NULL for defaults
+ * Plan compilation (host): consecutive commuting gates are grouped into
+ * passes whose non-diagonal gates act on at most `tile` qubits; diagonal
+ * gates (RZ, RZZ, CZ) sharing a parameter fuse into one phase-table lookup
+ * (the paper's "preprocessing" absorbs gates into neighbours, Section
+ * "Custom contraction settings").  Returns TC_E_INVALID for out-of-range
+ * qubits, parameters or matrix offsets.
+ */
+TC_API tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc_op* ops, int n_ops,
+                            int n_params, const double* pool, int n_pool, const tc_options* opt,
+                            tc_circuit** out);
+TC_API void tc_circuit_destroy(tc_circuit* c);
+TC_API tc_status tc_circuit_info(const tc_circuit* c, tc_plan_info* out);
+
+/*
+ * tc_apply_layers — |psi_b> = U(theta_b)|psi_0> for every batch row b
+ * (Section "Basic circuits and outputs", batched as in Section "Batched
+ * circuits").
+ *   d_params      device [B][n_params] doubles (may be NULL if n_params == 0)
+ *   d_init        NULL = the circuit's tc_init state, else device [B][2^n]
+ *                 complex of the circuit's dtype (a batch of input states,
+ *                 Section "Batched input states")
+ *   seed          Philox4x32-10 key for noise events when d_status is NULL:
+ *                 event e of row b uses counter (e/4, row_offset+b, 0, 0),
+ *                 key (seed mod 2^32, seed / 2^32), output word e % 4, and
+ *                 u = (word >> 8) * 2^-24
+ *   d_status      NULL, or device [B][n_noise] floats in [0, 1): the uniform
+ *                 numbers of the noise events in op order (the paper's
+ *                 externalised `status`)
+ *   row_offset    global index of row 0 (trajectory numbering for Philox)
+ *   d_states_out  device [B][2^n] complex of the circuit's dtype (written)
+ * Scratch: none beyond d_states_out.
+ */
+TC_API tc_status tc_apply_layers(const tc_circuit* c, const double* d_params, int B, const void* d_init,
+                          uint64_t seed, const float* d_status, int64_t row_offset, void* d_states_out,
+                          void* stream);
+
+/*
+ * tc_expect_pauli_sum — E_b = sum_j w_j Re<psi_b|P_j|psi_b> for every row
+ * (Eq. H-pauli; the "vmap over Pauli structures" evaluation of Section
+ * "vmap over Pauli structures", fused: terms are grouped by their X/Y flip
+ * mask m and each group is one pass over amplitude pairs (x, x^m)).
+ *   d_states      device [B][2^n] complex of the circuit's dtype (read only)
+ *   structures    host [T][n] bytes in {0,1,2,3} (copied)
+ *   weights       host [T] doubles (copied)
+ *   d_energy_out  device [B] doubles (written)
+ * Scratch: one double per (row, shared-memory tile) inside the circuit's
+ * workspace.  Reductions: FP32/FP64 partial sums per tile, FP64 across tiles.
+ */
+TC_API tc_status tc_expect_pauli_sum(tc_circuit* c, const void* d_states, int B, const uint8_t* structures,
+                              const double* weights, int T, double* d_energy_out, void* stream);
+
+typedef enum { TC_GRAD_UNCOMPUTE = 0 } tc_grad_mode;
+
+typedef struct {
+  int32_t mode;        /* tc_grad_mode */
+  int32_t max_rows;    /* rows per device chunk (0 = as many as the budget allows) */
+  int32_t reserved[6];
+} tc_grad_options;
+
+/*
+ * tc_expect_grad — energy and full gradient for every row (Section "Batched
+ * VQE": vectorized_value_and_grad with argnums == vectorized_argnums).
+ * Method: one forward sweep, lambda = H|psi>, then one adjoint sweep over
+ * the gates in reverse that accumulates
+ *   dE/dtheta_k += s * Im <lambda|G|psi>   for each gate exp(-i s theta_k G/2)
+ * and un-applies the gate from psi and lambda (U^dagger).  The gradient is
+ * per row; the paper's summed vvag variant is the sum over rows.
+ *   d_params     device [B][n_params] doubles
+ *   d_energy_out device [B] doubles (written)
+ *   d_grad_out   device [B][n_params] doubles (written)
+ *   opt          NULL for defaults
+ * Noise events, if any, use `seed` as in tc_apply_layers (the gradient of
+ * each fixed trajectory).
+ * Scratch: two states per row in flight plus per-tile partial sums, from the
+ * circuit's workspace, capped by tc_options.mem_budget_bytes; larger batches
+ * run in chunks of rows.  TC_E_NOMEM if even one row does not fit.
+ */
+TC_API tc_status tc_expect_grad(tc_circuit* c, const double* d_params, int B, const uint8_t* structures,
+                         const double* weights, int T, uint64_t seed, double* d_energy_out,
+                         double* d_grad_out, const tc_grad_options* opt, void* stream);
+
+/*
+ * tc_expect_plain — the unfused per-circuit baseline: every gate is its own
+ * HBM sweep and every Pauli term its own reduction (the explicit-loop
+ * evaluation of Section "Explicit loop with c.expectation_ps").  Forward and
+ * energy only.  Same arguments and outputs as tc_apply_layers followed by
+ * tc_expect_pauli_sum; d_states_work is a caller buffer of [B][2^n].
+ */
+TC_API tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, const uint8_t* structures,
+                          const double* weights, int T, void* d_states_work, double* d_energy_out,
+                          void* stream);
+
+/*
+ * Launch profiling: between tc_profile_begin and tc_profile_end every kernel
+ * the library launches (from any thread) is bracketed by CUDA events recorded
+ * on its own launch stream.  tc_profile_end synchronises those events and
+ * reports, per kernel kind, the launch count, the summed device time and the
+ * summed algorithmic HBM bytes (each amplitude a launch must read or write,
+ * counted once).  Kinds: 0 forward tile pass, 1 adjoint tile pass,
+ * 2 Pauli-sum pass, 3 finalize reduction, 4 narrow-state padding,
+ * 5 unfused per-term reduction.  `out` may be NULL to count kinds only.
+ */
+typedef struct {
+  int32_t kind;
+  int32_t launches;
+  double total_ms;
+  double algo_bytes;
+} tc_kernel_stat;
+TC_API tc_status tc_profile_begin(void);
+TC_API tc_status tc_profile_end(tc_kernel_stat* out, int max_out, int* n_out);
+
+/* Thread-local message describing the last non-TC_OK status. */
+TC_API const char* tc_last_error(void);
+
+/* Library version string. */
+TC_API const char* tc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_B300_H */

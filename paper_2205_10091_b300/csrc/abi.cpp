@@ -1,0 +1,472 @@
+// C-ABI entry points of libtc_b300.so (declared in include/tc.h).
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace tcb {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+tc_status fail(tc_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+tc_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? TC_E_NOMEM : TC_E_CUDA;
+}
+void dev_free(void* p) {
+  if (p) cudaFree(p);
+}
+
+void DevPlan::release() {
+  dev_free(passes);
+  dev_free(stages);
+  dev_free(instrs);
+  dev_free(mats);
+  dev_free(diags);
+  dev_free(dents);
+  *this = DevPlan{};
+}
+cudaError_t DevPlan::upload(const PlanArrays& A) {
+  cudaError_t e;
+  if ((e = dev_upload(A.passes, &passes)) != cudaSuccess) return e;
+  if ((e = dev_upload(A.stages, &stages)) != cudaSuccess) return e;
+  if ((e = dev_upload(A.instrs, &instrs)) != cudaSuccess) return e;
+  if ((e = dev_upload(A.mats, &mats)) != cudaSuccess) return e;
+  if ((e = dev_upload(A.diags, &diags)) != cudaSuccess) return e;
+  return dev_upload(A.dents, &dents);
+}
+void DevHam::release() {
+  dev_free(passes);
+  dev_free(hdiag);
+  dev_free(hterms);
+  dev_free(hflips);
+  *this = DevHam{};
+}
+cudaError_t DevHam::upload(const HamPlan& H) {
+  cudaError_t e;
+  if ((e = dev_upload(H.passes, &passes)) != cudaSuccess) return e;
+  if ((e = dev_upload(H.hdiag, &hdiag)) != cudaSuccess) return e;
+  if ((e = dev_upload(H.hterms, &hterms)) != cudaSuccess) return e;
+  return dev_upload(H.hflips, &hflips);
+}
+
+}  // namespace tcb
+
+using namespace tcb;
+
+tc_circuit::~tc_circuit() {
+  if (uploaded) {
+    dplan.release();
+    dplain.release();
+    dham.release();
+    dev_free(d_pool);
+    dev_free(d_csr_off);
+    dev_free(d_csr_slots);
+  }
+  dev_free(ws);
+}
+
+namespace {
+
+bool is_dbl(const tc_circuit* c) { return c->dtype == TC_C128; }
+size_t amp_bytes(const tc_circuit* c) { return is_dbl(c) ? 16 : 8; }
+
+tc_status ensure_device(tc_circuit* c) {
+  if (c->uploaded) {
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != c->device) return fail(TC_E_INVALID, "circuit was first used on another device");
+    return TC_OK;
+  }
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if ((e = c->dplan.upload(c->A)) != cudaSuccess) return cuda_fail(e, "plan upload");
+  if ((e = dev_upload(c->pool, &c->d_pool)) != cudaSuccess) return cuda_fail(e, "pool upload");
+  if ((e = dev_upload(c->csr_off, &c->d_csr_off)) != cudaSuccess) return cuda_fail(e, "csr upload");
+  if ((e = dev_upload(c->csr_slots, &c->d_csr_slots)) != cudaSuccess) return cuda_fail(e, "csr upload");
+  c->uploaded = true;
+  return TC_OK;
+}
+
+tc_status ensure_ham(tc_circuit* c, const uint8_t* structures, const double* weights, int T) {
+  if (T < 0) return fail(TC_E_INVALID, "T < 0");
+  if (T > 0 && (!structures || !weights)) return fail(TC_E_INVALID, "structures/weights are NULL");
+  const size_t ns = (size_t)T * c->n;
+  if (c->h_T == T && c->h_struct.size() == ns && (ns == 0 || !memcmp(c->h_struct.data(), structures, ns)) &&
+      (T == 0 || !memcmp(c->h_w.data(), weights, T * sizeof(double))))
+    return TC_OK;
+  HamPlan H;
+  std::string err;
+  if (!build_hamiltonian(c->n, c->N, c->k_ham, structures, weights, T, H, err))
+    return fail(err.find("flips more") != std::string::npos ? TC_E_UNSUPPORTED : TC_E_INVALID, err);
+  c->dham.release();
+  cudaError_t e = c->dham.upload(H);
+  if (e != cudaSuccess) {
+    c->h_T = -1;
+    return cuda_fail(e, "hamiltonian upload");
+  }
+  c->H = H;
+  c->h_struct.assign(structures, structures + ns);
+  c->h_w.assign(weights, weights + T);
+  c->h_T = T;
+  return TC_OK;
+}
+
+tc_status ensure_ws(tc_circuit* c, size_t bytes) {
+  if (bytes <= c->ws_bytes) return TC_OK;
+  dev_free(c->ws);
+  c->ws = nullptr;
+  c->ws_bytes = 0;
+  cudaError_t e = cudaMalloc(&c->ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "workspace allocation");
+  }
+  c->ws_bytes = bytes;
+  return TC_OK;
+}
+
+int64_t budget(const tc_circuit* c) {
+  if (c->opt.mem_budget_bytes > 0) return c->opt.mem_budget_bytes;
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  return (int64_t)((double)(fr + c->ws_bytes) * 0.6);
+}
+
+KArgs base_args(const tc_circuit* c, const DevPlan& dp) {
+  KArgs a{};
+  a.passes = dp.passes;
+  a.stages = dp.stages;
+  a.instrs = dp.instrs;
+  a.mats = dp.mats;
+  a.diags = dp.diags;
+  a.dents = dp.dents;
+  a.pool = c->d_pool;
+  a.hpasses = c->dham.passes;
+  a.hdiag = c->dham.hdiag;
+  a.hterms = c->dham.hterms;
+  a.hflips = c->dham.hflips;
+  a.N = c->N;
+  a.n_user = c->n;
+  a.init = (int)c->init;
+  a.synth_init = 1;
+  a.n_params = c->n_params;
+  a.n_noise = c->n_noise;
+  return a;
+}
+
+#define TC_CHECK_CUDA(expr, where)               \
+  do {                                           \
+    cudaError_t _e = (expr);                     \
+    if (_e != cudaSuccess) return cuda_fail(_e, where); \
+  } while (0)
+
+tc_status run_forward(tc_circuit* c, const DevPlan& dp, const Schedule& sc, const PlanArrays& A, KArgs a,
+                      int rows, cudaStream_t s) {
+  for (int p = 0; p < sc.n_passes; ++p) {
+    a.pass = sc.first_pass + p;
+    TC_CHECK_CUDA(launch_pass(KM_FWD, is_dbl(c), a, A.passes[a.pass], rows, s), "forward pass");
+  }
+  return TC_OK;
+}
+
+tc_status run_ham(tc_circuit* c, KArgs a, int rows, bool store_lambda, cudaStream_t s) {
+  a.store_lambda = store_lambda ? 1 : 0;
+  a.n_hpasses = (int)c->H.passes.size();
+  for (int p = 0; p < (int)c->H.passes.size(); ++p) {
+    a.pass = p;
+    TC_CHECK_CUDA(launch_pass(KM_HAM, is_dbl(c), a, c->H.passes[p], rows, s), "hamiltonian pass");
+  }
+  return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tc_last_error(void) { return g_err.c_str(); }
+const char* tc_version(void) { return "tc_b300 0.1 (sm_103a)"; }
+
+tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc_op* ops, int n_ops, int n_params,
+                            const double* pool, int n_pool, const tc_options* opt, tc_circuit** out) {
+  if (!out) return fail(TC_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > kMaxQubits) return fail(TC_E_INVALID, "n_qubits must be in 1..30");
+  if (dtype != TC_C64 && dtype != TC_C128) return fail(TC_E_INVALID, "unknown dtype");
+  if (init != TC_INIT_ZERO && init != TC_INIT_PLUS) return fail(TC_E_INVALID, "unknown init");
+  if (n_ops < 0 || (n_ops > 0 && !ops)) return fail(TC_E_INVALID, "ops is NULL");
+  if (n_params < 0) return fail(TC_E_INVALID, "n_params < 0");
+  if (n_pool < 0 || (n_pool > 0 && !pool)) return fail(TC_E_INVALID, "pool is NULL");
+  auto* c = new tc_circuit();
+  c->n = n_qubits;
+  c->N = n_qubits < kMinQubits ? kMinQubits : n_qubits;
+  c->dtype = dtype;
+  c->init = init;
+  c->n_ops = n_ops;
+  c->n_params = n_params;
+  if (opt) c->opt = *opt;
+  const bool dbl = dtype == TC_C128;
+  auto pick = [&](int want, int dflt, int maxk) {
+    int k = want > 0 ? want : dflt;
+    if (k > maxk) k = maxk;
+    if (k < kMinQubits) k = kMinQubits;
+    if (k > c->N) k = c->N;
+    return k;
+  };
+  c->k_fwd = pick(c->opt.tile_qubits_fwd, dbl ? 12 : 13, 13);
+  c->k_bwd = pick(c->opt.tile_qubits_bwd, dbl ? 11 : 12, 12);
+  c->k_ham = c->k_fwd;
+  std::string err;
+  if (!normalise_ops(n_qubits, c->N, ops, n_ops, n_params, n_pool, c->gates, err)) {
+    delete c;
+    return fail(TC_E_INVALID, err);
+  }
+  for (auto& g : c->gates)
+    if (g.noise_event >= 0) c->n_noise++;
+  c->pool.assign(pool, pool + 2 * (size_t)n_pool);
+  c->fwd = build_schedule(c->gates, c->N, c->k_fwd, false, true, c->A);
+  c->bwd = build_schedule(c->gates, c->N, c->k_bwd, true, false, c->A);
+  // parameter -> gradient slots (CSR)
+  c->csr_off.assign(n_params + 1, 0);
+  for (int p : c->bwd.slot_param) c->csr_off[p + 1]++;
+  for (int p = 0; p < n_params; ++p) c->csr_off[p + 1] += c->csr_off[p];
+  c->csr_slots.assign(c->bwd.slot_param.size(), 0);
+  {
+    std::vector<int> fillp(c->csr_off.begin(), c->csr_off.end() - 1);
+    for (int s = 0; s < (int)c->bwd.slot_param.size(); ++s) c->csr_slots[fillp[c->bwd.slot_param[s]]++] = s;
+  }
+  if (c->csr_slots.empty()) c->csr_slots.push_back(0);
+  *out = c;
+  return TC_OK;
+}
+
+void tc_circuit_destroy(tc_circuit* c) { delete c; }
+
+tc_status tc_circuit_info(const tc_circuit* c, tc_plan_info* o) {
+  if (!c || !o) return fail(TC_E_INVALID, "NULL argument");
+  memset(o, 0, sizeof(*o));
+  o->n_qubits = c->n;
+  o->n_qubits_internal = c->N;
+  o->n_ops = c->n_ops;
+  o->n_params = c->n_params;
+  o->n_noise = c->n_noise;
+  o->fwd_passes = c->fwd.n_passes;
+  o->bwd_passes = c->bwd.n_passes;
+  o->fwd_stages = c->fwd.n_stages;
+  o->bwd_stages = c->bwd.n_stages;
+  o->tile_qubits_fwd = c->k_fwd;
+  o->tile_qubits_bwd = c->k_bwd;
+  return TC_OK;
+}
+
+tc_status tc_apply_layers(const tc_circuit* cc, const double* d_params, int B, const void* d_init, uint64_t seed,
+                          const float* d_status, int64_t row_offset, void* d_states_out, void* stream) {
+  tc_circuit* c = const_cast<tc_circuit*>(cc);
+  if (!c || !d_states_out) return fail(TC_E_INVALID, "NULL circuit or output");
+  if (B < 0) return fail(TC_E_INVALID, "B < 0");
+  if (c->n_params > 0 && !d_params && B > 0) return fail(TC_E_INVALID, "d_params is NULL");
+  if (B == 0) return TC_OK;
+  tc_status st = ensure_device(c);
+  if (st != TC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool padded = c->N != c->n;
+  const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
+  int chunk = B;
+  void* work = d_states_out;
+  if (padded) {
+    chunk = (int)std::min<int64_t>(B, std::max<int64_t>(1, (int64_t)(256u << 20) / (int64_t)per));
+    if ((st = ensure_ws(c, per * chunk)) != TC_OK) return st;
+    work = c->ws;
+  }
+  for (int r0 = 0; r0 < B; r0 += chunk) {
+    const int rows = std::min(chunk, B - r0);
+    const size_t ub = ((size_t)1 << c->n) * amp_bytes(c);
+    void* out_rows = (char*)d_states_out + (size_t)r0 * ub;
+    KArgs a = base_args(c, c->dplan);
+    a.psi = padded ? work : out_rows;
+    a.theta = d_params ? d_params + (size_t)r0 * c->n_params : nullptr;
+    a.status = d_status ? d_status + (size_t)r0 * c->n_noise : nullptr;
+    a.seed = seed;
+    a.row_offset = row_offset + r0;
+    if (d_init) {
+      a.synth_init = 0;
+      const void* in_rows = (const char*)d_init + (size_t)r0 * ub;
+      if (padded) {
+        TC_CHECK_CUDA(launch_pad_states(is_dbl(c), in_rows, work, c->n, c->N, rows, true, s), "pad");
+      } else if (in_rows != out_rows) {
+        TC_CHECK_CUDA(cudaMemcpyAsync(out_rows, in_rows, ub * rows, cudaMemcpyDeviceToDevice, s), "init copy");
+      }
+    }
+    if ((st = run_forward(c, c->dplan, c->fwd, c->A, a, rows, s)) != TC_OK) return st;
+    if (padded) TC_CHECK_CUDA(launch_pad_states(is_dbl(c), work, out_rows, c->n, c->N, rows, false, s), "unpad");
+  }
+  return TC_OK;
+}
+
+tc_status tc_expect_pauli_sum(tc_circuit* c, const void* d_states, int B, const uint8_t* structures,
+                              const double* weights, int T, double* d_energy_out, void* stream) {
+  if (!c || !d_states || !d_energy_out) return fail(TC_E_INVALID, "NULL argument");
+  if (B < 0) return fail(TC_E_INVALID, "B < 0");
+  if (B == 0) return TC_OK;
+  tc_status st = ensure_device(c);
+  if (st != TC_OK) return st;
+  if ((st = ensure_ham(c, structures, weights, T)) != TC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool padded = c->N != c->n;
+  const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
+  const int nh = (int)c->H.passes.size();
+  const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
+  const size_t epb = (size_t)nh * tiles_h * 8;
+  int chunk = B;
+  if (padded) chunk = (int)std::min<int64_t>(B, std::max<int64_t>(1, (int64_t)(256u << 20) / (int64_t)per));
+  else chunk = (int)std::min<int64_t>(B, std::max<int64_t>(1, (int64_t)(256u << 20) / (int64_t)epb));
+  const size_t need = (size_t)chunk * (epb + (padded ? per : 0)) + 256;
+  if ((st = ensure_ws(c, need)) != TC_OK) return st;
+  double* epart = (double*)c->ws;
+  void* work = (char*)c->ws + (((size_t)chunk * epb + 255) & ~(size_t)255);
+  const size_t ub = ((size_t)1 << c->n) * amp_bytes(c);
+  for (int r0 = 0; r0 < B; r0 += chunk) {
+    const int rows = std::min(chunk, B - r0);
+    const void* in_rows = (const char*)d_states + (size_t)r0 * ub;
+    KArgs a = base_args(c, c->dplan);
+    if (padded) {
+      TC_CHECK_CUDA(launch_pad_states(is_dbl(c), in_rows, work, c->n, c->N, rows, true, s), "pad");
+      a.psi = work;
+    } else {
+      a.psi = const_cast<void*>(in_rows);
+    }
+    a.lam = nullptr;
+    a.epart = epart;
+    if ((st = run_ham(c, a, rows, false, s)) != TC_OK) return st;
+    TC_CHECK_CUDA(launch_finalize(epart, nh, (int)tiles_h, nullptr, 0, 1, c->d_csr_off, c->d_csr_slots, 0, rows,
+                                  d_energy_out + r0, nullptr, s),
+                  "finalize");
+  }
+  return TC_OK;
+}
+
+tc_status tc_expect_grad(tc_circuit* c, const double* d_params, int B, const uint8_t* structures,
+                         const double* weights, int T, uint64_t seed, double* d_energy_out, double* d_grad_out,
+                         const tc_grad_options* gopt, void* stream) {
+  if (!c || !d_energy_out) return fail(TC_E_INVALID, "NULL argument");
+  if (B < 0) return fail(TC_E_INVALID, "B < 0");
+  if (c->n_params > 0 && (!d_params || !d_grad_out) && B > 0) return fail(TC_E_INVALID, "d_params/d_grad_out NULL");
+  if (gopt && gopt->mode != TC_GRAD_UNCOMPUTE) return fail(TC_E_UNSUPPORTED, "unknown gradient mode");
+  if (B == 0) return TC_OK;
+  tc_status st = ensure_device(c);
+  if (st != TC_OK) return st;
+  if ((st = ensure_ham(c, structures, weights, T)) != TC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
+  const int nh = (int)c->H.passes.size();
+  const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
+  const size_t tiles_b = (size_t)1 << (c->N - c->k_bwd);
+  const int G = c->bwd.n_gslots;
+  const size_t row_bytes = 2 * per + (size_t)nh * tiles_h * 8 + (size_t)G * tiles_b * 8 + 64;
+  int64_t cap = budget(c) / (int64_t)row_bytes;
+  if (gopt && gopt->max_rows > 0) cap = std::min<int64_t>(cap, gopt->max_rows);
+  if (cap < 1) return fail(TC_E_NOMEM, "one row of states does not fit the memory budget");
+  const int chunk = (int)std::min<int64_t>(B, cap);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_lam = al(per * chunk);
+  const size_t o_ep = o_lam + al(per * chunk);
+  const size_t o_gp = o_ep + al((size_t)chunk * nh * tiles_h * 8);
+  const size_t need = o_gp + al((size_t)chunk * std::max(G, 1) * tiles_b * 8);
+  if ((st = ensure_ws(c, need)) != TC_OK) return st;
+  char* w = (char*)c->ws;
+  for (int r0 = 0; r0 < B; r0 += chunk) {
+    const int rows = std::min(chunk, B - r0);
+    KArgs a = base_args(c, c->dplan);
+    a.psi = w;
+    a.lam = w + o_lam;
+    a.epart = (double*)(w + o_ep);
+    a.gpart = (double*)(w + o_gp);
+    a.gslots_total = G;
+    a.theta = d_params ? d_params + (size_t)r0 * c->n_params : nullptr;
+    a.seed = seed;
+    a.row_offset = r0;
+    if ((st = run_forward(c, c->dplan, c->fwd, c->A, a, rows, s)) != TC_OK) return st;
+    if ((st = run_ham(c, a, rows, true, s)) != TC_OK) return st;
+    for (int p = 0; p < c->bwd.n_passes; ++p) {
+      a.pass = c->bwd.first_pass + p;
+      TC_CHECK_CUDA(launch_pass(KM_BWD, is_dbl(c), a, c->A.passes[a.pass], rows, s), "adjoint pass");
+    }
+    TC_CHECK_CUDA(launch_finalize(a.epart, nh, (int)tiles_h, a.gpart, G, (int)tiles_b, c->d_csr_off,
+                                  c->d_csr_slots, c->n_params, rows, d_energy_out + r0,
+                                  c->n_params ? d_grad_out + (size_t)r0 * c->n_params : nullptr, s),
+                  "finalize");
+  }
+  return TC_OK;
+}
+
+tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, const uint8_t* structures,
+                          const double* weights, int T, void* d_states_work, double* d_energy_out, void* stream) {
+  if (!c || !d_states_work || !d_energy_out) return fail(TC_E_INVALID, "NULL argument");
+  if (B < 0 || T < 0) return fail(TC_E_INVALID, "B < 0 or T < 0");
+  if (T > 0 && (!structures || !weights)) return fail(TC_E_INVALID, "structures/weights NULL");
+  if (c->N != c->n) return fail(TC_E_UNSUPPORTED, "the unfused baseline needs n >= 9");
+  if (B > 65535) return fail(TC_E_UNSUPPORTED, "the unfused baseline takes at most 65535 rows per call");
+  if (B == 0) return TC_OK;
+  tc_status st = ensure_device(c);
+  if (st != TC_OK) return st;
+  if (!c->plain_built) {
+    c->plain = build_plain_schedule(c->gates, c->N, c->Ap);
+    cudaError_t e = c->dplain.upload(c->Ap);
+    if (e != cudaSuccess) return cuda_fail(e, "plain plan upload");
+    c->plain_built = true;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  KArgs a = base_args(c, c->dplain);
+  a.psi = d_states_work;
+  a.theta = d_params;
+  a.seed = 0;
+  // pass 0 of the unfused plan writes the initial state, then one pass per gate
+  if ((st = run_forward(c, c->dplain, c->plain, c->Ap, a, B, s)) != TC_OK) return st;
+  TC_CHECK_CUDA(cudaMemsetAsync(d_energy_out, 0, sizeof(double) * B, s), "memset");
+  for (int t = 0; t < T; ++t) {
+    uint32_t f = 0, sm = 0;
+    int ny = 0;
+    for (int q = 0; q < c->n; ++q) {
+      const uint8_t code = structures[(size_t)t * c->n + q];
+      if (code > 3) return fail(TC_E_INVALID, "structure entry outside {0,1,2,3}");
+      const uint32_t b = 1u << (c->N - 1 - q);
+      if (code == 1 || code == 2) f |= b;
+      if (code == 2 || code == 3) sm |= b;
+      if (code == 2) ny++;
+    }
+    TC_CHECK_CUDA(launch_plain_term(is_dbl(c), d_states_work, c->N, B, f, sm, ny & 3, weights[t], d_energy_out, s),
+                  "plain term");
+  }
+  return TC_OK;
+}
+
+tc_status tc_profile_begin(void) {
+  prof_begin();
+  return TC_OK;
+}
+
+tc_status tc_profile_end(tc_kernel_stat* out, int max_out, int* n_out) {
+  int launches[PK_COUNT];
+  double ms[PK_COUNT], bytes[PK_COUNT];
+  const bool ok = prof_end(launches, ms, bytes);
+  int n = 0;
+  for (int k = 0; k < PK_COUNT; ++k) {
+    if (!launches[k]) continue;
+    if (out && n < max_out) {
+      out[n].kind = k;
+      out[n].launches = launches[k];
+      out[n].total_ms = ms[k];
+      out[n].algo_bytes = bytes[k];
+    }
+    ++n;
+  }
+  if (n_out) *n_out = n;
+  return ok ? TC_OK : fail(TC_E_CUDA, "event timing failed");
+}
+
+}  // extern "C"

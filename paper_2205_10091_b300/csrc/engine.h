@@ -1,0 +1,88 @@
+// Engine object behind the opaque tc_circuit handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "planner.h"
+#include "sv_kernels.cuh"
+
+namespace tcb {
+
+void set_error(const std::string& msg);
+tc_status fail(tc_status st, const std::string& msg);
+tc_status cuda_fail(cudaError_t e, const char* where);
+
+// Device copy of a vector (freed with dev_free).
+template <typename T>
+cudaError_t dev_upload(const std::vector<T>& v, T** out) {
+  *out = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)out, v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+void dev_free(void* p);
+
+struct DevPlan {
+  DevPass* passes = nullptr;
+  DevStage* stages = nullptr;
+  DevInstr* instrs = nullptr;
+  DevMat* mats = nullptr;
+  DevDiag* diags = nullptr;
+  DevDiagEnt* dents = nullptr;
+  void release();
+  cudaError_t upload(const PlanArrays& A);
+};
+
+struct DevHam {
+  DevPass* passes = nullptr;
+  DevHDiag* hdiag = nullptr;
+  DevHTerm* hterms = nullptr;
+  DevHFlip* hflips = nullptr;
+  void release();
+  cudaError_t upload(const HamPlan& H);
+};
+
+}  // namespace tcb
+
+struct tc_circuit {
+  int n = 0, N = 0;
+  tc_dtype dtype = TC_C64;
+  tc_init init = TC_INIT_ZERO;
+  int n_ops = 0, n_params = 0, n_noise = 0;
+  tc_options opt{};
+  int k_fwd = 0, k_bwd = 0, k_ham = 0;
+  std::vector<tcb::HGate> gates;
+  std::vector<double> pool;
+
+  tcb::PlanArrays A;       // forward + adjoint schedules
+  tcb::Schedule fwd, bwd;
+  std::vector<int> csr_off, csr_slots;  // parameter -> adjoint gradient slots
+
+  tcb::PlanArrays Ap;      // unfused baseline (built on first use)
+  tcb::Schedule plain;
+  bool plain_built = false;
+
+  // device state (uploaded on first compute call)
+  bool uploaded = false;
+  int device = -1;
+  tcb::DevPlan dplan, dplain;
+  double* d_pool = nullptr;
+  int* d_csr_off = nullptr;
+  int* d_csr_slots = nullptr;
+
+  // Hamiltonian cache (last compiled Pauli sum)
+  std::vector<uint8_t> h_struct;
+  std::vector<double> h_w;
+  int h_T = -1;
+  tcb::HamPlan H;
+  tcb::DevHam dham;
+
+  // scratch workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+
+  ~tc_circuit();
+};

@@ -1,0 +1,544 @@
+// Host planner: op list -> fused shared-memory tile passes -> register stages.
+//
+// Fusion rule (the "preprocessing" idea of Section "Custom contraction
+// settings", restated for a state vector): gates are taken in list order and
+// a gate may move ahead of deferred gates only if it shares no qubit with any
+// of them, so every reordering is between commuting gates.  A pass takes the
+// gates whose non-diagonal qubits fit in k tile qubits; diagonal gates (RZ,
+// RZZ, CZ) need no tile qubit because their phase depends only on the
+// amplitude index, and those sharing (parameter, scale) merge into one
+// phase-table lookup.  Inside a pass the same rule splits the gates into
+// register stages of kRB qubits.
+#include "planner.h"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <numeric>
+#include <tuple>
+
+namespace tcb {
+
+static inline int popc(uint32_t x) { return __builtin_popcount(x); }
+static inline uint32_t bit(int p) { return p >= 0 ? (1u << p) : 0u; }
+
+bool normalise_ops(int n_user, int N, const tc_op* ops, int n_ops, int n_params, int n_pool,
+                   std::vector<HGate>& out, std::string& err) {
+  out.clear();
+  int ev = 0;
+  for (int i = 0; i < n_ops; ++i) {
+    const tc_op& o = ops[i];
+    auto bad = [&](const char* m) {
+      err = "op " + std::to_string(i) + ": " + m;
+      return false;
+    };
+    if (o.kind < TC_OP_H || o.kind > TC_OP_PAULI_NOISE) return bad("unknown kind");
+    const bool two = o.kind == TC_OP_RZZ || o.kind == TC_OP_CNOT || o.kind == TC_OP_CZ || o.kind == TC_OP_U2;
+    if (o.q0 < 0 || o.q0 >= n_user) return bad("q0 out of range");
+    if (two && (o.q1 < 0 || o.q1 >= n_user || o.q1 == o.q0)) return bad("q1 out of range or equal to q0");
+    HGate g;
+    g.kind = o.kind;
+    g.p0 = N - 1 - o.q0;
+    g.p1 = two ? N - 1 - o.q1 : -1;
+    const bool rot = o.kind == TC_OP_RX || o.kind == TC_OP_RY || o.kind == TC_OP_RZ || o.kind == TC_OP_RZZ;
+    if (rot) {
+      if (o.param < -1 || o.param >= n_params) return bad("param out of range");
+      if (!std::isfinite(o.scale)) return bad("scale not finite");
+      g.param = o.param;
+      g.scale = o.scale;
+    }
+    if (o.kind == TC_OP_U1 && (o.mat < 0 || (int64_t)o.mat + 4 > n_pool)) return bad("U1 matrix offset out of range");
+    if (o.kind == TC_OP_U2 && (o.mat < 0 || (int64_t)o.mat + 16 > n_pool)) return bad("U2 matrix offset out of range");
+    g.pool = o.mat;
+    if (o.kind == TC_OP_PAULI_NOISE) {
+      if (!(o.px >= 0 && o.py >= 0 && o.pz >= 0) || !(o.px + o.py + o.pz <= 1.0))
+        return bad("noise probabilities must be >= 0 and sum to <= 1");
+      // interval ends for [I, X, Y, Z]; the same arithmetic as the selection rule
+      g.t1 = 1.0 - (o.px + o.py + o.pz);
+      g.t2 = g.t1 + o.px;
+      g.t3 = g.t2 + o.py;
+      g.noise_event = ev++;
+    }
+    g.diag = o.kind == TC_OP_RZ || o.kind == TC_OP_RZZ || o.kind == TC_OP_CZ;
+    g.sign_mode = o.kind == TC_OP_CZ;
+    out.push_back(g);
+  }
+  return true;
+}
+
+namespace {
+
+struct Item {
+  bool group = false;
+  int gate = -1;
+  std::vector<int> members;
+  uint32_t touch = 0;
+};
+
+uint32_t gate_touch(const HGate& g) { return bit(g.p0) | bit(g.p1); }
+
+// register-tile bits an item needs
+uint32_t item_need(const Item& it, const std::vector<HGate>& gates, const int* tb) {
+  if (it.group) return 0;
+  const HGate& g = gates[it.gate];
+  if (g.kind == TC_OP_CNOT) return 1u << tb[g.p1];
+  if (g.kind == TC_OP_U2) return (1u << tb[g.p0]) | (1u << tb[g.p1]);
+  return 1u << tb[g.p0];
+}
+
+}  // namespace
+
+Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjoint, bool first_init,
+                        PlanArrays& A) {
+  Schedule sc;
+  sc.first_pass = (int)A.passes.size();
+  sc.k = k;
+  std::vector<int> remaining(gates.size());
+  std::iota(remaining.begin(), remaining.end(), 0);
+  if (adjoint) std::reverse(remaining.begin(), remaining.end());
+  const uint32_t low = (1u << kLaneBits) - 1;
+  const uint32_t all = (N >= 32) ? 0xffffffffu : ((1u << N) - 1);
+  bool first = true;
+
+  while (!remaining.empty() || (first && first_init)) {
+    // ---- choose the pass's gates and tile -------------------------------
+    uint32_t tile = low, blocked = 0;
+    std::vector<int> taken, deferred;
+    for (int gi : remaining) {
+      const HGate& g = gates[gi];
+      const uint32_t touch = gate_touch(g);
+      if (touch & blocked) {
+        deferred.push_back(gi);
+        blocked |= touch;
+        continue;
+      }
+      if (g.diag) {
+        taken.push_back(gi);
+        continue;
+      }
+      const uint32_t need = g.kind == TC_OP_CNOT ? bit(g.p1) : touch;
+      if (popc(tile | need) <= k) {
+        tile |= need;
+        taken.push_back(gi);
+      } else {
+        deferred.push_back(gi);
+        blocked |= touch;
+      }
+    }
+    for (int p = 0; popc(tile) < k && p < N; ++p) tile |= bit(p);  // fill with low positions
+    (void)all;
+
+    DevPass P{};
+    P.k = k;
+    P.nfix = N - k;
+    int tb[32];
+    for (int p = 0; p < 32; ++p) tb[p] = -1;
+    {
+      int j = 0, f = 0;
+      for (int p = 0; p < N; ++p) {
+        if (tile & bit(p)) {
+          P.pos[j] = (uint8_t)p;
+          tb[p] = j++;
+        } else {
+          P.fixpos[f++] = (uint8_t)p;
+        }
+      }
+    }
+    P.flags = (first && first_init && !adjoint) ? PF_INIT : 0;
+
+    // ---- items: non-diagonal gates, and diagonal groups ------------------
+    std::vector<Item> items;
+    std::map<std::tuple<int, int, double>, int> open;  // key -> item index
+    int last_touch[32];
+    for (int p = 0; p < 32; ++p) last_touch[p] = -1;
+    for (int gi : taken) {
+      const HGate& g = gates[gi];
+      if (g.diag) {
+        auto key = std::make_tuple((int)g.sign_mode, g.sign_mode ? -1 : g.param, g.sign_mode ? 0.0 : g.scale);
+        auto itk = open.find(key);
+        bool joined = false;
+        if (itk != open.end()) {
+          const int gidx = itk->second;
+          bool ok = true;
+          for (int p : {g.p0, g.p1})
+            if (p >= 0 && last_touch[p] > gidx) ok = false;
+          if (ok) {
+            items[gidx].members.push_back(gi);
+            items[gidx].touch |= gate_touch(g);
+            joined = true;
+          }
+        }
+        if (!joined) {
+          Item it;
+          it.group = true;
+          it.members.push_back(gi);
+          it.touch = gate_touch(g);
+          items.push_back(it);
+          open[key] = (int)items.size() - 1;
+        }
+      } else {
+        Item it;
+        it.gate = gi;
+        it.touch = gate_touch(g);
+        items.push_back(it);
+        for (int p : {g.p0, g.p1})
+          if (p >= 0) last_touch[p] = (int)items.size() - 1;
+      }
+    }
+
+    // ---- register stages ------------------------------------------------
+    std::vector<std::pair<uint32_t, std::vector<int>>> stages;  // (S mask in tile bits, item ids)
+    {
+      std::vector<int> rem(items.size());
+      std::iota(rem.begin(), rem.end(), 0);
+      while (!rem.empty()) {
+        uint32_t S = 0, blk = 0;
+        std::vector<int> tk, df;
+        for (int ii : rem) {
+          const Item& it = items[ii];
+          if (it.touch & blk) {
+            df.push_back(ii);
+            blk |= it.touch;
+            continue;
+          }
+          const uint32_t need = item_need(it, gates, tb);
+          if (popc(S | need) <= kRB) {
+            S |= need;
+            tk.push_back(ii);
+          } else {
+            df.push_back(ii);
+            blk |= it.touch;
+          }
+        }
+        stages.push_back({S, tk});
+        rem = df;
+      }
+    }
+    const uint32_t high_tile = ((k >= 32) ? 0xffffffffu : ((1u << k) - 1)) & ~low;
+    auto fill = [&](uint32_t S) {
+      // complete S to kRB bits, preferring high tile bits (keeps lanes on bits 0..4)
+      for (int j = k - 1; popc(S) < kRB && j >= kLaneBits; --j) S |= 1u << j;
+      for (int j = 0; popc(S) < kRB && j < k; ++j) S |= 1u << j;
+      return S;
+    };
+    if (stages.empty()) stages.push_back({0u, {}});
+    for (auto& st : stages) st.first = fill(st.first);
+    if (stages.front().first & ~high_tile) stages.insert(stages.begin(), {fill(0u), {}});
+    if (stages.back().first & ~high_tile) stages.push_back({fill(0u), {}});
+
+    // ---- emit -----------------------------------------------------------
+    P.stage_off = (int)A.stages.size();
+    P.n_stages = (int)stages.size();
+    P.mat_off = (int)A.mats.size();
+    P.gslot_base = sc.n_gslots;
+    int table = 0;
+    std::map<int, int> local_slot;  // param -> local slot
+    auto slot_of = [&](int param) {
+      auto it = local_slot.find(param);
+      if (it != local_slot.end()) return it->second;
+      const int s = (int)local_slot.size();
+      local_slot[param] = s;
+      sc.slot_param.push_back(param);
+      return s;
+    };
+    for (auto& st : stages) {
+      DevStage ds{};
+      int jof[32];
+      for (int j = 0; j < 32; ++j) jof[j] = -1;
+      {
+        int r = 0;
+        for (int j = 0; j < k; ++j)
+          if (st.first & (1u << j)) {
+            ds.S[r] = (int8_t)j;
+            jof[j] = r++;
+          }
+      }
+      ds.instr_off = (int)A.instrs.size();
+      for (int ii : st.second) {
+        const Item& it = items[ii];
+        if (it.group) {
+          const HGate& g0 = gates[it.members[0]];
+          DevDiag dg{};
+          dg.sign_mode = g0.sign_mode ? 1 : 0;
+          dg.T = (int)it.members.size();
+          dg.ent_off = (int)A.dents.size();
+          // entries: one (d, mask) per distance, duplicates start a new entry
+          std::vector<DevDiagEnt> ents;
+          for (int gi : it.members) {
+            const HGate& g = gates[gi];
+            uint32_t d, m;
+            if (g.p1 < 0) {
+              d = 0;
+              m = bit(g.p0);
+            } else {
+              const int a = std::min(g.p0, g.p1), b = std::max(g.p0, g.p1);
+              d = (uint32_t)(b - a);
+              m = bit(a);
+            }
+            bool placed = false;
+            for (auto& e : ents)
+              if (e.d == d && !(e.mask & m)) {
+                e.mask |= m;
+                placed = true;
+                break;
+              }
+            if (!placed) ents.push_back({d, m});
+          }
+          for (auto& e : ents) A.dents.push_back(e);
+          dg.n_ent = (int)ents.size();
+          dg.tab = -1;
+          if (!dg.sign_mode) {
+            DevMat m{};
+            m.type = MT_DIAGTAB;
+            m.adj = adjoint ? 1 : 0;
+            m.param = g0.param;
+            m.scale = g0.scale;
+            m.dst = table;
+            m.T = dg.T;
+            A.mats.push_back(m);
+            dg.tab = table;
+            table += dg.T + 1;
+          }
+          const int di = (int)A.diags.size();
+          A.diags.push_back(dg);
+          if (adjoint && !dg.sign_mode && g0.param >= 0) {
+            DevInstr gi{};
+            gi.kind = IK_GRADDIAG;
+            gi.aux = di;
+            gi.gslot = slot_of(g0.param);
+            gi.gscale = (float)g0.scale;
+            gi.jc = -1;
+            A.instrs.push_back(gi);
+          }
+          DevInstr in{};
+          in.kind = IK_DIAG;
+          in.aux = di;
+          in.gslot = -1;
+          in.jc = -1;
+          A.instrs.push_back(in);
+          continue;
+        }
+        const HGate& g = gates[it.gate];
+        DevInstr in{};
+        in.gslot = -1;
+        in.jc = -1;
+        if (g.kind == TC_OP_CNOT) {
+          in.kind = IK_CNOT;
+          in.j0 = (int8_t)jof[tb[g.p1]];
+          in.pos = g.p0;
+          in.jc = (int8_t)((tb[g.p0] >= 0) ? jof[tb[g.p0]] : -1);
+          A.instrs.push_back(in);
+          continue;
+        }
+        DevMat m{};
+        m.adj = adjoint ? 1 : 0;
+        m.param = g.param;
+        m.scale = g.scale;
+        m.pool = g.pool;
+        m.dst = table;
+        if (g.kind == TC_OP_U2) {
+          m.type = MT_U2;
+          table += 16;
+          in.kind = IK_MAT4;
+          in.j0 = (int8_t)jof[tb[g.p0]];
+          in.j1 = (int8_t)jof[tb[g.p1]];
+        } else {
+          switch (g.kind) {
+            case TC_OP_H: m.type = MT_H; break;
+            case TC_OP_X: m.type = MT_X; break;
+            case TC_OP_RX: m.type = MT_RX; break;
+            case TC_OP_RY: m.type = MT_RY; break;
+            case TC_OP_U1: m.type = MT_U1; break;
+            case TC_OP_PAULI_NOISE:
+              m.type = MT_NOISE;
+              m.T = g.noise_event;
+              m.t1 = g.t1;
+              m.t2 = g.t2;
+              m.t3 = g.t3;
+              break;
+            default: m.type = MT_X; break;
+          }
+          table += 4;
+          in.kind = IK_MAT2;
+          in.j0 = (int8_t)jof[tb[g.p0]];
+        }
+        in.mslot = m.dst;
+        A.mats.push_back(m);
+        if (adjoint && g.param >= 0 && (g.kind == TC_OP_RX || g.kind == TC_OP_RY)) {
+          DevInstr gi{};
+          gi.kind = g.kind == TC_OP_RX ? IK_GRADX : IK_GRADY;
+          gi.j0 = in.j0;
+          gi.jc = -1;
+          gi.gslot = slot_of(g.param);
+          gi.gscale = (float)g.scale;
+          A.instrs.push_back(gi);
+        }
+        A.instrs.push_back(in);
+      }
+      ds.n_instr = (int)A.instrs.size() - ds.instr_off;
+      A.stages.push_back(ds);
+    }
+    P.n_mats = (int)A.mats.size() - P.mat_off;
+    P.table_size = table;
+    P.n_gslots = (int)local_slot.size();
+    sc.n_gslots += P.n_gslots;
+    sc.n_stages += P.n_stages;
+    A.passes.push_back(P);
+    remaining = deferred;
+    first = false;
+  }
+  sc.n_passes = (int)A.passes.size() - sc.first_pass;
+  return sc;
+}
+
+Schedule build_plain_schedule(const std::vector<HGate>& gates, int N, PlanArrays& A) {
+  Schedule sc;
+  sc.first_pass = (int)A.passes.size();
+  sc.k = kMinQubits;
+  {
+    // a gate-free pass that writes the initial state
+    Schedule s0 = build_schedule({}, N, kMinQubits, false, true, A);
+    sc.n_stages += s0.n_stages;
+  }
+  for (size_t i = 0; i < gates.size(); ++i) {
+    std::vector<HGate> one{gates[i]};
+    Schedule s = build_schedule(one, N, kMinQubits, false, false, A);
+    sc.n_stages += s.n_stages;
+  }
+  sc.n_passes = (int)A.passes.size() - sc.first_pass;
+  return sc;
+}
+
+bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, const double* weights, int T,
+                       HamPlan& H, std::string& err) {
+  H = HamPlan{};
+  H.k = k;
+  const uint32_t low = (1u << kLaneBits) - 1;
+  // ---- classify terms -----------------------------------------------------
+  std::map<std::pair<double, uint32_t>, std::vector<uint32_t>> zz;  // (w, d) -> lower-position bits
+  std::map<uint32_t, std::vector<DevHTerm>> flips;
+  std::vector<DevHDiag> diag;
+  for (int t = 0; t < T; ++t) {
+    uint32_t mx = 0, my = 0, mz = 0;
+    for (int q = 0; q < n_user; ++q) {
+      const uint8_t c = structures[(size_t)t * n_user + q];
+      if (c > 3) {
+        err = "structure entry outside {0,1,2,3} in term " + std::to_string(t);
+        return false;
+      }
+      const uint32_t b = 1u << (N - 1 - q);
+      if (c == 1) mx |= b;
+      if (c == 2) my |= b;
+      if (c == 3) mz |= b;
+    }
+    const double w = weights[t];
+    if (!std::isfinite(w)) {
+      err = "weight not finite in term " + std::to_string(t);
+      return false;
+    }
+    const uint32_t f = mx | my;
+    if (f) {
+      DevHTerm ht{};
+      ht.sm = my | mz;
+      ht.ny = popc(my) & 3;
+      ht.w = w;
+      flips[f].push_back(ht);
+    } else if (popc(mz) == 2) {
+      const int a = __builtin_ctz(mz), b = 31 - __builtin_clz(mz);
+      zz[{w, (uint32_t)(b - a)}].push_back(1u << a);
+    } else {
+      DevHDiag d{};
+      d.d = 0;
+      d.mask = mz;
+      d.cnt = -1;  // parity form
+      d.w = w;
+      diag.push_back(d);
+    }
+  }
+  for (auto& kv : zz) {
+    std::vector<DevHDiag> ents;
+    for (uint32_t m : kv.second) {
+      bool placed = false;
+      for (auto& e : ents)
+        if (!(e.mask & m)) {
+          e.mask |= m;
+          e.cnt++;
+          placed = true;
+          break;
+        }
+      if (!placed) {
+        DevHDiag e{};
+        e.d = kv.first.second;
+        e.mask = m;
+        e.cnt = 1;
+        e.w = kv.first.first;
+        ents.push_back(e);
+      }
+    }
+    for (auto& e : ents) diag.push_back(e);
+  }
+  // ---- passes ---------------------------------------------------------------
+  std::vector<std::pair<uint32_t, std::vector<DevHTerm>>> groups(flips.begin(), flips.end());
+  std::vector<bool> done(groups.size(), false);
+  size_t n_done = 0;
+  bool first = true;
+  while (first || n_done < groups.size()) {
+    uint32_t tile = low;
+    std::vector<int> mine;
+    for (size_t g = 0; g < groups.size(); ++g) {
+      if (done[g]) continue;
+      if (popc(tile | groups[g].first) <= k) {
+        tile |= groups[g].first;
+        mine.push_back((int)g);
+      }
+    }
+    if (!first && mine.empty()) {
+      err = "a Pauli term flips more qubits than one shared-memory tile holds";
+      return false;
+    }
+    for (int p = 0; popc(tile) < k && p < N; ++p) tile |= bit(p);
+    DevPass P{};
+    P.k = k;
+    P.nfix = N - k;
+    int tbit[32];
+    {
+      int j = 0, f = 0;
+      for (int p = 0; p < N; ++p) {
+        if (tile & bit(p)) {
+          P.pos[j] = (uint8_t)p;
+          tbit[p] = j++;
+        } else {
+          P.fixpos[f++] = (uint8_t)p;
+        }
+      }
+    }
+    P.flags = first ? PF_LAM_STORE : (PF_LAM_LOAD | PF_LAM_STORE);
+    if (first) {
+      P.hdiag_off = (int)H.hdiag.size();
+      P.n_hdiag = (int)diag.size();
+      for (auto& d : diag) H.hdiag.push_back(d);
+    }
+    P.hflip_off = (int)H.hflips.size();
+    P.n_hflip = (int)mine.size();
+    for (int g : mine) {
+      DevHFlip fl{};
+      fl.f = groups[g].first;
+      uint32_t ft = 0;
+      for (int p = 0; p < N; ++p)
+        if (fl.f & bit(p)) ft |= 1u << tbit[p];
+      fl.f_tile = ft;
+      fl.term_off = (int)H.hterms.size();
+      fl.n_terms = (int)groups[g].second.size();
+      for (auto& t : groups[g].second) H.hterms.push_back(t);
+      H.hflips.push_back(fl);
+      done[g] = true;
+      n_done++;
+    }
+    P.epart_index = (int)H.passes.size();
+    H.passes.push_back(P);
+    first = false;
+  }
+  return true;
+}
+
+}  // namespace tcb

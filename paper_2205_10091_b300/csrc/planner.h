@@ -1,0 +1,65 @@
+// Host-side planner: op list -> fused tile passes (see plan.h for the format).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "plan.h"
+#include "../../include/tc.h"
+
+namespace tcb {
+
+// A gate after validation, in internal positions.
+struct HGate {
+  int kind = 0;        // tc_opkind
+  int p0 = -1, p1 = -1;
+  int param = -1;
+  double scale = 1.0;
+  int pool = -1;
+  int noise_event = -1;
+  double t1 = 0, t2 = 0, t3 = 0;
+  bool diag = false;
+  bool sign_mode = false;  // CZ
+};
+
+struct PlanArrays {
+  std::vector<DevPass> passes;
+  std::vector<DevStage> stages;
+  std::vector<DevInstr> instrs;
+  std::vector<DevMat> mats;
+  std::vector<DevDiag> diags;
+  std::vector<DevDiagEnt> dents;
+};
+
+struct Schedule {
+  int first_pass = 0, n_passes = 0;
+  int k = 0;
+  int n_gslots = 0;               // global gradient slots (adjoint schedules)
+  std::vector<int> slot_param;    // global slot -> parameter
+  int n_stages = 0;
+};
+
+struct HamPlan {
+  std::vector<DevPass> passes;
+  std::vector<DevHDiag> hdiag;
+  std::vector<DevHTerm> hterms;
+  std::vector<DevHFlip> hflips;
+  int k = 0;
+};
+
+// Normalise and validate ops; returns false and sets err on bad input.
+bool normalise_ops(int n_user, int n_internal, const tc_op* ops, int n_ops, int n_params, int n_pool,
+                   std::vector<HGate>& out, std::string& err);
+
+// Schedule gates (forward order, or reversed with adjoint=true) into passes.
+Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjoint, bool first_init,
+                        PlanArrays& A);
+
+// Compile a Pauli sum (user structures) into Hamiltonian passes.
+bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, const double* weights, int T,
+                       HamPlan& H, std::string& err);
+
+// Unfused baseline: one pass per gate (k = N tile not required; uses kMinQubits-bit tiles).
+Schedule build_plain_schedule(const std::vector<HGate>& gates, int N, PlanArrays& A);
+
+}  // namespace tcb

@@ -1,0 +1,75 @@
+// Launch interface of the state-vector kernels (sv_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "plan.h"
+
+namespace tcb {
+
+enum KMode : int { KM_FWD = 0, KM_BWD = 1, KM_HAM = 2 };
+
+struct KArgs {
+  // circuit plan (device)
+  const DevPass* passes;
+  const DevStage* stages;
+  const DevInstr* instrs;
+  const DevMat* mats;
+  const DevDiag* diags;
+  const DevDiagEnt* dents;
+  const double* pool;  // complex128, interleaved
+  // Hamiltonian plan (device)
+  const DevPass* hpasses;
+  const DevHDiag* hdiag;
+  const DevHTerm* hterms;
+  const DevHFlip* hflips;
+  int pass;   // index into passes (KM_FWD/KM_BWD) or hpasses (KM_HAM)
+  int N;      // internal qubits
+  int n_user; // user qubits (INIT_PLUS covers only these)
+  int init;   // tc_init
+  int synth_init;  // 1: a pass flagged PF_INIT synthesises the initial state
+  // data
+  void* psi;
+  void* lam;
+  const double* theta;
+  int n_params;
+  const float* status;
+  int n_noise;
+  uint64_t seed;
+  int64_t row_offset;
+  double* gpart;   // [rows][gslots_total][tiles]
+  int gslots_total;
+  double* epart;   // [rows][n_hpasses][tiles]
+  int n_hpasses;
+  int store_lambda;
+};
+
+// Launch one pass for `rows` batch rows.  smem_bytes from pass_smem_bytes().
+cudaError_t launch_pass(int mode, bool dbl, const KArgs& a, const DevPass& host_pass, int rows,
+                        cudaStream_t s);
+size_t pass_smem_bytes(int mode, bool dbl, const DevPass& p);
+
+// E[b] = sum of energy partials; grad[b][p] = sum over slots of p and tiles.
+cudaError_t launch_finalize(const double* epart, int n_hpasses, int tiles_h, const double* gpart, int gslots,
+                            int tiles_b, const int* csr_off, const int* csr_slots, int n_params, int rows,
+                            double* e_out, double* g_out, cudaStream_t s);
+
+// Copy a narrow (n < 9) state batch in or out of the padded internal layout.
+cudaError_t launch_pad_states(bool dbl, const void* src, void* dst, int n_user, int N, int rows, bool to_padded,
+                              cudaStream_t s);
+
+// Explicit-loop baseline: E_b += w * <psi_b|P|psi_b> for one Pauli term, one
+// full sweep of the state per term.
+cudaError_t launch_plain_term(bool dbl, const void* psi, int N, int rows, uint32_t f, uint32_t sm, int ny,
+                              double w, double* e_acc, cudaStream_t s);
+
+// Optional event timing of every launch (enabled by tc_profile_begin).
+enum ProfKind : int { PK_FWD = 0, PK_BWD = 1, PK_HAM = 2, PK_FINALIZE = 3, PK_PAD = 4, PK_PLAIN = 5, PK_COUNT = 6 };
+void prof_begin();
+bool prof_enabled();
+void prof_before(int kind, double algo_bytes, cudaStream_t s);
+void prof_after(cudaStream_t s);
+// fills launches/ms/bytes per kind; returns false on a CUDA error
+bool prof_end(int* launches, double* ms, double* bytes);
+
+}  // namespace tcb

@@ -1,0 +1,241 @@
+"""ctypes binding for libtc_b300.so (argument marshalling only).
+
+Every computation runs in the CUDA library; this module converts Python/
+torch objects to the pointers and sizes that include/tc.h declares.  Device
+buffers are torch CUDA tensors (torch is used for device memory and streams
+only).  There is no fallback: if the library is missing, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtc_b300.so")
+
+TC_OK, TC_E_INVALID, TC_E_NOMEM, TC_E_CUDA, TC_E_TIMEOUT, TC_E_UNSUPPORTED, TC_E_BUSY, TC_E_CANCELLED = range(8)
+TC_C64, TC_C128 = 0, 1
+
+
+class TcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tc status {status}: {msg}")
+        self.status = status
+
+
+class tc_op(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32),
+        ("q0", C.c_int32),
+        ("q1", C.c_int32),
+        ("param", C.c_int32),
+        ("scale", C.c_double),
+        ("mat", C.c_int32),
+        ("pad", C.c_int32),
+        ("px", C.c_double),
+        ("py", C.c_double),
+        ("pz", C.c_double),
+    ]
+
+
+class tc_options(C.Structure):
+    _fields_ = [
+        ("tile_qubits_fwd", C.c_int32),
+        ("tile_qubits_bwd", C.c_int32),
+        ("mem_budget_bytes", C.c_int64),
+        ("reserved", C.c_int32 * 8),
+    ]
+
+
+class tc_plan_info(C.Structure):
+    _fields_ = [
+        ("n_qubits", C.c_int32),
+        ("n_qubits_internal", C.c_int32),
+        ("n_ops", C.c_int32),
+        ("n_params", C.c_int32),
+        ("n_noise", C.c_int32),
+        ("fwd_passes", C.c_int32),
+        ("bwd_passes", C.c_int32),
+        ("fwd_stages", C.c_int32),
+        ("bwd_stages", C.c_int32),
+        ("tile_qubits_fwd", C.c_int32),
+        ("tile_qubits_bwd", C.c_int32),
+        ("reserved", C.c_int32 * 5),
+    ]
+
+
+class tc_grad_options(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("max_rows", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
+class tc_kernel_stat(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("launches", C.c_int32), ("total_ms", C.c_double), ("algo_bytes", C.c_double)]
+
+
+KERNEL_KINDS = ["tile_pass_forward", "tile_pass_adjoint", "pauli_sum_pass", "finalize", "pad", "plain_term"]
+
+assert C.sizeof(tc_op) == W.OP_DTYPE.itemsize == 56
+
+_lib = None
+
+# name -> (restype, argtypes); every symbol include/tc.h declares
+SIGNATURES = {
+    "tc_circuit_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                    C.c_void_p, C.POINTER(C.c_void_p)]),
+    "tc_circuit_destroy": (None, [C.c_void_p]),
+    "tc_circuit_info": (C.c_int, [C.c_void_p, C.POINTER(tc_plan_info)]),
+    "tc_apply_layers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64,
+                                  C.c_void_p, C.c_void_p]),
+    "tc_expect_pauli_sum": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                      C.c_void_p]),
+    "tc_expect_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_uint64,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tc_expect_plain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]),
+    "tc_profile_begin": (C.c_int, []),
+    "tc_profile_end": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    "tc_last_error": (C.c_char_p, []),
+    "tc_version": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load libtc_b300.so (raises if it is missing: no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2205_10091_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != TC_OK:
+        raise TcError(st, lib().tc_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def profile_begin():
+    _check(lib().tc_profile_begin())
+
+
+def profile_end() -> dict:
+    """Per kernel kind: launches, device ms (CUDA events) and algorithmic bytes."""
+    arr = (tc_kernel_stat * 16)()
+    n = C.c_int()
+    _check(lib().tc_profile_end(arr, 16, C.byref(n)))
+    return {KERNEL_KINDS[arr[i].kind]: {"launches": arr[i].launches, "ms": arr[i].total_ms,
+                                        "algo_bytes": arr[i].algo_bytes} for i in range(min(n.value, 16))}
+
+
+class Hamiltonian:
+    """Host copy of a Pauli sum in the ABI's layout (structures [T][n] u8, weights [T] f64)."""
+
+    def __init__(self, ps: W.PauliSum):
+        self.structures = np.ascontiguousarray(ps.structures, dtype=np.uint8)
+        self.weights = np.ascontiguousarray(ps.weights, dtype=np.float64)
+        self.T = int(self.weights.shape[0])
+
+    def args(self):
+        return (self.structures.ctypes.data_as(C.c_void_p), self.weights.ctypes.data_as(C.c_void_p), self.T)
+
+
+class Circuit:
+    """Owns a tc_circuit handle compiled from a workloads.Circuit."""
+
+    def __init__(self, circ: W.Circuit, dtype: int = TC_C64, tile_fwd: int = 0, tile_bwd: int = 0,
+                 mem_budget_bytes: int = 0):
+        self.circ = circ
+        self.n = circ.n
+        self.dtype = dtype
+        self.n_params = circ.n_params
+        ops = np.ascontiguousarray(circ.ops, dtype=W.OP_DTYPE)
+        pool = np.ascontiguousarray(np.stack([circ.pool.real, circ.pool.imag], -1).ravel(), dtype=np.float64)
+        opt = tc_options(tile_fwd, tile_bwd, mem_budget_bytes)
+        h = C.c_void_p()
+        _check(lib().tc_circuit_create(circ.n, dtype, circ.init, ops.ctypes.data_as(C.c_void_p), len(ops),
+                                       circ.n_params, pool.ctypes.data_as(C.c_void_p) if len(circ.pool) else None,
+                                       len(circ.pool), C.byref(opt), C.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.tc_circuit_destroy(h)
+            self.h = None
+
+    def info(self) -> dict:
+        o = tc_plan_info()
+        _check(lib().tc_circuit_info(self.h, C.byref(o)))
+        return {f: getattr(o, f) for f, _ in tc_plan_info._fields_ if f != "reserved"}
+
+    @property
+    def state_dtype(self):
+        import torch
+
+        return torch.complex128 if self.dtype == TC_C128 else torch.complex64
+
+    def apply(self, params, B: int, init=None, seed: int = 0, status=None, row_offset: int = 0, out=None,
+              stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty((B, 1 << self.n), dtype=self.state_dtype, device="cuda")
+        _check(lib().tc_apply_layers(self.h, _ptr(params), B, _ptr(init), C.c_uint64(seed), _ptr(status),
+                                     C.c_int64(row_offset), _ptr(out), _stream(stream)))
+        return out
+
+    def expect(self, states, ham: Hamiltonian, out=None, stream=None):
+        import torch
+
+        B = states.shape[0]
+        if out is None:
+            out = torch.empty(B, dtype=torch.float64, device="cuda")
+        s, w, T = ham.args()
+        _check(lib().tc_expect_pauli_sum(self.h, _ptr(states), B, s, w, T, _ptr(out), _stream(stream)))
+        return out
+
+    def expect_grad(self, params, ham: Hamiltonian, seed: int = 0, energy=None, grad=None, max_rows: int = 0,
+                    stream=None):
+        import torch
+
+        B = params.shape[0]
+        if energy is None:
+            energy = torch.empty(B, dtype=torch.float64, device="cuda")
+        if grad is None:
+            grad = torch.empty((B, self.n_params), dtype=torch.float64, device="cuda")
+        s, w, T = ham.args()
+        go = tc_grad_options(0, max_rows)
+        _check(lib().tc_expect_grad(self.h, _ptr(params), B, s, w, T, C.c_uint64(seed), _ptr(energy), _ptr(grad),
+                                    C.byref(go), _stream(stream)))
+        return energy, grad
+
+    def expect_plain(self, params, ham: Hamiltonian, work, energy=None, stream=None):
+        import torch
+
+        B = params.shape[0]
+        if energy is None:
+            energy = torch.empty(B, dtype=torch.float64, device="cuda")
+        s, w, T = ham.args()
+        _check(lib().tc_expect_plain(self.h, _ptr(params), B, s, w, T, _ptr(work), _ptr(energy), _stream(stream)))
+        return energy

@@ -1,0 +1,91 @@
+"""C-ABI host-side checks (CPU only: no compute calls)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2205_10091_b300 import native as nt
+from paper_2205_10091_b300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "tc.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"TC_API\s+[\w\s\*]+?\b(tc_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = _declared()
+    assert len(names) >= 9
+    L = nt.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(nt.SIGNATURES), set(names) - set(nt.SIGNATURES)
+
+
+def test_enum_values_match_generator():
+    src = open(HEADER).read()
+    for i, name in enumerate(W.OP_NAMES):
+        m = re.search(r"TC_OP_%s\s*=\s*(\d+)" % name, src)
+        assert m and int(m.group(1)) == i, name
+    assert re.search(r"TC_INIT_ZERO\s*=\s*0", src) and re.search(r"TC_INIT_PLUS\s*=\s*1", src)
+
+
+def test_op_struct_layout():
+    assert C.sizeof(nt.tc_op) == 56 == W.OP_DTYPE.itemsize
+    for f, _ in nt.tc_op._fields_:
+        assert getattr(nt.tc_op, f).offset == W.OP_DTYPE.fields[f][1], f
+
+
+def test_plan_tfim20_fuses_layers():
+    info = nt.Circuit(W.tfim_circuit(20, 10)).info()
+    assert info["n_ops"] == 390 and info["n_params"] == 20
+    # fewer HBM sweeps than layers: commuting gates of consecutive layers share passes
+    assert 1 <= info["fwd_passes"] <= 10
+    assert info["tile_qubits_fwd"] == 13
+
+
+def test_plan_narrow_circuit_is_padded():
+    info = nt.Circuit(W.tfim_circuit(3, 2)).info()
+    assert info["n_qubits"] == 3 and info["n_qubits_internal"] == 9
+
+
+def test_noise_events_counted():
+    circ, _, _, _ = W.noisy16_workload()
+    assert nt.Circuit(circ).info()["n_noise"] == circ.n_noise == 372
+
+
+@pytest.mark.parametrize("bad", ["q0", "q1", "param", "mat", "noise"])
+def test_invalid_ops_rejected(bad):
+    b = W.OpBuilder(4)
+    b.rx(0, 0)
+    b.cnot(1, 2)
+    b.unitary1(3, np.eye(2))
+    b.depolarizing(2, 0.1, 0.1, 0.1)
+    circ = b.build()
+    ops = circ.ops.copy()
+    if bad == "q0":
+        ops[0]["q0"] = 4
+    elif bad == "q1":
+        ops[1]["q1"] = 1
+    elif bad == "param":
+        ops[0]["param"] = 5
+    elif bad == "mat":
+        ops[2]["mat"] = 1
+    else:
+        ops[3]["px"] = 0.9
+    circ.ops = ops
+    with pytest.raises(nt.TcError) as e:
+        nt.Circuit(circ)
+    assert e.value.status == nt.TC_E_INVALID
+    assert "op " in str(e.value)
+
+
+def test_bad_sizes_rejected():
+    h = C.c_void_p()
+    assert nt.lib().tc_circuit_create(0, 0, 0, None, 0, 0, None, 0, None, C.byref(h)) == nt.TC_E_INVALID
+    assert nt.lib().tc_circuit_create(31, 0, 0, None, 0, 0, None, 0, None, C.byref(h)) == nt.TC_E_INVALID
+    assert nt.lib().tc_circuit_create(4, 7, 0, None, 0, 0, None, 0, None, C.byref(h)) == nt.TC_E_INVALID
