@@ -244,7 +244,8 @@ TC_API tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, c
  * summed algorithmic HBM bytes (each amplitude a launch must read or write,
  * counted once).  Kinds: 0 forward tile pass, 1 adjoint tile pass,
  * 2 Pauli-sum pass, 3 finalize reduction, 4 narrow-state padding,
- * 5 unfused per-term reduction.  `out` may be NULL to count kinds only.
+ * 5 unfused per-term reduction, 6 per-row gate-table build.  `out` may be
+ * NULL to count kinds only.
  */
 typedef struct {
   int32_t kind;

@@ -166,11 +166,14 @@ KArgs base_args(const tc_circuit* c, const DevPlan& dp) {
     if (_e != cudaSuccess) return cuda_fail(_e, where); \
   } while (0)
 
-tc_status run_forward(tc_circuit* c, const DevPlan& dp, const Schedule& sc, const PlanArrays& A, KArgs a,
-                      int rows, cudaStream_t s) {
+tc_status run_schedule(tc_circuit* c, int mode, const Schedule& sc, const PlanArrays& A, KArgs a, void* tables,
+                       int rows, cudaStream_t s) {
+  a.tables = tables;
+  a.table_stride = sc.table_total;
+  TC_CHECK_CUDA(launch_tables(is_dbl(c), a, sc.first_mat, sc.n_mats, rows, s), "gate tables");
   for (int p = 0; p < sc.n_passes; ++p) {
     a.pass = sc.first_pass + p;
-    TC_CHECK_CUDA(launch_pass(KM_FWD, is_dbl(c), a, A.passes[a.pass], rows, s), "forward pass");
+    TC_CHECK_CUDA(launch_pass(mode, is_dbl(c), a, A.passes[a.pass], rows, s), mode == KM_FWD ? "forward pass" : "adjoint pass");
   }
   return TC_OK;
 }
@@ -220,7 +223,7 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
   };
   c->k_fwd = pick(c->opt.tile_qubits_fwd, dbl ? 12 : 13, 13);
   c->k_bwd = pick(c->opt.tile_qubits_bwd, dbl ? 11 : 12, 12);
-  c->k_ham = c->k_fwd;
+  c->k_ham = c->k_fwd < 12 ? c->k_fwd : 12;  // 256-thread Pauli-sum passes
   std::string err;
   if (!normalise_ops(n_qubits, c->N, ops, n_ops, n_params, n_pool, c->gates, err)) {
     delete c;
@@ -229,8 +232,8 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
   for (auto& g : c->gates)
     if (g.noise_event >= 0) c->n_noise++;
   c->pool.assign(pool, pool + 2 * (size_t)n_pool);
-  c->fwd = build_schedule(c->gates, c->N, c->k_fwd, false, true, c->A);
-  c->bwd = build_schedule(c->gates, c->N, c->k_bwd, true, false, c->A);
+  c->fwd = build_schedule(c->gates, c->N, c->k_fwd, kRBFwd, false, true, c->A);
+  c->bwd = build_schedule(c->gates, c->N, c->k_bwd, kRBBwd, true, false, c->A);
   // parameter -> gradient slots (CSR)
   c->csr_off.assign(n_params + 1, 0);
   for (int p : c->bwd.slot_param) c->csr_off[p + 1]++;
@@ -276,13 +279,13 @@ tc_status tc_apply_layers(const tc_circuit* cc, const double* d_params, int B, c
   cudaStream_t s = (cudaStream_t)stream;
   const bool padded = c->N != c->n;
   const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
-  int chunk = B;
-  void* work = d_states_out;
-  if (padded) {
-    chunk = (int)std::min<int64_t>(B, std::max<int64_t>(1, (int64_t)(256u << 20) / (int64_t)per));
-    if ((st = ensure_ws(c, per * chunk)) != TC_OK) return st;
-    work = c->ws;
-  }
+  const size_t trow = (size_t)c->fwd.table_total * amp_bytes(c);
+  const size_t row_ws = (padded ? per : 0) + trow;
+  int chunk = (int)std::min<int64_t>(B, std::max<int64_t>(1, (int64_t)(256u << 20) / (int64_t)std::max<size_t>(row_ws, 1)));
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  if ((st = ensure_ws(c, al(padded ? per * chunk : 0) + al(trow * chunk) + 256)) != TC_OK) return st;
+  void* work = padded ? c->ws : d_states_out;
+  void* tables = (char*)c->ws + al(padded ? per * chunk : 0);
   for (int r0 = 0; r0 < B; r0 += chunk) {
     const int rows = std::min(chunk, B - r0);
     const size_t ub = ((size_t)1 << c->n) * amp_bytes(c);
@@ -302,7 +305,7 @@ tc_status tc_apply_layers(const tc_circuit* cc, const double* d_params, int B, c
         TC_CHECK_CUDA(cudaMemcpyAsync(out_rows, in_rows, ub * rows, cudaMemcpyDeviceToDevice, s), "init copy");
       }
     }
-    if ((st = run_forward(c, c->dplan, c->fwd, c->A, a, rows, s)) != TC_OK) return st;
+    if ((st = run_schedule(c, KM_FWD, c->fwd, c->A, a, tables, rows, s)) != TC_OK) return st;
     if (padded) TC_CHECK_CUDA(launch_pad_states(is_dbl(c), work, out_rows, c->n, c->N, rows, false, s), "unpad");
   }
   return TC_OK;
@@ -367,7 +370,8 @@ tc_status tc_expect_grad(tc_circuit* c, const double* d_params, int B, const uin
   const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
   const size_t tiles_b = (size_t)1 << (c->N - c->k_bwd);
   const int G = c->bwd.n_gslots;
-  const size_t row_bytes = 2 * per + (size_t)nh * tiles_h * 8 + (size_t)G * tiles_b * 8 + 64;
+  const size_t tf = (size_t)c->fwd.table_total * amp_bytes(c), tb = (size_t)c->bwd.table_total * amp_bytes(c);
+  const size_t row_bytes = 2 * per + (size_t)nh * tiles_h * 8 + (size_t)G * tiles_b * 8 + tf + tb + 64;
   int64_t cap = budget(c) / (int64_t)row_bytes;
   if (gopt && gopt->max_rows > 0) cap = std::min<int64_t>(cap, gopt->max_rows);
   if (cap < 1) return fail(TC_E_NOMEM, "one row of states does not fit the memory budget");
@@ -376,7 +380,9 @@ tc_status tc_expect_grad(tc_circuit* c, const double* d_params, int B, const uin
   const size_t o_lam = al(per * chunk);
   const size_t o_ep = o_lam + al(per * chunk);
   const size_t o_gp = o_ep + al((size_t)chunk * nh * tiles_h * 8);
-  const size_t need = o_gp + al((size_t)chunk * std::max(G, 1) * tiles_b * 8);
+  const size_t o_tf = o_gp + al((size_t)chunk * std::max(G, 1) * tiles_b * 8);
+  const size_t o_tb = o_tf + al(tf * chunk);
+  const size_t need = o_tb + al(tb * chunk);
   if ((st = ensure_ws(c, need)) != TC_OK) return st;
   char* w = (char*)c->ws;
   for (int r0 = 0; r0 < B; r0 += chunk) {
@@ -390,12 +396,9 @@ tc_status tc_expect_grad(tc_circuit* c, const double* d_params, int B, const uin
     a.theta = d_params ? d_params + (size_t)r0 * c->n_params : nullptr;
     a.seed = seed;
     a.row_offset = r0;
-    if ((st = run_forward(c, c->dplan, c->fwd, c->A, a, rows, s)) != TC_OK) return st;
+    if ((st = run_schedule(c, KM_FWD, c->fwd, c->A, a, w + o_tf, rows, s)) != TC_OK) return st;
     if ((st = run_ham(c, a, rows, true, s)) != TC_OK) return st;
-    for (int p = 0; p < c->bwd.n_passes; ++p) {
-      a.pass = c->bwd.first_pass + p;
-      TC_CHECK_CUDA(launch_pass(KM_BWD, is_dbl(c), a, c->A.passes[a.pass], rows, s), "adjoint pass");
-    }
+    if ((st = run_schedule(c, KM_BWD, c->bwd, c->A, a, w + o_tb, rows, s)) != TC_OK) return st;
     TC_CHECK_CUDA(launch_finalize(a.epart, nh, (int)tiles_h, a.gpart, G, (int)tiles_b, c->d_csr_off,
                                   c->d_csr_slots, c->n_params, rows, d_energy_out + r0,
                                   c->n_params ? d_grad_out + (size_t)r0 * c->n_params : nullptr, s),
@@ -421,12 +424,14 @@ tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, const ui
     c->plain_built = true;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  const size_t trow = (size_t)c->plain.table_total * amp_bytes(c);
+  if ((st = ensure_ws(c, trow * B + 256)) != TC_OK) return st;
   KArgs a = base_args(c, c->dplain);
   a.psi = d_states_work;
   a.theta = d_params;
   a.seed = 0;
   // pass 0 of the unfused plan writes the initial state, then one pass per gate
-  if ((st = run_forward(c, c->dplain, c->plain, c->Ap, a, B, s)) != TC_OK) return st;
+  if ((st = run_schedule(c, KM_FWD, c->plain, c->Ap, a, c->ws, B, s)) != TC_OK) return st;
   TC_CHECK_CUDA(cudaMemsetAsync(d_energy_out, 0, sizeof(double) * B, s), "memset");
   for (int t = 0; t < T; ++t) {
     uint32_t f = 0, sm = 0;

@@ -1,4 +1,4 @@
-// Internal plan format: plain structs written by the host planner (plan.cpp)
+// Internal plan format: plain structs written by the host planner (planner.cpp)
 // and read by the tile-pass kernels (sv_kernels.cu).  Everything is POD so the
 // whole plan uploads to the device with one copy per array.
 //
@@ -15,46 +15,52 @@
 
 namespace tcb {
 
-constexpr int kRB = 4;          // register bits per thread (16 amplitudes)
-constexpr int kR = 1 << kRB;    // amplitudes per thread
+constexpr int kRBFwd = 5;       // register bits per thread, forward passes (32 amplitudes)
+constexpr int kRBBwd = 4;       // adjoint passes hold psi and lambda (2 x 16 amplitudes)
+constexpr int kRBHam = 4;       // Pauli-sum passes
+constexpr int kRBMax = 5;
 constexpr int kLaneBits = 5;    // lowest tile bits mapped to warp lanes
-constexpr int kMinQubits = kRB + kLaneBits;  // narrower circuits get idle low qubits
+constexpr int kMinQubits = kRBMax + kLaneBits;  // narrower circuits get idle low qubits
 constexpr int kMaxK = 14;
 constexpr int kMaxQubits = 30;
 
 // Instruction kinds executed on the register tile.
 enum : int8_t {
-  IK_MAT2 = 0,      // 2x2 complex matrix on register bit j0 (table slot mslot)
-  IK_CNOT = 1,      // flip register bit j0 where global position `pos` is 1
+  IK_MAT2 = 0,      // general 2x2 complex matrix on register bit j0 (table[slot..slot+3])
+  IK_CNOT = 1,      // flip register bit j0 where the control (global position `pos`) is 1
   IK_MAT4 = 2,      // 4x4 complex matrix on register bits (j0 = q0, j1 = q1)
-  IK_DIAG = 3,      // diagonal group `aux` (phases from the full index)
-  IK_GRADX = 4,     // gslot += scale * Im <lam|X_j0|psi>
-  IK_GRADY = 5,     // gslot += scale * Im <lam|Y_j0|psi>
-  IK_GRADDIAG = 6,  // gslot += scale * Im <lam|G|psi>, G(x) = T - 2 m(x) of group aux
-  IK_SKIP = 7,      // no-op (identity noise outcome placeholder)
+  IK_DIAG = 3,      // diagonal group `slot` (phases from the full index)
+  IK_GRADDIAG = 4,  // gslot += gscale * Im <lam|G|psi>, G(x) = T - 2 m(x) of group `slot`
+  IK_RX = 5,        // RX: table[slot] = (c, s), a0' = c a0 - i s a1, a1' = c a1 - i s a0
+  IK_RY = 6,        // RY: table[slot] = (c, s), a0' = c a0 - s a1, a1' = s a0 + c a1
+  IK_H = 7,
+  IK_X = 8,
+  IK_PAULI = 9,     // noise outcome: table[slot].x = 0,1,2,3 (I, X, Y, Z)
+  IK_RX_ADJ = 10,   // adjoint step of RX: gslot += gscale*Im<lam|X|psi>; then RX(-a) on psi, lam
+  IK_RY_ADJ = 11,   // same for RY
+  IK_GRADX = 12,    // gslot += gscale * Im <lam|X_j0|psi> (no update)
+  IK_GRADY = 13,
 };
 
-// Per-CTA matrix-table entries built from theta[b] at the start of a pass.
+// Per-CTA table entries built from theta[b] at the start of a pass.
 enum : int8_t {
   MT_H = 0,
   MT_X = 1,
-  MT_RX = 2,
-  MT_RY = 3,
-  MT_U1 = 4,      // 2x2 from pool
-  MT_U2 = 5,      // 4x4 from pool
+  MT_RX = 2,      // 1 entry (c, s) of the effective angle
+  MT_RY = 3,      // 1 entry (c, s)
+  MT_U1 = 4,      // 2x2 from pool (4 entries)
+  MT_U2 = 5,      // 4x4 from pool (16 entries)
   MT_DIAGTAB = 6, // phases exp(-i s theta/2 (T - 2m)), m = 0..T  (T+1 entries)
-  MT_NOISE = 7,   // Pauli selected by the event's uniform number
-  MT_CZTAB = 8,   // the two signs {+1, -1} (CZ parity groups)
+  MT_NOISE = 7,   // 1 entry: selected Pauli code in .x
 };
 
-struct DevInstr {
+struct DevInstr {  // 16 bytes
   int8_t kind;
   int8_t j0, j1;   // register-bit indices
   int8_t jc;       // CNOT: register bit of the control, or -1 (control from the thread base)
-  int32_t pos;     // CNOT: global position of the control
-  int32_t aux;     // IK_DIAG / IK_GRADDIAG: diagonal-group index
-  int32_t mslot;   // first complex entry in the per-CTA table
-  int32_t gslot;   // local gradient slot (-1 = none)
+  int16_t pos;     // CNOT: global position of the control
+  int16_t gslot;   // local gradient slot (-1 = none)
+  int32_t slot;    // table entry (or diagonal-group index for IK_DIAG / IK_GRADDIAG)
   float gscale;    // gradient scale s
 };
 
@@ -65,7 +71,7 @@ struct DevMat {
   int32_t param;   // -1 = none
   double scale;
   int32_t pool;    // MT_U1/MT_U2 offset (complex entries) into the pool
-  int32_t dst;     // first complex entry in the per-CTA table
+  int32_t dst;     // entry offset in the per-row table array of the schedule
   int32_t T;       // MT_DIAGTAB: number of terms; MT_NOISE: event index
   int32_t pad2;
   double t1, t2, t3;  // MT_NOISE: interval ends of I, X, Y (left-closed)
@@ -74,7 +80,7 @@ struct DevMat {
 // A diagonal group: m(x) = sum_e popc(op_e(x) & mask_e), with
 //   op_e(x) = x ^ (x >> d_e)   (ZZ pairs at distance d_e; d_e = 0 means x: single Z)
 //   op_e(x) = x & (x >> d_e)   (CZ pairs) when `sign_mode`.
-// Phase mode: amplitude *= table[m]; sign mode: amplitude *= (-1)^m.
+// Phase mode: amplitude *= table[tab + m]; sign mode: amplitude *= (-1)^m.
 struct DevDiag {
   int32_t sign_mode;
   int32_t n_ent;
@@ -89,14 +95,14 @@ struct DevDiagEnt {
 };
 
 struct DevStage {
-  int8_t S[kRB];     // register tile bits
+  int8_t S[8];       // register tile bits (first RB used)
   int32_t n_instr;
-  int32_t instr_off;
+  int32_t instr_off; // relative to the pass's first instruction
 };
 
 // Pauli-sum terms, compiled per Hamiltonian.
-//  Diagonal terms: value(x) = w * (cnt - 2 popc((x ^ (x >> d)) & mask)) when d > 0,
-//                  w * (-1)^popc(x & mask) when d == 0.
+//  Diagonal terms: value(x) = w * (cnt - 2 popc((x ^ (x >> d)) & mask)) when cnt >= 0
+//                  (d == 0: popc(x & mask)), w * (-1)^popc(x & mask) when cnt < 0.
 //  Flip group f:   h_f(x) = sum_t w_t * i^{ny_t} * (-1)^popc(x & sm_t), and
 //                  (P psi)_y = h_f(y ^ f) psi_{y ^ f}.
 struct DevHDiag {
@@ -119,16 +125,22 @@ enum : int32_t {
   PF_INIT = 1,       // forward pass 0: synthesise the initial state instead of loading
   PF_LAM_LOAD = 2,   // Hamiltonian pass: accumulate into lambda (else start from 0)
   PF_LAM_STORE = 4,  // Hamiltonian pass: write lambda
+  PF_FULL = 8,       // the pass needs the full instruction set (CNOT, 4x4, multi-entry or CZ groups)
 };
 
 struct DevPass {
   int32_t k;            // tile bits
   int32_t nfix;         // N - k
+  int32_t rb;           // register bits of this pass's kernel
   uint8_t pos[32];      // tile bit -> global position
   uint8_t fixpos[32];   // fixed (per-tile) bits -> global position, ascending
   int32_t n_stages, stage_off;
+  int32_t n_instr, instr_off;  // all instructions of the pass (contiguous)
   int32_t n_mats, mat_off;
+  int32_t n_diag, diag_off;    // diagonal groups of the pass (contiguous)
+  int32_t n_dent, dent_off;    // their entries (contiguous)
   int32_t table_size;   // complex entries of the per-CTA table
+  int32_t table_off;    // offset of this pass's table in the per-row table array
   int32_t n_gslots;     // local gradient slots
   int32_t gslot_base;   // first global slot
   int32_t flags;
@@ -136,7 +148,6 @@ struct DevPass {
   int32_t n_hdiag, hdiag_off;
   int32_t n_hflip, hflip_off;
   int32_t epart_index;  // which energy partial this pass writes
-  int32_t pad;
 };
 
 }  // namespace tcb

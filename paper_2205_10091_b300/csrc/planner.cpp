@@ -8,7 +8,7 @@
 // RZZ, CZ) need no tile qubit because their phase depends only on the
 // amplitude index, and those sharing (parameter, scale) merge into one
 // phase-table lookup.  Inside a pass the same rule splits the gates into
-// register stages of kRB qubits.
+// register stages of RB qubits.
 #include "planner.h"
 
 #include <algorithm>
@@ -88,16 +88,16 @@ uint32_t item_need(const Item& it, const std::vector<HGate>& gates, const int* t
 
 }  // namespace
 
-Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjoint, bool first_init,
+Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, bool adjoint, bool first_init,
                         PlanArrays& A) {
   Schedule sc;
   sc.first_pass = (int)A.passes.size();
+  sc.first_mat = (int)A.mats.size();
   sc.k = k;
   std::vector<int> remaining(gates.size());
   std::iota(remaining.begin(), remaining.end(), 0);
   if (adjoint) std::reverse(remaining.begin(), remaining.end());
   const uint32_t low = (1u << kLaneBits) - 1;
-  const uint32_t all = (N >= 32) ? 0xffffffffu : ((1u << N) - 1);
   bool first = true;
 
   while (!remaining.empty() || (first && first_init)) {
@@ -126,11 +126,11 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjo
       }
     }
     for (int p = 0; popc(tile) < k && p < N; ++p) tile |= bit(p);  // fill with low positions
-    (void)all;
 
     DevPass P{};
     P.k = k;
     P.nfix = N - k;
+    P.rb = rb;
     int tb[32];
     for (int p = 0; p < 32; ++p) tb[p] = -1;
     {
@@ -187,38 +187,65 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjo
     }
 
     // ---- register stages ------------------------------------------------
+    // Every stage is one linear scan that keeps list order between items on
+    // shared qubits.  The first stage only takes items on high tile bits (so
+    // it can load straight from HBM), the next ones first take items on the
+    // lane bits 0..4 and then fill up; the pass ends on a high-bit stage.
+    const uint32_t kmask = (k >= 32) ? 0xffffffffu : ((1u << k) - 1);
+    const uint32_t high_tile = kmask & ~low;
     std::vector<std::pair<uint32_t, std::vector<int>>> stages;  // (S mask in tile bits, item ids)
     {
       std::vector<int> rem(items.size());
       std::iota(rem.begin(), rem.end(), 0);
+      int si = 0;
       while (!rem.empty()) {
         uint32_t S = 0, blk = 0;
         std::vector<int> tk, df;
-        for (int ii : rem) {
-          const Item& it = items[ii];
-          if (it.touch & blk) {
-            df.push_back(ii);
-            blk |= it.touch;
-            continue;
+        std::vector<char> took(items.size(), 0);
+        const bool prefer_low = si > 0;
+        for (int scan = 0; scan < 2; ++scan) {
+          blk = 0;
+          for (int ii : rem) {
+            if (took[ii]) continue;
+            const Item& it = items[ii];
+            if (it.touch & blk) {
+              blk |= it.touch;
+              continue;
+            }
+            const uint32_t need = item_need(it, gates, tb);
+            bool allowed;
+            if (si == 0) allowed = !(need & ~high_tile);
+            else if (prefer_low && scan == 0) allowed = !need || (need & low);
+            else allowed = true;
+            if (allowed && popc(S | need) <= rb) {
+              S |= need;
+              took[ii] = 1;
+              tk.push_back(ii);
+            } else {
+              blk |= it.touch;
+            }
           }
-          const uint32_t need = item_need(it, gates, tb);
-          if (popc(S | need) <= kRB) {
-            S |= need;
-            tk.push_back(ii);
-          } else {
-            df.push_back(ii);
-            blk |= it.touch;
-          }
+          if (si == 0) break;
         }
+        for (int ii : rem)
+          if (!took[ii]) df.push_back(ii);
+        if (tk.empty() && si == 0) {
+          // nothing fits a high-bit stage: start with an empty load stage
+          stages.push_back({0u, {}});
+          ++si;
+          continue;
+        }
+        // keep scan order inside the stage equal to list order where it matters:
+        // scan-1 items first, then scan-2 items, each in list order (tk already is)
         stages.push_back({S, tk});
         rem = df;
+        ++si;
       }
     }
-    const uint32_t high_tile = ((k >= 32) ? 0xffffffffu : ((1u << k) - 1)) & ~low;
     auto fill = [&](uint32_t S) {
-      // complete S to kRB bits, preferring high tile bits (keeps lanes on bits 0..4)
-      for (int j = k - 1; popc(S) < kRB && j >= kLaneBits; --j) S |= 1u << j;
-      for (int j = 0; popc(S) < kRB && j < k; ++j) S |= 1u << j;
+      // complete S to rb bits, preferring high tile bits (keeps lanes on bits 0..4)
+      for (int j = k - 1; popc(S) < rb && j >= kLaneBits; --j) S |= 1u << j;
+      for (int j = 0; popc(S) < rb && j < k; ++j) S |= 1u << j;
       return S;
     };
     if (stages.empty()) stages.push_back({0u, {}});
@@ -229,7 +256,10 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjo
     // ---- emit -----------------------------------------------------------
     P.stage_off = (int)A.stages.size();
     P.n_stages = (int)stages.size();
+    P.instr_off = (int)A.instrs.size();
     P.mat_off = (int)A.mats.size();
+    P.diag_off = (int)A.diags.size();
+    P.dent_off = (int)A.dents.size();
     P.gslot_base = sc.n_gslots;
     int table = 0;
     std::map<int, int> local_slot;  // param -> local slot
@@ -240,6 +270,25 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjo
       local_slot[param] = s;
       sc.slot_param.push_back(param);
       return s;
+    };
+    auto add_mat = [&](int8_t type, const HGate& g, int entries) {
+      DevMat m{};
+      m.type = type;
+      m.adj = adjoint ? 1 : 0;
+      m.param = g.param;
+      m.scale = g.scale;
+      m.pool = g.pool;
+      m.dst = sc.table_total + table;
+      if (type == MT_NOISE) {
+        m.T = g.noise_event;
+        m.t1 = g.t1;
+        m.t2 = g.t2;
+        m.t3 = g.t3;
+      }
+      A.mats.push_back(m);
+      const int local = table;
+      table += entries;
+      return local;
     };
     for (auto& st : stages) {
       DevStage ds{};
@@ -253,16 +302,18 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjo
             jof[j] = r++;
           }
       }
-      ds.instr_off = (int)A.instrs.size();
+      ds.instr_off = (int)A.instrs.size() - P.instr_off;
       for (int ii : st.second) {
         const Item& it = items[ii];
+        DevInstr in{};
+        in.gslot = -1;
+        in.jc = -1;
         if (it.group) {
           const HGate& g0 = gates[it.members[0]];
           DevDiag dg{};
           dg.sign_mode = g0.sign_mode ? 1 : 0;
           dg.T = (int)it.members.size();
-          dg.ent_off = (int)A.dents.size();
-          // entries: one (d, mask) per distance, duplicates start a new entry
+          dg.ent_off = (int)A.dents.size() - P.dent_off;
           std::vector<DevDiagEnt> ents;
           for (int gi : it.members) {
             const HGate& g = gates[gi];
@@ -286,100 +337,89 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjo
           }
           for (auto& e : ents) A.dents.push_back(e);
           dg.n_ent = (int)ents.size();
-          dg.tab = -1;
-          if (!dg.sign_mode) {
-            DevMat m{};
-            m.type = MT_DIAGTAB;
-            m.adj = adjoint ? 1 : 0;
-            m.param = g0.param;
-            m.scale = g0.scale;
-            m.dst = table;
-            m.T = dg.T;
-            A.mats.push_back(m);
-            dg.tab = table;
-            table += dg.T + 1;
-          }
-          const int di = (int)A.diags.size();
+          dg.tab = dg.sign_mode ? -1 : add_mat(MT_DIAGTAB, g0, dg.T + 1);
+          if (!dg.sign_mode) A.mats.back().T = dg.T;
+          const int di = (int)A.diags.size() - P.diag_off;
           A.diags.push_back(dg);
           if (adjoint && !dg.sign_mode && g0.param >= 0) {
-            DevInstr gi{};
+            DevInstr gi = in;
             gi.kind = IK_GRADDIAG;
-            gi.aux = di;
-            gi.gslot = slot_of(g0.param);
+            gi.slot = di;
+            gi.gslot = (int16_t)slot_of(g0.param);
             gi.gscale = (float)g0.scale;
-            gi.jc = -1;
             A.instrs.push_back(gi);
           }
-          DevInstr in{};
           in.kind = IK_DIAG;
-          in.aux = di;
-          in.gslot = -1;
-          in.jc = -1;
+          in.slot = di;
           A.instrs.push_back(in);
           continue;
         }
         const HGate& g = gates[it.gate];
-        DevInstr in{};
-        in.gslot = -1;
-        in.jc = -1;
         if (g.kind == TC_OP_CNOT) {
           in.kind = IK_CNOT;
           in.j0 = (int8_t)jof[tb[g.p1]];
-          in.pos = g.p0;
+          in.pos = (int16_t)g.p0;
           in.jc = (int8_t)((tb[g.p0] >= 0) ? jof[tb[g.p0]] : -1);
           A.instrs.push_back(in);
           continue;
         }
-        DevMat m{};
-        m.adj = adjoint ? 1 : 0;
-        m.param = g.param;
-        m.scale = g.scale;
-        m.pool = g.pool;
-        m.dst = table;
-        if (g.kind == TC_OP_U2) {
-          m.type = MT_U2;
-          table += 16;
-          in.kind = IK_MAT4;
-          in.j0 = (int8_t)jof[tb[g.p0]];
-          in.j1 = (int8_t)jof[tb[g.p1]];
-        } else {
-          switch (g.kind) {
-            case TC_OP_H: m.type = MT_H; break;
-            case TC_OP_X: m.type = MT_X; break;
-            case TC_OP_RX: m.type = MT_RX; break;
-            case TC_OP_RY: m.type = MT_RY; break;
-            case TC_OP_U1: m.type = MT_U1; break;
-            case TC_OP_PAULI_NOISE:
-              m.type = MT_NOISE;
-              m.T = g.noise_event;
-              m.t1 = g.t1;
-              m.t2 = g.t2;
-              m.t3 = g.t3;
-              break;
-            default: m.type = MT_X; break;
-          }
-          table += 4;
-          in.kind = IK_MAT2;
-          in.j0 = (int8_t)jof[tb[g.p0]];
-        }
-        in.mslot = m.dst;
-        A.mats.push_back(m);
-        if (adjoint && g.param >= 0 && (g.kind == TC_OP_RX || g.kind == TC_OP_RY)) {
-          DevInstr gi{};
-          gi.kind = g.kind == TC_OP_RX ? IK_GRADX : IK_GRADY;
-          gi.j0 = in.j0;
-          gi.jc = -1;
-          gi.gslot = slot_of(g.param);
-          gi.gscale = (float)g.scale;
-          A.instrs.push_back(gi);
+        in.j0 = (int8_t)jof[tb[g.p0]];
+        switch (g.kind) {
+          case TC_OP_U2:
+            in.kind = IK_MAT4;
+            in.j1 = (int8_t)jof[tb[g.p1]];
+            in.slot = add_mat(MT_U2, g, 16);
+            break;
+          case TC_OP_U1:
+            in.kind = IK_MAT2;
+            in.slot = add_mat(MT_U1, g, 4);
+            break;
+          case TC_OP_H:
+            in.kind = IK_H;
+            break;
+          case TC_OP_X:
+            in.kind = IK_X;
+            break;
+          case TC_OP_PAULI_NOISE:
+            in.kind = IK_PAULI;
+            in.slot = add_mat(MT_NOISE, g, 1);
+            break;
+          case TC_OP_RX:
+          case TC_OP_RY: {
+            const bool rx = g.kind == TC_OP_RX;
+            in.slot = add_mat(rx ? MT_RX : MT_RY, g, 1);
+            if (adjoint && g.param >= 0) {
+              in.kind = rx ? IK_RX_ADJ : IK_RY_ADJ;
+              in.gslot = (int16_t)slot_of(g.param);
+              in.gscale = (float)g.scale;
+            } else {
+              in.kind = rx ? IK_RX : IK_RY;
+            }
+          } break;
+          default:
+            in.kind = IK_X;
+            break;
         }
         A.instrs.push_back(in);
       }
-      ds.n_instr = (int)A.instrs.size() - ds.instr_off;
+      ds.n_instr = (int)A.instrs.size() - P.instr_off - ds.instr_off;
       A.stages.push_back(ds);
     }
+    P.n_instr = (int)A.instrs.size() - P.instr_off;
+    for (int i = P.instr_off; i < (int)A.instrs.size(); ++i) {
+      const DevInstr& in = A.instrs[i];
+      if (in.kind == IK_CNOT || in.kind == IK_MAT4) P.flags |= PF_FULL;
+      if (in.kind == IK_DIAG || in.kind == IK_GRADDIAG) {
+        const DevDiag& dg = A.diags[P.diag_off + in.slot];
+        if (dg.n_ent != 1 || dg.sign_mode) P.flags |= PF_FULL;
+      }
+    }
     P.n_mats = (int)A.mats.size() - P.mat_off;
+    P.n_diag = (int)A.diags.size() - P.diag_off;
+    P.n_dent = (int)A.dents.size() - P.dent_off;
     P.table_size = table;
+    P.table_off = sc.table_total;
+    sc.table_total += table;
     P.n_gslots = (int)local_slot.size();
     sc.n_gslots += P.n_gslots;
     sc.n_stages += P.n_stages;
@@ -388,24 +428,30 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjo
     first = false;
   }
   sc.n_passes = (int)A.passes.size() - sc.first_pass;
+  sc.n_mats = (int)A.mats.size() - sc.first_mat;
   return sc;
 }
 
 Schedule build_plain_schedule(const std::vector<HGate>& gates, int N, PlanArrays& A) {
   Schedule sc;
   sc.first_pass = (int)A.passes.size();
+  sc.first_mat = (int)A.mats.size();
   sc.k = kMinQubits;
-  {
-    // a gate-free pass that writes the initial state
-    Schedule s0 = build_schedule({}, N, kMinQubits, false, true, A);
-    sc.n_stages += s0.n_stages;
-  }
+  auto absorb = [&](const Schedule& s) {
+    // shift the sub-schedule's tables behind the ones already placed
+    for (int p = s.first_pass; p < s.first_pass + s.n_passes; ++p) A.passes[p].table_off += sc.table_total;
+    for (int m = s.first_mat; m < s.first_mat + s.n_mats; ++m) A.mats[m].dst += sc.table_total;
+    sc.table_total += s.table_total;
+    sc.n_stages += s.n_stages;
+  };
+  // a gate-free pass that writes the initial state, then one pass per gate
+  absorb(build_schedule({}, N, kMinQubits, kRBFwd, false, true, A));
   for (size_t i = 0; i < gates.size(); ++i) {
     std::vector<HGate> one{gates[i]};
-    Schedule s = build_schedule(one, N, kMinQubits, false, false, A);
-    sc.n_stages += s.n_stages;
+    absorb(build_schedule(one, N, kMinQubits, kRBFwd, false, false, A));
   }
   sc.n_passes = (int)A.passes.size() - sc.first_pass;
+  sc.n_mats = (int)A.mats.size() - sc.first_mat;
   return sc;
 }
 
@@ -500,6 +546,7 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
     DevPass P{};
     P.k = k;
     P.nfix = N - k;
+    P.rb = kRBHam;
     int tbit[32];
     {
       int j = 0, f = 0;

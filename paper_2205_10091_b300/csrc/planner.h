@@ -37,6 +37,8 @@ struct Schedule {
   int n_gslots = 0;               // global gradient slots (adjoint schedules)
   std::vector<int> slot_param;    // global slot -> parameter
   int n_stages = 0;
+  int first_mat = 0, n_mats = 0;  // table-building records of the schedule
+  int table_total = 0;            // table entries per batch row
 };
 
 struct HamPlan {
@@ -52,7 +54,7 @@ bool normalise_ops(int n_user, int n_internal, const tc_op* ops, int n_ops, int 
                    std::vector<HGate>& out, std::string& err);
 
 // Schedule gates (forward order, or reversed with adjoint=true) into passes.
-Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, bool adjoint, bool first_init,
+Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, bool adjoint, bool first_init,
                         PlanArrays& A);
 
 // Compile a Pauli sum (user structures) into Hamiltonian passes.

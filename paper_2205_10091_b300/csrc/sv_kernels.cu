@@ -2,7 +2,7 @@
 //
 // One CTA owns one tile of 2^k amplitudes of one batch row (its k tile bits
 // sit at the positions listed in the pass; the other bits are fixed by the
-// CTA index).  Each thread keeps 2^kRB amplitudes in registers.  A pass runs
+// CTA index).  Each thread keeps 2^RB amplitudes in registers.  A pass runs
 // a list of register stages: the first stage loads straight from HBM with the
 // warp's lanes on positions 0..4 (fully coalesced 256-byte rows), each later
 // stage re-maps the register bits through a swizzled shared-memory transpose,
@@ -112,21 +112,13 @@ __device__ void build_mat(const DevMat& m, V* tab, const double* th, const doubl
       t[2] = mk<V>((S)1, (S)0);
       t[3] = mk<V>((S)0, (S)0);
       break;
-    case MT_RX: {
-      double s, c;
-      sincos(0.5 * ang, &s, &c);
-      t[0] = mk<V>((S)c, (S)0);
-      t[1] = mk<V>((S)0, (S)-s);
-      t[2] = mk<V>((S)0, (S)-s);
-      t[3] = mk<V>((S)c, (S)0);
-    } break;
+    case MT_RX:
     case MT_RY: {
+      // (cos(a/2), sin(a/2)) of the effective angle; the kernel applies
+      // RX = [[c, -is], [-is, c]] or RY = [[c, -s], [s, c]]
       double s, c;
       sincos(0.5 * ang, &s, &c);
-      t[0] = mk<V>((S)c, (S)0);
-      t[1] = mk<V>((S)-s, (S)0);
-      t[2] = mk<V>((S)s, (S)0);
-      t[3] = mk<V>((S)c, (S)0);
+      t[0] = mk<V>((S)c, (S)s);
     } break;
     case MT_U1:
     case MT_U2: {
@@ -148,18 +140,8 @@ __device__ void build_mat(const DevMat& m, V* tab, const double* th, const doubl
     } break;
     case MT_NOISE: {
       const double u = noise_uniform(a, row, m.T);
-      const int w = u < m.t1 ? 0 : u < m.t2 ? 1 : u < m.t3 ? 2 : 3;
-      // I, X, Y, Z (all Hermitian: the adjoint is the same matrix)
-      const S z = 0, o = 1;
-      if (w == 0) {
-        t[0] = mk<V>(o, z); t[1] = mk<V>(z, z); t[2] = mk<V>(z, z); t[3] = mk<V>(o, z);
-      } else if (w == 1) {
-        t[0] = mk<V>(z, z); t[1] = mk<V>(o, z); t[2] = mk<V>(o, z); t[3] = mk<V>(z, z);
-      } else if (w == 2) {
-        t[0] = mk<V>(z, z); t[1] = mk<V>(z, -o); t[2] = mk<V>(z, o); t[3] = mk<V>(z, z);
-      } else {
-        t[0] = mk<V>(o, z); t[1] = mk<V>(z, z); t[2] = mk<V>(z, z); t[3] = mk<V>(-o, z);
-      }
+      const int w = u < m.t1 ? 0 : u < m.t2 ? 1 : u < m.t3 ? 2 : 3;  // I, X, Y, Z
+      t[0] = mk<V>((S)w, (S)0);
     } break;
     default:
       break;
@@ -169,20 +151,22 @@ __device__ void build_mat(const DevMat& m, V* tab, const double* th, const doubl
 // ---------------------------------------------------------------------------
 // Thread <-> amplitude mapping for one stage
 // ---------------------------------------------------------------------------
+template <int RB>
 struct Map {
-  uint32_t g;          // global index of register 0 (within the state)
-  uint32_t t;          // tile index of register 0
-  uint32_t ro[kRB];    // global offset of register bit r
-  uint32_t rt[kRB];    // tile offset of register bit r
+  uint32_t g;         // global index of register 0 (within the state)
+  uint32_t t;         // tile index of register 0
+  uint32_t ro[RB];    // global offset of register bit r
+  uint32_t rt[RB];    // tile offset of register bit r
 };
 
-__device__ __forceinline__ Map make_map(const DevPass& P, const int8_t* S, uint32_t tid, uint32_t base) {
-  Map m;
+template <int RB>
+__device__ __forceinline__ Map<RB> make_map(const DevPass& P, const int8_t* S, uint32_t tid, uint32_t base) {
+  Map<RB> m;
   m.g = base;
   m.t = 0;
   uint32_t smask = 0;
 #pragma unroll
-  for (int r = 0; r < kRB; ++r) {
+  for (int r = 0; r < RB; ++r) {
     smask |= 1u << S[r];
     m.ro[r] = 1u << P.pos[S[r]];
     m.rt[r] = 1u << S[r];
@@ -199,79 +183,149 @@ __device__ __forceinline__ Map make_map(const DevPass& P, const int8_t* S, uint3
   return m;
 }
 
-__device__ __forceinline__ uint32_t offg(const Map& m, int i) {
+template <int RB>
+__device__ __forceinline__ uint32_t offg(const Map<RB>& m, int i) {
   uint32_t o = 0;
 #pragma unroll
-  for (int r = 0; r < kRB; ++r)
+  for (int r = 0; r < RB; ++r)
     if ((i >> r) & 1) o |= m.ro[r];
   return o;
 }
-__device__ __forceinline__ uint32_t offt(const Map& m, int i) {
+template <int RB>
+__device__ __forceinline__ uint32_t offt(const Map<RB>& m, int i) {
   uint32_t o = 0;
 #pragma unroll
-  for (int r = 0; r < kRB; ++r)
+  for (int r = 0; r < RB; ++r)
     if ((i >> r) & 1) o |= m.rt[r];
   return o;
 }
 
-// XOR swizzle of the tile index in shared memory: the 16-byte/8-byte bank
-// group of an amplitude is mixed with bits 4.. of its index so that both
-// "lanes along bits 0..4" and "lanes along bits 4..8" access patterns are
-// conflict-free.
+// XOR swizzle of the tile index in shared memory: the bank group of an
+// amplitude is mixed with bits 4.. of its index so that both "lanes along
+// bits 0..4" and "lanes along bits 4..8" access patterns are conflict-free.
 template <typename V>
 __device__ __forceinline__ uint32_t swz(uint32_t t) {
   return t ^ ((t >> 4) & (sizeof(V) == 8 ? 15u : 7u));
 }
 
-template <typename V>
-__device__ __forceinline__ void load_regs(V (&A)[kR], const V* st, const Map& m) {
-#pragma unroll
-  for (int i = 0; i < kR; ++i) A[i] = st[m.g | offg(m, i)];
+// Lowest set bit of a compile-time constant j > 0 (folds after unrolling).
+__host__ __device__ constexpr int low_bit(int j) {
+  return (j & 1) ? 0 : (j & 2) ? 1 : (j & 4) ? 2 : (j & 8) ? 3 : 4;
 }
-template <typename V>
-__device__ __forceinline__ void store_regs(const V (&A)[kR], V* st, const Map& m) {
+
+// Register i of a stage lives at index base ^ XOR_{r in i} off[r].  Walking
+// i in reflected Gray-code order (j -> j ^ (j >> 1)) changes one register bit
+// per step, so each address is one XOR from the previous one.
+template <int RB, typename V>
+__device__ __forceinline__ void load_regs(V (&A)[1 << RB], const V* st, const Map<RB>& m) {
+  uint32_t idx = m.g;
 #pragma unroll
-  for (int i = 0; i < kR; ++i) st[m.g | offg(m, i)] = A[i];
+  for (int j = 0; j < (1 << RB); ++j) {
+    if (j) idx ^= m.ro[low_bit(j)];
+    A[j ^ (j >> 1)] = st[idx];
+  }
 }
-template <typename V>
-__device__ __forceinline__ void smem_write(const V (&A)[kR], V* sm, const Map& m) {
+template <int RB, typename V>
+__device__ __forceinline__ void store_regs(const V (&A)[1 << RB], V* st, const Map<RB>& m) {
+  uint32_t idx = m.g;
 #pragma unroll
-  for (int i = 0; i < kR; ++i) sm[swz<V>(m.t | offt(m, i))] = A[i];
+  for (int j = 0; j < (1 << RB); ++j) {
+    if (j) idx ^= m.ro[low_bit(j)];
+    st[idx] = A[j ^ (j >> 1)];
+  }
 }
-template <typename V>
-__device__ __forceinline__ void smem_read(V (&A)[kR], const V* sm, const Map& m) {
+template <int RB, typename V>
+__device__ __forceinline__ void smem_write(const V (&A)[1 << RB], V* sm, const Map<RB>& m) {
+  // swz is linear over XOR and t, rt[r] have disjoint bits
+  uint32_t idx = swz<V>(m.t);
 #pragma unroll
-  for (int i = 0; i < kR; ++i) A[i] = sm[swz<V>(m.t | offt(m, i))];
+  for (int j = 0; j < (1 << RB); ++j) {
+    if (j) idx ^= swz<V>(m.rt[low_bit(j)]);
+    sm[idx] = A[j ^ (j >> 1)];
+  }
+}
+template <int RB, typename V>
+__device__ __forceinline__ void smem_read(V (&A)[1 << RB], const V* sm, const Map<RB>& m) {
+  uint32_t idx = swz<V>(m.t);
+#pragma unroll
+  for (int j = 0; j < (1 << RB); ++j) {
+    if (j) idx ^= swz<V>(m.rt[low_bit(j)]);
+    A[j ^ (j >> 1)] = sm[idx];
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Register-tile gate primitives (J = register bit; compile-time indices)
 // ---------------------------------------------------------------------------
-template <int J, typename V>
-__device__ __forceinline__ void mat2(V (&A)[kR], V m00, V m01, V m10, V m11) {
+template <int RB, int J, typename V>
+__device__ __forceinline__ void g_mat2(V (&A)[1 << RB], const V* t) {
+  const V m00 = t[0], m01 = t[1], m10 = t[2], m11 = t[3];
 #pragma unroll
-  for (int i = 0; i < kR; ++i) {
+  for (int i = 0; i < (1 << RB); ++i) {
     if (i & (1 << J)) continue;
     const V x0 = A[i], x1 = A[i | (1 << J)];
     A[i] = cmac2(m00, x0, m01, x1);
     A[i | (1 << J)] = cmac2(m10, x0, m11, x1);
   }
 }
-template <typename V>
-__device__ __forceinline__ void mat2_dispatch(V (&A)[kR], int j, const V* t) {
-  const V m00 = t[0], m01 = t[1], m10 = t[2], m11 = t[3];
-  switch (j) {
-    case 0: mat2<0>(A, m00, m01, m10, m11); break;
-    case 1: mat2<1>(A, m00, m01, m10, m11); break;
-    case 2: mat2<2>(A, m00, m01, m10, m11); break;
-    default: mat2<3>(A, m00, m01, m10, m11); break;
+// RX: a0' = c a0 - i s a1, a1' = c a1 - i s a0
+template <int RB, int J, typename V>
+__device__ __forceinline__ void g_rx(V (&A)[1 << RB], V cs) {
+  const auto c = cs.x, s = cs.y;
+#pragma unroll
+  for (int i = 0; i < (1 << RB); ++i) {
+    if (i & (1 << J)) continue;
+    const V x0 = A[i], x1 = A[i | (1 << J)];
+    A[i] = mk<V>(fma(c, x0.x, s * x1.y), fma(c, x0.y, -s * x1.x));
+    A[i | (1 << J)] = mk<V>(fma(c, x1.x, s * x0.y), fma(c, x1.y, -s * x0.x));
   }
 }
-
-template <int J, typename V>
-__device__ __forceinline__ void cnot(V (&A)[kR], int jc, uint32_t cbase) {
+// RY: a0' = c a0 - s a1, a1' = s a0 + c a1
+template <int RB, int J, typename V>
+__device__ __forceinline__ void g_ry(V (&A)[1 << RB], V cs) {
+  const auto c = cs.x, s = cs.y;
 #pragma unroll
-  for (int i = 0; i < kR; ++i) {
+  for (int i = 0; i < (1 << RB); ++i) {
+    if (i & (1 << J)) continue;
+    const V x0 = A[i], x1 = A[i | (1 << J)];
+    A[i] = mk<V>(fma(c, x0.x, -s * x1.x), fma(c, x0.y, -s * x1.y));
+    A[i | (1 << J)] = mk<V>(fma(s, x0.x, c * x1.x), fma(s, x0.y, c * x1.y));
+  }
+}
+template <int RB, int J, typename V>
+__device__ __forceinline__ void g_h(V (&A)[1 << RB]) {
+  using S = decltype(V::x);
+  const S r = (S)0.70710678118654752440;
+#pragma unroll
+  for (int i = 0; i < (1 << RB); ++i) {
+    if (i & (1 << J)) continue;
+    const V x0 = A[i], x1 = A[i | (1 << J)];
+    A[i] = mk<V>(r * (x0.x + x1.x), r * (x0.y + x1.y));
+    A[i | (1 << J)] = mk<V>(r * (x0.x - x1.x), r * (x0.y - x1.y));
+  }
+}
+// Pauli p = 1 (X), 2 (Y), 3 (Z); Y|0> = i|1>, Y|1> = -i|0>
+template <int RB, int J, typename V>
+__device__ __forceinline__ void g_pauli(V (&A)[1 << RB], int p) {
+#pragma unroll
+  for (int i = 0; i < (1 << RB); ++i) {
+    if (i & (1 << J)) continue;
+    const V x0 = A[i], x1 = A[i | (1 << J)];
+    if (p == 1) {
+      A[i] = x1;
+      A[i | (1 << J)] = x0;
+    } else if (p == 2) {
+      A[i] = mk<V>(x1.y, -x1.x);
+      A[i | (1 << J)] = mk<V>(-x0.y, x0.x);
+    } else if (p == 3) {
+      A[i | (1 << J)] = mk<V>(-x1.x, -x1.y);
+    }
+  }
+}
+template <int RB, int J, typename V>
+__device__ __forceinline__ void g_cnot(V (&A)[1 << RB], int jc, uint32_t cbase) {
+#pragma unroll
+  for (int i = 0; i < (1 << RB); ++i) {
     if (i & (1 << J)) continue;
     const uint32_t c = cbase | (jc >= 0 ? ((uint32_t)i >> jc) & 1u : 0u);
     const V x0 = A[i], x1 = A[i | (1 << J)];
@@ -279,84 +333,84 @@ __device__ __forceinline__ void cnot(V (&A)[kR], int jc, uint32_t cbase) {
     A[i | (1 << J)] = c ? x0 : x1;
   }
 }
-template <typename V>
-__device__ __forceinline__ void cnot_dispatch(V (&A)[kR], int j, int jc, uint32_t cbase) {
-  switch (j) {
-    case 0: cnot<0>(A, jc, cbase); break;
-    case 1: cnot<1>(A, jc, cbase); break;
-    case 2: cnot<2>(A, jc, cbase); break;
-    default: cnot<3>(A, jc, cbase); break;
-  }
-}
-
-template <int J0, int J1, typename V>
-__device__ __forceinline__ void mat4(V (&A)[kR], const V* t) {
-  V m[16];
+template <int RB, int J0, int J1, typename V>
+__device__ __forceinline__ void g_mat4(V (&A)[1 << RB], const V* t) {
 #pragma unroll
-  for (int e = 0; e < 16; ++e) m[e] = t[e];
-#pragma unroll
-  for (int i = 0; i < kR; ++i) {
+  for (int i = 0; i < (1 << RB); ++i) {
     if (i & ((1 << J0) | (1 << J1))) continue;
     // row/column index 2*b(q0) + b(q1); q0 on register bit J0, q1 on J1
     const int i00 = i, i01 = i | (1 << J1), i10 = i | (1 << J0), i11 = i | (1 << J0) | (1 << J1);
     const V v0 = A[i00], v1 = A[i01], v2 = A[i10], v3 = A[i11];
-    V r0 = cmac2(m[0], v0, m[1], v1), s0 = cmac2(m[2], v2, m[3], v3);
-    V r1 = cmac2(m[4], v0, m[5], v1), s1 = cmac2(m[6], v2, m[7], v3);
-    V r2 = cmac2(m[8], v0, m[9], v1), s2 = cmac2(m[10], v2, m[11], v3);
-    V r3 = cmac2(m[12], v0, m[13], v1), s3 = cmac2(m[14], v2, m[15], v3);
-    r0.x += s0.x; r0.y += s0.y;
-    r1.x += s1.x; r1.y += s1.y;
-    r2.x += s2.x; r2.y += s2.y;
-    r3.x += s3.x; r3.y += s3.y;
-    A[i00] = r0;
-    A[i01] = r1;
-    A[i10] = r2;
-    A[i11] = r3;
+    V r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      V a = cmac2(t[4 * q], v0, t[4 * q + 1], v1), b = cmac2(t[4 * q + 2], v2, t[4 * q + 3], v3);
+      r[q] = mk<V>(a.x + b.x, a.y + b.y);
+    }
+    A[i00] = r[0];
+    A[i01] = r[1];
+    A[i10] = r[2];
+    A[i11] = r[3];
   }
 }
 
-template <typename V>
-__device__ __forceinline__ void mat4_dispatch(V (&A)[kR], int j0, int j1, const V* t) {
-  switch (j0 * 4 + j1) {
-    case 0 * 4 + 1: mat4<0, 1>(A, t); break;
-    case 0 * 4 + 2: mat4<0, 2>(A, t); break;
-    case 0 * 4 + 3: mat4<0, 3>(A, t); break;
-    case 1 * 4 + 0: mat4<1, 0>(A, t); break;
-    case 1 * 4 + 2: mat4<1, 2>(A, t); break;
-    case 1 * 4 + 3: mat4<1, 3>(A, t); break;
-    case 2 * 4 + 0: mat4<2, 0>(A, t); break;
-    case 2 * 4 + 1: mat4<2, 1>(A, t); break;
-    case 2 * 4 + 3: mat4<2, 3>(A, t); break;
-    case 3 * 4 + 0: mat4<3, 0>(A, t); break;
-    case 3 * 4 + 1: mat4<3, 1>(A, t); break;
-    default: mat4<3, 2>(A, t); break;
-  }
-}
-
-// Gradient primitives: return sum over pairs of Im<lam|X|psi> / Im<lam|Y|psi>.
-template <int J, typename V>
-__device__ __forceinline__ auto gradx(const V (&P)[kR], const V (&L)[kR]) {
+// Adjoint steps: return sum over pairs of Im<lam|G|psi> (G = X or Y) with the
+// states as they are, then (if cs != nullptr) apply RX/RY(-a) to psi and lam.
+template <int RB, int J, bool ISX, typename V>
+__device__ __forceinline__ decltype(V::x) g_adj(V (&P)[1 << RB], V (&L)[1 << RB], V cs, bool update) {
   decltype(V::x) acc = 0;
 #pragma unroll
-  for (int i = 0; i < kR; ++i) {
+  for (int i = 0; i < (1 << RB); ++i) {
     if (i & (1 << J)) continue;
     const V p0 = P[i], p1 = P[i | (1 << J)], l0 = L[i], l1 = L[i | (1 << J)];
-    acc += l0.x * p1.y - l0.y * p1.x + l1.x * p0.y - l1.y * p0.x;
+    if (ISX) acc += l0.x * p1.y - l0.y * p1.x + l1.x * p0.y - l1.y * p0.x;
+    else acc += -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
   }
-  return acc;
-}
-template <int J, typename V>
-__device__ __forceinline__ auto grady(const V (&P)[kR], const V (&L)[kR]) {
-  decltype(V::x) acc = 0;
-#pragma unroll
-  for (int i = 0; i < kR; ++i) {
-    if (i & (1 << J)) continue;
-    const V p0 = P[i], p1 = P[i | (1 << J)], l0 = L[i], l1 = L[i | (1 << J)];
-    acc += -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
+  if (update) {
+    if (ISX) {
+      g_rx<RB, J>(P, cs);
+      g_rx<RB, J>(L, cs);
+    } else {
+      g_ry<RB, J>(P, cs);
+      g_ry<RB, J>(L, cs);
+    }
   }
   return acc;
 }
 
+// switch helpers: run F<J>() for the runtime register bit j
+#define TC_DISPATCH_J(RB, j, CALL)         \
+  switch (j) {                             \
+    case 0: { constexpr int J = 0; CALL; } break; \
+    case 1: { constexpr int J = 1; CALL; } break; \
+    case 2: { constexpr int J = 2; CALL; } break; \
+    case 3: { constexpr int J = 3; CALL; } break; \
+    default: if (RB > 4) { constexpr int J = (RB > 4 ? 4 : 0); CALL; } break; \
+  }
+
+template <int RB, typename V>
+__device__ __forceinline__ void mat4_dispatch(V (&A)[1 << RB], int j0, int j1, const V* t) {
+#define TC_M4(a, b) \
+  case a * 8 + b: g_mat4<RB, a, (b < RB ? b : 0)>(A, t); break;
+  if (RB == 4) {
+    switch (j0 * 8 + j1) {
+      TC_M4(0, 1) TC_M4(0, 2) TC_M4(0, 3) TC_M4(1, 0) TC_M4(1, 2) TC_M4(1, 3)
+      TC_M4(2, 0) TC_M4(2, 1) TC_M4(2, 3) TC_M4(3, 0) TC_M4(3, 1) TC_M4(3, 2)
+      default: break;
+    }
+  } else {
+    switch (j0 * 8 + j1) {
+      TC_M4(0, 1) TC_M4(0, 2) TC_M4(0, 3) TC_M4(0, 4) TC_M4(1, 0) TC_M4(1, 2) TC_M4(1, 3) TC_M4(1, 4)
+      TC_M4(2, 0) TC_M4(2, 1) TC_M4(2, 3) TC_M4(2, 4) TC_M4(3, 0) TC_M4(3, 1) TC_M4(3, 2) TC_M4(3, 4)
+      case 4 * 8 + 0: g_mat4<RB, (RB > 4 ? 4 : 1), 0>(A, t); break;
+      case 4 * 8 + 1: g_mat4<RB, (RB > 4 ? 4 : 0), 1>(A, t); break;
+      case 4 * 8 + 2: g_mat4<RB, (RB > 4 ? 4 : 0), 2>(A, t); break;
+      case 4 * 8 + 3: g_mat4<RB, (RB > 4 ? 4 : 0), 3>(A, t); break;
+      default: break;
+    }
+  }
+#undef TC_M4
+}
 
 // Warp reduction in the working precision, then FP64 (T -> double).
 template <typename S>
@@ -367,40 +421,36 @@ __device__ __forceinline__ double warp_sum(S v) {
   return d;
 }
 
-// m(x) of a diagonal group for every register amplitude
-__device__ __forceinline__ void diag_counts(int (&cnt)[kR], const Map& m, const DevDiag& dg,
-                                            const DevDiagEnt* dents) {
-#pragma unroll
-  for (int i = 0; i < kR; ++i) cnt[i] = 0;
+// op(x) & mask of one diagonal entry.  For XOR (ZZ/Z) entries op is linear
+// over XOR; for AND (CZ) entries the register part is split with the
+// thread part g: (g ^ o) & ((g ^ o) >> d) = (g & g>>d) ^ (g & o>>d) ^ (o & g>>d) ^ (o & o>>d),
+// which is linear in o only when o is a single bit and o's partners are
+// fixed by g, so AND entries take the general path below.
+__device__ __forceinline__ uint32_t diag_op(uint32_t x, const DevDiagEnt& en, int sign_mode) {
+  const uint32_t v = en.d == 0 ? x : (sign_mode ? (x & (x >> en.d)) : (x ^ (x >> en.d)));
+  return v & en.mask;
+}
+__device__ __forceinline__ uint32_t diag_op_lin(uint32_t g, uint32_t o, const DevDiagEnt& en, int sign_mode) {
+  (void)g;
+  (void)sign_mode;
+  return (en.d == 0 ? o : (o ^ (o >> en.d))) & en.mask;
+}
+
+// m(x) of a diagonal group for one amplitude index
+__device__ __forceinline__ int diag_count(uint32_t x, const DevDiag& dg, const DevDiagEnt* ents) {
+  int c = 0;
   for (int e = 0; e < dg.n_ent; ++e) {
-    const DevDiagEnt en = dents[dg.ent_off + e];
-#pragma unroll
-    for (int i = 0; i < kR; ++i) {
-      const uint32_t x = m.g | offg(m, i);
-      const uint32_t v = en.d == 0 ? x : (dg.sign_mode ? (x & (x >> en.d)) : (x ^ (x >> en.d)));
-      cnt[i] += __popc(v & en.mask);
-    }
+    const DevDiagEnt en = ents[dg.ent_off + e];
+    const uint32_t v = en.d == 0 ? x : (dg.sign_mode ? (x & (x >> en.d)) : (x ^ (x >> en.d)));
+    c += __popc(v & en.mask);
   }
+  return c;
 }
 
-template <typename V>
-__device__ __forceinline__ void diag_apply(V (&A)[kR], const int (&cnt)[kR], const DevDiag& dg, const V* tab) {
-#pragma unroll
-  for (int i = 0; i < kR; ++i) {
-    if (dg.sign_mode) {
-      if (cnt[i] & 1) {
-        A[i].x = -A[i].x;
-        A[i].y = -A[i].y;
-      }
-    } else {
-      A[i] = cmul(tab[dg.tab + cnt[i]], A[i]);
-    }
-  }
-}
-
-template <typename T, int MODE>
-__global__ void __launch_bounds__(MODE == KM_BWD ? 256 : 512) k_pass(const __grid_constant__ KArgs a) {
+template <typename T, int MODE, int RB, bool FULL>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __grid_constant__ KArgs a) {
   using V = typename VT<T>::V;
+  constexpr int R = 1 << RB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ DevPass sp;
   if (threadIdx.x == 0) sp = (MODE == KM_HAM) ? a.hpasses[a.pass] : a.passes[a.pass];
@@ -419,28 +469,32 @@ __global__ void __launch_bounds__(MODE == KM_BWD ? 256 : 512) k_pass(const __gri
   V* psi = (V*)a.psi + soff;
   V* lam = a.lam ? (V*)a.lam + soff : nullptr;
 
+  // shared memory carve-up: tile(s) | table | instructions | diag groups | entries | reduction
   const int tsize = 1 << k;
   V* sm0 = (V*)smem_raw;
   V* sm1 = sm0 + tsize;
   V* tab = sm0 + (MODE == KM_BWD ? 2 * tsize : tsize);
-  double* red = (double*)(tab + ((sp.table_size + 1) & ~1));
+  DevInstr* ins = (DevInstr*)(tab + ((sp.table_size + 1) & ~1));
+  DevDiag* dgs = (DevDiag*)(ins + sp.n_instr);
+  DevDiagEnt* des = (DevDiagEnt*)(dgs + sp.n_diag);
+  double* red = (double*)(des + ((sp.n_dent + 1) & ~1));
 
-  V A[kR];
-  V L[kR];
+  V A[R];
+  V L[R];
 
   if (MODE == KM_HAM) {
     // ---------------- lambda (+)= H psi, energy partial -------------------
-    int8_t S[kRB];
+    int8_t S[RB];
 #pragma unroll
-    for (int r = 0; r < kRB; ++r) S[r] = (int8_t)(k - kRB + r);
-    const Map m = make_map(sp, S, tid, base);
-    load_regs(A, psi, m);
-    smem_write(A, sm0, m);
+    for (int r = 0; r < RB; ++r) S[r] = (int8_t)(k - RB + r);
+    const Map<RB> m = make_map<RB>(sp, S, tid, base);
+    load_regs<RB>(A, psi, m);
+    smem_write<RB>(A, sm0, m);
     if ((sp.flags & PF_LAM_LOAD) && lam) {
-      load_regs(L, lam, m);
+      load_regs<RB>(L, lam, m);
     } else {
 #pragma unroll
-      for (int i = 0; i < kR; ++i) L[i] = mk<V>((T)0, (T)0);
+      for (int i = 0; i < R; ++i) L[i] = mk<V>((T)0, (T)0);
     }
     __syncthreads();
     T eacc = 0;
@@ -448,7 +502,7 @@ __global__ void __launch_bounds__(MODE == KM_BWD ? 256 : 512) k_pass(const __gri
       const DevHDiag hd = a.hdiag[sp.hdiag_off + e];
       const T w = (T)hd.w;
 #pragma unroll
-      for (int i = 0; i < kR; ++i) {
+      for (int i = 0; i < R; ++i) {
         const uint32_t x = m.g | offg(m, i);
         T h;
         if (hd.cnt < 0) {
@@ -464,16 +518,31 @@ __global__ void __launch_bounds__(MODE == KM_BWD ? 256 : 512) k_pass(const __gri
     }
     for (int g = 0; g < sp.n_hflip; ++g) {
       const DevHFlip fl = a.hflips[sp.hflip_off + g];
+      if (fl.n_terms == 1) {
+        const DevHTerm ht = a.hterms[fl.term_off];
+        const T w = (T)ht.w;
 #pragma unroll
-      for (int i = 0; i < kR; ++i) {
-        const uint32_t x = m.g | offg(m, i);
-        const uint32_t xp = x ^ fl.f;
+        for (int i = 0; i < R; ++i) {
+          const uint32_t xp = (m.g | offg(m, i)) ^ fl.f;
+          const V pp = sm0[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
+          const T ws = (__popc(xp & ht.sm) & 1) ? -w : w;
+          const T hr = (ht.ny == 0) ? ws : (ht.ny == 2) ? -ws : (T)0;
+          const T hi = (ht.ny == 1) ? ws : (ht.ny == 3) ? -ws : (T)0;
+          const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
+          L[i].x += vr;
+          L[i].y += vi;
+          eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
+        }
+        continue;
+      }
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        const uint32_t xp = (m.g | offg(m, i)) ^ fl.f;
         const V pp = sm0[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
         T hr = 0, hi = 0;
         for (int q = 0; q < fl.n_terms; ++q) {
           const DevHTerm ht = a.hterms[fl.term_off + q];
           const T w = (__popc(xp & ht.sm) & 1) ? -(T)ht.w : (T)ht.w;
-          // times i^ny
           if (ht.ny == 0) hr += w;
           else if (ht.ny == 1) hi += w;
           else if (ht.ny == 2) hr -= w;
@@ -486,7 +555,7 @@ __global__ void __launch_bounds__(MODE == KM_BWD ? 256 : 512) k_pass(const __gri
         eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
       }
     }
-    if ((sp.flags & PF_LAM_STORE) && lam && a.store_lambda) store_regs(L, lam, m);
+    if ((sp.flags & PF_LAM_STORE) && lam && a.store_lambda) store_regs<RB>(L, lam, m);
     const double ws = warp_sum(eacc);
     if (lane == 0) red[warp] = ws;
     __syncthreads();
@@ -500,106 +569,194 @@ __global__ void __launch_bounds__(MODE == KM_BWD ? 256 : 512) k_pass(const __gri
 
   // ---------------- gate passes (forward / adjoint) ------------------------
   {
-    const double* th = a.theta ? a.theta + (size_t)row * a.n_params : nullptr;
-    for (int i = tid; i < sp.n_mats; i += blockDim.x) build_mat<V>(a.mats[sp.mat_off + i], tab, th, a.pool, a, row);
+    const V* trow = (const V*)a.tables + (size_t)row * a.table_stride + sp.table_off;
+    for (int i = tid; i < sp.table_size; i += blockDim.x) tab[i] = trow[i];
+    for (int i = tid; i < sp.n_instr; i += blockDim.x) ins[i] = a.instrs[sp.instr_off + i];
+    for (int i = tid; i < sp.n_diag; i += blockDim.x) dgs[i] = a.diags[sp.diag_off + i];
+    for (int i = tid; i < sp.n_dent; i += blockDim.x) des[i] = a.dents[sp.dent_off + i];
     if (MODE == KM_BWD)
       for (int i = tid; i < sp.n_gslots * nwarps; i += blockDim.x) red[i] = 0.0;
   }
   const DevStage* st = a.stages + sp.stage_off;
-  int8_t S[kRB];
+  T gacc = 0;
+  int cur_slot = -1;
+  auto flush = [&]() {
+    if (MODE != KM_BWD || cur_slot < 0) return;
+    T v = gacc;
 #pragma unroll
-  for (int r = 0; r < kRB; ++r) S[r] = st[0].S[r];
-  Map m = make_map(sp, S, tid, base);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[cur_slot * nwarps + warp] += (double)v;
+    gacc = 0;
+  };
+  int8_t S[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) S[r] = st[0].S[r];
+  Map<RB> m = make_map<RB>(sp, S, tid, base);
   if (MODE == KM_FWD && (sp.flags & PF_INIT) && a.synth_init) {
     if (a.init == 1) {
       const uint32_t anc = (1u << (a.N - a.n_user)) - 1u;
       const T amp = (T)exp2(-0.5 * (double)a.n_user);
 #pragma unroll
-      for (int i = 0; i < kR; ++i) A[i] = mk<V>(((m.g | offg(m, i)) & anc) ? (T)0 : amp, (T)0);
+      for (int i = 0; i < R; ++i) A[i] = mk<V>(((m.g | offg(m, i)) & anc) ? (T)0 : amp, (T)0);
     } else {
 #pragma unroll
-      for (int i = 0; i < kR; ++i) A[i] = mk<V>((m.g | offg(m, i)) == 0 ? (T)1 : (T)0, (T)0);
+      for (int i = 0; i < R; ++i) A[i] = mk<V>((m.g | offg(m, i)) == 0 ? (T)1 : (T)0, (T)0);
     }
   } else {
-    load_regs(A, psi, m);
-    if (MODE == KM_BWD) load_regs(L, lam, m);
+    load_regs<RB>(A, psi, m);
+    if (MODE == KM_BWD) load_regs<RB>(L, lam, m);
   }
-  __syncthreads();  // matrix table ready
+  __syncthreads();  // table, instructions and groups ready
 
   for (int s = 0; s < sp.n_stages; ++s) {
     const DevStage ds = st[s];
     if (s > 0) {
-      smem_write(A, sm0, m);
-      if (MODE == KM_BWD) smem_write(L, sm1, m);
+      smem_write<RB>(A, sm0, m);
+      if (MODE == KM_BWD) smem_write<RB>(L, sm1, m);
 #pragma unroll
-      for (int r = 0; r < kRB; ++r) S[r] = ds.S[r];
-      m = make_map(sp, S, tid, base);
+      for (int r = 0; r < RB; ++r) S[r] = ds.S[r];
+      m = make_map<RB>(sp, S, tid, base);
       __syncthreads();
-      smem_read(A, sm0, m);
-      if (MODE == KM_BWD) smem_read(L, sm1, m);
+      smem_read<RB>(A, sm0, m);
+      if (MODE == KM_BWD) smem_read<RB>(L, sm1, m);
       __syncthreads();
     }
     for (int q = 0; q < ds.n_instr; ++q) {
-      const DevInstr in = a.instrs[ds.instr_off + q];
+      const DevInstr in = ins[ds.instr_off + q];
       switch (in.kind) {
+        case IK_RX: {
+          const V cs = tab[in.slot];
+          TC_DISPATCH_J(RB, in.j0, (g_rx<RB, J>(A, cs)));
+          if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_rx<RB, J>(L, cs)));
+        } break;
+        case IK_RY: {
+          const V cs = tab[in.slot];
+          TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(A, cs)));
+          if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(L, cs)));
+        } break;
+        case IK_H:
+          TC_DISPATCH_J(RB, in.j0, (g_h<RB, J>(A)));
+          if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_h<RB, J>(L)));
+          break;
+        case IK_X:
+          TC_DISPATCH_J(RB, in.j0, (g_pauli<RB, J>(A, 1)));
+          if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_pauli<RB, J>(L, 1)));
+          break;
+        case IK_PAULI: {
+          const int p = (int)tab[in.slot].x;
+          if (p) {
+            TC_DISPATCH_J(RB, in.j0, (g_pauli<RB, J>(A, p)));
+            if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_pauli<RB, J>(L, p)));
+          }
+        } break;
         case IK_MAT2:
-          mat2_dispatch(A, in.j0, tab + in.mslot);
-          if (MODE == KM_BWD) mat2_dispatch(L, in.j0, tab + in.mslot);
+          TC_DISPATCH_J(RB, in.j0, (g_mat2<RB, J>(A, tab + in.slot)));
+          if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_mat2<RB, J>(L, tab + in.slot)));
           break;
         case IK_CNOT: {
+          if (!FULL) break;
           const uint32_t cb = (m.g >> in.pos) & 1u;
-          cnot_dispatch(A, in.j0, in.jc, cb);
-          if (MODE == KM_BWD) cnot_dispatch(L, in.j0, in.jc, cb);
+          TC_DISPATCH_J(RB, in.j0, (g_cnot<RB, J>(A, in.jc, cb)));
+          if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_cnot<RB, J>(L, in.jc, cb)));
         } break;
         case IK_MAT4:
-          mat4_dispatch(A, in.j0, in.j1, tab + in.mslot);
-          if (MODE == KM_BWD) mat4_dispatch(L, in.j0, in.j1, tab + in.mslot);
+          if (!FULL) break;
+          mat4_dispatch<RB>(A, in.j0, in.j1, tab + in.slot);
+          if (MODE == KM_BWD) mat4_dispatch<RB>(L, in.j0, in.j1, tab + in.slot);
           break;
         case IK_DIAG: {
-          const DevDiag dg = a.diags[in.aux];
-          int cnt[kR];
-          diag_counts(cnt, m, dg, a.dents);
-          diag_apply(A, cnt, dg, tab);
-          if (MODE == KM_BWD) diag_apply(L, cnt, dg, tab);
+          const DevDiag dg = dgs[in.slot];
+          if (dg.n_ent == 1 && !dg.sign_mode) {
+            // v(x) = op(x) & mask is linear over XOR: v(g ^ o_i) = v(g) ^ v(o_i)
+            const DevDiagEnt en = des[dg.ent_off];
+            const uint32_t vg = diag_op(m.g, en, dg.sign_mode);
+            uint32_t vr[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) vr[r] = diag_op_lin(m.g, m.ro[r], en, dg.sign_mode);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              uint32_t v = vg;
+#pragma unroll
+              for (int r = 0; r < RB; ++r)
+                if ((i >> r) & 1) v ^= vr[r];
+              const V ph = tab[dg.tab + __popc(v)];
+              A[i] = cmul(ph, A[i]);
+              if (MODE == KM_BWD) L[i] = cmul(ph, L[i]);
+            }
+            break;
+          }
+          if (!FULL) break;
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const int c = diag_count(m.g | offg(m, i), dg, des);
+            if (dg.sign_mode) {
+              if (c & 1) {
+                A[i] = mk<V>(-A[i].x, -A[i].y);
+                if (MODE == KM_BWD) L[i] = mk<V>(-L[i].x, -L[i].y);
+              }
+            } else {
+              const V ph = tab[dg.tab + c];
+              A[i] = cmul(ph, A[i]);
+              if (MODE == KM_BWD) L[i] = cmul(ph, L[i]);
+            }
+          }
         } break;
+        case IK_GRADDIAG:
+        case IK_RX_ADJ:
+        case IK_RY_ADJ:
         case IK_GRADX:
-        case IK_GRADY:
-        case IK_GRADDIAG: {
+        case IK_GRADY: {
           if (MODE != KM_BWD) break;
           T acc = 0;
           if (in.kind == IK_GRADDIAG) {
-            const DevDiag dg = a.diags[in.aux];
-            int cnt[kR];
-            diag_counts(cnt, m, dg, a.dents);
+            const DevDiag dg = dgs[in.slot];
+            if (dg.n_ent == 1 && !dg.sign_mode) {
+              const DevDiagEnt en = des[dg.ent_off];
+              const uint32_t vg = diag_op(m.g, en, 0);
+              uint32_t vr[RB];
 #pragma unroll
-            for (int i = 0; i < kR; ++i)
-              acc += (T)(dg.T - 2 * cnt[i]) * (L[i].x * A[i].y - L[i].y * A[i].x);
-          } else if (in.kind == IK_GRADX) {
-            switch (in.j0) {
-              case 0: acc = gradx<0>(A, L); break;
-              case 1: acc = gradx<1>(A, L); break;
-              case 2: acc = gradx<2>(A, L); break;
-              default: acc = gradx<3>(A, L); break;
+              for (int r = 0; r < RB; ++r) vr[r] = diag_op_lin(m.g, m.ro[r], en, 0);
+#pragma unroll
+              for (int i = 0; i < R; ++i) {
+                uint32_t v = vg;
+#pragma unroll
+                for (int r = 0; r < RB; ++r)
+                  if ((i >> r) & 1) v ^= vr[r];
+                acc += (T)(dg.T - 2 * __popc(v)) * (L[i].x * A[i].y - L[i].y * A[i].x);
+              }
+            } else if (FULL) {
+#pragma unroll
+              for (int i = 0; i < R; ++i) {
+                const int c = diag_count(m.g | offg(m, i), dg, des);
+                acc += (T)(dg.T - 2 * c) * (L[i].x * A[i].y - L[i].y * A[i].x);
+              }
             }
           } else {
-            switch (in.j0) {
-              case 0: acc = grady<0>(A, L); break;
-              case 1: acc = grady<1>(A, L); break;
-              case 2: acc = grady<2>(A, L); break;
-              default: acc = grady<3>(A, L); break;
+            const bool upd = in.kind == IK_RX_ADJ || in.kind == IK_RY_ADJ;
+            const V cs = upd ? tab[in.slot] : mk<V>((T)1, (T)0);
+            if (in.kind == IK_RX_ADJ || in.kind == IK_GRADX) {
+              TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, true>(A, L, cs, upd)));
+            } else {
+              TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, false>(A, L, cs, upd)));
             }
           }
-          const double ws = warp_sum(acc * (T)in.gscale);
-          if (lane == 0) red[in.gslot * nwarps + warp] += ws;
+          // consecutive contributions to one slot accumulate per thread and
+          // are reduced once per run (FP32 warp sum, FP64 across warps)
+          if (in.gslot != cur_slot) {
+            flush();
+            cur_slot = in.gslot;
+          }
+          gacc = fma(acc, (T)in.gscale, gacc);
         } break;
         default:
           break;
       }
     }
   }
-  store_regs(A, psi, m);
+  store_regs<RB>(A, psi, m);
   if (MODE == KM_BWD) {
-    store_regs(L, lam, m);
+    store_regs<RB>(L, lam, m);
+    flush();
     __syncthreads();
     for (int g = tid; g < sp.n_gslots; g += blockDim.x) {
       double s = 0;
@@ -609,38 +766,62 @@ __global__ void __launch_bounds__(MODE == KM_BWD ? 256 : 512) k_pass(const __gri
   }
 }
 
+template <typename V>
+__global__ void __launch_bounds__(128) k_tables(const __grid_constant__ KArgs a, int first_mat, int n_mats) {
+  const int row = blockIdx.x;
+  const double* th = a.theta ? a.theta + (size_t)row * a.n_params : nullptr;
+  V* trow = (V*)a.tables + (size_t)row * a.table_stride;
+  for (int i = threadIdx.x; i < n_mats; i += blockDim.x) build_mat<V>(a.mats[first_mat + i], trow, th, a.pool, a, row);
+}
+
+cudaError_t launch_tables(bool dbl, const KArgs& a, int first_mat, int n_mats, int rows, cudaStream_t s) {
+  if (rows <= 0 || n_mats <= 0) return cudaSuccess;
+  prof_before(PK_TABLES, (double)rows * a.table_stride * (dbl ? 16.0 : 8.0), s);
+  if (dbl)
+    k_tables<double2><<<rows, 128, 0, s>>>(a, first_mat, n_mats);
+  else
+    k_tables<float2><<<rows, 128, 0, s>>>(a, first_mat, n_mats);
+  prof_after(s);
+  return cudaGetLastError();
+}
+
 size_t pass_smem_bytes(int mode, bool dbl, const DevPass& p) {
   const size_t v = dbl ? 16 : 8;
   const size_t tsize = (size_t)1 << p.k;
-  const int nwarps = (int)((tsize >> kRB) >> 5) > 0 ? (int)((tsize >> kRB) >> 5) : 1;
+  const int threads = (int)(tsize >> p.rb);
+  const int nwarps = threads >= 32 ? threads / 32 : 1;
   size_t b = tsize * v * (mode == KM_BWD ? 2 : 1);
   b += (size_t)((p.table_size + 1) & ~1) * v;
+  b += (size_t)p.n_instr * sizeof(DevInstr) + (size_t)p.n_diag * sizeof(DevDiag);
+  b += (size_t)((p.n_dent + 1) & ~1) * sizeof(DevDiagEnt);
   if (mode == KM_BWD) b += (size_t)p.n_gslots * nwarps * 8;
   if (mode == KM_HAM) b += (size_t)nwarps * 8;
   return b + 16;
 }
 
-template <typename T, int MODE>
-static cudaError_t launch_t(const KArgs& a, const DevPass& hp, int rows, cudaStream_t s, size_t smem) {
+template <typename T, int MODE, int RB, bool FULL>
+static cudaError_t launch_tf(const KArgs& a, const DevPass& hp, int rows, cudaStream_t s, size_t smem) {
   static int configured_max = -1;
   if (configured_max < 0) {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_pass<T, MODE>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_pass<T, MODE, RB, FULL>);
     if (e != cudaSuccess) return e;
     const int dyn = optin - (int)fa.sharedSizeBytes;
-    e = cudaFuncSetAttribute(k_pass<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    e = cudaFuncSetAttribute(k_pass<T, MODE, RB, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
     configured_max = dyn;
   }
   if ((int)smem > configured_max) return cudaErrorInvalidConfiguration;
-  const unsigned threads = 1u << (hp.k - kRB);
+  if (hp.rb != RB) return cudaErrorInvalidValue;
+  const unsigned threads = 1u << (hp.k - RB);
+  if (threads < 32 || threads > 256) return cudaErrorInvalidConfiguration;
   const size_t blocks = (size_t)rows << hp.nfix;
   if (blocks == 0) return cudaSuccess;
   if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-  k_pass<T, MODE><<<(unsigned)blocks, threads, smem, s>>>(a);
+  k_pass<T, MODE, RB, FULL><<<(unsigned)blocks, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -721,19 +902,25 @@ static double pass_bytes(int mode, bool dbl, const DevPass& hp, const KArgs& a, 
   return amps * t;
 }
 
+template <typename T, int MODE, int RB>
+static cudaError_t launch_t(const KArgs& a, const DevPass& hp, int rows, cudaStream_t s, size_t smem) {
+  if (MODE != KM_HAM && (hp.flags & PF_FULL)) return launch_tf<T, MODE, RB, true>(a, hp, rows, s, smem);
+  return launch_tf<T, MODE, RB, false>(a, hp, rows, s, smem);
+}
+
 cudaError_t launch_pass(int mode, bool dbl, const KArgs& a, const DevPass& hp, int rows, cudaStream_t s) {
   const size_t smem = pass_smem_bytes(mode, dbl, hp);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   prof_before(mode == KM_FWD ? PK_FWD : mode == KM_BWD ? PK_BWD : PK_HAM, pass_bytes(mode, dbl, hp, a, rows), s);
   cudaError_t e;
   if (dbl) {
-    if (mode == KM_FWD) e = launch_t<double, KM_FWD>(a, hp, rows, s, smem);
-    else if (mode == KM_BWD) e = launch_t<double, KM_BWD>(a, hp, rows, s, smem);
-    else e = launch_t<double, KM_HAM>(a, hp, rows, s, smem);
+    if (mode == KM_FWD) e = launch_t<double, KM_FWD, kRBFwd>(a, hp, rows, s, smem);
+    else if (mode == KM_BWD) e = launch_t<double, KM_BWD, kRBBwd>(a, hp, rows, s, smem);
+    else e = launch_t<double, KM_HAM, kRBHam>(a, hp, rows, s, smem);
   } else {
-    if (mode == KM_FWD) e = launch_t<float, KM_FWD>(a, hp, rows, s, smem);
-    else if (mode == KM_BWD) e = launch_t<float, KM_BWD>(a, hp, rows, s, smem);
-    else e = launch_t<float, KM_HAM>(a, hp, rows, s, smem);
+    if (mode == KM_FWD) e = launch_t<float, KM_FWD, kRBFwd>(a, hp, rows, s, smem);
+    else if (mode == KM_BWD) e = launch_t<float, KM_BWD, kRBBwd>(a, hp, rows, s, smem);
+    else e = launch_t<float, KM_HAM, kRBHam>(a, hp, rows, s, smem);
   }
   prof_after(s);
   return e;

@@ -42,12 +42,20 @@ struct KArgs {
   double* epart;   // [rows][n_hpasses][tiles]
   int n_hpasses;
   int store_lambda;
+  // per-row gate tables (built by launch_tables) and their row stride (entries)
+  const void* tables;
+  int table_stride;
 };
 
 // Launch one pass for `rows` batch rows.  smem_bytes from pass_smem_bytes().
 cudaError_t launch_pass(int mode, bool dbl, const KArgs& a, const DevPass& host_pass, int rows,
                         cudaStream_t s);
 size_t pass_smem_bytes(int mode, bool dbl, const DevPass& p);
+
+// Build the gate tables (rotation cos/sin pairs, phase tables, 2x2/4x4
+// matrices, noise outcomes) of DevMat records [first_mat, first_mat+n_mats)
+// for `rows` batch rows into a.tables (row stride a.table_stride entries).
+cudaError_t launch_tables(bool dbl, const KArgs& a, int first_mat, int n_mats, int rows, cudaStream_t s);
 
 // E[b] = sum of energy partials; grad[b][p] = sum over slots of p and tiles.
 cudaError_t launch_finalize(const double* epart, int n_hpasses, int tiles_h, const double* gpart, int gslots,
@@ -64,7 +72,7 @@ cudaError_t launch_plain_term(bool dbl, const void* psi, int N, int rows, uint32
                               double w, double* e_acc, cudaStream_t s);
 
 // Optional event timing of every launch (enabled by tc_profile_begin).
-enum ProfKind : int { PK_FWD = 0, PK_BWD = 1, PK_HAM = 2, PK_FINALIZE = 3, PK_PAD = 4, PK_PLAIN = 5, PK_COUNT = 6 };
+enum ProfKind : int { PK_FWD = 0, PK_BWD = 1, PK_HAM = 2, PK_FINALIZE = 3, PK_PAD = 4, PK_PLAIN = 5, PK_TABLES = 6, PK_COUNT = 7 };
 void prof_begin();
 bool prof_enabled();
 void prof_before(int kind, double algo_bytes, cudaStream_t s);

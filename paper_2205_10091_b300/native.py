@@ -76,7 +76,8 @@ class tc_kernel_stat(C.Structure):
     _fields_ = [("kind", C.c_int32), ("launches", C.c_int32), ("total_ms", C.c_double), ("algo_bytes", C.c_double)]
 
 
-KERNEL_KINDS = ["tile_pass_forward", "tile_pass_adjoint", "pauli_sum_pass", "finalize", "pad", "plain_term"]
+KERNEL_KINDS = ["tile_pass_forward", "tile_pass_adjoint", "pauli_sum_pass", "finalize", "pad", "plain_term",
+                "gate_tables"]
 
 assert C.sizeof(tc_op) == W.OP_DTYPE.itemsize == 56
 

@@ -50,7 +50,7 @@ def test_plan_tfim20_fuses_layers():
 
 def test_plan_narrow_circuit_is_padded():
     info = nt.Circuit(W.tfim_circuit(3, 2)).info()
-    assert info["n_qubits"] == 3 and info["n_qubits_internal"] == 9
+    assert info["n_qubits"] == 3 and info["n_qubits_internal"] == 10
 
 
 def test_noise_events_counted():
