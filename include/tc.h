@@ -237,6 +237,29 @@ TC_API tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, c
                           void* stream);
 
 /*
+ * tc_expect_pauli_sum_noalloc — the energies of tc_expect_pauli_sum, for
+ * callers that cannot allocate device memory at the call site (a fixed
+ * memory reservation, an allocator callback, a latency-critical loop where
+ * cudaMalloc's implicit synchronisation is not acceptable).  The paper has no
+ * counterpart; this is a property of this library's interface.
+ *   Arguments, layout and results are those of tc_expect_pauli_sum, except:
+ *   - n_qubits of the circuit must be >= 10 (TC_E_UNSUPPORTED otherwise);
+ *   - scratch is one 8 MiB array in the library's device memory (held by
+ *     every GPU that loads the library until exit): the compiled Pauli sum
+ *     plus one double per (row, Pauli-sum pass, tile).  A call that needs
+ *     more returns TC_E_INVALID before touching the GPU; call with fewer rows.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.  The
+ *     plan is copied in with cudaMemcpyAsync from host memory.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the array and overwrites what it uses; calls that
+ *     overlap on the GPU (other streams, other host threads) race.
+ */
+TC_API tc_status tc_expect_pauli_sum_noalloc(const tc_circuit* c, const void* d_states, int B,
+                                             const uint8_t* structures, const double* weights, int T,
+                                             double* d_energy_out, void* stream);
+
+/*
  * Launch profiling: between tc_profile_begin and tc_profile_end every kernel
  * the library launches (from any thread) is bracketed by CUDA events recorded
  * on its own launch stream.  tc_profile_end synchronises those events and

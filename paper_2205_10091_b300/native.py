@@ -97,6 +97,8 @@ SIGNATURES = {
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_expect_plain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                   C.c_void_p, C.c_void_p]),
+    "tc_expect_pauli_sum_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                              C.c_void_p, C.c_void_p]),
     "tc_profile_begin": (C.c_int, []),
     "tc_profile_end": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "tc_last_error": (C.c_char_p, []),
@@ -214,6 +216,13 @@ class Circuit:
             out = torch.empty(B, dtype=torch.float64, device="cuda")
         s, w, T = ham.args()
         _check(lib().tc_expect_pauli_sum(self.h, _ptr(states), B, s, w, T, _ptr(out), _stream(stream)))
+        return out
+
+    def expect_noalloc(self, states, ham: Hamiltonian, out, stream=None):
+        """Energies through the allocation-free entry point (`out` is caller-owned)."""
+        B = states.shape[0]
+        s, w, T = ham.args()
+        _check(lib().tc_expect_pauli_sum_noalloc(self.h, _ptr(states), B, s, w, T, _ptr(out), _stream(stream)))
         return out
 
     def expect_grad(self, params, ham: Hamiltonian, seed: int = 0, energy=None, grad=None, max_rows: int = 0,
