@@ -40,6 +40,8 @@ enum : int8_t {
   IK_RY_ADJ = 11,   // same for RY
   IK_GRADX = 12,    // gslot += gscale * Im <lam|X_j0|psi> (no update)
   IK_GRADY = 13,
+  IK_RXM = 14,      // RX on several register bits: j0 = bit mask, entry of bit r = slot + rank of r in mask
+  IK_RXM_ADJ = 15,  // adjoint of IK_RXM: all bits share gslot/gscale
 };
 
 // Per-CTA table entries built from theta[b] at the start of a pass.

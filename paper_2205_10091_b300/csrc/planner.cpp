@@ -86,6 +86,65 @@ uint32_t item_need(const Item& it, const std::vector<HGate>& gates, const int* t
   return 1u << tb[g.p0];
 }
 
+// Merge each run of consecutive RX instructions (or adjoint RX steps with one
+// shared gradient slot and scale) on distinct register bits into one multi-bit
+// instruction.  RX gates on different qubits commute, and Im<lam|X_q|psi> is
+// unchanged by RX on other qubits, so the run may be reordered by bit index.
+// Their per-row table entries are moved so that bit r reads entry
+// slot + rank(r) (rank among the run's bits).
+void merge_rx_runs(PlanArrays& A, int first, int rb, int table_base) {
+  std::vector<DevInstr> out;
+  const int end = (int)A.instrs.size();
+  int i = first;
+  while (i < end) {
+    const DevInstr& in0 = A.instrs[i];
+    const bool fwd = in0.kind == IK_RX, adj = in0.kind == IK_RX_ADJ;
+    if (!fwd && !adj) {
+      out.push_back(in0);
+      ++i;
+      continue;
+    }
+    int j = i;
+    uint32_t mask = 0;
+    while (j < end && A.instrs[j].kind == in0.kind && !(mask & (1u << A.instrs[j].j0)) &&
+           (!adj || (A.instrs[j].gslot == in0.gslot && A.instrs[j].gscale == in0.gscale))) {
+      mask |= 1u << A.instrs[j].j0;
+      ++j;
+    }
+    if (j - i < 2) {
+      out.push_back(in0);
+      ++i;
+      continue;
+    }
+    // table entries of the run, sorted by bit
+    std::vector<std::pair<int, int>> bit_slot;
+    for (int q = i; q < j; ++q) bit_slot.push_back({A.instrs[q].j0, A.instrs[q].slot});
+    std::sort(bit_slot.begin(), bit_slot.end());
+    int lo = bit_slot[0].second;
+    for (auto& bs : bit_slot) lo = std::min(lo, bs.second);
+    // move the DevMat records: the entry of the r-th smallest bit goes to lo + r
+    std::vector<std::pair<int, int>> moves;  // (mat index, new local entry)
+    for (size_t r = 0; r < bit_slot.size(); ++r) {
+      const int old_local = bit_slot[r].second;
+      for (int mi = (int)A.mats.size() - 1; mi >= 0; --mi)
+        if (A.mats[mi].type == MT_RX && A.mats[mi].dst == table_base + old_local) {
+          moves.push_back({mi, lo + (int)r});
+          break;
+        }
+    }
+    for (auto& mv : moves) A.mats[mv.first].dst = table_base + mv.second;
+    DevInstr mi = in0;
+    mi.kind = fwd ? IK_RXM : IK_RXM_ADJ;
+    mi.j0 = (int8_t)mask;
+    mi.slot = lo;
+    out.push_back(mi);
+    i = j;
+  }
+  (void)rb;
+  A.instrs.resize(first);
+  A.instrs.insert(A.instrs.end(), out.begin(), out.end());
+}
+
 }  // namespace
 
 Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, bool adjoint, bool first_init,
@@ -402,6 +461,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
         }
         A.instrs.push_back(in);
       }
+      merge_rx_runs(A, P.instr_off + ds.instr_off, rb, sc.table_total);
       ds.n_instr = (int)A.instrs.size() - P.instr_off - ds.instr_off;
       A.stages.push_back(ds);
     }

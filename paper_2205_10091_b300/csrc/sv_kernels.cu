@@ -354,17 +354,36 @@ __device__ __forceinline__ void g_mat4(V (&A)[1 << RB], const V* t) {
   }
 }
 
+// Two lowest register bits other than J (compile-time), used to spread a
+// reduction over four independent accumulators.
+template <int RB, int J>
+struct AccBits {
+  static constexpr int b0 = (J == 0) ? 1 : 0;
+  static constexpr int b1 = (J <= 1) ? 2 : 1;
+};
+
 // Adjoint steps: return sum over pairs of Im<lam|G|psi> (G = X or Y) with the
-// states as they are, then (if cs != nullptr) apply RX/RY(-a) to psi and lam.
+// states as they are, then (if update) apply RX/RY(-a) to psi and lam.
 template <int RB, int J, bool ISX, typename V>
 __device__ __forceinline__ decltype(V::x) g_adj(V (&P)[1 << RB], V (&L)[1 << RB], V cs, bool update) {
-  decltype(V::x) acc = 0;
+  using S = decltype(V::x);
+  S acc[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int i = 0; i < (1 << RB); ++i) {
     if (i & (1 << J)) continue;
+    const int k = ((i >> AccBits<RB, J>::b0) & 1) | (((i >> AccBits<RB, J>::b1) & 1) << 1);
     const V p0 = P[i], p1 = P[i | (1 << J)], l0 = L[i], l1 = L[i | (1 << J)];
-    if (ISX) acc += l0.x * p1.y - l0.y * p1.x + l1.x * p0.y - l1.y * p0.x;
-    else acc += -(l0.x * p1.x + l0.y * p1.y) + (l1.x * p0.x + l1.y * p0.y);
+    if (ISX) {
+      acc[k] = fma(l0.x, p1.y, acc[k]);
+      acc[k] = fma(-l0.y, p1.x, acc[k]);
+      acc[k] = fma(l1.x, p0.y, acc[k]);
+      acc[k] = fma(-l1.y, p0.x, acc[k]);
+    } else {
+      acc[k] = fma(-l0.x, p1.x, acc[k]);
+      acc[k] = fma(-l0.y, p1.y, acc[k]);
+      acc[k] = fma(l1.x, p0.x, acc[k]);
+      acc[k] = fma(l1.y, p0.y, acc[k]);
+    }
   }
   if (update) {
     if (ISX) {
@@ -375,8 +394,26 @@ __device__ __forceinline__ decltype(V::x) g_adj(V (&P)[1 << RB], V (&L)[1 << RB]
       g_ry<RB, J>(L, cs);
     }
   }
-  return acc;
+  return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
+
+// RX on every register bit (entry of bit r at t[r]), unrolled at compile time.
+template <int RB, int R0, typename V>
+struct RxAll {
+  __device__ __forceinline__ static void run(V (&A)[1 << RB], const V* t) {
+    g_rx<RB, R0>(A, t[R0]);
+    RxAll<RB, R0 + 1, V>::run(A, t);
+  }
+  __device__ __forceinline__ static decltype(V::x) adj(V (&P)[1 << RB], V (&L)[1 << RB], const V* t) {
+    const decltype(V::x) a = g_adj<RB, R0, true>(P, L, t[R0], true);
+    return a + RxAll<RB, R0 + 1, V>::adj(P, L, t);
+  }
+};
+template <int RB, typename V>
+struct RxAll<RB, RB, V> {
+  __device__ __forceinline__ static void run(V (&)[1 << RB], const V*) {}
+  __device__ __forceinline__ static decltype(V::x) adj(V (&)[1 << RB], V (&)[1 << RB], const V*) { return 0; }
+};
 
 // switch helpers: run F<J>() for the runtime register bit j
 #define TC_DISPATCH_J(RB, j, CALL)         \
@@ -629,6 +666,21 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
           TC_DISPATCH_J(RB, in.j0, (g_rx<RB, J>(A, cs)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_rx<RB, J>(L, cs)));
         } break;
+        case IK_RXM: {
+          const uint32_t mask = (uint8_t)in.j0;
+          if (mask == (1u << RB) - 1u) {
+            RxAll<RB, 0, V>::run(A, tab + in.slot);
+            if (MODE == KM_BWD) RxAll<RB, 0, V>::run(L, tab + in.slot);
+          } else {
+            int e = 0;
+            for (int r = 0; r < RB; ++r) {
+              if (!((mask >> r) & 1u)) continue;
+              const V cs = tab[in.slot + e++];
+              TC_DISPATCH_J(RB, r, (g_rx<RB, J>(A, cs)));
+              if (MODE == KM_BWD) TC_DISPATCH_J(RB, r, (g_rx<RB, J>(L, cs)));
+            }
+          }
+        } break;
         case IK_RY: {
           const V cs = tab[in.slot];
           TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(A, cs)));
@@ -701,6 +753,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
             }
           }
         } break;
+        case IK_RXM_ADJ:
         case IK_GRADDIAG:
         case IK_RX_ADJ:
         case IK_RY_ADJ:
@@ -708,7 +761,21 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
         case IK_GRADY: {
           if (MODE != KM_BWD) break;
           T acc = 0;
-          if (in.kind == IK_GRADDIAG) {
+          if (in.kind == IK_RXM_ADJ) {
+            const uint32_t mask = (uint8_t)in.j0;
+            if (mask == (1u << RB) - 1u) {
+              acc = RxAll<RB, 0, V>::adj(A, L, tab + in.slot);
+            } else {
+              int e = 0;
+              for (int r = 0; r < RB; ++r) {
+                if (!((mask >> r) & 1u)) continue;
+                const V cs = tab[in.slot + e++];
+                T part = 0;
+                TC_DISPATCH_J(RB, r, (part = g_adj<RB, J, true>(A, L, cs, true)));
+                acc += part;
+              }
+            }
+          } else if (in.kind == IK_GRADDIAG) {
             const DevDiag dg = dgs[in.slot];
             if (dg.n_ent == 1 && !dg.sign_mode) {
               const DevDiagEnt en = des[dg.ent_off];
@@ -716,14 +783,16 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
               uint32_t vr[RB];
 #pragma unroll
               for (int r = 0; r < RB; ++r) vr[r] = diag_op_lin(m.g, m.ro[r], en, 0);
+              T a2[2] = {0, 0};
 #pragma unroll
               for (int i = 0; i < R; ++i) {
                 uint32_t v = vg;
 #pragma unroll
                 for (int r = 0; r < RB; ++r)
                   if ((i >> r) & 1) v ^= vr[r];
-                acc += (T)(dg.T - 2 * __popc(v)) * (L[i].x * A[i].y - L[i].y * A[i].x);
+                a2[i & 1] = fma((T)(dg.T - 2 * __popc(v)), fma(L[i].x, A[i].y, -L[i].y * A[i].x), a2[i & 1]);
               }
+              acc = a2[0] + a2[1];
             } else if (FULL) {
 #pragma unroll
               for (int i = 0; i < R; ++i) {
