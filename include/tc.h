@@ -279,6 +279,57 @@ typedef struct {
 TC_API tc_status tc_profile_begin(void);
 TC_API tc_status tc_profile_end(tc_kernel_stat* out, int max_out, int* n_out);
 
+/*
+ * Light-cone tensor-network contraction (Section "Tensor network engine",
+ * Section "Custom contraction settings", Table "contractor").
+ *
+ * tc_tn_lightcone_create — plan <0|U^dagger Z_{z_0} ... Z_{z_m} U|0> for a
+ * circuit of two-qubit gates on n_qubits.
+ *   gate_qubits  host [n_gates][2] qubit pairs in circuit order (copied); gate
+ *                matrices are supplied at contraction time (row index
+ *                2*b(q0) + b(q1), like TC_OP_U2)
+ *   z_qubits     host [n_z] qubits of the Z observable (copied)
+ *   rank_cap     largest rank an intermediate tensor may have (every index
+ *                has dimension 2)
+ *   path         NULL = greedy path found on the host; else an
+ *                opt_einsum-style list of n_path_steps position pairs over
+ *                the plan's input tensors (operands removed, result appended)
+ * Only gates in the backward causal cone of the observable enter the network
+ * (the rest cancel against their conjugates).  The network holds the cone's
+ * gates, their conjugates, |0> vectors and Z.  Greedy rule: contract the
+ * connected pair minimising size(out) - size(a) - size(b), ties to the
+ * smallest tensor ids, skipping pairs above rank_cap.  Host only.
+ *
+ * tc_contract_path — contract B instances of the planned network (same
+ * structure, different gate values) along the plan's path.
+ *   d_gates  device [B][n_gates][16] complex64 (interleaved floats): the
+ *            4x4 gate matrices of every gate of the circuit (cone gates used)
+ *   d_out    device [B][2] doubles: the complex scalar of each instance
+ * Each path step is one complex GEMM (FP32 accumulate) whose operand index
+ * permutation is folded into precomputed gather tables; the whole sequence
+ * is captured once as a CUDA graph and replayed.  Scratch (inputs and all
+ * intermediates of B instances) is owned by the plan.
+ */
+typedef struct tc_tn tc_tn;
+typedef struct {
+  double flops;   /* real FLOPs of the path's complex multiply-adds (8 per MAC) */
+  double cmacs;   /* complex multiply-adds */
+  double write;   /* elements written over all intermediates (the paper's WRITE) */
+  double size;    /* elements of the largest intermediate (the paper's SIZE) */
+  int32_t n_steps;
+  int32_t max_rank;
+  int32_t n_cone_gates;
+  int32_t cone_lo, cone_hi; /* qubit span of the light cone */
+  int32_t n_inputs;         /* input tensors of the doubled network */
+  int32_t reserved[4];
+} tc_path_info;
+TC_API tc_status tc_tn_lightcone_create(int n_qubits, const int32_t* gate_qubits, int n_gates,
+                                        const int32_t* z_qubits, int n_z, int rank_cap, const int32_t* path,
+                                        int n_path_steps, tc_tn** out);
+TC_API tc_status tc_tn_info(const tc_tn* t, tc_path_info* out);
+TC_API tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out, void* stream);
+TC_API void tc_tn_destroy(tc_tn* t);
+
 /* Thread-local message describing the last non-TC_OK status. */
 TC_API const char* tc_last_error(void);
 

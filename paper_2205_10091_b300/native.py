@@ -72,6 +72,12 @@ class tc_grad_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("max_rows", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
+class tc_path_info(C.Structure):
+    _fields_ = [("flops", C.c_double), ("cmacs", C.c_double), ("write", C.c_double), ("size", C.c_double),
+                ("n_steps", C.c_int32), ("max_rank", C.c_int32), ("n_cone_gates", C.c_int32), ("cone_lo", C.c_int32),
+                ("cone_hi", C.c_int32), ("n_inputs", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
 class tc_kernel_stat(C.Structure):
     _fields_ = [("kind", C.c_int32), ("launches", C.c_int32), ("total_ms", C.c_double), ("algo_bytes", C.c_double)]
 
@@ -99,6 +105,11 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p]),
     "tc_expect_pauli_sum_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                               C.c_void_p, C.c_void_p]),
+    "tc_tn_lightcone_create": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                         C.c_int, C.POINTER(C.c_void_p)]),
+    "tc_tn_info": (C.c_int, [C.c_void_p, C.POINTER(tc_path_info)]),
+    "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tc_tn_destroy": (None, [C.c_void_p]),
     "tc_profile_begin": (C.c_int, []),
     "tc_profile_end": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "tc_last_error": (C.c_char_p, []),
@@ -249,3 +260,40 @@ class Circuit:
         s, w, T = ham.args()
         _check(lib().tc_expect_plain(self.h, _ptr(params), B, s, w, T, _ptr(work), _ptr(energy), _stream(stream)))
         return energy
+
+
+class LightCone:
+    """Light-cone tensor-network plan for <Z..Z> of a two-qubit-gate circuit."""
+
+    def __init__(self, n_qubits: int, gate_qubits, z_qubits, rank_cap: int = 18, path=None):
+        gq = np.ascontiguousarray(np.asarray(gate_qubits, dtype=np.int32).reshape(-1, 2))
+        zq = np.ascontiguousarray(np.asarray(z_qubits, dtype=np.int32))
+        pth = None if path is None else np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1, 2))
+        h = C.c_void_p()
+        _check(lib().tc_tn_lightcone_create(n_qubits, gq.ctypes.data_as(C.c_void_p), len(gq),
+                                            zq.ctypes.data_as(C.c_void_p), len(zq), rank_cap,
+                                            None if pth is None else pth.ctypes.data_as(C.c_void_p),
+                                            0 if pth is None else len(pth), C.byref(h)))
+        self.h = h
+        self.n_gates = len(gq)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.tc_tn_destroy(h)
+            self.h = None
+
+    def info(self) -> dict:
+        o = tc_path_info()
+        _check(lib().tc_tn_info(self.h, C.byref(o)))
+        return {f: getattr(o, f) for f, _ in tc_path_info._fields_ if f != "reserved"}
+
+    def contract(self, d_gates, out=None, stream=None):
+        """d_gates: CUDA complex64 tensor [B][n_gates][4][4]; returns CUDA float64 [B][2]."""
+        import torch
+
+        B = d_gates.shape[0]
+        if out is None:
+            out = torch.empty((B, 2), dtype=torch.float64, device="cuda")
+        _check(lib().tc_contract_path(self.h, B, _ptr(d_gates), _ptr(out), _stream(stream)))
+        return out

@@ -1,0 +1,60 @@
+"""GPU parity: light-cone contraction against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import tensornet as T
+from paper_2205_10091_b300 import native as nt
+from paper_2205_10091_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_ZZ = 1e-5  # absolute: |<Z Z>| <= 1
+
+
+def _gates_tensor(gate_lists):
+    import torch
+
+    arr = np.stack([np.stack([u for (_, _, u) in g]) for g in gate_lists]).astype(np.complex64)
+    return torch.as_tensor(arr, device="cuda")
+
+
+def test_brick200_depth8_zz_vs_oracle():
+    n, gates, obs = W.brick200_workload()
+    lc = nt.LightCone(n, [(a, b) for a, b, _ in gates], obs)
+    out = lc.contract(_gates_tensor([gates])).cpu().numpy()
+    ref = T.cone_statevector_expectation(gates, obs)
+    assert abs(out[0, 0] - ref.real) <= TOL_ZZ and abs(out[0, 1]) <= TOL_ZZ
+
+
+def test_batch_of_seeds_each_matches():
+    n, depth, obs = 60, 8, (29, 30)
+    gl = [W.brickwork_u4(n, depth, np.random.default_rng(s)) for s in range(6)]
+    lc = nt.LightCone(n, [(a, b) for a, b, _ in gl[0]], obs)
+    out = lc.contract(_gates_tensor(gl)).cpu().numpy()
+    for b in range(6):
+        ref = T.cone_statevector_expectation(gl[b], obs).real
+        assert abs(out[b, 0] - ref) <= TOL_ZZ
+    # batch row alone equals in batch
+    one = lc.contract(_gates_tensor(gl[3:4])).cpu().numpy()
+    assert np.array_equal(one[0], out[3])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_small_brickwork_vs_full_network(seed):
+    n = 6
+    gates = W.brickwork_u4(n, 4, np.random.default_rng(seed))
+    for obs in ((2, 3), (0,), (1, 4)):
+        lc = nt.LightCone(n, [(a, b) for a, b, _ in gates], obs)
+        out = lc.contract(_gates_tensor([gates])).cpu().numpy()
+        net = T.network_expectation(n, gates, obs)
+        ref = T.contract(net, T.greedy_path(net)).real
+        assert abs(out[0, 0] - ref) <= TOL_ZZ
+
+
+def test_repeated_calls_reuse_graph_and_agree():
+    n, gates, obs = W.brick200_workload()
+    lc = nt.LightCone(n, [(a, b) for a, b, _ in gates], obs)
+    g = _gates_tensor([gates])
+    a = lc.contract(g).cpu().numpy()
+    b = lc.contract(g).cpu().numpy()
+    assert np.array_equal(a, b)

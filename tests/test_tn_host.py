@@ -1,0 +1,71 @@
+"""Light-cone planner host checks (CPU only: plans are built on the host)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import tensornet as T
+from paper_2205_10091_b300 import native as nt
+from paper_2205_10091_b300 import workloads as W
+
+
+def _plan(n, depth, obs, seed=0, cap=18, path=None):
+    gates = W.brickwork_u4(n, depth, np.random.default_rng(seed))
+    return nt.LightCone(n, [(a, b) for a, b, _ in gates], obs, rank_cap=cap, path=path), gates
+
+
+def test_brick200_cone_matches_oracle_cone():
+    n, gates, obs = W.brick200_workload()
+    lc = nt.LightCone(n, [(a, b) for a, b, _ in gates], obs)
+    info = lc.info()
+    cone = T.light_cone(gates, obs)
+    assert info["n_cone_gates"] == len(cone) == 36
+    assert (info["cone_lo"], info["cone_hi"]) == (92, 107)
+    # 16 qubits x (|0> ket + |0> bra) + 36 x (gate + conjugate) + 2 Z
+    assert info["n_inputs"] == 32 + 72 + 2
+    assert info["n_steps"] == info["n_inputs"] - 1
+    assert info["max_rank"] <= 18
+    assert info["flops"] == 8 * info["cmacs"]
+    assert info["size"] <= info["write"]
+
+
+@pytest.mark.parametrize("cap", [6, 8, 12])
+def test_rank_cap_respected_or_refused(cap):
+    try:
+        lc, _ = _plan(40, 6, (19, 20), cap=cap)
+    except nt.TcError as e:
+        assert e.status == nt.TC_E_INVALID and "rank cap" in str(e)
+        return
+    assert lc.info()["max_rank"] <= cap
+
+
+def test_user_path_accepted_and_checked():
+    lc, gates = _plan(6, 2, (2, 3))
+    n_in = lc.info()["n_inputs"]
+    seq = [(0, 1)] + [(0, k) for k in range(n_in - 2, 0, -1)]
+    try:
+        p = nt.LightCone(6, [(a, b) for a, b, _ in gates], (2, 3), rank_cap=26, path=seq)
+        assert p.info()["n_steps"] == n_in - 1
+    except nt.TcError as e:  # a sequential fold may create outer products; must be a clean refusal
+        assert e.status == nt.TC_E_INVALID
+    with pytest.raises(nt.TcError):
+        nt.LightCone(6, [(a, b) for a, b, _ in gates], (2, 3), path=[(0, 0)])
+
+
+def test_bad_inputs_rejected():
+    with pytest.raises(nt.TcError):
+        nt.LightCone(4, [(0, 4)], (0,))
+    with pytest.raises(nt.TcError):
+        nt.LightCone(4, [(1, 1)], (0,))
+    with pytest.raises(nt.TcError):
+        nt.LightCone(4, [(0, 1)], (7,))
+
+
+def test_example_block_shaped_metrics_reported():
+    # the contractor-table testbed shape (n=40, d=6, <Z_20>), with brickwork
+    # gates: the greedy path and its log10 FLOPs / log2 SIZE / log2 WRITE
+    n = 40
+    gates = W.brickwork_u4(n, 6, np.random.default_rng(1))
+    info = nt.LightCone(n, [(a, b) for a, b, _ in gates], (20,)).info()
+    assert 0 < math.log10(info["flops"]) < 10
+    assert math.log2(info["size"]) <= 18
