@@ -237,6 +237,14 @@ TC_API tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, c
                           void* stream);
 
 /*
+ * tc_mean_stderr — d_out[0] = mean of d_x[0..n), d_out[1] = its standard
+ * error (sample standard deviation with ddof = 1, over sqrt(n)), in FP64 with
+ * a fixed-order reduction: the Monte Carlo estimate over trajectories
+ * (Section "Batched Monte Carlo trajectory noise simulation").
+ */
+TC_API tc_status tc_mean_stderr(const double* d_x, int n, double* d_out, void* stream);
+
+/*
  * tc_expect_pauli_sum_noalloc — the energies of tc_expect_pauli_sum, for
  * callers that cannot allocate device memory at the call site (a fixed
  * memory reservation, an allocator callback, a latency-critical loop where

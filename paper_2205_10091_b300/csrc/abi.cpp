@@ -63,7 +63,7 @@ tc_circuit::~tc_circuit() {
   if (uploaded) {
     dplan.release();
     dplain.release();
-    dham.release();
+    for (auto& e : hcache) e.dev.release();
     dev_free(d_pool);
     dev_free(d_csr_off);
     dev_free(d_csr_slots);
@@ -97,23 +97,40 @@ tc_status ensure_ham(tc_circuit* c, const uint8_t* structures, const double* wei
   if (T < 0) return fail(TC_E_INVALID, "T < 0");
   if (T > 0 && (!structures || !weights)) return fail(TC_E_INVALID, "structures/weights are NULL");
   const size_t ns = (size_t)T * c->n;
-  if (c->h_T == T && c->h_struct.size() == ns && (ns == 0 || !memcmp(c->h_struct.data(), structures, ns)) &&
-      (T == 0 || !memcmp(c->h_w.data(), weights, T * sizeof(double))))
-    return TC_OK;
-  HamPlan H;
+  for (auto& e : c->hcache) {
+    if (e.T == T && e.st.size() == ns && (ns == 0 || !memcmp(e.st.data(), structures, ns)) &&
+        (T == 0 || !memcmp(e.w.data(), weights, T * sizeof(double)))) {
+      e.used = ++c->hclock;
+      c->H = e.H;
+      c->dham = e.dev;
+      return TC_OK;
+    }
+  }
+  tc_circuit::HamEntry ent;
   std::string err;
-  if (!build_hamiltonian(c->n, c->N, c->k_ham, structures, weights, T, H, err))
+  if (!build_hamiltonian(c->n, c->N, c->k_ham, structures, weights, T, ent.H, err))
     return fail(err.find("flips more") != std::string::npos ? TC_E_UNSUPPORTED : TC_E_INVALID, err);
-  c->dham.release();
-  cudaError_t e = c->dham.upload(H);
+  cudaError_t e = ent.dev.upload(ent.H);
   if (e != cudaSuccess) {
-    c->h_T = -1;
+    ent.dev.release();
     return cuda_fail(e, "hamiltonian upload");
   }
-  c->H = H;
-  c->h_struct.assign(structures, structures + ns);
-  c->h_w.assign(weights, weights + T);
-  c->h_T = T;
+  ent.st.assign(structures, structures + ns);
+  ent.w.assign(weights, weights + T);
+  ent.T = T;
+  ent.used = ++c->hclock;
+  constexpr size_t kMaxCached = 8;
+  if (c->hcache.size() >= kMaxCached) {
+    // evict the least recently used entry (its device arrays are no longer referenced)
+    size_t lru = 0;
+    for (size_t i = 1; i < c->hcache.size(); ++i)
+      if (c->hcache[i].used < c->hcache[lru].used) lru = i;
+    c->hcache[lru].dev.release();
+    c->hcache.erase(c->hcache.begin() + lru);
+  }
+  c->hcache.push_back(std::move(ent));
+  c->H = c->hcache.back().H;
+  c->dham = c->hcache.back().dev;
   return TC_OK;
 }
 
@@ -447,6 +464,12 @@ tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, const ui
     TC_CHECK_CUDA(launch_plain_term(is_dbl(c), d_states_work, c->N, B, f, sm, ny & 3, weights[t], d_energy_out, s),
                   "plain term");
   }
+  return TC_OK;
+}
+
+tc_status tc_mean_stderr(const double* d_x, int n, double* d_out, void* stream) {
+  if (!d_x || !d_out || n < 1) return fail(TC_E_INVALID, "NULL argument or n < 1");
+  TC_CHECK_CUDA(launch_mean_stderr(d_x, n, d_out, (cudaStream_t)stream), "mean/stderr");
   return TC_OK;
 }
 

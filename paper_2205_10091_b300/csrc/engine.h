@@ -73,12 +73,19 @@ struct tc_circuit {
   int* d_csr_off = nullptr;
   int* d_csr_slots = nullptr;
 
-  // Hamiltonian cache (last compiled Pauli sum)
-  std::vector<uint8_t> h_struct;
-  std::vector<double> h_w;
-  int h_T = -1;
-  tcb::HamPlan H;
-  tcb::DevHam dham;
+  // Hamiltonian cache: the most recently used compiled Pauli sums
+  struct HamEntry {
+    std::vector<uint8_t> st;
+    std::vector<double> w;
+    int T = -1;
+    tcb::HamPlan H;
+    tcb::DevHam dev;
+    uint64_t used = 0;
+  };
+  std::vector<HamEntry> hcache;
+  uint64_t hclock = 0;
+  tcb::HamPlan H;     // the selected entry's plan (host copy)
+  tcb::DevHam dham;   // the selected entry's device arrays (owned by hcache)
 
   // scratch workspace
   void* ws = nullptr;

@@ -471,7 +471,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
       if (in.kind == IK_CNOT || in.kind == IK_MAT4) P.flags |= PF_FULL;
       if (in.kind == IK_DIAG || in.kind == IK_GRADDIAG) {
         const DevDiag& dg = A.diags[P.diag_off + in.slot];
-        if (dg.n_ent != 1 || dg.sign_mode) P.flags |= PF_FULL;
+        if (dg.n_ent != 1 || (dg.sign_mode && in.kind == IK_GRADDIAG)) P.flags |= PF_FULL;
       }
     }
     P.n_mats = (int)A.mats.size() - P.mat_off;

@@ -449,6 +449,38 @@ __device__ __forceinline__ void mat4_dispatch(V (&A)[1 << RB], int j0, int j1, c
 #undef TC_M4
 }
 
+// Mean and standard error (sample std, ddof = 1, over sqrt(n)) of n doubles,
+// FP64, fixed-order reduction (one block).
+__global__ void __launch_bounds__(256) k_mean_stderr(const double* x, int n, double* out) {
+  __shared__ double s1[256], s2[256];
+  double a = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += x[i];
+  s1[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s1[threadIdx.x] += s1[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double mean = s1[0] / n;
+  double b = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) b += (x[i] - mean) * (x[i] - mean);
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s2[threadIdx.x] += s2[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = mean;
+    out[1] = n > 1 ? sqrt(s2[0] / (n - 1) / n) : 0.0;
+  }
+}
+
+cudaError_t launch_mean_stderr(const double* x, int n, double* out, cudaStream_t s) {
+  k_mean_stderr<<<1, 256, 0, s>>>(x, n, out);
+  return cudaGetLastError();
+}
+
 // Warp reduction in the working precision, then FP64 (T -> double).
 template <typename S>
 __device__ __forceinline__ double warp_sum(S v) {
@@ -734,6 +766,21 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
               const V ph = tab[dg.tab + __popc(v)];
               A[i] = cmul(ph, A[i]);
               if (MODE == KM_BWD) L[i] = cmul(ph, L[i]);
+            }
+            break;
+          }
+          if (dg.n_ent == 1) {
+            // CZ-type (AND) group: per-amplitude index in Gray-code order
+            const DevDiagEnt en = des[dg.ent_off];
+            uint32_t x = m.g;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              if (j) x ^= m.ro[low_bit(j)];
+              const int i = j ^ (j >> 1);
+              if (__popc(x & (x >> en.d) & en.mask) & 1) {
+                A[i] = mk<V>(-A[i].x, -A[i].y);
+                if (MODE == KM_BWD) L[i] = mk<V>(-L[i].x, -L[i].y);
+              }
             }
             break;
           }

@@ -71,6 +71,9 @@ cudaError_t launch_pad_states(bool dbl, const void* src, void* dst, int n_user, 
 cudaError_t launch_plain_term(bool dbl, const void* psi, int N, int rows, uint32_t f, uint32_t sm, int ny,
                               double w, double* e_acc, cudaStream_t s);
 
+// Mean and standard error of n doubles into out[0], out[1].
+cudaError_t launch_mean_stderr(const double* x, int n, double* out, cudaStream_t s);
+
 // Optional event timing of every launch (enabled by tc_profile_begin).
 enum ProfKind : int { PK_FWD = 0, PK_BWD = 1, PK_HAM = 2, PK_FINALIZE = 3, PK_PAD = 4, PK_PLAIN = 5, PK_TABLES = 6, PK_COUNT = 7 };
 void prof_begin();

@@ -110,6 +110,7 @@ SIGNATURES = {
     "tc_tn_info": (C.c_int, [C.c_void_p, C.POINTER(tc_path_info)]),
     "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_tn_destroy": (None, [C.c_void_p]),
+    "tc_mean_stderr": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tc_profile_begin": (C.c_int, []),
     "tc_profile_end": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "tc_last_error": (C.c_char_p, []),
@@ -160,6 +161,16 @@ def profile_end() -> dict:
     _check(lib().tc_profile_end(arr, 16, C.byref(n)))
     return {KERNEL_KINDS[arr[i].kind]: {"launches": arr[i].launches, "ms": arr[i].total_ms,
                                         "algo_bytes": arr[i].algo_bytes} for i in range(min(n.value, 16))}
+
+
+def mean_stderr(x, out=None, stream=None):
+    """(mean, standard error) of a CUDA float64 vector, computed on the device."""
+    import torch
+
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device="cuda")
+    _check(lib().tc_mean_stderr(_ptr(x), x.numel(), _ptr(out), _stream(stream)))
+    return out
 
 
 class Hamiltonian:
