@@ -338,6 +338,73 @@ TC_API tc_status tc_tn_info(const tc_tn* t, tc_path_info* out);
 TC_API tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out, void* stream);
 TC_API void tc_tn_destroy(tc_tn* t);
 
+/*
+ * Serving loop (continuous batching of circuit-evaluation requests).
+ *
+ * A request is one energy + gradient evaluation: an op list, its parameters
+ * and a Pauli sum (the arguments of tc_expect_grad with B = 1; complex64).
+ * tc_submit queues it and returns at once.  A scheduler thread admits queued
+ * requests in arrival order whenever a stream slot and enough of the memory
+ * budget are free; each admitted request takes one stream-ordered block from
+ * the server's own memory pool (plan, Pauli sum, parameters, two states,
+ * outputs) and runs on its own CUDA stream, so requests that arrive while
+ * others run overlap with them on the device.  The block returns to the pool
+ * when the request completes and the next request is admitted.  A request's
+ * arithmetic is exactly tc_expect_grad's: its result does not depend on what
+ * else is in flight.  The paper has no serving layer; this realises the
+ * batched evaluation of Section "Batched VQE" for a stream of independent
+ * circuits.
+ *
+ * Errors: a malformed request is refused by tc_submit (TC_E_INVALID); a full
+ * queue returns TC_E_BUSY; a request larger than the whole budget completes
+ * with TC_E_NOMEM; one that waited longer than timeout_ms before admission
+ * completes with TC_E_TIMEOUT; tc_cancel removes a request not yet admitted
+ * (TC_E_CANCELLED).  tc_poll returns TC_E_BUSY while a request is pending or
+ * running, and TC_OK with its result (whose `status` may be an error) once it
+ * is done; the id is then released.
+ */
+typedef struct tc_server tc_server;
+typedef struct {
+  int64_t mem_budget_bytes; /* device memory for in-flight requests (0 = 8 GiB) */
+  int32_t max_inflight;     /* concurrent requests = CUDA streams (0 = 16, at most 256) */
+  int32_t max_queue;        /* queued requests before tc_submit returns TC_E_BUSY (0 = unbounded) */
+  int32_t timeout_ms;       /* queued longer than this -> TC_E_TIMEOUT (0 = never) */
+  int32_t start_paused;     /* 1 = admit nothing (and touch no GPU) until tc_server_resume */
+  int32_t reserved[6];
+} tc_server_options;
+typedef struct {
+  int32_t n_qubits;
+  int32_t init;     /* tc_init */
+  int32_t n_ops;
+  int32_t n_params; /* at most 256 */
+  int32_t n_pool;
+  int32_t T;        /* Pauli terms */
+  const tc_op* ops;               /* host, copied */
+  const double* pool;             /* host [2*n_pool], copied (may be NULL) */
+  const double* theta;            /* host [n_params], copied */
+  const uint8_t* structures;      /* host [T][n_qubits], copied */
+  const double* weights;          /* host [T], copied */
+} tc_request;
+typedef struct {
+  uint64_t id;
+  int32_t status;   /* tc_status of the evaluation */
+  int32_t n_params;
+  double energy;
+  double t_submit, t_start, t_done; /* seconds on the host steady clock */
+} tc_result;
+typedef struct {
+  int64_t submitted, completed, cancelled, timed_out, failed, rejected;
+  int32_t pending, inflight, peak_inflight, pad;
+  int64_t bytes_in_use, peak_bytes;
+} tc_server_stats;
+TC_API tc_status tc_server_create(const tc_server_options* opt, tc_server** out);
+TC_API tc_status tc_submit(tc_server* s, const tc_request* req, uint64_t* id_out);
+TC_API tc_status tc_poll(tc_server* s, uint64_t id, tc_result* out, double* grad_out, int max_params);
+TC_API tc_status tc_cancel(tc_server* s, uint64_t id);
+TC_API tc_status tc_server_resume(tc_server* s);
+TC_API tc_status tc_server_get_stats(tc_server* s, tc_server_stats* out);
+TC_API tc_status tc_server_destroy(tc_server* s);
+
 /* Thread-local message describing the last non-TC_OK status. */
 TC_API const char* tc_last_error(void);
 

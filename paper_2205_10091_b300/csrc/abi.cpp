@@ -60,7 +60,7 @@ cudaError_t DevHam::upload(const HamPlan& H) {
 using namespace tcb;
 
 tc_circuit::~tc_circuit() {
-  if (uploaded) {
+  if (uploaded && !external_dev) {
     dplan.release();
     dplain.release();
     for (auto& e : hcache) e.dev.release();
@@ -206,6 +206,119 @@ tc_status run_ham(tc_circuit* c, KArgs a, int rows, bool store_lambda, cudaStrea
 }
 
 }  // namespace
+
+namespace tcb {
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t grad_row_bytes(const tc_circuit* c) {
+  const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
+  const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
+  const size_t tiles_b = (size_t)1 << (c->N - c->k_bwd);
+  const size_t tf = (size_t)c->fwd.table_total * amp_bytes(c), tb = (size_t)c->bwd.table_total * amp_bytes(c);
+  return 2 * per + (size_t)c->H.passes.size() * tiles_h * 8 + (size_t)std::max(c->bwd.n_gslots, 1) * tiles_b * 8 + tf +
+         tb + 64;
+}
+
+size_t grad_ws_bytes(const tc_circuit* c, int chunk) {
+  const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
+  const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
+  const size_t tiles_b = (size_t)1 << (c->N - c->k_bwd);
+  const size_t tf = (size_t)c->fwd.table_total * amp_bytes(c), tb = (size_t)c->bwd.table_total * amp_bytes(c);
+  return 2 * al256(per * chunk) + al256((size_t)chunk * c->H.passes.size() * tiles_h * 8) +
+         al256((size_t)chunk * std::max(c->bwd.n_gslots, 1) * tiles_b * 8) + al256(tf * chunk) + al256(tb * chunk);
+}
+
+tc_status expect_grad_run(tc_circuit* c, const double* d_params, int B, uint64_t seed, double* d_energy_out,
+                          double* d_grad_out, int chunk, char* w, cudaStream_t s) {
+  const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
+  const int nh = (int)c->H.passes.size();
+  const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
+  const size_t tiles_b = (size_t)1 << (c->N - c->k_bwd);
+  const int G = c->bwd.n_gslots;
+  const size_t tf = (size_t)c->fwd.table_total * amp_bytes(c);
+  const size_t o_lam = al256(per * chunk);
+  const size_t o_ep = o_lam + al256(per * chunk);
+  const size_t o_gp = o_ep + al256((size_t)chunk * nh * tiles_h * 8);
+  const size_t o_tf = o_gp + al256((size_t)chunk * std::max(G, 1) * tiles_b * 8);
+  const size_t o_tb = o_tf + al256(tf * chunk);
+  tc_status st;
+  for (int r0 = 0; r0 < B; r0 += chunk) {
+    const int rows = std::min(chunk, B - r0);
+    KArgs a = base_args(c, c->dplan);
+    a.psi = w;
+    a.lam = w + o_lam;
+    a.epart = (double*)(w + o_ep);
+    a.gpart = (double*)(w + o_gp);
+    a.gslots_total = G;
+    a.theta = d_params ? d_params + (size_t)r0 * c->n_params : nullptr;
+    a.seed = seed;
+    a.row_offset = r0;
+    if ((st = run_schedule(c, KM_FWD, c->fwd, c->A, a, w + o_tf, rows, s)) != TC_OK) return st;
+    if ((st = run_ham(c, a, rows, true, s)) != TC_OK) return st;
+    if ((st = run_schedule(c, KM_BWD, c->bwd, c->A, a, w + o_tb, rows, s)) != TC_OK) return st;
+    TC_CHECK_CUDA(launch_finalize(a.epart, nh, (int)tiles_h, a.gpart, G, (int)tiles_b, c->d_csr_off,
+                                  c->d_csr_slots, c->n_params, rows, d_energy_out + r0,
+                                  c->n_params ? d_grad_out + (size_t)r0 * c->n_params : nullptr, s),
+                  "finalize");
+  }
+  return TC_OK;
+}
+
+// ---- plan arrays in caller-provided device memory (serving loop) -----------
+template <typename T>
+static void place(std::vector<std::pair<const void*, size_t>>& cp, char*& cur, const std::vector<T>& v, T** dst) {
+  *dst = v.empty() ? nullptr : (T*)cur;
+  if (!v.empty()) cp.push_back({v.data(), v.size() * sizeof(T)});
+  cur += al256(v.size() * sizeof(T));
+}
+
+size_t plan_dev_bytes(const tc_circuit* c) {
+  const PlanArrays& A = c->A;
+  return al256(A.passes.size() * sizeof(DevPass)) + al256(A.stages.size() * sizeof(DevStage)) +
+         al256(A.instrs.size() * sizeof(DevInstr)) + al256(A.mats.size() * sizeof(DevMat)) +
+         al256(A.diags.size() * sizeof(DevDiag)) + al256(A.dents.size() * sizeof(DevDiagEnt)) +
+         al256(c->pool.size() * 8) + al256(c->csr_off.size() * 4) + al256(c->csr_slots.size() * 4);
+}
+
+size_t ham_dev_bytes(const HamPlan& H) {
+  return al256(H.passes.size() * sizeof(DevPass)) + al256(H.hdiag.size() * sizeof(DevHDiag)) +
+         al256(H.hterms.size() * sizeof(DevHTerm)) + al256(H.hflips.size() * sizeof(DevHFlip));
+}
+
+tc_status place_plan_and_ham(tc_circuit* c, const HamPlan& H, char* base, cudaStream_t s) {
+  std::vector<std::pair<const void*, size_t>> cp;
+  std::vector<char*> dst;
+  char* cur = base;
+  auto rec = [&](auto& v, auto** d) {
+    char* at = cur;
+    place(cp, cur, v, d);
+    if (!v.empty()) dst.push_back(at);
+  };
+  const PlanArrays& A = c->A;
+  rec(A.passes, &c->dplan.passes);
+  rec(A.stages, &c->dplan.stages);
+  rec(A.instrs, &c->dplan.instrs);
+  rec(A.mats, &c->dplan.mats);
+  rec(A.diags, &c->dplan.diags);
+  rec(A.dents, &c->dplan.dents);
+  rec(c->pool, &c->d_pool);
+  rec(c->csr_off, &c->d_csr_off);
+  rec(c->csr_slots, &c->d_csr_slots);
+  c->H = H;
+  rec(c->H.passes, &c->dham.passes);
+  rec(c->H.hdiag, &c->dham.hdiag);
+  rec(c->H.hterms, &c->dham.hterms);
+  rec(c->H.hflips, &c->dham.hflips);
+  for (size_t i = 0; i < cp.size(); ++i)
+    TC_CHECK_CUDA(cudaMemcpyAsync(dst[i], cp[i].first, cp[i].second, cudaMemcpyHostToDevice, s), "plan copy");
+  c->uploaded = true;
+  c->external_dev = true;
+  cudaGetDevice(&c->device);
+  return TC_OK;
+}
+
+}  // namespace tcb
 
 extern "C" {
 
@@ -381,47 +494,12 @@ tc_status tc_expect_grad(tc_circuit* c, const double* d_params, int B, const uin
   tc_status st = ensure_device(c);
   if (st != TC_OK) return st;
   if ((st = ensure_ham(c, structures, weights, T)) != TC_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
-  const int nh = (int)c->H.passes.size();
-  const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
-  const size_t tiles_b = (size_t)1 << (c->N - c->k_bwd);
-  const int G = c->bwd.n_gslots;
-  const size_t tf = (size_t)c->fwd.table_total * amp_bytes(c), tb = (size_t)c->bwd.table_total * amp_bytes(c);
-  const size_t row_bytes = 2 * per + (size_t)nh * tiles_h * 8 + (size_t)G * tiles_b * 8 + tf + tb + 64;
-  int64_t cap = budget(c) / (int64_t)row_bytes;
+  int64_t cap = budget(c) / (int64_t)grad_row_bytes(c);
   if (gopt && gopt->max_rows > 0) cap = std::min<int64_t>(cap, gopt->max_rows);
   if (cap < 1) return fail(TC_E_NOMEM, "one row of states does not fit the memory budget");
   const int chunk = (int)std::min<int64_t>(B, cap);
-  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t o_lam = al(per * chunk);
-  const size_t o_ep = o_lam + al(per * chunk);
-  const size_t o_gp = o_ep + al((size_t)chunk * nh * tiles_h * 8);
-  const size_t o_tf = o_gp + al((size_t)chunk * std::max(G, 1) * tiles_b * 8);
-  const size_t o_tb = o_tf + al(tf * chunk);
-  const size_t need = o_tb + al(tb * chunk);
-  if ((st = ensure_ws(c, need)) != TC_OK) return st;
-  char* w = (char*)c->ws;
-  for (int r0 = 0; r0 < B; r0 += chunk) {
-    const int rows = std::min(chunk, B - r0);
-    KArgs a = base_args(c, c->dplan);
-    a.psi = w;
-    a.lam = w + o_lam;
-    a.epart = (double*)(w + o_ep);
-    a.gpart = (double*)(w + o_gp);
-    a.gslots_total = G;
-    a.theta = d_params ? d_params + (size_t)r0 * c->n_params : nullptr;
-    a.seed = seed;
-    a.row_offset = r0;
-    if ((st = run_schedule(c, KM_FWD, c->fwd, c->A, a, w + o_tf, rows, s)) != TC_OK) return st;
-    if ((st = run_ham(c, a, rows, true, s)) != TC_OK) return st;
-    if ((st = run_schedule(c, KM_BWD, c->bwd, c->A, a, w + o_tb, rows, s)) != TC_OK) return st;
-    TC_CHECK_CUDA(launch_finalize(a.epart, nh, (int)tiles_h, a.gpart, G, (int)tiles_b, c->d_csr_off,
-                                  c->d_csr_slots, c->n_params, rows, d_energy_out + r0,
-                                  c->n_params ? d_grad_out + (size_t)r0 * c->n_params : nullptr, s),
-                  "finalize");
-  }
-  return TC_OK;
+  if ((st = ensure_ws(c, grad_ws_bytes(c, chunk))) != TC_OK) return st;
+  return expect_grad_run(c, d_params, B, seed, d_energy_out, d_grad_out, chunk, (char*)c->ws, (cudaStream_t)stream);
 }
 
 tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, const uint8_t* structures,

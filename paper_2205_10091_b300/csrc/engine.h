@@ -47,6 +47,21 @@ struct DevHam {
 
 }  // namespace tcb
 
+struct tc_circuit;
+
+namespace tcb {
+// Workspace of tc_expect_grad per row / for `chunk` rows, and its body with a
+// caller-provided workspace (used by the serving loop).
+size_t grad_row_bytes(const tc_circuit* c);
+size_t grad_ws_bytes(const tc_circuit* c, int chunk);
+tc_status expect_grad_run(tc_circuit* c, const double* d_params, int B, uint64_t seed, double* d_energy_out,
+                          double* d_grad_out, int chunk, char* ws, cudaStream_t s);
+// Plan + compiled Pauli sum placed in caller-provided device memory.
+size_t plan_dev_bytes(const tc_circuit* c);
+size_t ham_dev_bytes(const HamPlan& H);
+tc_status place_plan_and_ham(tc_circuit* c, const HamPlan& H, char* base, cudaStream_t s);
+}  // namespace tcb
+
 struct tc_circuit {
   int n = 0, N = 0;
   tc_dtype dtype = TC_C64;
@@ -67,6 +82,7 @@ struct tc_circuit {
 
   // device state (uploaded on first compute call)
   bool uploaded = false;
+  bool external_dev = false;  // plan arrays live in caller-owned memory (serving loop)
   int device = -1;
   tcb::DevPlan dplan, dplain;
   double* d_pool = nullptr;

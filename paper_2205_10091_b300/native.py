@@ -78,6 +78,29 @@ class tc_path_info(C.Structure):
                 ("cone_hi", C.c_int32), ("n_inputs", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
+class tc_server_options(C.Structure):
+    _fields_ = [("mem_budget_bytes", C.c_int64), ("max_inflight", C.c_int32), ("max_queue", C.c_int32),
+                ("timeout_ms", C.c_int32), ("start_paused", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
+class tc_request(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("init", C.c_int32), ("n_ops", C.c_int32), ("n_params", C.c_int32),
+                ("n_pool", C.c_int32), ("T", C.c_int32), ("ops", C.c_void_p), ("pool", C.c_void_p),
+                ("theta", C.c_void_p), ("structures", C.c_void_p), ("weights", C.c_void_p)]
+
+
+class tc_result(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int32), ("n_params", C.c_int32), ("energy", C.c_double),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
+class tc_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("cancelled", C.c_int64),
+                ("timed_out", C.c_int64), ("failed", C.c_int64), ("rejected", C.c_int64), ("pending", C.c_int32),
+                ("inflight", C.c_int32), ("peak_inflight", C.c_int32), ("pad", C.c_int32),
+                ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64)]
+
+
 class tc_kernel_stat(C.Structure):
     _fields_ = [("kind", C.c_int32), ("launches", C.c_int32), ("total_ms", C.c_double), ("algo_bytes", C.c_double)]
 
@@ -111,6 +134,13 @@ SIGNATURES = {
     "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_tn_destroy": (None, [C.c_void_p]),
     "tc_mean_stderr": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "tc_server_create": (C.c_int, [C.POINTER(tc_server_options), C.POINTER(C.c_void_p)]),
+    "tc_submit": (C.c_int, [C.c_void_p, C.POINTER(tc_request), C.POINTER(C.c_uint64)]),
+    "tc_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(tc_result), C.c_void_p, C.c_int]),
+    "tc_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "tc_server_resume": (C.c_int, [C.c_void_p]),
+    "tc_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(tc_server_stats)]),
+    "tc_server_destroy": (C.c_int, [C.c_void_p]),
     "tc_profile_begin": (C.c_int, []),
     "tc_profile_end": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "tc_last_error": (C.c_char_p, []),
@@ -308,3 +338,71 @@ class LightCone:
             out = torch.empty((B, 2), dtype=torch.float64, device="cuda")
         _check(lib().tc_contract_path(self.h, B, _ptr(d_gates), _ptr(out), _stream(stream)))
         return out
+
+
+class Server:
+    """Continuous-batching request server (tc_server_*)."""
+
+    def __init__(self, mem_budget_bytes: int = 0, max_inflight: int = 0, max_queue: int = 0, timeout_ms: int = 0,
+                 start_paused: bool = False):
+        o = tc_server_options(mem_budget_bytes, max_inflight, max_queue, timeout_ms, int(start_paused))
+        h = C.c_void_p()
+        _check(lib().tc_server_create(C.byref(o), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().tc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
+
+    def submit(self, circ: W.Circuit, theta, ham: W.PauliSum) -> int:
+        ops = np.ascontiguousarray(circ.ops, dtype=W.OP_DTYPE)
+        pool = np.ascontiguousarray(np.stack([circ.pool.real, circ.pool.imag], -1).ravel(), dtype=np.float64)
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).ravel())
+        st = np.ascontiguousarray(ham.structures, dtype=np.uint8)
+        w = np.ascontiguousarray(ham.weights, dtype=np.float64)
+        req = tc_request(circ.n, circ.init, len(ops), circ.n_params, len(circ.pool), len(w),
+                         ops.ctypes.data, pool.ctypes.data if len(circ.pool) else None, th.ctypes.data,
+                         st.ctypes.data, w.ctypes.data)
+        rid = C.c_uint64()
+        _check(lib().tc_submit(self.h, C.byref(req), C.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int, max_params: int = 256):
+        """None while pending/running, else a dict (the id is then released)."""
+        r = tc_result()
+        g = np.zeros(max_params)
+        st = lib().tc_poll(self.h, C.c_uint64(rid), C.byref(r), g.ctypes.data_as(C.c_void_p), max_params)
+        if st == TC_E_BUSY:
+            return None
+        _check(st)
+        return {"id": r.id, "status": r.status, "energy": r.energy, "grad": g[:r.n_params].copy(),
+                "t_submit": r.t_submit, "t_start": r.t_start, "t_done": r.t_done,
+                "error": None if r.status == TC_OK else lib().tc_last_error().decode()}
+
+    def cancel(self, rid: int):
+        _check(lib().tc_cancel(self.h, C.c_uint64(rid)))
+
+    def resume(self):
+        _check(lib().tc_server_resume(self.h))
+
+    def stats(self) -> dict:
+        o = tc_server_stats()
+        _check(lib().tc_server_get_stats(self.h, C.byref(o)))
+        return {f: getattr(o, f) for f, _ in tc_server_stats._fields_ if f != "pad"}
+
+    def wait(self, rid: int, timeout_s: float = 60.0, sleep_s: float = 0.0002):
+        import time
+
+        t0 = time.monotonic()
+        while True:
+            r = self.poll(rid)
+            if r is not None:
+                return r
+            if time.monotonic() - t0 > timeout_s:
+                raise TimeoutError(f"request {rid} not done after {timeout_s} s")
+            time.sleep(sleep_s)
