@@ -284,13 +284,7 @@ def run_gpu(args):
     kname, kst = top
     achieved = kst["algo_bytes"] / (kst["ms"] / 1e3) / 1e9
     hbm = float(peaks["hbm_gbs"])
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tj = json.load(f)
-        if tj.get("kernel") == kname and tj.get("source_hash") == _source_hash():
-            traffic = tj.get("bytes_per_launch")
+    traffic = _traffic(kname)
     launches = sum(v["launches"] for v in prof.values())
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -312,12 +306,155 @@ def run_gpu(args):
                        "ms_per_eval": plain_ms, "what": "unfused: one HBM sweep per gate, one per Pauli term"},
         "clocks": clk,
     }
+    if world == 1 and not args.no_extra:
+        out["workloads"] = extra_workloads()
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(circ, theta, ham)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# ---------------------------------------------------------------------------
+# the other hot-path workloads (bounded, rank 0 at N=1)
+# ---------------------------------------------------------------------------
+def _time_cuda(fn, reps: int, warm: int = 3) -> float:
+    """Mean ms per call of fn() on the current stream (CUDA events)."""
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extra_workloads(serve_rates=(250.0, 500.0), serve_seconds: float = 2.0) -> dict:
+    import time
+
+    import torch
+
+    from paper_2205_10091_b300 import native as nt
+
+    out = {}
+    # ---- HEA-10, complex128: one circuit, state + two observables ----------
+    circ, theta, obs = W.hea10_workload()
+    c = nt.Circuit(circ, dtype=nt.TC_C128)
+    d_th = torch.as_tensor(theta, device="cuda")
+    st = torch.empty((1, 1 << 10), dtype=torch.complex128, device="cuda")
+    Hs = [nt.Hamiltonian(o) for o in obs]
+    e_out = [torch.empty(1, dtype=torch.float64, device="cuda") for _ in Hs]
+
+    def one():
+        c.apply(d_th, 1, out=st)
+        for H, e in zip(Hs, e_out):
+            c.expect(st, H, out=e)
+
+    ms1 = _time_cuda(one, 200)
+    Bb = 65536
+    d_thb = torch.as_tensor(np.tile(theta, (Bb, 1)), device="cuda")
+    stb = torch.empty((Bb, 1 << 10), dtype=torch.complex128, device="cuda")
+    msb = _time_cuda(lambda: c.apply(d_thb, Bb, out=stb), 5, warm=2)
+    out["hea10_c128"] = {"us_per_circuit_state_and_2_observables": ms1 * 1e3,
+                         "batched_states_per_s": Bb / (msb / 1e3), "batch": Bb,
+                         "zz01": float(e_out[0].item()), "x5": float(e_out[1].item())}
+    del stb, d_thb
+    # ---- light-cone TN, 200-qubit brickwork depth 8, <Z99 Z100> -----------
+    n, gates, zq = W.brick200_workload()
+    lc = nt.LightCone(n, [(a, b) for a, b, _ in gates], zq)
+    g1 = torch.as_tensor(np.stack([u for (_, _, u) in gates])[None].astype(np.complex64), device="cuda")
+    o1 = torch.empty((1, 2), dtype=torch.float64, device="cuda")
+    ms_tn = _time_cuda(lambda: lc.contract(g1, out=o1), 200)
+    Bt = 1024
+    gb = torch.as_tensor(np.stack([np.stack([u for (_, _, u) in W.brickwork_u4(n, 8, np.random.default_rng(s))])
+                                   for s in range(Bt)]).astype(np.complex64), device="cuda")
+    ob = torch.empty((Bt, 2), dtype=torch.float64, device="cuda")
+    ms_tnb = _time_cuda(lambda: lc.contract(gb, out=ob), 20)
+    info = lc.info()
+    out["brick200_lightcone_tn"] = {
+        "zz": float(o1[0, 0].item()), "us_per_contraction": ms_tn * 1e3,
+        "batched_contractions_per_s": Bt / (ms_tnb / 1e3), "batch_seeds": Bt,
+        "log10_flops": float(np.log10(info["flops"])), "log2_size": float(np.log2(info["size"])),
+        "log2_write": float(np.log2(info["write"])), "steps": info["n_steps"], "cone_gates": info["n_cone_gates"]}
+    del gb, ob
+    # ---- noisy 16-qubit trajectories ---------------------------------------
+    circ, n_traj, seed, obs = W.noisy16_workload()
+    c = nt.Circuit(circ)
+    sts = torch.empty((n_traj, 1 << 16), dtype=torch.complex64, device="cuda")
+    Hs = [nt.Hamiltonian(o) for o in obs]
+    vals = [torch.empty(n_traj, dtype=torch.float64, device="cuda") for _ in Hs]
+    ests = [torch.empty(2, dtype=torch.float64, device="cuda") for _ in Hs]
+
+    def traj():
+        c.apply(None, n_traj, seed=seed, out=sts)
+        for H, v, e in zip(Hs, vals, ests):
+            c.expect(sts, H, out=v)
+            nt.mean_stderr(v, out=e)
+
+    ms_tr = _time_cuda(traj, 5, warm=2)
+    out["noisy16_trajectories"] = {
+        "trajectories_per_s": n_traj / (ms_tr / 1e3), "ms_per_run": ms_tr, "trajectories": n_traj,
+        "z0": [float(x) for x in ests[0].tolist()], "sum_zz": [float(x) for x in ests[1].tolist()]}
+    del sts
+    torch.cuda.synchronize()
+    # ---- QAOA serving: Poisson arrivals, continuous admission ---------------
+    serv = {}
+    for rate in serve_rates:
+        reqs = W.qaoa_stream(rate_hz=rate, duration_s=serve_seconds)
+        prep = [(W.qaoa_circuit(r.n, r.edges, r.p), r.theta, W.zz_on_edges(r.n, r.edges), r.t_arrive)
+                for r in reqs]
+        srv = nt.Server(mem_budget_bytes=48 << 30, max_inflight=32)
+        for w in range(8, 27, 2):  # warm one request per width
+            for cc, th, hh, _ in [p for p in prep if p[0].n == w][:1]:
+                srv.wait(srv.submit(cc, th, hh), timeout_s=300)
+        t0 = time.monotonic()
+        ids = []
+        for cc, th, hh, ta in prep:
+            while time.monotonic() - t0 < ta:
+                pass
+            ids.append((srv.submit(cc, th, hh), ta))
+        lat, last = [], 0.0
+        for rid, ta in ids:
+            r = srv.wait(rid, timeout_s=600)
+            lat.append(r["t_done"] - (t0 + ta))
+            last = max(last, r["t_done"] - t0)
+        stt = srv.stats()
+        srv.close()
+        lat = np.asarray(lat)
+        serv[f"{rate:g}_per_s"] = {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                                  "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                                  "completed_per_s": len(lat) / last, "peak_inflight": stt["peak_inflight"]}
+    out["qaoa_serving"] = {"n_qubits": "8..26 (even)", "layers": "1..6", "arrivals": "Poisson",
+                           "seconds_per_rate": serve_seconds, "by_offered_rate": serv}
+    return out
+
+
+def _traffic(kernel: str):
+    """DRAM bytes per full-size launch of `kernel` from the committed ncu
+    summary (profiles/traffic_<kernel>.txt, 'key: value' lines), or None when
+    the kernel sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("source_hash") != _source_hash():
+        return None
+    try:
+        return float(kv["bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def _source_hash() -> str:
@@ -339,6 +476,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other hot-path workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
