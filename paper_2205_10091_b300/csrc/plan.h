@@ -42,7 +42,10 @@ enum : int8_t {
   IK_GRADY = 13,
   IK_RXM = 14,      // RX on several register bits: j0 = bit mask, entry of bit r = slot + rank of r in mask
   IK_RXM_ADJ = 15,  // adjoint of IK_RXM: all bits share gslot/gscale
+  IK_DIAG_ADJ = 16, // IK_GRADDIAG then IK_DIAG of the same group, fused
 };
+
+constexpr int kLocalSlots = 32;  // gradient slots a pass accumulates per thread before one reduction
 
 // Per-CTA table entries built from theta[b] at the start of a pass.
 enum : int8_t {
@@ -127,7 +130,8 @@ enum : int32_t {
   PF_INIT = 1,       // forward pass 0: synthesise the initial state instead of loading
   PF_LAM_LOAD = 2,   // Hamiltonian pass: accumulate into lambda (else start from 0)
   PF_LAM_STORE = 4,  // Hamiltonian pass: write lambda
-  PF_FULL = 8,       // the pass needs the full instruction set (CNOT, 4x4, multi-entry or CZ groups)
+  PF_FULL = 8,       // the pass needs the full instruction set (CNOT, 4x4, multi-entry groups)
+  PF_LEAN = 16,      // the pass needs more than rotation layers (RY, H, X, noise, 2x2, CZ groups)
 };
 
 struct DevPass {

@@ -400,16 +400,14 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
           if (!dg.sign_mode) A.mats.back().T = dg.T;
           const int di = (int)A.diags.size() - P.diag_off;
           A.diags.push_back(dg);
-          if (adjoint && !dg.sign_mode && g0.param >= 0) {
-            DevInstr gi = in;
-            gi.kind = IK_GRADDIAG;
-            gi.slot = di;
-            gi.gslot = (int16_t)slot_of(g0.param);
-            gi.gscale = (float)g0.scale;
-            A.instrs.push_back(gi);
-          }
           in.kind = IK_DIAG;
           in.slot = di;
+          if (adjoint && !dg.sign_mode && g0.param >= 0) {
+            // gradient of the group's parameter, then the group's inverse phases
+            in.kind = IK_DIAG_ADJ;
+            in.gslot = (int16_t)slot_of(g0.param);
+            in.gscale = (float)g0.scale;
+          }
           A.instrs.push_back(in);
           continue;
         }
@@ -469,9 +467,13 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
     for (int i = P.instr_off; i < (int)A.instrs.size(); ++i) {
       const DevInstr& in = A.instrs[i];
       if (in.kind == IK_CNOT || in.kind == IK_MAT4) P.flags |= PF_FULL;
-      if (in.kind == IK_DIAG || in.kind == IK_GRADDIAG) {
+      if (in.kind != IK_RX && in.kind != IK_RXM && in.kind != IK_RX_ADJ && in.kind != IK_RXM_ADJ &&
+          in.kind != IK_DIAG && in.kind != IK_DIAG_ADJ)
+        P.flags |= PF_LEAN;
+      if (in.kind == IK_DIAG || in.kind == IK_GRADDIAG || in.kind == IK_DIAG_ADJ) {
         const DevDiag& dg = A.diags[P.diag_off + in.slot];
-        if (dg.n_ent != 1 || (dg.sign_mode && in.kind == IK_GRADDIAG)) P.flags |= PF_FULL;
+        if (dg.n_ent != 1) P.flags |= PF_FULL;
+        if (dg.sign_mode) P.flags |= PF_LEAN;
       }
     }
     P.n_mats = (int)A.mats.size() - P.mat_off;

@@ -516,8 +516,15 @@ __device__ __forceinline__ int diag_count(uint32_t x, const DevDiag& dg, const D
   return c;
 }
 
-template <typename T, int MODE, int RB, bool FULL>
+// VAR selects the instruction set compiled into an instantiation (smaller
+// code and fewer live registers for simpler passes):
+//   0  rotation layers: RX, RX multi, their adjoint steps, single-entry ZZ/Z phase groups
+//   1  lean: every kind except CNOT, 4x4 and multi-entry diagonal groups
+//   2  full
+template <typename T, int MODE, int RB, int VAR>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __grid_constant__ KArgs a) {
+  constexpr bool FULL = VAR >= 2;
+  constexpr bool LEAN = VAR >= 1;
   using V = typename VT<T>::V;
   constexpr int R = 1 << RB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -647,15 +654,19 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
       for (int i = tid; i < sp.n_gslots * nwarps; i += blockDim.x) red[i] = 0.0;
   }
   const DevStage* st = a.stages + sp.stage_off;
-  T gacc = 0;
-  int cur_slot = -1;
-  auto flush = [&]() {
-    if (MODE != KM_BWD || cur_slot < 0) return;
-    T v = gacc;
+  // gradient partials: one per-thread accumulator per local slot (reduced
+  // once at the end of the pass); slots beyond kLocalSlots reduce at once
+  T gl[kLocalSlots];
+  if (MODE == KM_BWD)
+    for (int g = 0; g < sp.n_gslots && g < kLocalSlots; ++g) gl[g] = 0;
+  auto add_grad = [&](int slot, T v) {
+    if (slot < kLocalSlots) {
+      gl[slot] += v;
+      return;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[cur_slot * nwarps + warp] += (double)v;
-    gacc = 0;
+    if (lane == 0) red[slot * nwarps + warp] += (double)v;
   };
   int8_t S[RB];
 #pragma unroll
@@ -714,19 +725,23 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
           }
         } break;
         case IK_RY: {
+          if (!LEAN) break;
           const V cs = tab[in.slot];
           TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(A, cs)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(L, cs)));
         } break;
         case IK_H:
+          if (!LEAN) break;
           TC_DISPATCH_J(RB, in.j0, (g_h<RB, J>(A)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_h<RB, J>(L)));
           break;
         case IK_X:
+          if (!LEAN) break;
           TC_DISPATCH_J(RB, in.j0, (g_pauli<RB, J>(A, 1)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_pauli<RB, J>(L, 1)));
           break;
         case IK_PAULI: {
+          if (!LEAN) break;
           const int p = (int)tab[in.slot].x;
           if (p) {
             TC_DISPATCH_J(RB, in.j0, (g_pauli<RB, J>(A, p)));
@@ -734,6 +749,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
           }
         } break;
         case IK_MAT2:
+          if (!LEAN) break;
           TC_DISPATCH_J(RB, in.j0, (g_mat2<RB, J>(A, tab + in.slot)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_mat2<RB, J>(L, tab + in.slot)));
           break;
@@ -753,23 +769,21 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
           if (dg.n_ent == 1 && !dg.sign_mode) {
             // v(x) = op(x) & mask is linear over XOR: v(g ^ o_i) = v(g) ^ v(o_i)
             const DevDiagEnt en = des[dg.ent_off];
-            const uint32_t vg = diag_op(m.g, en, dg.sign_mode);
+            uint32_t v = diag_op(m.g, en, dg.sign_mode);
             uint32_t vr[RB];
 #pragma unroll
             for (int r = 0; r < RB; ++r) vr[r] = diag_op_lin(m.g, m.ro[r], en, dg.sign_mode);
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-              uint32_t v = vg;
-#pragma unroll
-              for (int r = 0; r < RB; ++r)
-                if ((i >> r) & 1) v ^= vr[r];
+            for (int j = 0; j < R; ++j) {
+              if (j) v ^= vr[low_bit(j)];
+              const int i = j ^ (j >> 1);
               const V ph = tab[dg.tab + __popc(v)];
               A[i] = cmul(ph, A[i]);
               if (MODE == KM_BWD) L[i] = cmul(ph, L[i]);
             }
             break;
           }
-          if (dg.n_ent == 1) {
+          if (dg.n_ent == 1 && LEAN) {
             // CZ-type (AND) group: per-amplitude index in Gray-code order
             const DevDiagEnt en = des[dg.ent_off];
             uint32_t x = m.g;
@@ -808,6 +822,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
         case IK_GRADY: {
           if (MODE != KM_BWD) break;
           T acc = 0;
+          if (!LEAN && in.kind != IK_RXM_ADJ && in.kind != IK_RX_ADJ) break;
           if (in.kind == IK_RXM_ADJ) {
             const uint32_t mask = (uint8_t)in.j0;
             if (mask == (1u << RB) - 1u) {
@@ -856,13 +871,42 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
               TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, false>(A, L, cs, upd)));
             }
           }
-          // consecutive contributions to one slot accumulate per thread and
-          // are reduced once per run (FP32 warp sum, FP64 across warps)
-          if (in.gslot != cur_slot) {
-            flush();
-            cur_slot = in.gslot;
+          add_grad(in.gslot, acc * (T)in.gscale);
+        } break;
+        case IK_DIAG_ADJ: {
+          if (MODE != KM_BWD) break;
+          const DevDiag dg = dgs[in.slot];
+          if (dg.n_ent == 1 && !dg.sign_mode) {
+            // gradient and inverse phase from one index count per amplitude
+            const DevDiagEnt en = des[dg.ent_off];
+            uint32_t v = diag_op(m.g, en, 0);
+            uint32_t vr[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) vr[r] = diag_op_lin(m.g, m.ro[r], en, 0);
+            T a2[2] = {0, 0};
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+              if (j) v ^= vr[low_bit(j)];
+              const int i = j ^ (j >> 1);
+              const int c = __popc(v);
+              a2[j & 1] = fma((T)(dg.T - 2 * c), fma(L[i].x, A[i].y, -L[i].y * A[i].x), a2[j & 1]);
+              const V ph = tab[dg.tab + c];
+              A[i] = cmul(ph, A[i]);
+              L[i] = cmul(ph, L[i]);
+            }
+            add_grad(in.gslot, (a2[0] + a2[1]) * (T)in.gscale);
+          } else if (FULL) {
+            T acc = 0;
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              const int c = diag_count(m.g | offg(m, i), dg, des);
+              acc += (T)(dg.T - 2 * c) * (L[i].x * A[i].y - L[i].y * A[i].x);
+              const V ph = tab[dg.tab + c];
+              A[i] = cmul(ph, A[i]);
+              L[i] = cmul(ph, L[i]);
+            }
+            add_grad(in.gslot, acc * (T)in.gscale);
           }
-          gacc = fma(acc, (T)in.gscale, gacc);
         } break;
         default:
           break;
@@ -872,7 +916,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
   store_regs<RB>(A, psi, m);
   if (MODE == KM_BWD) {
     store_regs<RB>(L, lam, m);
-    flush();
+    for (int g = 0; g < sp.n_gslots && g < kLocalSlots; ++g) {
+      T v = gl[g];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[g * nwarps + warp] += (double)v;
+    }
     __syncthreads();
     for (int g = tid; g < sp.n_gslots; g += blockDim.x) {
       double s = 0;
@@ -915,7 +964,7 @@ size_t pass_smem_bytes(int mode, bool dbl, const DevPass& p) {
   return b + 16;
 }
 
-template <typename T, int MODE, int RB, bool FULL>
+template <typename T, int MODE, int RB, int VAR>
 static cudaError_t launch_tf(const KArgs& a, const DevPass& hp, int rows, cudaStream_t s, size_t smem) {
   static int configured_max = -1;
   if (configured_max < 0) {
@@ -923,10 +972,10 @@ static cudaError_t launch_tf(const KArgs& a, const DevPass& hp, int rows, cudaSt
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_pass<T, MODE, RB, FULL>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_pass<T, MODE, RB, VAR>);
     if (e != cudaSuccess) return e;
     const int dyn = optin - (int)fa.sharedSizeBytes;
-    e = cudaFuncSetAttribute(k_pass<T, MODE, RB, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    e = cudaFuncSetAttribute(k_pass<T, MODE, RB, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
     configured_max = dyn;
   }
@@ -937,7 +986,7 @@ static cudaError_t launch_tf(const KArgs& a, const DevPass& hp, int rows, cudaSt
   const size_t blocks = (size_t)rows << hp.nfix;
   if (blocks == 0) return cudaSuccess;
   if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-  k_pass<T, MODE, RB, FULL><<<(unsigned)blocks, threads, smem, s>>>(a);
+  k_pass<T, MODE, RB, VAR><<<(unsigned)blocks, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -1020,8 +1069,10 @@ static double pass_bytes(int mode, bool dbl, const DevPass& hp, const KArgs& a, 
 
 template <typename T, int MODE, int RB>
 static cudaError_t launch_t(const KArgs& a, const DevPass& hp, int rows, cudaStream_t s, size_t smem) {
-  if (MODE != KM_HAM && (hp.flags & PF_FULL)) return launch_tf<T, MODE, RB, true>(a, hp, rows, s, smem);
-  return launch_tf<T, MODE, RB, false>(a, hp, rows, s, smem);
+  if (MODE == KM_HAM) return launch_tf<T, MODE, RB, 0>(a, hp, rows, s, smem);
+  if (hp.flags & PF_FULL) return launch_tf<T, MODE, RB, 2>(a, hp, rows, s, smem);
+  if (hp.flags & PF_LEAN) return launch_tf<T, MODE, RB, 1>(a, hp, rows, s, smem);
+  return launch_tf<T, MODE, RB, 0>(a, hp, rows, s, smem);
 }
 
 cudaError_t launch_pass(int mode, bool dbl, const KArgs& a, const DevPass& hp, int rows, cudaStream_t s) {
