@@ -115,7 +115,8 @@ typedef struct {
   int32_t tile_qubits_fwd;  /* qubits per shared-memory tile, forward (0 = default) */
   int32_t tile_qubits_bwd;  /* same for adjoint passes (0 = default) */
   int64_t mem_budget_bytes; /* scratch cap for tc_expect_grad (0 = 60% of free memory) */
-  int32_t reserved[8];
+  int32_t max_gates_per_pass; /* cap on non-diagonal gates fused into one pass (0 = default, <0 = none) */
+  int32_t reserved[7];
 } tc_options;
 
 /* Plan statistics, filled by tc_circuit_info. */

@@ -362,8 +362,14 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
   for (auto& g : c->gates)
     if (g.noise_event >= 0) c->n_noise++;
   c->pool.assign(pool, pool + 2 * (size_t)n_pool);
-  c->fwd = build_schedule(c->gates, c->N, c->k_fwd, kRBFwd, false, true, c->A);
-  c->bwd = build_schedule(c->gates, c->N, c->k_bwd, kRBBwd, true, false, c->A);
+  // cap on gates per pass: deep multi-layer passes need many register stages
+  // whose mixed register-bit sets conflict in shared memory
+  const int mg_f = c->opt.max_gates_per_pass > 0 ? c->opt.max_gates_per_pass
+                                                 : (c->opt.max_gates_per_pass < 0 ? 0 : kDefaultGateCapFactor * c->k_fwd);
+  const int mg_b = c->opt.max_gates_per_pass > 0 ? c->opt.max_gates_per_pass
+                                                 : (c->opt.max_gates_per_pass < 0 ? 0 : kDefaultGateCapFactor * c->k_bwd);
+  c->fwd = build_schedule(c->gates, c->N, c->k_fwd, kRBFwd, false, true, c->A, mg_f);
+  c->bwd = build_schedule(c->gates, c->N, c->k_bwd, kRBBwd, true, false, c->A, mg_b);
   // parameter -> gradient slots (CSR)
   c->csr_off.assign(n_params + 1, 0);
   for (int p : c->bwd.slot_param) c->csr_off[p + 1]++;

@@ -23,6 +23,7 @@ constexpr int kLaneBits = 5;    // lowest tile bits mapped to warp lanes
 constexpr int kMinQubits = kRBMax + kLaneBits;  // narrower circuits get idle low qubits
 constexpr int kMaxK = 14;
 constexpr int kMaxQubits = 30;
+constexpr int kDefaultGateCapFactor = 0;  // default gates-per-pass cap = factor x tile qubits (0 = none)
 
 // Instruction kinds executed on the register tile.
 enum : int8_t {

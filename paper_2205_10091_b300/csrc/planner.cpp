@@ -148,7 +148,7 @@ void merge_rx_runs(PlanArrays& A, int first, int rb, int table_base) {
 }  // namespace
 
 Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, bool adjoint, bool first_init,
-                        PlanArrays& A) {
+                        PlanArrays& A, int max_gates) {
   Schedule sc;
   sc.first_pass = (int)A.passes.size();
   sc.first_mat = (int)A.mats.size();
@@ -162,6 +162,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
   while (!remaining.empty() || (first && first_init)) {
     // ---- choose the pass's gates and tile -------------------------------
     uint32_t tile = low, blocked = 0;
+    int n_nondiag = 0;
     std::vector<int> taken, deferred;
     for (int gi : remaining) {
       const HGate& g = gates[gi];
@@ -176,9 +177,10 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
         continue;
       }
       const uint32_t need = g.kind == TC_OP_CNOT ? bit(g.p1) : touch;
-      if (popc(tile | need) <= k) {
+      if (popc(tile | need) <= k && (max_gates <= 0 || n_nondiag < max_gates)) {
         tile |= need;
         taken.push_back(gi);
+        ++n_nondiag;
       } else {
         deferred.push_back(gi);
         blocked |= touch;
@@ -507,10 +509,10 @@ Schedule build_plain_schedule(const std::vector<HGate>& gates, int N, PlanArrays
     sc.n_stages += s.n_stages;
   };
   // a gate-free pass that writes the initial state, then one pass per gate
-  absorb(build_schedule({}, N, kMinQubits, kRBFwd, false, true, A));
+  absorb(build_schedule({}, N, kMinQubits, kRBFwd, false, true, A, 0));
   for (size_t i = 0; i < gates.size(); ++i) {
     std::vector<HGate> one{gates[i]};
-    absorb(build_schedule(one, N, kMinQubits, kRBFwd, false, false, A));
+    absorb(build_schedule(one, N, kMinQubits, kRBFwd, false, false, A, 0));
   }
   sc.n_passes = (int)A.passes.size() - sc.first_pass;
   sc.n_mats = (int)A.mats.size() - sc.first_mat;

@@ -54,8 +54,9 @@ bool normalise_ops(int n_user, int n_internal, const tc_op* ops, int n_ops, int 
                    std::vector<HGate>& out, std::string& err);
 
 // Schedule gates (forward order, or reversed with adjoint=true) into passes.
+// max_gates: cap on non-diagonal gates per pass (<= 0: no cap).
 Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, bool adjoint, bool first_init,
-                        PlanArrays& A);
+                        PlanArrays& A, int max_gates);
 
 // Compile a Pauli sum (user structures) into Hamiltonian passes.
 bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, const double* weights, int T,
