@@ -361,6 +361,8 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
   }
   for (auto& g : c->gates)
     if (g.noise_event >= 0) c->n_noise++;
+  c->gates_orig = c->gates;
+  if (dtype == TC_C64) c->gates = rewrite_rx_frames(c->gates, c->N);
   c->pool.assign(pool, pool + 2 * (size_t)n_pool);
   // cap on gates per pass: deep multi-layer passes need many register stages
   // whose mixed register-bit sets conflict in shared memory
@@ -519,7 +521,7 @@ tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, const ui
   tc_status st = ensure_device(c);
   if (st != TC_OK) return st;
   if (!c->plain_built) {
-    c->plain = build_plain_schedule(c->gates, c->N, c->Ap);
+    c->plain = build_plain_schedule(c->gates_orig, c->N, c->Ap);
     cudaError_t e = c->dplain.upload(c->Ap);
     if (e != cudaSuccess) return cuda_fail(e, "plain plan upload");
     c->plain_built = true;

@@ -69,7 +69,8 @@ struct tc_circuit {
   int n_ops = 0, n_params = 0, n_noise = 0;
   tc_options opt{};
   int k_fwd = 0, k_bwd = 0, k_ham = 0;
-  std::vector<tcb::HGate> gates;
+  std::vector<tcb::HGate> gates;       // as planned (RX rewritten to framed RY for complex64)
+  std::vector<tcb::HGate> gates_orig;  // as given (the unfused baseline applies these)
   std::vector<double> pool;
 
   tcb::PlanArrays A;       // forward + adjoint schedules

@@ -44,6 +44,8 @@ enum : int8_t {
   IK_RXM = 14,      // RX on several register bits: j0 = bit mask, entry of bit r = slot + rank of r in mask
   IK_RXM_ADJ = 15,  // adjoint of IK_RXM: all bits share gslot/gscale
   IK_DIAG_ADJ = 16, // IK_GRADDIAG then IK_DIAG of the same group, fused
+  IK_RYM = 17,      // RY on several register bits (layout as IK_RXM)
+  IK_RYM_ADJ = 18,  // adjoint of IK_RYM
 };
 
 constexpr int kLocalSlots = 32;  // gradient slots a pass accumulates per thread before one reduction
@@ -58,6 +60,7 @@ enum : int8_t {
   MT_U2 = 5,      // 4x4 from pool (16 entries)
   MT_DIAGTAB = 6, // phases exp(-i s theta/2 (T - 2m)), m = 0..T  (T+1 entries)
   MT_NOISE = 7,   // 1 entry: selected Pauli code in .x
+  MT_QUARTER = 8, // quarter phases (i^{s m}), m = 0..T  (T+1 entries; s = +1 for S, -1 for S^dagger)
 };
 
 struct DevInstr {  // 16 bytes

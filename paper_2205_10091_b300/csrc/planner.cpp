@@ -66,6 +66,46 @@ bool normalise_ops(int n_user, int N, const tc_op* ops, int n_ops, int n_params,
   return true;
 }
 
+std::vector<HGate> rewrite_rx_frames(const std::vector<HGate>& gates, int N) {
+  std::vector<HGate> out;
+  std::vector<char> frame(N, 0);
+  auto sphase = [&](int p, double sign) {
+    HGate g;
+    g.kind = -1;
+    g.p0 = p;
+    g.diag = true;
+    g.quarter = true;
+    g.scale = sign;
+    out.push_back(g);
+  };
+  for (const HGate& g : gates) {
+    if (g.kind == TC_OP_RX) {
+      if (!frame[g.p0]) {
+        sphase(g.p0, +1.0);  // enter: S
+        frame[g.p0] = 1;
+      }
+      HGate r = g;
+      r.kind = TC_OP_RY;
+      out.push_back(r);
+      continue;
+    }
+    if (!g.diag) {
+      // CNOT commutes with S on its control; every other qubit it touches
+      // leaves the frame first
+      for (int p : {g.p0, g.p1}) {
+        if (p < 0 || !frame[p]) continue;
+        if (g.kind == TC_OP_CNOT && p == g.p0) continue;
+        sphase(p, -1.0);  // leave: S^dagger
+        frame[p] = 0;
+      }
+    }
+    out.push_back(g);
+  }
+  for (int p = 0; p < N; ++p)
+    if (frame[p]) sphase(p, -1.0);
+  return out;
+}
+
 namespace {
 
 struct Item {
@@ -98,7 +138,9 @@ void merge_rx_runs(PlanArrays& A, int first, int rb, int table_base) {
   int i = first;
   while (i < end) {
     const DevInstr& in0 = A.instrs[i];
-    const bool fwd = in0.kind == IK_RX, adj = in0.kind == IK_RX_ADJ;
+    const bool isy = in0.kind == IK_RY || in0.kind == IK_RY_ADJ;
+    const bool fwd = in0.kind == IK_RX || in0.kind == IK_RY, adj = in0.kind == IK_RX_ADJ || in0.kind == IK_RY_ADJ;
+    const int8_t mtype = isy ? MT_RY : MT_RX;
     if (!fwd && !adj) {
       out.push_back(in0);
       ++i;
@@ -127,14 +169,14 @@ void merge_rx_runs(PlanArrays& A, int first, int rb, int table_base) {
     for (size_t r = 0; r < bit_slot.size(); ++r) {
       const int old_local = bit_slot[r].second;
       for (int mi = (int)A.mats.size() - 1; mi >= 0; --mi)
-        if (A.mats[mi].type == MT_RX && A.mats[mi].dst == table_base + old_local) {
+        if (A.mats[mi].type == mtype && A.mats[mi].dst == table_base + old_local) {
           moves.push_back({mi, lo + (int)r});
           break;
         }
     }
     for (auto& mv : moves) A.mats[mv.first].dst = table_base + mv.second;
     DevInstr mi = in0;
-    mi.kind = fwd ? IK_RXM : IK_RXM_ADJ;
+    mi.kind = isy ? (fwd ? IK_RYM : IK_RYM_ADJ) : (fwd ? IK_RXM : IK_RXM_ADJ);
     mi.j0 = (int8_t)mask;
     mi.slot = lo;
     out.push_back(mi);
@@ -215,7 +257,8 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
     for (int gi : taken) {
       const HGate& g = gates[gi];
       if (g.diag) {
-        auto key = std::make_tuple((int)g.sign_mode, g.sign_mode ? -1 : g.param, g.sign_mode ? 0.0 : g.scale);
+        const int mode = g.sign_mode ? 1 : (g.quarter ? 2 : 0);
+        auto key = std::make_tuple(mode, mode == 0 ? g.param : -1, mode == 1 ? 0.0 : g.scale);
         auto itk = open.find(key);
         bool joined = false;
         if (itk != open.end()) {
@@ -398,13 +441,13 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
           }
           for (auto& e : ents) A.dents.push_back(e);
           dg.n_ent = (int)ents.size();
-          dg.tab = dg.sign_mode ? -1 : add_mat(MT_DIAGTAB, g0, dg.T + 1);
+          dg.tab = dg.sign_mode ? -1 : add_mat(g0.quarter ? MT_QUARTER : MT_DIAGTAB, g0, dg.T + 1);
           if (!dg.sign_mode) A.mats.back().T = dg.T;
           const int di = (int)A.diags.size() - P.diag_off;
           A.diags.push_back(dg);
           in.kind = IK_DIAG;
           in.slot = di;
-          if (adjoint && !dg.sign_mode && g0.param >= 0) {
+          if (adjoint && !dg.sign_mode && !g0.quarter && g0.param >= 0) {
             // gradient of the group's parameter, then the group's inverse phases
             in.kind = IK_DIAG_ADJ;
             in.gslot = (int16_t)slot_of(g0.param);
@@ -469,7 +512,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
     for (int i = P.instr_off; i < (int)A.instrs.size(); ++i) {
       const DevInstr& in = A.instrs[i];
       if (in.kind == IK_CNOT || in.kind == IK_MAT4) P.flags |= PF_FULL;
-      if (in.kind != IK_RX && in.kind != IK_RXM && in.kind != IK_RX_ADJ && in.kind != IK_RXM_ADJ &&
+      if (in.kind != IK_RY && in.kind != IK_RYM && in.kind != IK_RY_ADJ && in.kind != IK_RYM_ADJ &&
           in.kind != IK_DIAG && in.kind != IK_DIAG_ADJ)
         P.flags |= PF_LEAN;
       if (in.kind == IK_DIAG || in.kind == IK_GRADDIAG || in.kind == IK_DIAG_ADJ) {

@@ -20,7 +20,16 @@ struct HGate {
   double t1 = 0, t2 = 0, t3 = 0;
   bool diag = false;
   bool sign_mode = false;  // CZ
+  bool quarter = false;    // S (scale +1) or S^dagger (scale -1) on p0: phase i^{scale * bit}
 };
+
+// Rewrite every RX(a) as S^dagger RY(a) S (an exact identity).  The S phases
+// are diagonal, commute with every diagonal gate and cancel between two RX on
+// the same qubit, so each qubit carries a "frame" flag and S / S^dagger are
+// emitted only where a non-diagonal, non-RX gate needs the plain frame (and
+// at the end).  RY has real coefficients, which the kernels evaluate with
+// packed FP32x2 arithmetic.
+std::vector<HGate> rewrite_rx_frames(const std::vector<HGate>& gates, int N);
 
 struct PlanArrays {
   std::vector<DevPass> passes;

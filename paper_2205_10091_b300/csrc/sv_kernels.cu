@@ -138,6 +138,14 @@ __device__ void build_mat(const DevMat& m, V* tab, const double* th, const doubl
         t[j] = mk<V>((S)c, (S)s);
       }
     } break;
+    case MT_QUARTER: {
+      // i^{q m}: S (q = +1) or S^dagger (q = -1) on each member qubit with bit 1
+      const int q = (m.scale > 0 ? 1 : -1) * (m.adj ? -1 : 1);
+      for (int j = 0; j <= m.T; ++j) {
+        const int e = ((q * j) % 4 + 4) % 4;
+        t[j] = mk<V>((S)(e == 0 ? 1 : e == 2 ? -1 : 0), (S)(e == 1 ? 1 : e == 3 ? -1 : 0));
+      }
+    } break;
     case MT_NOISE: {
       const double u = noise_uniform(a, row, m.T);
       const int w = u < m.t1 ? 0 : u < m.t2 ? 1 : u < m.t3 ? 2 : 3;  // I, X, Y, Z
@@ -280,9 +288,42 @@ __device__ __forceinline__ void g_rx(V (&A)[1 << RB], V cs) {
     A[i | (1 << J)] = mk<V>(fma(c, x1.x, s * x0.y), fma(c, x1.y, -s * x0.x));
   }
 }
+// Packed FP32x2 arithmetic (sm_100+ fma/mul .f32x2 on a 64-bit register pair).
+__device__ __forceinline__ unsigned long long f2u(float2 v) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+  return r;
+}
+__device__ __forceinline__ float2 u2f(unsigned long long r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+  return u2f(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+  return u2f(d);
+}
+
 // RY: a0' = c a0 - s a1, a1' = s a0 + c a1
 template <int RB, int J, typename V>
 __device__ __forceinline__ void g_ry(V (&A)[1 << RB], V cs) {
+  if constexpr (sizeof(V) == 8) {
+    const float2 c2 = make_float2(cs.x, cs.x), s2 = make_float2(cs.y, cs.y), n2 = make_float2(-cs.y, -cs.y);
+#pragma unroll
+    for (int i = 0; i < (1 << RB); ++i) {
+      if (i & (1 << J)) continue;
+      const float2 x0 = A[i], x1 = A[i | (1 << J)];
+      A[i] = fma2(c2, x0, mul2(n2, x1));
+      A[i | (1 << J)] = fma2(c2, x1, mul2(s2, x0));
+    }
+    return;
+  }
   const auto c = cs.x, s = cs.y;
 #pragma unroll
   for (int i = 0; i < (1 << RB); ++i) {
@@ -396,6 +437,33 @@ __device__ __forceinline__ decltype(V::x) g_adj(V (&P)[1 << RB], V (&L)[1 << RB]
   }
   return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
+
+// Adjoint step of RY: sum over pairs of Im<lam|Y|psi> = (l1 . p0) - (l0 . p1)
+// in four scalar accumulators, then RY(-a) on psi and lam (the table holds the
+// adjoint's (c, s); packed FP32x2 for complex64).  Packing the accumulation
+// as well costs more registers than it saves issue slots.
+template <int RB, int J, typename V>
+__device__ __forceinline__ decltype(V::x) g_ry_adj(V (&P)[1 << RB], V (&L)[1 << RB], V cs) {
+  return g_adj<RB, J, false>(P, L, cs, true);
+}
+
+// RY on every register bit (entry of bit r at t[r]).
+template <int RB, int R0, typename V>
+struct RyAll {
+  __device__ __forceinline__ static void run(V (&A)[1 << RB], const V* t) {
+    g_ry<RB, R0>(A, t[R0]);
+    RyAll<RB, R0 + 1, V>::run(A, t);
+  }
+  __device__ __forceinline__ static decltype(V::x) adj(V (&P)[1 << RB], V (&L)[1 << RB], const V* t) {
+    const decltype(V::x) a = g_ry_adj<RB, R0>(P, L, t[R0]);
+    return a + RyAll<RB, R0 + 1, V>::adj(P, L, t);
+  }
+};
+template <int RB, typename V>
+struct RyAll<RB, RB, V> {
+  __device__ __forceinline__ static void run(V (&)[1 << RB], const V*) {}
+  __device__ __forceinline__ static decltype(V::x) adj(V (&)[1 << RB], V (&)[1 << RB], const V*) { return 0; }
+};
 
 // RX on every register bit (entry of bit r at t[r]), unrolled at compile time.
 template <int RB, int R0, typename V>
@@ -518,7 +586,7 @@ __device__ __forceinline__ int diag_count(uint32_t x, const DevDiag& dg, const D
 
 // VAR selects the instruction set compiled into an instantiation (smaller
 // code and fewer live registers for simpler passes):
-//   0  rotation layers: RX, RX multi, their adjoint steps, single-entry ZZ/Z phase groups
+//   0  rotation layers: RY, RY multi, their adjoint steps, single-entry ZZ/Z/S phase groups
 //   1  lean: every kind except CNOT, 4x4 and multi-entry diagonal groups
 //   2  full
 template <typename T, int MODE, int RB, int VAR>
@@ -705,11 +773,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
       const DevInstr in = ins[ds.instr_off + q];
       switch (in.kind) {
         case IK_RX: {
+          if (!LEAN) break;
           const V cs = tab[in.slot];
           TC_DISPATCH_J(RB, in.j0, (g_rx<RB, J>(A, cs)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_rx<RB, J>(L, cs)));
         } break;
         case IK_RXM: {
+          if (!LEAN) break;
           const uint32_t mask = (uint8_t)in.j0;
           if (mask == (1u << RB) - 1u) {
             RxAll<RB, 0, V>::run(A, tab + in.slot);
@@ -724,8 +794,22 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
             }
           }
         } break;
+        case IK_RYM: {
+          const uint32_t mask = (uint8_t)in.j0;
+          if (mask == (1u << RB) - 1u) {
+            RyAll<RB, 0, V>::run(A, tab + in.slot);
+            if (MODE == KM_BWD) RyAll<RB, 0, V>::run(L, tab + in.slot);
+          } else {
+            int e = 0;
+            for (int r = 0; r < RB; ++r) {
+              if (!((mask >> r) & 1u)) continue;
+              const V cs = tab[in.slot + e++];
+              TC_DISPATCH_J(RB, r, (g_ry<RB, J>(A, cs)));
+              if (MODE == KM_BWD) TC_DISPATCH_J(RB, r, (g_ry<RB, J>(L, cs)));
+            }
+          }
+        } break;
         case IK_RY: {
-          if (!LEAN) break;
           const V cs = tab[in.slot];
           TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(A, cs)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(L, cs)));
@@ -814,6 +898,24 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
             }
           }
         } break;
+        case IK_RYM_ADJ: {
+          if (MODE != KM_BWD) break;
+          const uint32_t mask = (uint8_t)in.j0;
+          T acc = 0;
+          if (mask == (1u << RB) - 1u) {
+            acc = RyAll<RB, 0, V>::adj(A, L, tab + in.slot);
+          } else {
+            int e = 0;
+            for (int r = 0; r < RB; ++r) {
+              if (!((mask >> r) & 1u)) continue;
+              const V cs = tab[in.slot + e++];
+              T part = 0;
+              TC_DISPATCH_J(RB, r, (part = g_ry_adj<RB, J>(A, L, cs)));
+              acc += part;
+            }
+          }
+          add_grad(in.gslot, acc * (T)in.gscale);
+        } break;
         case IK_RXM_ADJ:
         case IK_GRADDIAG:
         case IK_RX_ADJ:
@@ -822,7 +924,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
         case IK_GRADY: {
           if (MODE != KM_BWD) break;
           T acc = 0;
-          if (!LEAN && in.kind != IK_RXM_ADJ && in.kind != IK_RX_ADJ) break;
+          if (!LEAN && in.kind != IK_RY_ADJ) break;
           if (in.kind == IK_RXM_ADJ) {
             const uint32_t mask = (uint8_t)in.j0;
             if (mask == (1u << RB) - 1u) {
@@ -867,8 +969,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
             const V cs = upd ? tab[in.slot] : mk<V>((T)1, (T)0);
             if (in.kind == IK_RX_ADJ || in.kind == IK_GRADX) {
               TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, true>(A, L, cs, upd)));
+            } else if (upd) {
+              TC_DISPATCH_J(RB, in.j0, (acc = g_ry_adj<RB, J>(A, L, cs)));
             } else {
-              TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, false>(A, L, cs, upd)));
+              TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, false>(A, L, cs, false)));
             }
           }
           add_grad(in.gslot, acc * (T)in.gscale);
