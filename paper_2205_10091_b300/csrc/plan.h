@@ -135,7 +135,8 @@ enum : int32_t {
   PF_LAM_LOAD = 2,   // Hamiltonian pass: accumulate into lambda (else start from 0)
   PF_LAM_STORE = 4,  // Hamiltonian pass: write lambda
   PF_FULL = 8,       // the pass needs the full instruction set (CNOT, 4x4, multi-entry groups)
-  PF_LEAN = 16,      // the pass needs more than rotation layers (RY, H, X, noise, 2x2, CZ groups)
+  PF_LEAN = 16,      // the pass needs more than rotation layers (RX, H, X, noise, 2x2, CZ groups)
+  PF_MULTI = 32,     // the pass has an XOR-type diagonal group with several entries
 };
 
 struct DevPass {

@@ -517,7 +517,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
         P.flags |= PF_LEAN;
       if (in.kind == IK_DIAG || in.kind == IK_GRADDIAG || in.kind == IK_DIAG_ADJ) {
         const DevDiag& dg = A.diags[P.diag_off + in.slot];
-        if (dg.n_ent != 1) P.flags |= PF_FULL;
+        if (dg.n_ent != 1) P.flags |= dg.sign_mode ? PF_FULL : PF_MULTI;
         if (dg.sign_mode) P.flags |= PF_LEAN;
       }
     }

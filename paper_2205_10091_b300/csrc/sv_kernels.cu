@@ -573,6 +573,27 @@ __device__ __forceinline__ uint32_t diag_op_lin(uint32_t g, uint32_t o, const De
   return (en.d == 0 ? o : (o ^ (o >> en.d))) & en.mask;
 }
 
+// m(x) of an XOR-type diagonal group for every register amplitude: per entry
+// the count is popc(v(g) ^ v(o_i)), walked in Gray-code order.
+template <int RB>
+__device__ __forceinline__ void diag_counts_lin(int (&cnt)[1 << RB], const Map<RB>& m, const DevDiag& dg,
+                                                const DevDiagEnt* ents) {
+#pragma unroll
+  for (int i = 0; i < (1 << RB); ++i) cnt[i] = 0;
+  for (int e = 0; e < dg.n_ent; ++e) {
+    const DevDiagEnt en = ents[dg.ent_off + e];
+    uint32_t v = diag_op(m.g, en, 0);
+    uint32_t vr[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) vr[r] = diag_op_lin(m.g, m.ro[r], en, 0);
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) {
+      if (j) v ^= vr[low_bit(j)];
+      cnt[j ^ (j >> 1)] += __popc(v);
+    }
+  }
+}
+
 // m(x) of a diagonal group for one amplitude index
 __device__ __forceinline__ int diag_count(uint32_t x, const DevDiag& dg, const DevDiagEnt* ents) {
   int c = 0;
@@ -585,14 +606,17 @@ __device__ __forceinline__ int diag_count(uint32_t x, const DevDiag& dg, const D
 }
 
 // VAR selects the instruction set compiled into an instantiation (smaller
-// code and fewer live registers for simpler passes):
-//   0  rotation layers: RY, RY multi, their adjoint steps, single-entry ZZ/Z/S phase groups
-//   1  lean: every kind except CNOT, 4x4 and multi-entry diagonal groups
-//   2  full
+// code and fewer live registers for simpler passes); bit flags over the
+// rotation-layer core (RY, RY multi, their adjoint steps, single-entry
+// ZZ/Z/S phase groups):
+//   +1  lean: RX, H, X, noise outcomes, 2x2 matrices, CZ groups
+//   +2  full: CNOT, 4x4 matrices
+//   +4  multi-entry ZZ/Z phase groups (ZZ at several qubit distances)
 template <typename T, int MODE, int RB, int VAR>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __grid_constant__ KArgs a) {
-  constexpr bool FULL = VAR >= 2;
-  constexpr bool LEAN = VAR >= 1;
+  constexpr bool FULL = (VAR & 2) != 0;
+  constexpr bool LEAN = (VAR & 1) != 0;
+  constexpr bool MULTI = (VAR & 4) != 0;
   using V = typename VT<T>::V;
   constexpr int R = 1 << RB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -867,6 +891,18 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
             }
             break;
           }
+          if (MULTI && !dg.sign_mode) {
+            // several entries: per entry, the count is XOR-linear in the register offset
+            int cnt[R];
+            diag_counts_lin<RB>(cnt, m, dg, des);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              const V ph = tab[dg.tab + cnt[i]];
+              A[i] = cmul(ph, A[i]);
+              if (MODE == KM_BWD) L[i] = cmul(ph, L[i]);
+            }
+            break;
+          }
           if (dg.n_ent == 1 && LEAN) {
             // CZ-type (AND) group: per-amplitude index in Gray-code order
             const DevDiagEnt en = des[dg.ent_off];
@@ -995,6 +1031,18 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
               const int c = __popc(v);
               a2[j & 1] = fma((T)(dg.T - 2 * c), fma(L[i].x, A[i].y, -L[i].y * A[i].x), a2[j & 1]);
               const V ph = tab[dg.tab + c];
+              A[i] = cmul(ph, A[i]);
+              L[i] = cmul(ph, L[i]);
+            }
+            add_grad(in.gslot, (a2[0] + a2[1]) * (T)in.gscale);
+          } else if (MULTI && !dg.sign_mode) {
+            int cnt[R];
+            diag_counts_lin<RB>(cnt, m, dg, des);
+            T a2[2] = {0, 0};
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+              a2[i & 1] = fma((T)(dg.T - 2 * cnt[i]), fma(L[i].x, A[i].y, -L[i].y * A[i].x), a2[i & 1]);
+              const V ph = tab[dg.tab + cnt[i]];
               A[i] = cmul(ph, A[i]);
               L[i] = cmul(ph, L[i]);
             }
@@ -1174,8 +1222,10 @@ static double pass_bytes(int mode, bool dbl, const DevPass& hp, const KArgs& a, 
 template <typename T, int MODE, int RB>
 static cudaError_t launch_t(const KArgs& a, const DevPass& hp, int rows, cudaStream_t s, size_t smem) {
   if (MODE == KM_HAM) return launch_tf<T, MODE, RB, 0>(a, hp, rows, s, smem);
-  if (hp.flags & PF_FULL) return launch_tf<T, MODE, RB, 2>(a, hp, rows, s, smem);
-  if (hp.flags & PF_LEAN) return launch_tf<T, MODE, RB, 1>(a, hp, rows, s, smem);
+  const bool lean = hp.flags & PF_LEAN, full = hp.flags & PF_FULL, multi = hp.flags & PF_MULTI;
+  if (full || (lean && multi)) return launch_tf<T, MODE, RB, 7>(a, hp, rows, s, smem);
+  if (lean) return launch_tf<T, MODE, RB, 1>(a, hp, rows, s, smem);
+  if (multi) return launch_tf<T, MODE, RB, 4>(a, hp, rows, s, smem);
   return launch_tf<T, MODE, RB, 0>(a, hp, rows, s, smem);
 }
 
