@@ -72,6 +72,7 @@ struct tc_server {
   std::vector<cudaEvent_t> events;
   std::vector<double*> h_out;  // pinned, per slot: [energy, grad...]
   std::vector<char> slot_busy;
+  int n_high = 0;  // slots [0, n_high) use high-priority streams (small requests)
   cudaMemPool_t pool = nullptr;
   int64_t used = 0;
   tc_server_stats stats{};
@@ -81,6 +82,7 @@ struct tc_server {
 namespace {
 
 constexpr int kMaxParams = 256;
+constexpr int kSmallQubits = 20;
 
 tc_status gpu_init(tc_server* s) {
   if (s->gpu_ready) return TC_OK;
@@ -98,8 +100,14 @@ tc_status gpu_init(tc_server* s) {
   s->events.resize(slots);
   s->h_out.resize(slots);
   s->slot_busy.assign(slots, 0);
+  // the first half of the slots run on high-priority streams: small requests
+  // placed there are not held back by the thread blocks of large ones
+  int lo_prio = 0, hi_prio = 0;
+  cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+  s->n_high = slots / 2;
   for (int i = 0; i < slots; ++i) {
-    if ((e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking)) != cudaSuccess)
+    if ((e = cudaStreamCreateWithPriority(&s->streams[i], cudaStreamNonBlocking, i < s->n_high ? hi_prio : lo_prio)) !=
+        cudaSuccess)
       return cuda_fail(e, "stream");
     if ((e = cudaEventCreateWithFlags(&s->events[i], cudaEventDisableTiming)) != cudaSuccess)
       return cuda_fail(e, "event");
@@ -125,14 +133,17 @@ void finish(tc_server* s, const std::shared_ptr<Req>& r, tc_status st, const std
 // Returns false if it does not fit right now.
 bool try_admit(tc_server* s, std::unique_lock<std::mutex>& lk) {
   if (s->pending.empty()) return false;
+  std::shared_ptr<Req> r = s->pending.front();
+  // small requests (two states of at most 2^20 amplitudes) prefer the
+  // high-priority slots and may use any; large ones use the others
+  const bool small = r->n <= kSmallQubits;
   int slot = -1;
-  for (int i = 0; i < (int)s->slot_busy.size(); ++i)
+  for (int i = small ? 0 : s->n_high; i < (int)s->slot_busy.size(); ++i)
     if (!s->slot_busy[i]) {
       slot = i;
       break;
     }
   if (slot < 0) return false;
-  std::shared_ptr<Req> r = s->pending.front();
   // plan on the host (no device memory yet)
   tc_circuit* c = nullptr;
   tc_status st = tc_circuit_create(r->n, TC_C64, (tc_init)r->init, r->ops.data(), (int)r->ops.size(), r->n_params,
