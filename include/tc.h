@@ -167,7 +167,8 @@ TC_API tc_status tc_circuit_info(const tc_circuit* c, tc_plan_info* out);
  *                 complex of the circuit's dtype (a batch of input states,
  *                 Section "Batched input states")
  *   seed          Philox4x32-10 key for noise events when d_status is NULL:
- *                 event e of row b uses counter (e/4, row_offset+b, 0, 0),
+ *                 event e of trajectory t = row_offset + b uses counter
+ *                 (e/4, t mod 2^32, t / 2^32, 0),
  *                 key (seed mod 2^32, seed / 2^32), output word e % 4, and
  *                 u = (word >> 8) * 2^-24
  *   d_status      NULL, or device [B][n_noise] floats in [0, 1): the uniform
