@@ -103,11 +103,30 @@ struct DevDiagEnt {
   uint32_t mask;
 };
 
-struct DevStage {
+// A run of consecutive thread-index (or tile-index) bits [b, b + len) that
+// lands on consecutive tile bits [j, j + len) at consecutive global positions
+// [p, p + len): the thread -> amplitude map of a stage is a few shift/mask
+// steps, one per run.
+struct DevRun {
+  uint8_t b, len, j, p;
+};
+
+struct DevStage {    // 72 bytes
   int8_t S[8];       // register tile bits (first RB used)
+  int8_t P[8];       // their global positions
+  DevRun run[10];    // thread-index bits -> tile bits / global positions
+  int32_t n_runs;
   int32_t n_instr;
   int32_t instr_off; // relative to the pass's first instruction
+  int32_t pad;
 };
+
+// The kernels carve these out of shared memory back to back, ahead of a
+// double-precision reduction buffer: every size keeps 8-byte alignment.
+static_assert(sizeof(DevInstr) == 16, "DevInstr layout");
+static_assert(sizeof(DevStage) == 72, "DevStage layout");
+static_assert(sizeof(DevDiag) % 8 == 0, "DevDiag layout");
+static_assert(sizeof(DevDiagEnt) == 8, "DevDiagEnt layout");
 
 // Pauli-sum terms, compiled per Hamiltonian.
 //  Diagonal terms: value(x) = w * (cnt - 2 popc((x ^ (x >> d)) & mask)) when cnt >= 0
@@ -145,6 +164,8 @@ struct DevPass {
   int32_t rb;           // register bits of this pass's kernel
   uint8_t pos[32];      // tile bit -> global position
   uint8_t fixpos[32];   // fixed (per-tile) bits -> global position, ascending
+  DevRun fixrun[32];    // the same map as runs (b = CTA tile-index bit, p = position; j unused)
+  int32_t n_fixruns;
   int32_t n_stages, stage_off;
   int32_t n_instr, instr_off;  // all instructions of the pass (contiguous)
   int32_t n_mats, mat_off;

@@ -106,6 +106,44 @@ std::vector<HGate> rewrite_rx_frames(const std::vector<HGate>& gates, int N) {
   return out;
 }
 
+// Thread -> amplitude runs of a stage (see DevRun), and the CTA -> fixed bits runs of a pass.
+void fill_stage_runs(const DevPass& P, int rb, DevStage& ds) {
+  uint32_t smask = 0;
+  for (int r = 0; r < rb; ++r) {
+    smask |= 1u << ds.S[r];
+    ds.P[r] = (int8_t)P.pos[ds.S[r]];
+  }
+  int b = 0;
+  ds.n_runs = 0;
+  for (int j = 0; j < P.k; ++j) {
+    if ((smask >> j) & 1u) continue;
+    if (ds.n_runs > 0) {
+      DevRun& u = ds.run[ds.n_runs - 1];
+      if (u.b + u.len == b && u.j + u.len == j && u.p + u.len == P.pos[j]) {
+        ++u.len;
+        ++b;
+        continue;
+      }
+    }
+    ds.run[ds.n_runs++] = DevRun{(uint8_t)b, 1, (uint8_t)j, P.pos[j]};
+    ++b;
+  }
+}
+
+void fill_fix_runs(DevPass& P) {
+  P.n_fixruns = 0;
+  for (int f = 0; f < P.nfix; ++f) {
+    if (P.n_fixruns > 0) {
+      DevRun& u = P.fixrun[P.n_fixruns - 1];
+      if (u.b + u.len == f && u.p + u.len == P.fixpos[f]) {
+        ++u.len;
+        continue;
+      }
+    }
+    P.fixrun[P.n_fixruns++] = DevRun{(uint8_t)f, 1, 0, P.fixpos[f]};
+  }
+}
+
 namespace {
 
 struct Item {
@@ -247,6 +285,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
         }
       }
     }
+    fill_fix_runs(P);
     P.flags = (first && first_init && !adjoint) ? PF_INIT : 0;
 
     // ---- items: non-diagonal gates, and diagonal groups ------------------
@@ -406,6 +445,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
             jof[j] = r++;
           }
       }
+      fill_stage_runs(P, rb, ds);
       ds.instr_off = (int)A.instrs.size() - P.instr_off;
       for (int ii : st.second) {
         const Item& it = items[ii];
@@ -666,6 +706,7 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
         }
       }
     }
+    fill_fix_runs(P);
     P.flags = first ? PF_LAM_STORE : (PF_LAM_LOAD | PF_LAM_STORE);
     if (first) {
       P.hdiag_off = (int)H.hdiag.size();

@@ -191,6 +191,27 @@ __device__ __forceinline__ Map<RB> make_map(const DevPass& P, const int8_t* S, u
   return m;
 }
 
+// Map of a gate-pass stage from its precomputed runs (a few shifts per run).
+template <int RB>
+__device__ __forceinline__ Map<RB> stage_map(const DevStage& st, uint32_t tid, uint32_t base) {
+  Map<RB> m;
+  m.g = base;
+  m.t = 0;
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    m.ro[r] = 1u << st.P[r];
+    m.rt[r] = 1u << st.S[r];
+  }
+  const int n = st.n_runs;
+  for (int q = 0; q < n; ++q) {
+    const DevRun u = st.run[q];
+    const uint32_t v = (tid >> u.b) & ((1u << u.len) - 1u);
+    m.t |= v << u.j;
+    m.g |= v << u.p;
+  }
+  return m;
+}
+
 template <int RB>
 __device__ __forceinline__ uint32_t offg(const Map<RB>& m, int i) {
   uint32_t o = 0;
@@ -288,27 +309,9 @@ __device__ __forceinline__ void g_rx(V (&A)[1 << RB], V cs) {
     A[i | (1 << J)] = mk<V>(fma(c, x1.x, s * x0.y), fma(c, x1.y, -s * x0.x));
   }
 }
-// Packed FP32x2 arithmetic (sm_100+ fma/mul .f32x2 on a 64-bit register pair).
-__device__ __forceinline__ unsigned long long f2u(float2 v) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
-  return r;
-}
-__device__ __forceinline__ float2 u2f(unsigned long long r) {
-  float2 v;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-  return v;
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
-  return u2f(d);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
-  return u2f(d);
-}
+// Packed FP32x2 arithmetic (sm_100+ FFMA2/FMUL2 on a 64-bit register pair).
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 
 // RY: a0' = c a0 - s a1, a1' = s a0 + c a1
 template <int RB, int J, typename V>
@@ -447,41 +450,70 @@ __device__ __forceinline__ decltype(V::x) g_ry_adj(V (&P)[1 << RB], V (&L)[1 << 
   return g_adj<RB, J, false>(P, L, cs, true);
 }
 
-// RY on every register bit (entry of bit r at t[r]).
-template <int RB, int R0, typename V>
-struct RyAll {
+// Rotations on the register bits of a compile-time mask (entry of bit r at
+// t[rank of r in the mask]); AdjM returns the summed gradient terms.
+template <int RB, int MASK, bool ISX, int R0 = 0, int E = 0>
+struct RotM {
+  template <typename V>
   __device__ __forceinline__ static void run(V (&A)[1 << RB], const V* t) {
-    g_ry<RB, R0>(A, t[R0]);
-    RyAll<RB, R0 + 1, V>::run(A, t);
+    if constexpr (R0 < RB) {
+      if constexpr (((MASK >> R0) & 1) != 0) {
+        if constexpr (ISX) g_rx<RB, R0>(A, t[E]);
+        else g_ry<RB, R0>(A, t[E]);
+        RotM<RB, MASK, ISX, R0 + 1, E + 1>::run(A, t);
+      } else {
+        RotM<RB, MASK, ISX, R0 + 1, E>::run(A, t);
+      }
+    }
   }
+  template <typename V>
   __device__ __forceinline__ static decltype(V::x) adj(V (&P)[1 << RB], V (&L)[1 << RB], const V* t) {
-    const decltype(V::x) a = g_ry_adj<RB, R0>(P, L, t[R0]);
-    return a + RyAll<RB, R0 + 1, V>::adj(P, L, t);
+    if constexpr (R0 < RB) {
+      if constexpr (((MASK >> R0) & 1) != 0) {
+        const decltype(V::x) a = g_adj<RB, R0, ISX>(P, L, t[E], true);
+        return a + RotM<RB, MASK, ISX, R0 + 1, E + 1>::adj(P, L, t);
+      } else {
+        return RotM<RB, MASK, ISX, R0 + 1, E>::adj(P, L, t);
+      }
+    } else {
+      return 0;
+    }
   }
-};
-template <int RB, typename V>
-struct RyAll<RB, RB, V> {
-  __device__ __forceinline__ static void run(V (&)[1 << RB], const V*) {}
-  __device__ __forceinline__ static decltype(V::x) adj(V (&)[1 << RB], V (&)[1 << RB], const V*) { return 0; }
 };
 
-// RX on every register bit (entry of bit r at t[r]), unrolled at compile time.
-template <int RB, int R0, typename V>
-struct RxAll {
-  __device__ __forceinline__ static void run(V (&A)[1 << RB], const V* t) {
-    g_rx<RB, R0>(A, t[R0]);
-    RxAll<RB, R0 + 1, V>::run(A, t);
+// Jump-table dispatch of a runtime mask to its compile-time instantiation.
+#define TC_MASK_CASES(X) \
+  X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) \
+  X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31)
+
+template <int RB, bool ISX, typename V>
+__device__ __forceinline__ void rot_mask(int mask, V (&A)[1 << RB], const V* t) {
+  switch (mask) {
+#define TC_ROT_CASE(M) \
+  case M:              \
+    if constexpr ((M) < (1 << RB)) RotM<RB, (M), ISX>::run(A, t); \
+    break;
+    TC_MASK_CASES(TC_ROT_CASE)
+#undef TC_ROT_CASE
+    default:
+      break;
   }
-  __device__ __forceinline__ static decltype(V::x) adj(V (&P)[1 << RB], V (&L)[1 << RB], const V* t) {
-    const decltype(V::x) a = g_adj<RB, R0, true>(P, L, t[R0], true);
-    return a + RxAll<RB, R0 + 1, V>::adj(P, L, t);
+}
+template <int RB, bool ISX, typename V>
+__device__ __forceinline__ decltype(V::x) rot_mask_adj(int mask, V (&P)[1 << RB], V (&L)[1 << RB], const V* t) {
+  decltype(V::x) acc = 0;
+  switch (mask) {
+#define TC_ADJ_CASE(M) \
+  case M:              \
+    if constexpr ((M) < (1 << RB)) acc = RotM<RB, (M), ISX>::adj(P, L, t); \
+    break;
+    TC_MASK_CASES(TC_ADJ_CASE)
+#undef TC_ADJ_CASE
+    default:
+      break;
   }
-};
-template <int RB, typename V>
-struct RxAll<RB, RB, V> {
-  __device__ __forceinline__ static void run(V (&)[1 << RB], const V*) {}
-  __device__ __forceinline__ static decltype(V::x) adj(V (&)[1 << RB], V (&)[1 << RB], const V*) { return 0; }
-};
+  return acc;
+}
 
 // switch helpers: run F<J>() for the runtime register bit j
 #define TC_DISPATCH_J(RB, j, CALL)         \
@@ -631,8 +663,10 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
   const int row = (int)(blockIdx.x >> sp.nfix);
   const uint32_t tile = blockIdx.x & ((1u << sp.nfix) - 1u);
   uint32_t base = 0;
-  for (int f = 0; f < sp.nfix; ++f)
-    if ((tile >> f) & 1u) base |= 1u << sp.fixpos[f];
+  for (int q = 0; q < sp.n_fixruns; ++q) {
+    const DevRun u = sp.fixrun[q];
+    base |= ((tile >> u.b) & ((1u << u.len) - 1u)) << u.p;
+  }
   const size_t soff = (size_t)row << a.N;
   V* psi = (V*)a.psi + soff;
   V* lam = a.lam ? (V*)a.lam + soff : nullptr;
@@ -643,7 +677,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
   V* sm1 = sm0 + tsize;
   V* tab = sm0 + (MODE == KM_BWD ? 2 * tsize : tsize);
   DevInstr* ins = (DevInstr*)(tab + ((sp.table_size + 1) & ~1));
-  DevDiag* dgs = (DevDiag*)(ins + sp.n_instr);
+  DevStage* sst = (DevStage*)(ins + sp.n_instr);
+  DevDiag* dgs = (DevDiag*)(sst + (MODE == KM_HAM ? 0 : sp.n_stages));
   DevDiagEnt* des = (DevDiagEnt*)(dgs + sp.n_diag);
   double* red = (double*)(des + ((sp.n_dent + 1) & ~1));
 
@@ -740,12 +775,17 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
     const V* trow = (const V*)a.tables + (size_t)row * a.table_stride + sp.table_off;
     for (int i = tid; i < sp.table_size; i += blockDim.x) tab[i] = trow[i];
     for (int i = tid; i < sp.n_instr; i += blockDim.x) ins[i] = a.instrs[sp.instr_off + i];
+    {
+      const uint32_t* src = (const uint32_t*)(a.stages + sp.stage_off);
+      uint32_t* dst = (uint32_t*)sst;
+      const int words = sp.n_stages * (int)(sizeof(DevStage) / 4);
+      for (int i = tid; i < words; i += blockDim.x) dst[i] = src[i];
+    }
     for (int i = tid; i < sp.n_diag; i += blockDim.x) dgs[i] = a.diags[sp.diag_off + i];
     for (int i = tid; i < sp.n_dent; i += blockDim.x) des[i] = a.dents[sp.dent_off + i];
     if (MODE == KM_BWD)
       for (int i = tid; i < sp.n_gslots * nwarps; i += blockDim.x) red[i] = 0.0;
   }
-  const DevStage* st = a.stages + sp.stage_off;
   // gradient partials: one per-thread accumulator per local slot (reduced
   // once at the end of the pass); slots beyond kLocalSlots reduce at once
   T gl[kLocalSlots];
@@ -760,10 +800,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[slot * nwarps + warp] += (double)v;
   };
-  int8_t S[RB];
-#pragma unroll
-  for (int r = 0; r < RB; ++r) S[r] = st[0].S[r];
-  Map<RB> m = make_map<RB>(sp, S, tid, base);
+  // stage 0's map straight from global memory, so that the state loads are
+  // in flight while the per-CTA tables are being staged
+  Map<RB> m = stage_map<RB>(a.stages[sp.stage_off], tid, base);
   if (MODE == KM_FWD && (sp.flags & PF_INIT) && a.synth_init) {
     if (a.init == 1) {
       const uint32_t anc = (1u << (a.N - a.n_user)) - 1u;
@@ -778,23 +817,21 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
     load_regs<RB>(A, psi, m);
     if (MODE == KM_BWD) load_regs<RB>(L, lam, m);
   }
-  __syncthreads();  // table, instructions and groups ready
+  __syncthreads();  // table, instructions, stages and groups ready
 
   for (int s = 0; s < sp.n_stages; ++s) {
-    const DevStage ds = st[s];
+    const int n_instr = sst[s].n_instr, instr_off = sst[s].instr_off;
     if (s > 0) {
       smem_write<RB>(A, sm0, m);
       if (MODE == KM_BWD) smem_write<RB>(L, sm1, m);
-#pragma unroll
-      for (int r = 0; r < RB; ++r) S[r] = ds.S[r];
-      m = make_map<RB>(sp, S, tid, base);
+      m = stage_map<RB>(sst[s], tid, base);
       __syncthreads();
       smem_read<RB>(A, sm0, m);
       if (MODE == KM_BWD) smem_read<RB>(L, sm1, m);
       __syncthreads();
     }
-    for (int q = 0; q < ds.n_instr; ++q) {
-      const DevInstr in = ins[ds.instr_off + q];
+    for (int q = 0; q < n_instr; ++q) {
+      const DevInstr in = ins[instr_off + q];
       switch (in.kind) {
         case IK_RX: {
           if (!LEAN) break;
@@ -805,33 +842,17 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
         case IK_RXM: {
           if (!LEAN) break;
           const uint32_t mask = (uint8_t)in.j0;
-          if (mask == (1u << RB) - 1u) {
-            RxAll<RB, 0, V>::run(A, tab + in.slot);
-            if (MODE == KM_BWD) RxAll<RB, 0, V>::run(L, tab + in.slot);
-          } else {
-            int e = 0;
-            for (int r = 0; r < RB; ++r) {
-              if (!((mask >> r) & 1u)) continue;
-              const V cs = tab[in.slot + e++];
-              TC_DISPATCH_J(RB, r, (g_rx<RB, J>(A, cs)));
-              if (MODE == KM_BWD) TC_DISPATCH_J(RB, r, (g_rx<RB, J>(L, cs)));
-            }
+          int e = 0;
+          for (int r = 0; r < RB; ++r) {
+            if (!((mask >> r) & 1u)) continue;
+            const V cs = tab[in.slot + e++];
+            TC_DISPATCH_J(RB, r, (g_rx<RB, J>(A, cs)));
+            if (MODE == KM_BWD) TC_DISPATCH_J(RB, r, (g_rx<RB, J>(L, cs)));
           }
         } break;
         case IK_RYM: {
-          const uint32_t mask = (uint8_t)in.j0;
-          if (mask == (1u << RB) - 1u) {
-            RyAll<RB, 0, V>::run(A, tab + in.slot);
-            if (MODE == KM_BWD) RyAll<RB, 0, V>::run(L, tab + in.slot);
-          } else {
-            int e = 0;
-            for (int r = 0; r < RB; ++r) {
-              if (!((mask >> r) & 1u)) continue;
-              const V cs = tab[in.slot + e++];
-              TC_DISPATCH_J(RB, r, (g_ry<RB, J>(A, cs)));
-              if (MODE == KM_BWD) TC_DISPATCH_J(RB, r, (g_ry<RB, J>(L, cs)));
-            }
-          }
+          rot_mask<RB, false>((uint8_t)in.j0, A, tab + in.slot);
+          if (MODE == KM_BWD) rot_mask<RB, false>((uint8_t)in.j0, L, tab + in.slot);
         } break;
         case IK_RY: {
           const V cs = tab[in.slot];
@@ -936,20 +957,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
         } break;
         case IK_RYM_ADJ: {
           if (MODE != KM_BWD) break;
-          const uint32_t mask = (uint8_t)in.j0;
-          T acc = 0;
-          if (mask == (1u << RB) - 1u) {
-            acc = RyAll<RB, 0, V>::adj(A, L, tab + in.slot);
-          } else {
-            int e = 0;
-            for (int r = 0; r < RB; ++r) {
-              if (!((mask >> r) & 1u)) continue;
-              const V cs = tab[in.slot + e++];
-              T part = 0;
-              TC_DISPATCH_J(RB, r, (part = g_ry_adj<RB, J>(A, L, cs)));
-              acc += part;
-            }
-          }
+          const T acc = rot_mask_adj<RB, false>((uint8_t)in.j0, A, L, tab + in.slot);
           add_grad(in.gslot, acc * (T)in.gscale);
         } break;
         case IK_RXM_ADJ:
@@ -963,17 +971,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __
           if (!LEAN && in.kind != IK_RY_ADJ) break;
           if (in.kind == IK_RXM_ADJ) {
             const uint32_t mask = (uint8_t)in.j0;
-            if (mask == (1u << RB) - 1u) {
-              acc = RxAll<RB, 0, V>::adj(A, L, tab + in.slot);
-            } else {
-              int e = 0;
-              for (int r = 0; r < RB; ++r) {
-                if (!((mask >> r) & 1u)) continue;
-                const V cs = tab[in.slot + e++];
-                T part = 0;
-                TC_DISPATCH_J(RB, r, (part = g_adj<RB, J, true>(A, L, cs, true)));
-                acc += part;
-              }
+            int e = 0;
+            for (int r = 0; r < RB; ++r) {
+              if (!((mask >> r) & 1u)) continue;
+              const V cs = tab[in.slot + e++];
+              T part = 0;
+              TC_DISPATCH_J(RB, r, (part = g_adj<RB, J, true>(A, L, cs, true)));
+              acc += part;
             }
           } else if (in.kind == IK_GRADDIAG) {
             const DevDiag dg = dgs[in.slot];
@@ -1110,6 +1114,7 @@ size_t pass_smem_bytes(int mode, bool dbl, const DevPass& p) {
   size_t b = tsize * v * (mode == KM_BWD ? 2 : 1);
   b += (size_t)((p.table_size + 1) & ~1) * v;
   b += (size_t)p.n_instr * sizeof(DevInstr) + (size_t)p.n_diag * sizeof(DevDiag);
+  if (mode != KM_HAM) b += (size_t)p.n_stages * sizeof(DevStage);
   b += (size_t)((p.n_dent + 1) & ~1) * sizeof(DevDiagEnt);
   if (mode == KM_BWD) b += (size_t)p.n_gslots * nwarps * 8;
   if (mode == KM_HAM) b += (size_t)nwarps * 8;
