@@ -351,9 +351,10 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
     if (k > c->N) k = c->N;
     return k;
   };
-  c->k_fwd = pick(c->opt.tile_qubits_fwd, dbl ? 12 : 13, 13);
-  c->k_bwd = pick(c->opt.tile_qubits_bwd, dbl ? 11 : 12, 12);
-  c->k_ham = c->k_fwd < 12 ? c->k_fwd : 12;  // 256-thread Pauli-sum passes
+  // at most 256 threads per tile: k <= 8 + register bits
+  c->k_fwd = pick(c->opt.tile_qubits_fwd, dbl ? 12 : 13, 8 + (dbl ? kRBFwdC128 : kRBFwd));
+  c->k_bwd = pick(c->opt.tile_qubits_bwd, dbl ? 11 : 12, 8 + (dbl ? kRBBwdC128 : kRBBwd));
+  c->k_ham = pick(0, 8 + kRBHam, 8 + kRBHam);  // 256-thread Pauli-sum passes
   std::string err;
   if (!normalise_ops(n_qubits, c->N, ops, n_ops, n_params, n_pool, c->gates, err)) {
     delete c;
@@ -370,8 +371,8 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
                                                  : (c->opt.max_gates_per_pass < 0 ? 0 : kDefaultGateCapFactor * c->k_fwd);
   const int mg_b = c->opt.max_gates_per_pass > 0 ? c->opt.max_gates_per_pass
                                                  : (c->opt.max_gates_per_pass < 0 ? 0 : kDefaultGateCapFactor * c->k_bwd);
-  c->fwd = build_schedule(c->gates, c->N, c->k_fwd, kRBFwd, false, true, c->A, mg_f);
-  c->bwd = build_schedule(c->gates, c->N, c->k_bwd, kRBBwd, true, false, c->A, mg_b);
+  c->fwd = build_schedule(c->gates, c->N, c->k_fwd, dbl ? kRBFwdC128 : kRBFwd, false, true, c->A, mg_f);
+  c->bwd = build_schedule(c->gates, c->N, c->k_bwd, dbl ? kRBBwdC128 : kRBBwd, true, false, c->A, mg_b);
   // parameter -> gradient slots (CSR)
   c->csr_off.assign(n_params + 1, 0);
   for (int p : c->bwd.slot_param) c->csr_off[p + 1]++;
@@ -521,7 +522,7 @@ tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, const ui
   tc_status st = ensure_device(c);
   if (st != TC_OK) return st;
   if (!c->plain_built) {
-    c->plain = build_plain_schedule(c->gates_orig, c->N, c->Ap);
+    c->plain = build_plain_schedule(c->gates_orig, c->N, c->dtype == TC_C128 ? kRBFwdC128 : kRBFwd, c->Ap);
     cudaError_t e = c->dplain.upload(c->Ap);
     if (e != cudaSuccess) return cuda_fail(e, "plain plan upload");
     c->plain_built = true;

@@ -15,8 +15,10 @@
 
 namespace tcb {
 
-constexpr int kRBFwd = 5;       // register bits per thread, forward passes (32 amplitudes)
-constexpr int kRBBwd = 4;       // adjoint passes hold psi and lambda (2 x 16 amplitudes)
+constexpr int kRBFwd = 5;       // register bits per thread, complex64 forward passes (32 amplitudes)
+constexpr int kRBBwd = 4;       // complex64 adjoint passes hold psi and lambda (2 x 16 amplitudes)
+constexpr int kRBFwdC128 = 3;   // complex128: fewer amplitudes per thread, more threads per tile
+constexpr int kRBBwdC128 = 4;
 constexpr int kRBHam = 4;       // Pauli-sum passes
 constexpr int kRBMax = 5;
 constexpr int kLaneBits = 5;    // lowest tile bits mapped to warp lanes

@@ -579,7 +579,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
   return sc;
 }
 
-Schedule build_plain_schedule(const std::vector<HGate>& gates, int N, PlanArrays& A) {
+Schedule build_plain_schedule(const std::vector<HGate>& gates, int N, int rb, PlanArrays& A) {
   Schedule sc;
   sc.first_pass = (int)A.passes.size();
   sc.first_mat = (int)A.mats.size();
@@ -592,10 +592,10 @@ Schedule build_plain_schedule(const std::vector<HGate>& gates, int N, PlanArrays
     sc.n_stages += s.n_stages;
   };
   // a gate-free pass that writes the initial state, then one pass per gate
-  absorb(build_schedule({}, N, kMinQubits, kRBFwd, false, true, A, 0));
+  absorb(build_schedule({}, N, kMinQubits, rb, false, true, A, 0));
   for (size_t i = 0; i < gates.size(); ++i) {
     std::vector<HGate> one{gates[i]};
-    absorb(build_schedule(one, N, kMinQubits, kRBFwd, false, false, A, 0));
+    absorb(build_schedule(one, N, kMinQubits, rb, false, false, A, 0));
   }
   sc.n_passes = (int)A.passes.size() - sc.first_pass;
   sc.n_mats = (int)A.mats.size() - sc.first_mat;

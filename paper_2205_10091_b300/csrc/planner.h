@@ -72,6 +72,6 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
                        HamPlan& H, std::string& err);
 
 // Unfused baseline: one pass per gate (k = N tile not required; uses kMinQubits-bit tiles).
-Schedule build_plain_schedule(const std::vector<HGate>& gates, int N, PlanArrays& A);
+Schedule build_plain_schedule(const std::vector<HGate>& gates, int N, int rb, PlanArrays& A);
 
 }  // namespace tcb

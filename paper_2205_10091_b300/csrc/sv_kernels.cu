@@ -520,16 +520,26 @@ __device__ __forceinline__ decltype(V::x) rot_mask_adj(int mask, V (&P)[1 << RB]
   switch (j) {                             \
     case 0: { constexpr int J = 0; CALL; } break; \
     case 1: { constexpr int J = 1; CALL; } break; \
-    case 2: { constexpr int J = 2; CALL; } break; \
-    case 3: { constexpr int J = 3; CALL; } break; \
-    default: if (RB > 4) { constexpr int J = (RB > 4 ? 4 : 0); CALL; } break; \
+    case 2: if constexpr (RB > 2) { constexpr int J = 2; CALL; } break; \
+    case 3: if constexpr (RB > 3) { constexpr int J = 3; CALL; } break; \
+    default: if constexpr (RB > 4) { constexpr int J = 4; CALL; } break; \
   }
 
 template <int RB, typename V>
 __device__ __forceinline__ void mat4_dispatch(V (&A)[1 << RB], int j0, int j1, const V* t) {
 #define TC_M4(a, b) \
   case a * 8 + b: g_mat4<RB, a, (b < RB ? b : 0)>(A, t); break;
-  if (RB == 4) {
+  if constexpr (RB == 2) {
+    switch (j0 * 8 + j1) {
+      TC_M4(0, 1) TC_M4(1, 0)
+      default: break;
+    }
+  } else if constexpr (RB == 3) {
+    switch (j0 * 8 + j1) {
+      TC_M4(0, 1) TC_M4(0, 2) TC_M4(1, 0) TC_M4(1, 2) TC_M4(2, 0) TC_M4(2, 1)
+      default: break;
+    }
+  } else if constexpr (RB == 4) {
     switch (j0 * 8 + j1) {
       TC_M4(0, 1) TC_M4(0, 2) TC_M4(0, 3) TC_M4(1, 0) TC_M4(1, 2) TC_M4(1, 3)
       TC_M4(2, 0) TC_M4(2, 1) TC_M4(2, 3) TC_M4(3, 0) TC_M4(3, 1) TC_M4(3, 2)
@@ -645,7 +655,8 @@ __device__ __forceinline__ int diag_count(uint32_t x, const DevDiag& dg, const D
 //   +2  full: CNOT, 4x4 matrices
 //   +4  multi-entry ZZ/Z phase groups (ZZ at several qubit distances)
 template <typename T, int MODE, int RB, int VAR>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_pass(const __grid_constant__ KArgs a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB <= 3 ? 2 : 1)))
+    k_pass(const __grid_constant__ KArgs a) {
   constexpr bool FULL = (VAR & 2) != 0;
   constexpr bool LEAN = (VAR & 1) != 0;
   constexpr bool MULTI = (VAR & 4) != 0;
@@ -1240,8 +1251,8 @@ cudaError_t launch_pass(int mode, bool dbl, const KArgs& a, const DevPass& hp, i
   prof_before(mode == KM_FWD ? PK_FWD : mode == KM_BWD ? PK_BWD : PK_HAM, pass_bytes(mode, dbl, hp, a, rows), s);
   cudaError_t e;
   if (dbl) {
-    if (mode == KM_FWD) e = launch_t<double, KM_FWD, kRBFwd>(a, hp, rows, s, smem);
-    else if (mode == KM_BWD) e = launch_t<double, KM_BWD, kRBBwd>(a, hp, rows, s, smem);
+    if (mode == KM_FWD) e = launch_t<double, KM_FWD, kRBFwdC128>(a, hp, rows, s, smem);
+    else if (mode == KM_BWD) e = launch_t<double, KM_BWD, kRBBwdC128>(a, hp, rows, s, smem);
     else e = launch_t<double, KM_HAM, kRBHam>(a, hp, rows, s, smem);
   } else {
     if (mode == KM_FWD) e = launch_t<float, KM_FWD, kRBFwd>(a, hp, rows, s, smem);
