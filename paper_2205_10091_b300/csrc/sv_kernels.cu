@@ -312,6 +312,11 @@ __device__ __forceinline__ void g_rx(V (&A)[1 << RB], V cs) {
 // Packed FP32x2 arithmetic (sm_100+ FFMA2/FMUL2 on a 64-bit register pair).
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// element-wise a * b + c on both components (packed for complex64)
+__device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 cfma2(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
 
 // RY: a0' = c a0 - s a1, a1' = s a0 + c a1
 template <int RB, int J, typename V>
@@ -730,11 +735,31 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
         eacc = fma(h, fma(A[i].x, A[i].x, A[i].y * A[i].y), eacc);
       }
     }
+    // swizzled tile offsets of the register bits (the swizzle is XOR-linear)
+    uint32_t srt[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) srt[r] = swz<V>(m.rt[r]);
     for (int g = 0; g < sp.n_hflip; ++g) {
       const DevHFlip fl = a.hflips[sp.hflip_off + g];
       if (fl.n_terms == 1) {
         const DevHTerm ht = a.hterms[fl.term_off];
         const T w = (T)ht.w;
+        if (ht.sm == 0 && ht.ny == 0) {
+          // X string: (P psi)_x = w psi_{x ^ f}; partner index walked in Gray-code order
+          uint32_t tt = swz<V>(m.t) ^ swz<V>(fl.f_tile);
+          V e2 = mk<V>((T)0, (T)0);
+          const V w2 = mk<V>(w, w);
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            if (j) tt ^= srt[low_bit(j)];
+            const int i = j ^ (j >> 1);
+            const V pp = sm0[tt];
+            L[i] = cfma2(w2, pp, L[i]);
+            e2 = cfma2(A[i], pp, e2);
+          }
+          eacc = fma(w, e2.x + e2.y, eacc);
+          continue;
+        }
 #pragma unroll
         for (int i = 0; i < R; ++i) {
           const uint32_t xp = (m.g | offg(m, i)) ^ fl.f;
@@ -1237,12 +1262,15 @@ static double pass_bytes(int mode, bool dbl, const DevPass& hp, const KArgs& a, 
 
 template <typename T, int MODE, int RB>
 static cudaError_t launch_t(const KArgs& a, const DevPass& hp, int rows, cudaStream_t s, size_t smem) {
-  if (MODE == KM_HAM) return launch_tf<T, MODE, RB, 0>(a, hp, rows, s, smem);
-  const bool lean = hp.flags & PF_LEAN, full = hp.flags & PF_FULL, multi = hp.flags & PF_MULTI;
-  if (full || (lean && multi)) return launch_tf<T, MODE, RB, 7>(a, hp, rows, s, smem);
-  if (lean) return launch_tf<T, MODE, RB, 1>(a, hp, rows, s, smem);
-  if (multi) return launch_tf<T, MODE, RB, 4>(a, hp, rows, s, smem);
-  return launch_tf<T, MODE, RB, 0>(a, hp, rows, s, smem);
+  if constexpr (MODE == KM_HAM) {
+    return launch_tf<T, MODE, RB, 0>(a, hp, rows, s, smem);
+  } else {
+    const bool lean = hp.flags & PF_LEAN, full = hp.flags & PF_FULL, multi = hp.flags & PF_MULTI;
+    if (full || (lean && multi)) return launch_tf<T, MODE, RB, 7>(a, hp, rows, s, smem);
+    if (lean) return launch_tf<T, MODE, RB, 1>(a, hp, rows, s, smem);
+    if (multi) return launch_tf<T, MODE, RB, 4>(a, hp, rows, s, smem);
+    return launch_tf<T, MODE, RB, 0>(a, hp, rows, s, smem);
+  }
 }
 
 cudaError_t launch_pass(int mode, bool dbl, const KArgs& a, const DevPass& hp, int rows, cudaStream_t s) {
