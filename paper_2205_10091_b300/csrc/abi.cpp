@@ -190,7 +190,7 @@ tc_status run_schedule(tc_circuit* c, int mode, const Schedule& sc, const PlanAr
   TC_CHECK_CUDA(launch_tables(is_dbl(c), a, sc.first_mat, sc.n_mats, rows, s), "gate tables");
   for (int p = 0; p < sc.n_passes; ++p) {
     a.pass = sc.first_pass + p;
-    TC_CHECK_CUDA(launch_pass(mode, is_dbl(c), a, A.passes[a.pass], rows, s), mode == KM_FWD ? "forward pass" : "adjoint pass");
+    TC_CHECK_CUDA(launch_pass(mode, is_dbl(c), a, A.passes[a.pass], &A.stages[A.passes[a.pass].stage_off], rows, s), mode == KM_FWD ? "forward pass" : "adjoint pass");
   }
   return TC_OK;
 }
@@ -200,7 +200,7 @@ tc_status run_ham(tc_circuit* c, KArgs a, int rows, bool store_lambda, cudaStrea
   a.n_hpasses = (int)c->H.passes.size();
   for (int p = 0; p < (int)c->H.passes.size(); ++p) {
     a.pass = p;
-    TC_CHECK_CUDA(launch_pass(KM_HAM, is_dbl(c), a, c->H.passes[p], rows, s), "hamiltonian pass");
+    TC_CHECK_CUDA(launch_pass(KM_HAM, is_dbl(c), a, c->H.passes[p], nullptr, rows, s), "hamiltonian pass");
   }
   return TC_OK;
 }

@@ -107,7 +107,7 @@ extern "C" tc_status tc_expect_pauli_sum_noalloc(const tc_circuit* c, const void
   const bool dbl = c->dtype == TC_C128;
   for (int p = 0; p < nh; ++p) {
     a.pass = p;
-    if ((e = launch_pass(KM_HAM, dbl, a, H.passes[p], B, s)) != cudaSuccess) return cuda_fail(e, "pauli-sum pass");
+    if ((e = launch_pass(KM_HAM, dbl, a, H.passes[p], nullptr, B, s)) != cudaSuccess) return cuda_fail(e, "pauli-sum pass");
   }
   if ((e = launch_finalize(a.epart, nh, (int)tiles_h, nullptr, 0, 1, nullptr, nullptr, 0, B, d_energy_out, nullptr,
                            s)) != cudaSuccess)

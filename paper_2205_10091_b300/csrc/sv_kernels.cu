@@ -661,16 +661,16 @@ __device__ __forceinline__ int diag_count(uint32_t x, const DevDiag& dg, const D
 //   +4  multi-entry ZZ/Z phase groups (ZZ at several qubit distances)
 template <typename T, int MODE, int RB, int VAR>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB <= 3 ? 2 : 1)))
-    k_pass(const __grid_constant__ KArgs a) {
+    k_pass(const __grid_constant__ KArgs a, const __grid_constant__ PassArgs pa) {
   constexpr bool FULL = (VAR & 2) != 0;
   constexpr bool LEAN = (VAR & 1) != 0;
   constexpr bool MULTI = (VAR & 4) != 0;
   using V = typename VT<T>::V;
   constexpr int R = 1 << RB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ DevPass sp;
-  if (threadIdx.x == 0) sp = (MODE == KM_HAM) ? a.hpasses[a.pass] : a.passes[a.pass];
-  __syncthreads();
+  // the pass descriptor and its first stage arrive as kernel parameters, so
+  // the first state loads need no dependent global reads
+  const DevPass& sp = pa.pass;
 
   const int k = sp.k;
   const uint32_t tid = threadIdx.x;
@@ -836,9 +836,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) red[slot * nwarps + warp] += (double)v;
   };
-  // stage 0's map straight from global memory, so that the state loads are
-  // in flight while the per-CTA tables are being staged
-  Map<RB> m = stage_map<RB>(a.stages[sp.stage_off], tid, base);
+  // stage 0's map from the kernel parameters: the state loads are in flight
+  // while the per-CTA tables are being staged
+  Map<RB> m = stage_map<RB>(pa.st0, tid, base);
   if (MODE == KM_FWD && (sp.flags & PF_INIT) && a.synth_init) {
     if (a.init == 1) {
       const uint32_t anc = (1u << (a.N - a.n_user)) - 1u;
@@ -1158,7 +1158,8 @@ size_t pass_smem_bytes(int mode, bool dbl, const DevPass& p) {
 }
 
 template <typename T, int MODE, int RB, int VAR>
-static cudaError_t launch_tf(const KArgs& a, const DevPass& hp, int rows, cudaStream_t s, size_t smem) {
+static cudaError_t launch_tf(const KArgs& a, const PassArgs& pa, int rows, cudaStream_t s, size_t smem) {
+  const DevPass& hp = pa.pass;
   static int configured_max = -1;
   if (configured_max < 0) {
     int dev = 0, optin = 0;
@@ -1179,7 +1180,7 @@ static cudaError_t launch_tf(const KArgs& a, const DevPass& hp, int rows, cudaSt
   const size_t blocks = (size_t)rows << hp.nfix;
   if (blocks == 0) return cudaSuccess;
   if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-  k_pass<T, MODE, RB, VAR><<<(unsigned)blocks, threads, smem, s>>>(a);
+  k_pass<T, MODE, RB, VAR><<<(unsigned)blocks, threads, smem, s>>>(a, pa);
   return cudaGetLastError();
 }
 
@@ -1261,31 +1262,38 @@ static double pass_bytes(int mode, bool dbl, const DevPass& hp, const KArgs& a, 
 }
 
 template <typename T, int MODE, int RB>
-static cudaError_t launch_t(const KArgs& a, const DevPass& hp, int rows, cudaStream_t s, size_t smem) {
+static cudaError_t launch_t(const KArgs& a, const PassArgs& pa, int rows, cudaStream_t s, size_t smem) {
   if constexpr (MODE == KM_HAM) {
-    return launch_tf<T, MODE, RB, 0>(a, hp, rows, s, smem);
+    return launch_tf<T, MODE, RB, 0>(a, pa, rows, s, smem);
   } else {
+    const DevPass& hp = pa.pass;
     const bool lean = hp.flags & PF_LEAN, full = hp.flags & PF_FULL, multi = hp.flags & PF_MULTI;
-    if (full || (lean && multi)) return launch_tf<T, MODE, RB, 7>(a, hp, rows, s, smem);
-    if (lean) return launch_tf<T, MODE, RB, 1>(a, hp, rows, s, smem);
-    if (multi) return launch_tf<T, MODE, RB, 4>(a, hp, rows, s, smem);
-    return launch_tf<T, MODE, RB, 0>(a, hp, rows, s, smem);
+    if (full || (lean && multi)) return launch_tf<T, MODE, RB, 7>(a, pa, rows, s, smem);
+    if (lean) return launch_tf<T, MODE, RB, 1>(a, pa, rows, s, smem);
+    if (multi) return launch_tf<T, MODE, RB, 4>(a, pa, rows, s, smem);
+    return launch_tf<T, MODE, RB, 0>(a, pa, rows, s, smem);
   }
 }
 
-cudaError_t launch_pass(int mode, bool dbl, const KArgs& a, const DevPass& hp, int rows, cudaStream_t s) {
+cudaError_t launch_pass(int mode, bool dbl, const KArgs& a, const DevPass& hp, const DevStage* st0, int rows,
+                        cudaStream_t s) {
+  if (mode != KM_HAM && !st0) return cudaErrorInvalidValue;
+  PassArgs pa;
+  pa.pass = hp;
+  if (st0) pa.st0 = *st0;
+  else pa.st0 = DevStage{};
   const size_t smem = pass_smem_bytes(mode, dbl, hp);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   prof_before(mode == KM_FWD ? PK_FWD : mode == KM_BWD ? PK_BWD : PK_HAM, pass_bytes(mode, dbl, hp, a, rows), s);
   cudaError_t e;
   if (dbl) {
-    if (mode == KM_FWD) e = launch_t<double, KM_FWD, kRBFwdC128>(a, hp, rows, s, smem);
-    else if (mode == KM_BWD) e = launch_t<double, KM_BWD, kRBBwdC128>(a, hp, rows, s, smem);
-    else e = launch_t<double, KM_HAM, kRBHam>(a, hp, rows, s, smem);
+    if (mode == KM_FWD) e = launch_t<double, KM_FWD, kRBFwdC128>(a, pa, rows, s, smem);
+    else if (mode == KM_BWD) e = launch_t<double, KM_BWD, kRBBwdC128>(a, pa, rows, s, smem);
+    else e = launch_t<double, KM_HAM, kRBHam>(a, pa, rows, s, smem);
   } else {
-    if (mode == KM_FWD) e = launch_t<float, KM_FWD, kRBFwd>(a, hp, rows, s, smem);
-    else if (mode == KM_BWD) e = launch_t<float, KM_BWD, kRBBwd>(a, hp, rows, s, smem);
-    else e = launch_t<float, KM_HAM, kRBHam>(a, hp, rows, s, smem);
+    if (mode == KM_FWD) e = launch_t<float, KM_FWD, kRBFwd>(a, pa, rows, s, smem);
+    else if (mode == KM_BWD) e = launch_t<float, KM_BWD, kRBBwd>(a, pa, rows, s, smem);
+    else e = launch_t<float, KM_HAM, kRBHam>(a, pa, rows, s, smem);
   }
   prof_after(s);
   return e;

@@ -47,9 +47,17 @@ struct KArgs {
   int table_stride;
 };
 
-// Launch one pass for `rows` batch rows.  smem_bytes from pass_smem_bytes().
-cudaError_t launch_pass(int mode, bool dbl, const KArgs& a, const DevPass& host_pass, int rows,
-                        cudaStream_t s);
+// The pass descriptor and its first stage, passed by value as a kernel
+// parameter.
+struct PassArgs {
+  DevPass pass;
+  DevStage st0;  // unused by Pauli-sum passes
+};
+
+// Launch one pass for `rows` batch rows (st0: the pass's first stage; NULL for
+// a Pauli-sum pass).
+cudaError_t launch_pass(int mode, bool dbl, const KArgs& a, const DevPass& host_pass, const DevStage* st0,
+                        int rows, cudaStream_t s);
 size_t pass_smem_bytes(int mode, bool dbl, const DevPass& p);
 
 // Build the gate tables (rotation cos/sin pairs, phase tables, 2x2/4x4
