@@ -708,13 +708,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
     for (int r = 0; r < RB; ++r) S[r] = (int8_t)(k - RB + r);
     const Map<RB> m = make_map<RB>(sp, S, tid, base);
     load_regs<RB>(A, psi, m);
-    smem_write<RB>(A, sm0, m);
     if ((sp.flags & PF_LAM_LOAD) && lam) {
       load_regs<RB>(L, lam, m);
     } else {
 #pragma unroll
       for (int i = 0; i < R; ++i) L[i] = mk<V>((T)0, (T)0);
     }
+    smem_write<RB>(A, sm0, m);
     __syncthreads();
     T eacc = 0;
     for (int e = 0; e < sp.n_hdiag; ++e) {
