@@ -22,6 +22,7 @@ constexpr int kRBBwdC128 = 4;
 constexpr int kRBHam = 4;       // Pauli-sum passes
 constexpr int kRBMax = 5;
 constexpr int kLaneBits = 5;    // lowest tile bits mapped to warp lanes
+constexpr int kIOLowBits = 3;   // positions every tile holds: loads and stores move runs of 8 amplitudes
 constexpr int kMinQubits = kRBMax + kLaneBits;  // narrower circuits get idle low qubits
 constexpr int kMaxK = 14;
 constexpr int kMaxQubits = 30;

@@ -236,12 +236,13 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
   std::vector<int> remaining(gates.size());
   std::iota(remaining.begin(), remaining.end(), 0);
   if (adjoint) std::reverse(remaining.begin(), remaining.end());
-  const uint32_t low = (1u << kLaneBits) - 1;
+  const uint32_t low = (1u << kLaneBits) - 1;      // lane tile bits of the load/store stages
+  const uint32_t io_low = (1u << kIOLowBits) - 1;  // positions every tile holds
   bool first = true;
 
   while (!remaining.empty() || (first && first_init)) {
     // ---- choose the pass's gates and tile -------------------------------
-    uint32_t tile = low, blocked = 0;
+    uint32_t tile = io_low, blocked = 0;
     int n_nondiag = 0;
     std::vector<int> taken, deferred;
     for (int gi : remaining) {
@@ -606,7 +607,7 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
                        HamPlan& H, std::string& err) {
   H = HamPlan{};
   H.k = k;
-  const uint32_t low = (1u << kLaneBits) - 1;
+  const uint32_t io_low = (1u << kIOLowBits) - 1;  // positions every tile holds
   // ---- classify terms -----------------------------------------------------
   std::map<std::pair<double, uint32_t>, std::vector<uint32_t>> zz;  // (w, d) -> lower-position bits
   std::map<uint32_t, std::vector<DevHTerm>> flips;
@@ -676,7 +677,7 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
   size_t n_done = 0;
   bool first = true;
   while (first || n_done < groups.size()) {
-    uint32_t tile = low;
+    uint32_t tile = io_low;
     std::vector<int> mine;
     for (size_t g = 0; g < groups.size(); ++g) {
       if (done[g]) continue;

@@ -50,7 +50,7 @@ def test_noalloc_matches_allocating_entry_point_twice(dtype):
 def test_noalloc_rejects_oversize_request():
     import torch
 
-    n, B = 20, 1400  # 1400 rows x 3 passes x 256 tiles x 8 B > 8 MiB of scratch
+    n, B = 20, 2100  # 2100 rows x (2 or more) passes x 256 tiles x 8 B > 8 MiB of scratch
     c = nt.Circuit(W.OpBuilder(n).build())
     states = torch.empty((B, 1 << n), dtype=torch.complex64, device="cuda")
     out = torch.empty(B, dtype=torch.float64, device="cuda")
