@@ -115,10 +115,18 @@ __device__ void build_mat(const DevMat& m, V* tab, const double* th, const doubl
     case MT_RX:
     case MT_RY: {
       // (cos(a/2), sin(a/2)) of the effective angle; the kernel applies
-      // RX = [[c, -is], [-is, c]] or RY = [[c, -s], [s, c]]
+      // RX = [[c, -is], [-is, c]] or RY = [[c, -s], [s, c]].  Complex64 RY
+      // entries are (t, c) with t = s / c: the kernel applies c [[1, -t], [t, 1]]
+      // with c carried by a running scale (|c| kept >= 2^-60; the rotation
+      // error that clamp allows is below 1e-18)
       double s, c;
       sincos(0.5 * ang, &s, &c);
-      t[0] = mk<V>((S)c, (S)s);
+      if (m.type == MT_RY && sizeof(S) == 4) {
+        if (fabs(c) < 0x1p-60) c = c < 0 ? -0x1p-60 : 0x1p-60;
+        t[0] = mk<V>((S)(s / c), (S)c);
+      } else {
+        t[0] = mk<V>((S)c, (S)s);
+      }
     } break;
     case MT_U1:
     case MT_U2: {
@@ -312,23 +320,28 @@ __device__ __forceinline__ void g_rx(V (&A)[1 << RB], V cs) {
 // Packed FP32x2 arithmetic (sm_100+ FFMA2/FMUL2 on a 64-bit register pair).
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// element-wise a * b on both components (packed for complex64)
+__device__ __forceinline__ float2 cmul_re(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 cmul_re(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
 // element-wise a * b + c on both components (packed for complex64)
 __device__ __forceinline__ float2 cfma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ double2 cfma2(double2 a, double2 b, double2 c) {
   return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
 }
 
-// RY: a0' = c a0 - s a1, a1' = s a0 + c a1
+// RY: a0' = c a0 - s a1, a1' = s a0 + c a1.  Complex64 uses the tangent form
+// a0' = a0 - t a1, a1' = a1 + t a0 (cs = (t, c); the factor c is left to the
+// caller's running scale, see rot_scale): one packed FMA per output.
 template <int RB, int J, typename V>
 __device__ __forceinline__ void g_ry(V (&A)[1 << RB], V cs) {
   if constexpr (sizeof(V) == 8) {
-    const float2 c2 = make_float2(cs.x, cs.x), s2 = make_float2(cs.y, cs.y), n2 = make_float2(-cs.y, -cs.y);
+    const float2 t2 = make_float2(cs.x, cs.x), n2 = make_float2(-cs.x, -cs.x);
 #pragma unroll
     for (int i = 0; i < (1 << RB); ++i) {
       if (i & (1 << J)) continue;
       const float2 x0 = A[i], x1 = A[i | (1 << J)];
-      A[i] = fma2(c2, x0, mul2(n2, x1));
-      A[i | (1 << J)] = fma2(c2, x1, mul2(s2, x0));
+      A[i] = fma2(n2, x1, x0);
+      A[i | (1 << J)] = fma2(t2, x0, x1);
     }
     return;
   }
@@ -455,30 +468,63 @@ __device__ __forceinline__ decltype(V::x) g_ry_adj(V (&P)[1 << RB], V (&L)[1 << 
   return g_adj<RB, J, false>(P, L, cs, true);
 }
 
+// Running scale of complex64 tangent-form RY: every such gate multiplies the
+// true state by c = cs.y on top of what the registers hold.  Once the scale
+// falls below 2^-20 it is folded into the registers (the register values then
+// stay within 2^20 / |c| of the true ones, far from FP32 overflow).  TWO: the
+// adjoint's psi and lambda share the scale.  A no-op for complex128.
+template <int RB, bool TWO, typename V, typename T>
+__device__ __forceinline__ void rot_scale(T& sc, V cs, V (&A)[1 << RB], V (&L)[1 << RB]) {
+  if constexpr (sizeof(V) == 8) {
+    sc *= cs.y;
+    if (fabsf(sc) < 0x1p-20f) {
+      const float2 s2 = make_float2(sc, sc);
+#pragma unroll
+      for (int i = 0; i < (1 << RB); ++i) {
+        A[i] = mul2(s2, A[i]);
+        if (TWO) L[i] = mul2(s2, L[i]);
+      }
+      sc = 1.f;
+    }
+  }
+}
+
 // Rotations on the register bits of a compile-time mask (entry of bit r at
-// t[rank of r in the mask]); AdjM returns the summed gradient terms.
+// t[rank of r in the mask]); adj returns the summed gradient terms, each
+// weighted by the running scale squared at its gate.
 template <int RB, int MASK, bool ISX, int R0 = 0, int E = 0>
 struct RotM {
-  template <typename V>
-  __device__ __forceinline__ static void run(V (&A)[1 << RB], const V* t) {
+  // TWO: rotate A and L alike (non-parametric rotations inside an adjoint pass)
+  template <bool TWO, typename V, typename T>
+  __device__ __forceinline__ static void run(V (&A)[1 << RB], V (&L)[1 << RB], const V* t, T& sc) {
     if constexpr (R0 < RB) {
       if constexpr (((MASK >> R0) & 1) != 0) {
-        if constexpr (ISX) g_rx<RB, R0>(A, t[E]);
-        else g_ry<RB, R0>(A, t[E]);
-        RotM<RB, MASK, ISX, R0 + 1, E + 1>::run(A, t);
+        if constexpr (ISX) {
+          g_rx<RB, R0>(A, t[E]);
+          if (TWO) g_rx<RB, R0>(L, t[E]);
+        } else {
+          g_ry<RB, R0>(A, t[E]);
+          if (TWO) g_ry<RB, R0>(L, t[E]);
+          rot_scale<RB, TWO>(sc, t[E], A, L);
+        }
+        RotM<RB, MASK, ISX, R0 + 1, E + 1>::template run<TWO>(A, L, t, sc);
       } else {
-        RotM<RB, MASK, ISX, R0 + 1, E>::run(A, t);
+        RotM<RB, MASK, ISX, R0 + 1, E>::template run<TWO>(A, L, t, sc);
       }
     }
   }
-  template <typename V>
-  __device__ __forceinline__ static decltype(V::x) adj(V (&P)[1 << RB], V (&L)[1 << RB], const V* t) {
+  template <typename V, typename T>
+  __device__ __forceinline__ static decltype(V::x) adj(V (&P)[1 << RB], V (&L)[1 << RB], const V* t, T& sc) {
     if constexpr (R0 < RB) {
       if constexpr (((MASK >> R0) & 1) != 0) {
-        const decltype(V::x) a = g_adj<RB, R0, ISX>(P, L, t[E], true);
-        return a + RotM<RB, MASK, ISX, R0 + 1, E + 1>::adj(P, L, t);
+        decltype(V::x) a = g_adj<RB, R0, ISX>(P, L, t[E], true);
+        if constexpr (!ISX) {
+          a *= sc * sc;
+          rot_scale<RB, true>(sc, t[E], P, L);
+        }
+        return a + RotM<RB, MASK, ISX, R0 + 1, E + 1>::adj(P, L, t, sc);
       } else {
-        return RotM<RB, MASK, ISX, R0 + 1, E>::adj(P, L, t);
+        return RotM<RB, MASK, ISX, R0 + 1, E>::adj(P, L, t, sc);
       }
     } else {
       return 0;
@@ -491,12 +537,12 @@ struct RotM {
   X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) \
   X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31)
 
-template <int RB, bool ISX, typename V>
-__device__ __forceinline__ void rot_mask(int mask, V (&A)[1 << RB], const V* t) {
+template <int RB, bool ISX, bool TWO, typename V, typename T>
+__device__ __forceinline__ void rot_mask(int mask, V (&A)[1 << RB], V (&L)[1 << RB], const V* t, T& sc) {
   switch (mask) {
 #define TC_ROT_CASE(M) \
   case M:              \
-    if constexpr ((M) < (1 << RB)) RotM<RB, (M), ISX>::run(A, t); \
+    if constexpr ((M) < (1 << RB)) RotM<RB, (M), ISX>::template run<TWO>(A, L, t, sc); \
     break;
     TC_MASK_CASES(TC_ROT_CASE)
 #undef TC_ROT_CASE
@@ -504,13 +550,14 @@ __device__ __forceinline__ void rot_mask(int mask, V (&A)[1 << RB], const V* t) 
       break;
   }
 }
-template <int RB, bool ISX, typename V>
-__device__ __forceinline__ decltype(V::x) rot_mask_adj(int mask, V (&P)[1 << RB], V (&L)[1 << RB], const V* t) {
+template <int RB, bool ISX, typename V, typename T>
+__device__ __forceinline__ decltype(V::x) rot_mask_adj(int mask, V (&P)[1 << RB], V (&L)[1 << RB], const V* t,
+                                                       T& sc) {
   decltype(V::x) acc = 0;
   switch (mask) {
 #define TC_ADJ_CASE(M) \
   case M:              \
-    if constexpr ((M) < (1 << RB)) acc = RotM<RB, (M), ISX>::adj(P, L, t); \
+    if constexpr ((M) < (1 << RB)) acc = RotM<RB, (M), ISX>::adj(P, L, t, sc); \
     break;
     TC_MASK_CASES(TC_ADJ_CASE)
 #undef TC_ADJ_CASE
@@ -827,6 +874,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
   T gl[kLocalSlots];
   if (MODE == KM_BWD)
     for (int g = 0; g < sp.n_gslots && g < kLocalSlots; ++g) gl[g] = 0;
+  // running scale of tangent-form rotations (complex64; stays 1 for complex128)
+  T sc = 1;
   auto add_grad = [&](int slot, T v) {
     if (slot < kLocalSlots) {
       gl[slot] += v;
@@ -887,13 +936,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
           }
         } break;
         case IK_RYM: {
-          rot_mask<RB, false>((uint8_t)in.j0, A, tab + in.slot);
-          if (MODE == KM_BWD) rot_mask<RB, false>((uint8_t)in.j0, L, tab + in.slot);
+          rot_mask<RB, false, MODE == KM_BWD>((uint8_t)in.j0, A, L, tab + in.slot, sc);
         } break;
         case IK_RY: {
           const V cs = tab[in.slot];
           TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(A, cs)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(L, cs)));
+          rot_scale<RB, MODE == KM_BWD>(sc, cs, A, L);
         } break;
         case IK_H:
           if (!LEAN) break;
@@ -993,7 +1042,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
         } break;
         case IK_RYM_ADJ: {
           if (MODE != KM_BWD) break;
-          const T acc = rot_mask_adj<RB, false>((uint8_t)in.j0, A, L, tab + in.slot);
+          const T acc = rot_mask_adj<RB, false>((uint8_t)in.j0, A, L, tab + in.slot, sc);
           add_grad(in.gslot, acc * (T)in.gscale);
         } break;
         case IK_RXM_ADJ:
@@ -1051,7 +1100,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
               TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, false>(A, L, cs, false)));
             }
           }
-          add_grad(in.gslot, acc * (T)in.gscale);
+          add_grad(in.gslot, acc * (sc * sc) * (T)in.gscale);
+          if (in.kind == IK_RY_ADJ) rot_scale<RB, true>(sc, tab[in.slot], A, L);
         } break;
         case IK_DIAG_ADJ: {
           if (MODE != KM_BWD) break;
@@ -1074,7 +1124,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
               A[i] = cmul(ph, A[i]);
               L[i] = cmul(ph, L[i]);
             }
-            add_grad(in.gslot, (a2[0] + a2[1]) * (T)in.gscale);
+            add_grad(in.gslot, (a2[0] + a2[1]) * (sc * sc) * (T)in.gscale);
           } else if (MULTI && !dg.sign_mode) {
             int cnt[R];
             diag_counts_lin<RB>(cnt, m, dg, des);
@@ -1086,7 +1136,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
               A[i] = cmul(ph, A[i]);
               L[i] = cmul(ph, L[i]);
             }
-            add_grad(in.gslot, (a2[0] + a2[1]) * (T)in.gscale);
+            add_grad(in.gslot, (a2[0] + a2[1]) * (sc * sc) * (T)in.gscale);
           } else if (FULL) {
             T acc = 0;
 #pragma unroll
@@ -1097,12 +1147,20 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
               A[i] = cmul(ph, A[i]);
               L[i] = cmul(ph, L[i]);
             }
-            add_grad(in.gslot, acc * (T)in.gscale);
+            add_grad(in.gslot, acc * (sc * sc) * (T)in.gscale);
           }
         } break;
         default:
           break;
       }
+    }
+  }
+  if (sc != (T)1) {
+    const V s2 = mk<V>(sc, sc);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      A[i] = cmul_re(s2, A[i]);
+      if (MODE == KM_BWD) L[i] = cmul_re(s2, L[i]);
     }
   }
   store_regs<RB>(A, psi, m);
