@@ -429,6 +429,21 @@ struct AccBits {
 template <int RB, int J, bool ISX, typename V>
 __device__ __forceinline__ decltype(V::x) g_adj(V (&P)[1 << RB], V (&L)[1 << RB], V cs, bool update) {
   using S = decltype(V::x);
+  if constexpr (!ISX && sizeof(V) == 8) {
+    // (l1 . p0) - (l0 . p1) in two packed accumulators
+    float2 ap = make_float2(0.f, 0.f), an = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < (1 << RB); ++i) {
+      if (i & (1 << J)) continue;
+      ap = fma2(L[i | (1 << J)], P[i], ap);
+      an = fma2(L[i], P[i | (1 << J)], an);
+    }
+    if (update) {
+      g_ry<RB, J>(P, cs);
+      g_ry<RB, J>(L, cs);
+    }
+    return (ap.x + ap.y) - (an.x + an.y);
+  }
   S acc[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int i = 0; i < (1 << RB); ++i) {
@@ -460,9 +475,8 @@ __device__ __forceinline__ decltype(V::x) g_adj(V (&P)[1 << RB], V (&L)[1 << RB]
 }
 
 // Adjoint step of RY: sum over pairs of Im<lam|Y|psi> = (l1 . p0) - (l0 . p1)
-// in four scalar accumulators, then RY(-a) on psi and lam (the table holds the
-// adjoint's (c, s); packed FP32x2 for complex64).  Packing the accumulation
-// as well costs more registers than it saves issue slots.
+// (two packed accumulators for complex64, four scalar ones for complex128),
+// then RY(-a) on psi and lam (the table holds the adjoint's entry).
 template <int RB, int J, typename V>
 __device__ __forceinline__ decltype(V::x) g_ry_adj(V (&P)[1 << RB], V (&L)[1 << RB], V cs) {
   return g_adj<RB, J, false>(P, L, cs, true);
