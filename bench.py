@@ -336,7 +336,7 @@ def _time_cuda(fn, reps: int, warm: int = 3) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def extra_workloads(serve_rates=(250.0, 500.0, 1000.0), serve_seconds: float = 2.0) -> dict:
+def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: float = 2.0) -> dict:
     import time
 
     import torch
