@@ -21,6 +21,7 @@ constexpr int kRBFwdC128 = 3;   // complex128: fewer amplitudes per thread, more
 constexpr int kRBBwdC128 = 4;
 constexpr int kRBHam = 4;       // Pauli-sum passes
 constexpr int kRBMax = 5;
+constexpr int kRYEntries = 2;   // per-row table entries of one RY gate
 constexpr int kLaneBits = 5;    // lowest tile bits mapped to warp lanes
 constexpr int kIOLowBits = 3;   // positions every tile holds: loads and stores move runs of 8 amplitudes
 constexpr int kMinQubits = kRBMax + kLaneBits;  // narrower circuits get idle low qubits
@@ -58,7 +59,7 @@ enum : int8_t {
   MT_H = 0,
   MT_X = 1,
   MT_RX = 2,      // 1 entry (c, s) of the effective angle
-  MT_RY = 3,      // 1 entry (c, s)
+  MT_RY = 3,      // kRYEntries entries: complex64 (t, c_hi), (c_lo, 0); complex128 (c, s), (0, 0)
   MT_U1 = 4,      // 2x2 from pool (4 entries)
   MT_U2 = 5,      // 4x4 from pool (16 entries)
   MT_DIAGTAB = 6, // phases exp(-i s theta/2 (T - 2m)), m = 0..T  (T+1 entries)

@@ -169,7 +169,8 @@ uint32_t item_need(const Item& it, const std::vector<HGate>& gates, const int* t
 // instruction.  RX gates on different qubits commute, and Im<lam|X_q|psi> is
 // unchanged by RX on other qubits, so the run may be reordered by bit index.
 // Their per-row table entries are moved so that bit r reads entry
-// slot + rank(r) (rank among the run's bits).
+// slot + stride * rank(r) (rank among the run's bits; RY has kRYEntries
+// entries per gate, RX one).
 void merge_rx_runs(PlanArrays& A, int first, int rb, int table_base) {
   std::vector<DevInstr> out;
   const int end = (int)A.instrs.size();
@@ -202,13 +203,15 @@ void merge_rx_runs(PlanArrays& A, int first, int rb, int table_base) {
     std::sort(bit_slot.begin(), bit_slot.end());
     int lo = bit_slot[0].second;
     for (auto& bs : bit_slot) lo = std::min(lo, bs.second);
-    // move the DevMat records: the entry of the r-th smallest bit goes to lo + r
+    // move the DevMat records: the entries of the r-th smallest bit go to
+    // lo + stride * r (the run's entries are one contiguous block)
+    const int stride = isy ? kRYEntries : 1;
     std::vector<std::pair<int, int>> moves;  // (mat index, new local entry)
     for (size_t r = 0; r < bit_slot.size(); ++r) {
       const int old_local = bit_slot[r].second;
       for (int mi = (int)A.mats.size() - 1; mi >= 0; --mi)
         if (A.mats[mi].type == mtype && A.mats[mi].dst == table_base + old_local) {
-          moves.push_back({mi, lo + (int)r});
+          moves.push_back({mi, lo + stride * (int)r});
           break;
         }
     }
@@ -530,7 +533,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
           case TC_OP_RX:
           case TC_OP_RY: {
             const bool rx = g.kind == TC_OP_RX;
-            in.slot = add_mat(rx ? MT_RX : MT_RY, g, 1);
+            in.slot = add_mat(rx ? MT_RX : MT_RY, g, rx ? 1 : kRYEntries);
             if (adjoint && g.param >= 0) {
               in.kind = rx ? IK_RX_ADJ : IK_RY_ADJ;
               in.gslot = (int16_t)slot_of(g.param);

@@ -122,10 +122,19 @@ __device__ void build_mat(const DevMat& m, V* tab, const double* th, const doubl
       double s, c;
       sincos(0.5 * ang, &s, &c);
       if (m.type == MT_RY && sizeof(S) == 4) {
+        // c is recomputed from the rounded t, so that c [[1, -t], [t, 1]] is
+        // orthogonal; it is stored as hi + lo so the running scale sees it
+        // to ~2^-48 (a rounded c, repeated over a layer of gates that share
+        // an angle, would drift the norm systematically)
         if (fabs(c) < 0x1p-60) c = c < 0 ? -0x1p-60 : 0x1p-60;
-        t[0] = mk<V>((S)(s / c), (S)c);
+        const float tf = (float)(s / c);
+        const double ce = copysign(1.0 / sqrt(1.0 + (double)tf * (double)tf), c);
+        const float hi = (float)ce;
+        t[0] = mk<V>((S)tf, (S)hi);
+        t[1] = mk<V>((S)(ce - (double)hi), (S)0);
       } else {
         t[0] = mk<V>((S)c, (S)s);
+        if (m.type == MT_RY) t[1] = mk<V>((S)0, (S)0);
       }
     } break;
     case MT_U1:
@@ -483,22 +492,31 @@ __device__ __forceinline__ decltype(V::x) g_ry_adj(V (&P)[1 << RB], V (&L)[1 << 
 }
 
 // Running scale of complex64 tangent-form RY: every such gate multiplies the
-// true state by c = cs.y on top of what the registers hold.  Once the scale
-// falls below 2^-20 it is folded into the registers (the register values then
-// stay within 2^20 / |c| of the true ones, far from FP32 overflow).  TWO: the
-// adjoint's psi and lambda share the scale.  A no-op for complex128.
+// true state by c = cs.y on top of what the registers hold.  The scale is a
+// compensated product sc + sl (the rounding error of each sc * c is carried in
+// sl), so it adds no drift of its own.  Once |sc| falls below 2^-20 its
+// power-of-two part moves into the registers, which is exact; the register
+// values then stay within 2^21 / |c| of the true ones, far from FP32 overflow.
+// TWO: the adjoint's psi and lambda share the scale.  A no-op for complex128.
 template <int RB, bool TWO, typename V, typename T>
-__device__ __forceinline__ void rot_scale(T& sc, V cs, V (&A)[1 << RB], V (&L)[1 << RB]) {
+__device__ __forceinline__ void rot_scale(T& sc, T& sl, const V* e, V (&A)[1 << RB], V (&L)[1 << RB]) {
   if constexpr (sizeof(V) == 8) {
-    sc *= cs.y;
+    const float c = e[0].y, clo = e[1].x;  // c = c + clo to ~2^-48
+    const float p = sc * c;
+    sl = fmaf(sl, c, fmaf(sc, clo, fmaf(sc, c, -p)));
+    sc = p;
     if (fabsf(sc) < 0x1p-20f) {
-      const float2 s2 = make_float2(sc, sc);
+      // m = 2^floor(log2 |sc|); |sc| >= 2^-80 here, a normal number
+      const float m = __int_as_float(__float_as_int(sc) & 0x7f800000);
+      const float inv = __int_as_float((254 << 23) - __float_as_int(m));  // 1 / m, exact
+      const float2 m2 = make_float2(m, m);
 #pragma unroll
       for (int i = 0; i < (1 << RB); ++i) {
-        A[i] = mul2(s2, A[i]);
-        if (TWO) L[i] = mul2(s2, L[i]);
+        A[i] = mul2(m2, A[i]);
+        if (TWO) L[i] = mul2(m2, L[i]);
       }
-      sc = 1.f;
+      sc *= inv;
+      sl *= inv;
     }
   }
 }
@@ -510,35 +528,36 @@ template <int RB, int MASK, bool ISX, int R0 = 0, int E = 0>
 struct RotM {
   // TWO: rotate A and L alike (non-parametric rotations inside an adjoint pass)
   template <bool TWO, typename V, typename T>
-  __device__ __forceinline__ static void run(V (&A)[1 << RB], V (&L)[1 << RB], const V* t, T& sc) {
+  __device__ __forceinline__ static void run(V (&A)[1 << RB], V (&L)[1 << RB], const V* t, T& sc, T& sl) {
     if constexpr (R0 < RB) {
       if constexpr (((MASK >> R0) & 1) != 0) {
         if constexpr (ISX) {
           g_rx<RB, R0>(A, t[E]);
           if (TWO) g_rx<RB, R0>(L, t[E]);
         } else {
-          g_ry<RB, R0>(A, t[E]);
-          if (TWO) g_ry<RB, R0>(L, t[E]);
-          rot_scale<RB, TWO>(sc, t[E], A, L);
+          g_ry<RB, R0>(A, t[kRYEntries * E]);
+          if (TWO) g_ry<RB, R0>(L, t[kRYEntries * E]);
+          rot_scale<RB, TWO>(sc, sl, t + kRYEntries * E, A, L);
         }
-        RotM<RB, MASK, ISX, R0 + 1, E + 1>::template run<TWO>(A, L, t, sc);
+        RotM<RB, MASK, ISX, R0 + 1, E + 1>::template run<TWO>(A, L, t, sc, sl);
       } else {
-        RotM<RB, MASK, ISX, R0 + 1, E>::template run<TWO>(A, L, t, sc);
+        RotM<RB, MASK, ISX, R0 + 1, E>::template run<TWO>(A, L, t, sc, sl);
       }
     }
   }
   template <typename V, typename T>
-  __device__ __forceinline__ static decltype(V::x) adj(V (&P)[1 << RB], V (&L)[1 << RB], const V* t, T& sc) {
+  __device__ __forceinline__ static decltype(V::x) adj(V (&P)[1 << RB], V (&L)[1 << RB], const V* t, T& sc, T& sl) {
     if constexpr (R0 < RB) {
       if constexpr (((MASK >> R0) & 1) != 0) {
-        decltype(V::x) a = g_adj<RB, R0, ISX>(P, L, t[E], true);
+        decltype(V::x) a = g_adj<RB, R0, ISX>(P, L, t[ISX ? E : kRYEntries * E], true);
         if constexpr (!ISX) {
-          a *= sc * sc;
-          rot_scale<RB, true>(sc, t[E], P, L);
+          const T se = sc + sl;
+          a *= se * se;
+          rot_scale<RB, true>(sc, sl, t + kRYEntries * E, P, L);
         }
-        return a + RotM<RB, MASK, ISX, R0 + 1, E + 1>::adj(P, L, t, sc);
+        return a + RotM<RB, MASK, ISX, R0 + 1, E + 1>::adj(P, L, t, sc, sl);
       } else {
-        return RotM<RB, MASK, ISX, R0 + 1, E>::adj(P, L, t, sc);
+        return RotM<RB, MASK, ISX, R0 + 1, E>::adj(P, L, t, sc, sl);
       }
     } else {
       return 0;
@@ -552,11 +571,11 @@ struct RotM {
   X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31)
 
 template <int RB, bool ISX, bool TWO, typename V, typename T>
-__device__ __forceinline__ void rot_mask(int mask, V (&A)[1 << RB], V (&L)[1 << RB], const V* t, T& sc) {
+__device__ __forceinline__ void rot_mask(int mask, V (&A)[1 << RB], V (&L)[1 << RB], const V* t, T& sc, T& sl) {
   switch (mask) {
 #define TC_ROT_CASE(M) \
   case M:              \
-    if constexpr ((M) < (1 << RB)) RotM<RB, (M), ISX>::template run<TWO>(A, L, t, sc); \
+    if constexpr ((M) < (1 << RB)) RotM<RB, (M), ISX>::template run<TWO>(A, L, t, sc, sl); \
     break;
     TC_MASK_CASES(TC_ROT_CASE)
 #undef TC_ROT_CASE
@@ -566,12 +585,12 @@ __device__ __forceinline__ void rot_mask(int mask, V (&A)[1 << RB], V (&L)[1 << 
 }
 template <int RB, bool ISX, typename V, typename T>
 __device__ __forceinline__ decltype(V::x) rot_mask_adj(int mask, V (&P)[1 << RB], V (&L)[1 << RB], const V* t,
-                                                       T& sc) {
+                                                       T& sc, T& sl) {
   decltype(V::x) acc = 0;
   switch (mask) {
 #define TC_ADJ_CASE(M) \
   case M:              \
-    if constexpr ((M) < (1 << RB)) acc = RotM<RB, (M), ISX>::adj(P, L, t, sc); \
+    if constexpr ((M) < (1 << RB)) acc = RotM<RB, (M), ISX>::adj(P, L, t, sc, sl); \
     break;
     TC_MASK_CASES(TC_ADJ_CASE)
 #undef TC_ADJ_CASE
@@ -888,8 +907,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
   T gl[kLocalSlots];
   if (MODE == KM_BWD)
     for (int g = 0; g < sp.n_gslots && g < kLocalSlots; ++g) gl[g] = 0;
-  // running scale of tangent-form rotations (complex64; stays 1 for complex128)
-  T sc = 1;
+  // running scale sc + sl of tangent-form rotations (complex64; stays 1 for complex128)
+  T sc = 1, sl = 0;
+  auto sq = [](T x) { return x * x; };
   auto add_grad = [&](int slot, T v) {
     if (slot < kLocalSlots) {
       gl[slot] += v;
@@ -950,13 +970,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
           }
         } break;
         case IK_RYM: {
-          rot_mask<RB, false, MODE == KM_BWD>((uint8_t)in.j0, A, L, tab + in.slot, sc);
+          rot_mask<RB, false, MODE == KM_BWD>((uint8_t)in.j0, A, L, tab + in.slot, sc, sl);
         } break;
         case IK_RY: {
           const V cs = tab[in.slot];
           TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(A, cs)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(L, cs)));
-          rot_scale<RB, MODE == KM_BWD>(sc, cs, A, L);
+          rot_scale<RB, MODE == KM_BWD>(sc, sl, tab + in.slot, A, L);
         } break;
         case IK_H:
           if (!LEAN) break;
@@ -1056,7 +1076,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
         } break;
         case IK_RYM_ADJ: {
           if (MODE != KM_BWD) break;
-          const T acc = rot_mask_adj<RB, false>((uint8_t)in.j0, A, L, tab + in.slot, sc);
+          const T acc = rot_mask_adj<RB, false>((uint8_t)in.j0, A, L, tab + in.slot, sc, sl);
           add_grad(in.gslot, acc * (T)in.gscale);
         } break;
         case IK_RXM_ADJ:
@@ -1114,8 +1134,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
               TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, false>(A, L, cs, false)));
             }
           }
-          add_grad(in.gslot, acc * (sc * sc) * (T)in.gscale);
-          if (in.kind == IK_RY_ADJ) rot_scale<RB, true>(sc, tab[in.slot], A, L);
+          add_grad(in.gslot, acc * sq(sc + sl) * (T)in.gscale);
+          if (in.kind == IK_RY_ADJ) rot_scale<RB, true>(sc, sl, tab + in.slot, A, L);
         } break;
         case IK_DIAG_ADJ: {
           if (MODE != KM_BWD) break;
@@ -1138,7 +1158,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
               A[i] = cmul(ph, A[i]);
               L[i] = cmul(ph, L[i]);
             }
-            add_grad(in.gslot, (a2[0] + a2[1]) * (sc * sc) * (T)in.gscale);
+            add_grad(in.gslot, (a2[0] + a2[1]) * sq(sc + sl) * (T)in.gscale);
           } else if (MULTI && !dg.sign_mode) {
             int cnt[R];
             diag_counts_lin<RB>(cnt, m, dg, des);
@@ -1150,7 +1170,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
               A[i] = cmul(ph, A[i]);
               L[i] = cmul(ph, L[i]);
             }
-            add_grad(in.gslot, (a2[0] + a2[1]) * (sc * sc) * (T)in.gscale);
+            add_grad(in.gslot, (a2[0] + a2[1]) * sq(sc + sl) * (T)in.gscale);
           } else if (FULL) {
             T acc = 0;
 #pragma unroll
@@ -1161,7 +1181,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
               A[i] = cmul(ph, A[i]);
               L[i] = cmul(ph, L[i]);
             }
-            add_grad(in.gslot, acc * (sc * sc) * (T)in.gscale);
+            add_grad(in.gslot, acc * sq(sc + sl) * (T)in.gscale);
           }
         } break;
         default:
@@ -1169,8 +1189,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
       }
     }
   }
-  if (sc != (T)1) {
-    const V s2 = mk<V>(sc, sc);
+  if (sc != (T)1 || sl != (T)0) {
+    const T se = sc + sl;
+    const V s2 = mk<V>(se, se);
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       A[i] = cmul_re(s2, A[i]);
