@@ -22,6 +22,7 @@ constexpr int kRBBwdC128 = 4;
 constexpr int kRBHam = 4;       // Pauli-sum passes
 constexpr int kRBMax = 5;
 constexpr int kRYEntries = 2;   // per-row table entries of one RY gate
+constexpr int kHamStageBytes = 48 * 1024;  // Pauli-sum terms a pass stages in shared memory (soft cap)
 constexpr int kLaneBits = 5;    // lowest tile bits mapped to warp lanes
 constexpr int kIOLowBits = 3;   // positions every tile holds: loads and stores move runs of 8 amplitudes
 constexpr int kMinQubits = kRBMax + kLaneBits;  // narrower circuits get idle low qubits
@@ -152,6 +153,8 @@ struct DevHFlip {
   uint32_t f_tile;   // same mask in tile-local bits of its pass
   int32_t term_off, n_terms;
 };
+// staged back to back in shared memory after a double-precision buffer
+static_assert(sizeof(DevHDiag) == 24 && sizeof(DevHTerm) == 16 && sizeof(DevHFlip) == 16, "Pauli-sum layouts");
 
 enum : int32_t {
   PF_INIT = 1,       // forward pass 0: synthesise the initial state instead of loading
@@ -183,6 +186,7 @@ struct DevPass {
   // Hamiltonian passes
   int32_t n_hdiag, hdiag_off;
   int32_t n_hflip, hflip_off;
+  int32_t n_hterm, hterm_off;  // this pass's terms (contiguous), staged in shared memory with its groups
   int32_t epart_index;  // which energy partial this pass writes
 };
 

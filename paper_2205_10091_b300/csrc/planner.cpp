@@ -682,11 +682,16 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
   while (first || n_done < groups.size()) {
     uint32_t tile = io_low;
     std::vector<int> mine;
+    // the pass stages its diagonal entries, groups and terms in shared memory
+    size_t staged = first ? sizeof(DevHDiag) * diag.size() : 0;
     for (size_t g = 0; g < groups.size(); ++g) {
       if (done[g]) continue;
+      const size_t gb = sizeof(DevHFlip) + sizeof(DevHTerm) * groups[g].second.size();
+      if (!mine.empty() && staged + gb > (size_t)kHamStageBytes) continue;
       if (popc(tile | groups[g].first) <= k) {
         tile |= groups[g].first;
         mine.push_back((int)g);
+        staged += gb;
       }
     }
     if (!first && mine.empty()) {
@@ -719,6 +724,7 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
     }
     P.hflip_off = (int)H.hflips.size();
     P.n_hflip = (int)mine.size();
+    P.hterm_off = (int)H.hterms.size();
     for (int g : mine) {
       DevHFlip fl{};
       fl.f = groups[g].first;
@@ -733,6 +739,7 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
       done[g] = true;
       n_done++;
     }
+    P.n_hterm = (int)H.hterms.size() - P.hterm_off;
     P.epart_index = (int)H.passes.size();
     H.passes.push_back(P);
     first = false;

@@ -794,35 +794,67 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
 #pragma unroll
       for (int i = 0; i < R; ++i) L[i] = mk<V>((T)0, (T)0);
     }
+    // the pass's diagonal entries, flip groups and terms, staged in shared memory
+    DevHDiag* hds = (DevHDiag*)(red + nwarps);
+    DevHFlip* hfs = (DevHFlip*)(hds + sp.n_hdiag);
+    DevHTerm* hts = (DevHTerm*)(hfs + sp.n_hflip);
+    {
+      auto stage = [&](void* dst, const void* src, int bytes) {
+        for (int i = tid; i < bytes / 4; i += blockDim.x) ((uint32_t*)dst)[i] = ((const uint32_t*)src)[i];
+      };
+      stage(hds, a.hdiag + sp.hdiag_off, sp.n_hdiag * (int)sizeof(DevHDiag));
+      stage(hfs, a.hflips + sp.hflip_off, sp.n_hflip * (int)sizeof(DevHFlip));
+      stage(hts, a.hterms + sp.hterm_off, sp.n_hterm * (int)sizeof(DevHTerm));
+    }
     smem_write<RB>(A, sm0, m);
     __syncthreads();
     T eacc = 0;
-    for (int e = 0; e < sp.n_hdiag; ++e) {
-      const DevHDiag hd = a.hdiag[sp.hdiag_off + e];
-      const T w = (T)hd.w;
+    {
+      // diagonal terms: the count (or parity) is XOR-linear in the index, so
+      // it is walked in Gray-code order over the registers
+      V e2 = mk<V>((T)0, (T)0);
+      for (int e = 0; e < sp.n_hdiag; ++e) {
+        const DevHDiag hd = hds[e];
+        const T w = (T)hd.w;
+        const uint32_t dd = hd.cnt < 0 ? 0u : hd.d;
+        auto op = [&](uint32_t x) { return (dd == 0 ? x : (x ^ (x >> dd))) & hd.mask; };
+        uint32_t v = op(m.g);
+        uint32_t vr[RB];
 #pragma unroll
-      for (int i = 0; i < R; ++i) {
-        const uint32_t x = m.g | offg(m, i);
-        T h;
+        for (int r = 0; r < RB; ++r) vr[r] = op(m.ro[r]);
         if (hd.cnt < 0) {
-          h = (__popc(x & hd.mask) & 1) ? -w : w;
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            if (j) v ^= vr[low_bit(j)];
+            const int i = j ^ (j >> 1);
+            const T h = (__popc(v) & 1) ? -w : w;
+            const V h2 = mk<V>(h, h);
+            L[i] = cfma2(h2, A[i], L[i]);
+            e2 = cfma2(cmul_re(h2, A[i]), A[i], e2);
+          }
         } else {
-          const uint32_t v = hd.d == 0 ? x : (x ^ (x >> hd.d));
-          h = w * (T)(hd.cnt - 2 * __popc(v & hd.mask));
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            if (j) v ^= vr[low_bit(j)];
+            const int i = j ^ (j >> 1);
+            const T h = w * (T)(hd.cnt - 2 * __popc(v));
+            const V h2 = mk<V>(h, h);
+            L[i] = cfma2(h2, A[i], L[i]);
+            e2 = cfma2(cmul_re(h2, A[i]), A[i], e2);
+          }
         }
-        L[i].x = fma(h, A[i].x, L[i].x);
-        L[i].y = fma(h, A[i].y, L[i].y);
-        eacc = fma(h, fma(A[i].x, A[i].x, A[i].y * A[i].y), eacc);
       }
+      eacc = e2.x + e2.y;
     }
     // swizzled tile offsets of the register bits (the swizzle is XOR-linear)
     uint32_t srt[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) srt[r] = swz<V>(m.rt[r]);
     for (int g = 0; g < sp.n_hflip; ++g) {
-      const DevHFlip fl = a.hflips[sp.hflip_off + g];
+      const DevHFlip fl = hfs[g];
+      const DevHTerm* tt0 = hts + (fl.term_off - sp.hterm_off);
       if (fl.n_terms == 1) {
-        const DevHTerm ht = a.hterms[fl.term_off];
+        const DevHTerm ht = tt0[0];
         const T w = (T)ht.w;
         if (ht.sm == 0 && ht.ny == 0) {
           // X string: (P psi)_x = w psi_{x ^ f}; partner index walked in Gray-code order
@@ -860,7 +892,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
         const V pp = sm0[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
         T hr = 0, hi = 0;
         for (int q = 0; q < fl.n_terms; ++q) {
-          const DevHTerm ht = a.hterms[fl.term_off + q];
+          const DevHTerm ht = tt0[q];
           const T w = (__popc(xp & ht.sm) & 1) ? -(T)ht.w : (T)ht.w;
           if (ht.ny == 0) hr += w;
           else if (ht.ny == 1) hi += w;
@@ -1246,7 +1278,9 @@ size_t pass_smem_bytes(int mode, bool dbl, const DevPass& p) {
   if (mode != KM_HAM) b += (size_t)p.n_stages * sizeof(DevStage);
   b += (size_t)((p.n_dent + 1) & ~1) * sizeof(DevDiagEnt);
   if (mode == KM_BWD) b += (size_t)p.n_gslots * nwarps * 8;
-  if (mode == KM_HAM) b += (size_t)nwarps * 8;
+  if (mode == KM_HAM)
+    b += (size_t)nwarps * 8 + (size_t)p.n_hdiag * sizeof(DevHDiag) + (size_t)p.n_hflip * sizeof(DevHFlip) +
+         (size_t)p.n_hterm * sizeof(DevHTerm);
   return b + 16;
 }
 
