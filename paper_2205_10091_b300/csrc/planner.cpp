@@ -166,7 +166,8 @@ uint32_t item_need(const Item& it, const std::vector<HGate>& gates, const int* t
 
 // Merge each run of consecutive RX instructions (or adjoint RX steps with one
 // shared gradient slot and scale) on distinct register bits into one multi-bit
-// instruction.  RX gates on different qubits commute, and Im<lam|X_q|psi> is
+// instruction; RY always becomes the multi-bit form (a run of one included),
+// so the kernels carry one RY code path.  RX gates on different qubits commute, and Im<lam|X_q|psi> is
 // unchanged by RX on other qubits, so the run may be reordered by bit index.
 // Their per-row table entries are moved so that bit r reads entry
 // slot + stride * rank(r) (rank among the run's bits; RY has kRYEntries
@@ -192,7 +193,7 @@ void merge_rx_runs(PlanArrays& A, int first, int rb, int table_base) {
       mask |= 1u << A.instrs[j].j0;
       ++j;
     }
-    if (j - i < 2) {
+    if (j - i < 2 && !isy) {
       out.push_back(in0);
       ++i;
       continue;
@@ -538,6 +539,8 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
               in.kind = rx ? IK_RX_ADJ : IK_RY_ADJ;
               in.gslot = (int16_t)slot_of(g.param);
               in.gscale = (float)g.scale;
+            } else if (adjoint && !rx) {
+              in.kind = IK_RY_ADJ;  // fixed angle: uncompute only (no gradient slot)
             } else {
               in.kind = rx ? IK_RX : IK_RY;
             }

@@ -483,14 +483,6 @@ __device__ __forceinline__ decltype(V::x) g_adj(V (&P)[1 << RB], V (&L)[1 << RB]
   return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
-// Adjoint step of RY: sum over pairs of Im<lam|Y|psi> = (l1 . p0) - (l0 . p1)
-// (two packed accumulators for complex64, four scalar ones for complex128),
-// then RY(-a) on psi and lam (the table holds the adjoint's entry).
-template <int RB, int J, typename V>
-__device__ __forceinline__ decltype(V::x) g_ry_adj(V (&P)[1 << RB], V (&L)[1 << RB], V cs) {
-  return g_adj<RB, J, false>(P, L, cs, true);
-}
-
 // Running scale of complex64 tangent-form RY: every such gate multiplies the
 // true state by c = cs.y on top of what the registers hold.  The scale is a
 // compensated product sc + sl (the rounding error of each sc * c is carried in
@@ -1002,13 +994,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
           }
         } break;
         case IK_RYM: {
-          rot_mask<RB, false, MODE == KM_BWD>((uint8_t)in.j0, A, L, tab + in.slot, sc, sl);
-        } break;
-        case IK_RY: {
-          const V cs = tab[in.slot];
-          TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(A, cs)));
-          if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_ry<RB, J>(L, cs)));
-          rot_scale<RB, MODE == KM_BWD>(sc, sl, tab + in.slot, A, L);
+          // adjoint passes carry fixed-angle RY as IK_RYM_ADJ without a gradient slot
+          if (MODE != KM_FWD) break;
+          rot_mask<RB, false, false>((uint8_t)in.j0, A, L, tab + in.slot, sc, sl);
         } break;
         case IK_H:
           if (!LEAN) break;
@@ -1109,17 +1097,16 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
         case IK_RYM_ADJ: {
           if (MODE != KM_BWD) break;
           const T acc = rot_mask_adj<RB, false>((uint8_t)in.j0, A, L, tab + in.slot, sc, sl);
-          add_grad(in.gslot, acc * (T)in.gscale);
+          if (in.gslot >= 0) add_grad(in.gslot, acc * (T)in.gscale);
         } break;
         case IK_RXM_ADJ:
         case IK_GRADDIAG:
         case IK_RX_ADJ:
-        case IK_RY_ADJ:
         case IK_GRADX:
         case IK_GRADY: {
           if (MODE != KM_BWD) break;
           T acc = 0;
-          if (!LEAN && in.kind != IK_RY_ADJ) break;
+          if (!LEAN) break;
           if (in.kind == IK_RXM_ADJ) {
             const uint32_t mask = (uint8_t)in.j0;
             int e = 0;
@@ -1156,18 +1143,15 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
               }
             }
           } else {
-            const bool upd = in.kind == IK_RX_ADJ || in.kind == IK_RY_ADJ;
+            const bool upd = in.kind == IK_RX_ADJ;
             const V cs = upd ? tab[in.slot] : mk<V>((T)1, (T)0);
             if (in.kind == IK_RX_ADJ || in.kind == IK_GRADX) {
               TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, true>(A, L, cs, upd)));
-            } else if (upd) {
-              TC_DISPATCH_J(RB, in.j0, (acc = g_ry_adj<RB, J>(A, L, cs)));
             } else {
               TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, false>(A, L, cs, false)));
             }
           }
           add_grad(in.gslot, acc * sq(sc + sl) * (T)in.gscale);
-          if (in.kind == IK_RY_ADJ) rot_scale<RB, true>(sc, sl, tab + in.slot, A, L);
         } break;
         case IK_DIAG_ADJ: {
           if (MODE != KM_BWD) break;
