@@ -38,19 +38,18 @@ enum : int8_t {
   IK_DIAG = 3,      // diagonal group `slot` (phases from the full index)
   IK_GRADDIAG = 4,  // gslot += gscale * Im <lam|G|psi>, G(x) = T - 2 m(x) of group `slot`
   IK_RX = 5,        // RX: table[slot] = (c, s), a0' = c a0 - i s a1, a1' = c a1 - i s a0
-  IK_RY = 6,        // RY: table[slot] = (c, s), a0' = c a0 - s a1, a1' = s a0 + c a1
+  IK_RY = 6,        // RY a0' = c a0 - s a1, a1' = s a0 + c a1 (planner-internal: emitted as IK_RYM)
   IK_H = 7,
   IK_X = 8,
   IK_PAULI = 9,     // noise outcome: table[slot].x = 0,1,2,3 (I, X, Y, Z)
   IK_RX_ADJ = 10,   // adjoint step of RX: gslot += gscale*Im<lam|X|psi>; then RX(-a) on psi, lam
-  IK_RY_ADJ = 11,   // same for RY
-  IK_GRADX = 12,    // gslot += gscale * Im <lam|X_j0|psi> (no update)
-  IK_GRADY = 13,
+  IK_RY_ADJ = 11,   // same for RY (planner-internal: emitted as IK_RYM_ADJ)
+  // 12, 13: unused
   IK_RXM = 14,      // RX on several register bits: j0 = bit mask, entry of bit r = slot + rank of r in mask
   IK_RXM_ADJ = 15,  // adjoint of IK_RXM: all bits share gslot/gscale
   IK_DIAG_ADJ = 16, // IK_GRADDIAG then IK_DIAG of the same group, fused
-  IK_RYM = 17,      // RY on several register bits (layout as IK_RXM)
-  IK_RYM_ADJ = 18,  // adjoint of IK_RYM
+  IK_RYM = 17,      // RY on the register bits of mask j0; bit r's kRYEntries entries at slot + kRYEntries * rank
+  IK_RYM_ADJ = 18,  // adjoint of IK_RYM (gslot < 0: a fixed-angle rotation, uncompute only)
 };
 
 constexpr int kLocalSlots = 32;  // gradient slots a pass accumulates per thread before one reduction

@@ -1101,9 +1101,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
         } break;
         case IK_RXM_ADJ:
         case IK_GRADDIAG:
-        case IK_RX_ADJ:
-        case IK_GRADX:
-        case IK_GRADY: {
+        case IK_RX_ADJ: {
           if (MODE != KM_BWD) break;
           T acc = 0;
           if (!LEAN) break;
@@ -1143,13 +1141,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
               }
             }
           } else {
-            const bool upd = in.kind == IK_RX_ADJ;
-            const V cs = upd ? tab[in.slot] : mk<V>((T)1, (T)0);
-            if (in.kind == IK_RX_ADJ || in.kind == IK_GRADX) {
-              TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, true>(A, L, cs, upd)));
-            } else {
-              TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, false>(A, L, cs, false)));
-            }
+            const V cs = tab[in.slot];
+            TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, true>(A, L, cs, true)));
           }
           add_grad(in.gslot, acc * sq(sc + sl) * (T)in.gscale);
         } break;
