@@ -1,4 +1,5 @@
 // C-ABI entry points of libtc_b300.so (declared in include/tc.h).
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -463,7 +464,14 @@ tc_status tc_expect_pauli_sum(tc_circuit* c, const void* d_states, int B, const 
   const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
   const int nh = (int)c->H.passes.size();
   const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
-  const size_t epb = (size_t)nh * tiles_h * 8;
+  // few rows x tiles: split each pass's flip groups over several blocks
+  // (~4 blocks per SM in all, at least two groups each), each adding its own
+  // energy partial
+  int max_flips = 1;
+  for (const auto& P : c->H.passes) max_flips = std::max(max_flips, P.n_hflip);
+  const int64_t blocks = (int64_t)B * (int64_t)tiles_h;
+  const int hch = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)max_flips / 2, 256, 592 / std::max<int64_t>(blocks, 1)}));
+  const size_t epb = (size_t)nh * hch * tiles_h * 8;
   int chunk = B;
   if (padded) chunk = (int)std::min<int64_t>(B, std::max<int64_t>(1, (int64_t)(256u << 20) / (int64_t)per));
   else chunk = (int)std::min<int64_t>(B, std::max<int64_t>(1, (int64_t)(256u << 20) / (int64_t)epb));
@@ -484,8 +492,9 @@ tc_status tc_expect_pauli_sum(tc_circuit* c, const void* d_states, int B, const 
     }
     a.lam = nullptr;
     a.epart = epart;
+    a.hchunks = hch;
     if ((st = run_ham(c, a, rows, false, s)) != TC_OK) return st;
-    TC_CHECK_CUDA(launch_finalize(epart, nh, (int)tiles_h, nullptr, 0, 1, c->d_csr_off, c->d_csr_slots, 0, rows,
+    TC_CHECK_CUDA(launch_finalize(epart, nh * hch, (int)tiles_h, nullptr, 0, 1, c->d_csr_off, c->d_csr_slots, 0, rows,
                                   d_energy_out + r0, nullptr, s),
                   "finalize");
   }

@@ -786,17 +786,29 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
 #pragma unroll
       for (int i = 0; i < R; ++i) L[i] = mk<V>((T)0, (T)0);
     }
-    // the pass's diagonal entries, flip groups and terms, staged in shared memory
+    // energy-only calls split the pass's flip groups over gridDim.y blocks;
+    // the diagonal terms go to the first of them
+    const int nch = gridDim.y, ch = blockIdx.y;
+    const int g_lo = (int)(((long long)sp.n_hflip * ch) / nch), g_hi = (int)(((long long)sp.n_hflip * (ch + 1)) / nch);
+    // this block's diagonal entries, flip groups and their terms (contiguous),
+    // staged in shared memory
+    const int n_diag_here = ch == 0 ? sp.n_hdiag : 0;
+    int term_lo = 0, term_hi = 0;
+    if (g_hi > g_lo) {
+      term_lo = a.hflips[sp.hflip_off + g_lo].term_off;
+      const DevHFlip last = a.hflips[sp.hflip_off + g_hi - 1];
+      term_hi = last.term_off + last.n_terms;
+    }
     DevHDiag* hds = (DevHDiag*)(red + nwarps);
-    DevHFlip* hfs = (DevHFlip*)(hds + sp.n_hdiag);
-    DevHTerm* hts = (DevHTerm*)(hfs + sp.n_hflip);
+    DevHFlip* hfs = (DevHFlip*)(hds + n_diag_here);
+    DevHTerm* hts = (DevHTerm*)(hfs + (g_hi - g_lo));
     {
       auto stage = [&](void* dst, const void* src, int bytes) {
         for (int i = tid; i < bytes / 4; i += blockDim.x) ((uint32_t*)dst)[i] = ((const uint32_t*)src)[i];
       };
-      stage(hds, a.hdiag + sp.hdiag_off, sp.n_hdiag * (int)sizeof(DevHDiag));
-      stage(hfs, a.hflips + sp.hflip_off, sp.n_hflip * (int)sizeof(DevHFlip));
-      stage(hts, a.hterms + sp.hterm_off, sp.n_hterm * (int)sizeof(DevHTerm));
+      stage(hds, a.hdiag + sp.hdiag_off, n_diag_here * (int)sizeof(DevHDiag));
+      stage(hfs, a.hflips + sp.hflip_off + g_lo, (g_hi - g_lo) * (int)sizeof(DevHFlip));
+      stage(hts, a.hterms + term_lo, (term_hi - term_lo) * (int)sizeof(DevHTerm));
     }
     smem_write<RB>(A, sm0, m);
     __syncthreads();
@@ -805,7 +817,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
       // diagonal terms: the count (or parity) is XOR-linear in the index, so
       // it is walked in Gray-code order over the registers
       V e2 = mk<V>((T)0, (T)0);
-      for (int e = 0; e < sp.n_hdiag; ++e) {
+      for (int e = 0; e < n_diag_here; ++e) {
         const DevHDiag hd = hds[e];
         const T w = (T)hd.w;
         const uint32_t dd = hd.cnt < 0 ? 0u : hd.d;
@@ -842,9 +854,9 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
     uint32_t srt[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) srt[r] = swz<V>(m.rt[r]);
-    for (int g = 0; g < sp.n_hflip; ++g) {
+    for (int g = 0; g < g_hi - g_lo; ++g) {
       const DevHFlip fl = hfs[g];
-      const DevHTerm* tt0 = hts + (fl.term_off - sp.hterm_off);
+      const DevHTerm* tt0 = hts + (fl.term_off - term_lo);
       if (fl.n_terms == 1) {
         const DevHTerm ht = tt0[0];
         const T w = (T)ht.w;
@@ -898,14 +910,14 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
         eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
       }
     }
-    if ((sp.flags & PF_LAM_STORE) && lam && a.store_lambda) store_regs<RB>(L, lam, m);
+    if ((sp.flags & PF_LAM_STORE) && lam && a.store_lambda && nch == 1) store_regs<RB>(L, lam, m);
     const double ws = warp_sum(eacc);
     if (lane == 0) red[warp] = ws;
     __syncthreads();
     if (tid == 0) {
       double s = 0;
       for (int w = 0; w < nwarps; ++w) s += red[w];
-      a.epart[((size_t)row * a.n_hpasses + sp.epart_index) * (1u << sp.nfix) + tile] = s;
+      a.epart[(((size_t)row * a.n_hpasses + sp.epart_index) * nch + ch) * (1u << sp.nfix) + tile] = s;
     }
     return;
   }
@@ -1284,7 +1296,9 @@ static cudaError_t launch_tf(const KArgs& a, const PassArgs& pa, int rows, cudaS
   const size_t blocks = (size_t)rows << hp.nfix;
   if (blocks == 0) return cudaSuccess;
   if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-  k_pass<T, MODE, RB, VAR><<<(unsigned)blocks, threads, smem, s>>>(a, pa);
+  const unsigned chunks = (MODE == KM_HAM && a.hchunks > 1) ? (unsigned)a.hchunks : 1u;
+  if (chunks > 65535u) return cudaErrorInvalidConfiguration;
+  k_pass<T, MODE, RB, VAR><<<dim3((unsigned)blocks, chunks), threads, smem, s>>>(a, pa);
   return cudaGetLastError();
 }
 

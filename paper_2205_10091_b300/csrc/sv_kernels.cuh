@@ -45,6 +45,10 @@ struct KArgs {
   // per-row gate tables (built by launch_tables) and their row stride (entries)
   const void* tables;
   int table_stride;
+  // Pauli-sum passes of an energy-only call: the flip groups of a pass are
+  // split over hchunks blocks per tile (blockIdx.y), each writing its own
+  // energy partial; 0 or 1 = one block per tile (required when lambda is kept)
+  int hchunks;
 };
 
 // The pass descriptor and its first stage, passed by value as a kernel

@@ -316,6 +316,45 @@ def random_pauli_sum(n: int, n_terms: int, rng: np.random.Generator) -> PauliSum
     return PauliSum(s, w)
 
 
+def chem_pauli_sum(n: int = 12, n_terms: int = 1390, seed: int = 1006) -> PauliSum:
+    """A chemistry-shaped Pauli sum with the structure of a Jordan-Wigner
+    molecular Hamiltonian (the paper's H2O example has 12 qubits and 1390
+    terms; its data is not used here): Z_p and Z_p Z_q terms, hopping terms
+    X_p Z..Z X_q and Y_p Z..Z Y_q, and four-body terms O_p Z..Z O_q O_r Z..Z O_s
+    with O in {X, Y} and an even number of Y (a real Hamiltonian).  Weights are
+    N(0, 1) with a decaying envelope, largest for the one-body terms."""
+    rng = np.random.default_rng(seed)
+    terms = []
+
+    def zs(a, b):
+        return {k: 3 for k in range(a + 1, b)}
+
+    for p_ in range(n):
+        terms.append({p_: 3})
+    for p_ in range(n):
+        for q in range(p_ + 1, n):
+            terms.append({p_: 3, q: 3})
+    for p_ in range(n):
+        for q in range(p_ + 1, n):
+            for o in (1, 2):
+                d = zs(p_, q)
+                d[p_] = o
+                d[q] = o
+                terms.append(d)
+    quads = [(a, b, c, d) for a in range(n) for b in range(a + 1, n) for c in range(b + 1, n) for d in range(c + 1, n)]
+    pats = [(1, 1, 1, 1), (2, 2, 2, 2), (1, 1, 2, 2), (2, 2, 1, 1), (1, 2, 1, 2), (2, 1, 2, 1), (1, 2, 2, 1), (2, 1, 1, 2)]
+    cand = [(qd, pt) for qd in quads for pt in pats]
+    pick = rng.choice(len(cand), size=max(0, n_terms - len(terms)), replace=False)
+    for i in sorted(pick):
+        (a, b, c, d), (oa, ob, oc, od) = cand[i]
+        t = zs(a, b)
+        t.update(zs(c, d))
+        t.update({a: oa, b: ob, c: oc, d: od})
+        terms.append(t)
+    w = rng.standard_normal(len(terms)) * np.exp(-np.arange(len(terms)) / 400.0)
+    return pauli_sum(n, [(float(wi), t) for wi, t in zip(w, terms[:n_terms])])
+
+
 def brickwork_u4(n: int, depth: int, rng: np.random.Generator, round_c64: bool = True
                  ) -> list[tuple[int, int, np.ndarray]]:
     """1D brickwork of Haar U(4): layer 0 acts on pairs (2i, 2i+1), layer 1 on
