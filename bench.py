@@ -404,6 +404,20 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
         "z0": [float(x) for x in ests[0].tolist()], "sum_zz": [float(x) for x in ests[1].tolist()]}
     del sts
     torch.cuda.synchronize()
+    # ---- many-term Pauli sum: 12-qubit, 1390-term chemistry-shaped H ------
+    hc = W.chem_pauli_sum(12)
+    Hc = nt.Hamiltonian(hc)
+    cc = nt.Circuit(W.OpBuilder(12).build())
+    rngc = np.random.default_rng(1006)
+    chem = {"terms": int(hc.n_terms), "qubits": 12}
+    for Bc in (1, 1024):
+        xs = rngc.standard_normal((Bc, 1 << 12)) + 1j * rngc.standard_normal((Bc, 1 << 12))
+        xs /= np.linalg.norm(xs, axis=1, keepdims=True)
+        stc = torch.as_tensor(xs.astype(np.complex64), device="cuda")
+        ec = torch.empty(Bc, dtype=torch.float64, device="cuda")
+        msc = _time_cuda(lambda: cc.expect(stc, Hc, out=ec), 50 if Bc == 1 else 10)
+        chem[f"b{Bc}"] = {"us_per_call": msc * 1e3, "states_per_s": Bc / (msc / 1e3)}
+    out["chem12_pauli_sum"] = chem
     # ---- QAOA serving: Poisson arrivals, continuous admission ---------------
     serv = {}
     for rate in serve_rates:
