@@ -239,6 +239,35 @@ TC_API tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, c
                           void* stream);
 
 /*
+ * tc_dm_circuit_create — a density-matrix circuit (Section "Density matrix
+ * simulator"): the same op list acts on rho by U rho U^dagger and by exact
+ * Pauli channels rho -> (1-px-py-pz) rho + px X rho X + py Y rho Y + pz Z rho Z
+ * (the Kraus form of Section "Noisy circuits"; nothing is sampled).  rho is
+ * held vectorised as a 2n-qubit state |rho>> = sum_xy rho_xy |x>|y> (row index
+ * x on the first n qubits): each gate U becomes U on qubit q and conj(U) on
+ * qubit n + q, and each channel a 4x4 superoperator on (q, n + q).
+ *   n_qubits  1..15 (the state holds 4^n amplitudes)
+ *   other arguments as tc_circuit_create; init |0..0> gives rho = |0..0><0..0|,
+ *   TC_INIT_PLUS gives |+..+><+..+|
+ * The returned circuit works with tc_apply_layers (d_states_out: [B][4^n]
+ * entries of the dtype, rho_xy at x * 2^n + y; d_init, seed and d_status are
+ * ignored for channels) and tc_dm_expect_pauli_sum; tc_circuit_info reports
+ * the 2n-qubit plan.  Errors as tc_circuit_create.
+ */
+TC_API tc_status tc_dm_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc_op* ops, int n_ops,
+                                      int n_params, const double* pool, int n_pool, const tc_options* opt,
+                                      tc_circuit** out);
+
+/*
+ * tc_dm_expect_pauli_sum — d_out[b] = tr(rho_b H), H = sum_t w_t P_t over the
+ * circuit's n qubits (structures as tc_expect_pauli_sum), for B vectorised
+ * density matrices d_rho ([B][4^n], the circuit's dtype, device).  FP64
+ * accumulation.  TC_E_INVALID if c was not made by tc_dm_circuit_create.
+ */
+TC_API tc_status tc_dm_expect_pauli_sum(tc_circuit* c, const void* d_rho, int B, const uint8_t* structures,
+                                        const double* weights, int T, double* d_out, void* stream);
+
+/*
  * tc_mean_stderr — d_out[0] = mean of d_x[0..n), d_out[1] = its standard
  * error (sample standard deviation with ddof = 1, over sqrt(n)), in FP64 with
  * a fixed-order reduction: the Monte Carlo estimate over trajectories

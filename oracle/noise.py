@@ -89,13 +89,15 @@ def estimate(values: np.ndarray):
     return mean, se
 
 
-def density_matrix(circ: W.Circuit) -> np.ndarray:
+def density_matrix(circ: W.Circuit, theta=None) -> np.ndarray:
     """rho after the circuit, channels applied as sum_i K_i rho K_i^dagger
-    with K = sqrt(1-px-py-pz) I, sqrt(px) X, sqrt(py) Y, sqrt(pz) Z."""
+    with K = sqrt(1-px-py-pz) I, sqrt(px) X, sqrt(py) Y, sqrt(pz) Z; gates
+    with a parameter take theta[param] * scale as in run_circuit (theta =
+    None: all parameters 0)."""
     n = circ.n
     psi0 = sv.initial_state(n, circ.init)
     rho = np.outer(psi0, psi0.conj())
-    theta = np.zeros(max(circ.n_params, 1))
+    theta = np.zeros(max(circ.n_params, 1)) if theta is None else np.asarray(theta, dtype=np.float64)
 
     def conj_apply(rho, q, m, q1=None):
         # rho -> M rho M^dagger: apply M to the column index of rho (rows are

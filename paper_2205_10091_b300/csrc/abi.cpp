@@ -4,6 +4,7 @@
 #include <string>
 #include <vector>
 
+#include "dm.h"
 #include "engine.h"
 
 namespace tcb {
@@ -389,6 +390,58 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
 }
 
 void tc_circuit_destroy(tc_circuit* c) { delete c; }
+
+tc_status tc_dm_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc_op* ops, int n_ops,
+                               int n_params, const double* pool, int n_pool, const tc_options* opt,
+                               tc_circuit** out) {
+  if (!out) return fail(TC_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1 || 2 * n_qubits > kMaxQubits) return fail(TC_E_INVALID, "n_qubits must be in 1..15");
+  if (n_ops < 0 || (n_ops > 0 && !ops)) return fail(TC_E_INVALID, "ops is NULL");
+  if (n_pool < 0 || (n_pool > 0 && !pool)) return fail(TC_E_INVALID, "pool is NULL");
+  std::vector<tc_op> dops;
+  std::vector<double> dpool;
+  std::string err;
+  if (!build_dm_ops(n_qubits, ops, n_ops, pool, n_pool, dops, dpool, err)) return fail(TC_E_INVALID, err);
+  const tc_status st = tc_circuit_create(2 * n_qubits, dtype, init, dops.empty() ? nullptr : dops.data(),
+                                         (int)dops.size(), n_params, dpool.empty() ? nullptr : dpool.data(),
+                                         (int)(dpool.size() / 2), opt, out);
+  if (st == TC_OK) (*out)->dm_n = n_qubits;
+  return st;
+}
+
+tc_status tc_dm_expect_pauli_sum(tc_circuit* c, const void* d_rho, int B, const uint8_t* structures,
+                                 const double* weights, int T, double* d_out, void* stream) {
+  if (!c || !d_rho || !d_out) return fail(TC_E_INVALID, "NULL argument");
+  if (c->dm_n <= 0) return fail(TC_E_INVALID, "not a density-matrix circuit (tc_dm_circuit_create)");
+  if (B < 0 || T < 0 || (T > 0 && (!structures || !weights))) return fail(TC_E_INVALID, "bad Pauli sum or B");
+  if (B == 0) return TC_OK;
+  std::vector<DmTerm> terms;
+  std::string err;
+  if (!build_dm_terms(c->dm_n, structures, weights, T, terms, err)) return fail(TC_E_INVALID, err);
+  if (terms.empty()) terms.push_back(DmTerm{});  // H = 0: one zero-weight identity term
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = c->dm_n;
+  const int nblk = std::max(1, std::min(64, (1 << n) / 256));
+  const int chunk = std::min(B, 65535);
+  const size_t tb = (terms.size() * sizeof(DmTerm) + 255) & ~(size_t)255;
+  tc_status st = ensure_ws(c, tb + (size_t)chunk * nblk * sizeof(double));
+  if (st != TC_OK) return st;
+  DmTerm* d_terms = (DmTerm*)c->ws;
+  double* partial = (double*)((char*)c->ws + tb);
+  TC_CHECK_CUDA(cudaMemcpyAsync(d_terms, terms.data(), terms.size() * sizeof(DmTerm), cudaMemcpyHostToDevice, s),
+                "term upload");
+  const size_t rb = ((size_t)1 << (2 * n)) * amp_bytes(c);
+  for (int r0 = 0; r0 < B; r0 += chunk) {
+    const int rows = std::min(chunk, B - r0);
+    TC_CHECK_CUDA(launch_dm_trace(is_dbl(c), (const char*)d_rho + (size_t)r0 * rb, n, rows, d_terms,
+                                  (int)terms.size(), partial, nblk, s),
+                  "density-matrix trace");
+    TC_CHECK_CUDA(launch_finalize(partial, nblk, 1, nullptr, 0, 1, nullptr, nullptr, 0, rows, d_out + r0, nullptr, s),
+                  "finalize");
+  }
+  return TC_OK;
+}
 
 tc_status tc_circuit_info(const tc_circuit* c, tc_plan_info* o) {
   if (!c || !o) return fail(TC_E_INVALID, "NULL argument");

@@ -64,6 +64,7 @@ tc_status place_plan_and_ham(tc_circuit* c, const HamPlan& H, char* base, cudaSt
 
 struct tc_circuit {
   int n = 0, N = 0;
+  int dm_n = 0;  // density-matrix circuit: qubits of rho (n = 2 dm_n); 0 otherwise
   tc_dtype dtype = TC_C64;
   tc_init init = TC_INIT_ZERO;
   int n_ops = 0, n_params = 0, n_noise = 0;

@@ -118,6 +118,10 @@ SIGNATURES = {
     "tc_circuit_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                     C.c_void_p, C.POINTER(C.c_void_p)]),
     "tc_circuit_destroy": (None, [C.c_void_p]),
+    "tc_dm_circuit_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                       C.c_void_p, C.POINTER(C.c_void_p)]),
+    "tc_dm_expect_pauli_sum": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                         C.c_void_p]),
     "tc_circuit_info": (C.c_int, [C.c_void_p, C.POINTER(tc_plan_info)]),
     "tc_apply_layers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64,
                                   C.c_void_p, C.c_void_p]),
@@ -302,6 +306,36 @@ class Circuit:
         s, w, T = ham.args()
         _check(lib().tc_expect_plain(self.h, _ptr(params), B, s, w, T, _ptr(work), _ptr(energy), _stream(stream)))
         return energy
+
+
+class DensityMatrixCircuit(Circuit):
+    """A tc_dm_circuit_create handle: rho under the circuit's gates and exact
+    Pauli channels, held as [B][4^n] vectorised density matrices."""
+
+    def __init__(self, circ: W.Circuit, dtype: int = TC_C64):
+        self.circ = circ
+        self.n = 2 * circ.n  # qubits of the vectorised state (apply() returns [B][4^n])
+        self.n_rho = circ.n
+        self.dtype = dtype
+        self.n_params = circ.n_params
+        ops = np.ascontiguousarray(circ.ops, dtype=W.OP_DTYPE)
+        pool = np.ascontiguousarray(np.stack([circ.pool.real, circ.pool.imag], -1).ravel(), dtype=np.float64)
+        h = C.c_void_p()
+        _check(lib().tc_dm_circuit_create(circ.n, dtype, circ.init, ops.ctypes.data_as(C.c_void_p), len(ops),
+                                          circ.n_params, pool.ctypes.data_as(C.c_void_p) if len(circ.pool) else None,
+                                          len(circ.pool), None, C.byref(h)))
+        self.h = h
+
+    def expect(self, rho, ham: Hamiltonian, out=None, stream=None):
+        """tr(rho_b H) for every row of rho ([B][4^n])."""
+        import torch
+
+        B = rho.shape[0]
+        if out is None:
+            out = torch.empty(B, dtype=torch.float64, device="cuda")
+        s, w, T = ham.args()
+        _check(lib().tc_dm_expect_pauli_sum(self.h, _ptr(rho), B, s, w, T, _ptr(out), _stream(stream)))
+        return out
 
 
 class LightCone:
