@@ -404,6 +404,25 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
         "z0": [float(x) for x in ests[0].tolist()], "sum_zz": [float(x) for x in ests[1].tolist()]}
     del sts
     torch.cuda.synchronize()
+    # ---- exact density matrix of a 12-qubit noisy circuit --------------------
+    ndm, ldm = 12, 12
+    cdm = W.noisy_su2_cz_circuit(ndm, ldm, 0.01, np.random.default_rng(1007))
+    dmc = nt.DensityMatrixCircuit(cdm)
+    rho = torch.empty((1, 1 << (2 * ndm)), dtype=torch.complex64, device="cuda")
+    obs_dm = [nt.Hamiltonian(W.pauli_sum(ndm, [(1.0, {0: 3})])),
+              nt.Hamiltonian(W.pauli_sum(ndm, [(1.0, {i: 3, i + 1: 3}) for i in range(ndm - 1)]))]
+    vals_dm = [torch.empty(1, dtype=torch.float64, device="cuda") for _ in obs_dm]
+
+    def dm_run():
+        dmc.apply(None, 1, out=rho)
+        for H, v in zip(obs_dm, vals_dm):
+            dmc.expect(rho, H, out=v)
+
+    ms_dm = _time_cuda(dm_run, 20)
+    out["dm12_noisy_exact"] = {"ms_per_run": ms_dm, "qubits": ndm, "layers": ldm, "p": 0.01,
+                               "z0": float(vals_dm[0].item()), "sum_zz": float(vals_dm[1].item()),
+                               "plan": {k: v for k, v in dmc.info().items() if k in ("fwd_passes", "fwd_stages")}}
+    del rho
     # ---- many-term Pauli sum: 12-qubit, 1390-term chemistry-shaped H ------
     hc = W.chem_pauli_sum(12)
     Hc = nt.Hamiltonian(hc)
