@@ -367,6 +367,22 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
   c->gates_orig = c->gates;
   if (dtype == TC_C64) c->gates = rewrite_rx_frames(c->gates, c->N);
   c->pool.assign(pool, pool + 2 * (size_t)n_pool);
+  // 4x4 matrices of the Pauli-channel superoperator shape (real, two symmetric
+  // 2x2 blocks on (00, 11) and (01, 10); density-matrix circuits make them)
+  // run as two real 2x2 blocks instead of a dense complex 4x4
+  auto channel_shaped = [&](int off) {
+    auto re = [&](int r, int col) { return c->pool[2 * ((size_t)off + 4 * r + col)]; };
+    for (int e = 0; e < 16; ++e)
+      if (c->pool[2 * ((size_t)off + e) + 1] != 0.0) return false;
+    for (int r = 0; r < 4; ++r)
+      for (int col = 0; col < 4; ++col) {
+        const bool block = (r == col) || (r + col == 3);
+        if (!block && re(r, col) != 0.0) return false;
+      }
+    return re(0, 0) == re(3, 3) && re(0, 3) == re(3, 0) && re(1, 1) == re(2, 2) && re(1, 2) == re(2, 1);
+  };
+  for (auto& g : c->gates)
+    if (g.kind == TC_OP_U2 && channel_shaped(g.pool)) g.chan = true;
   // cap on gates per pass: deep multi-layer passes need many register stages
   // whose mixed register-bit sets conflict in shared memory
   const int mg_f = c->opt.max_gates_per_pass > 0 ? c->opt.max_gates_per_pass

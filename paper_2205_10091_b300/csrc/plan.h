@@ -44,7 +44,9 @@ enum : int8_t {
   IK_PAULI = 9,     // noise outcome: table[slot].x = 0,1,2,3 (I, X, Y, Z)
   IK_RX_ADJ = 10,   // adjoint step of RX: gslot += gscale*Im<lam|X|psi>; then RX(-a) on psi, lam
   IK_RY_ADJ = 11,   // same for RY (planner-internal: emitted as IK_RYM_ADJ)
-  // 12, 13: unused
+  IK_CHAN = 12,     // Pauli-channel superoperator on register bits (j0, j1): real 2x2 blocks on
+                    // (00, 11) with table[slot] = (a, b) and on (01, 10) with table[slot + 1] = (c, d)
+  // 13: unused
   IK_RXM = 14,      // RX on several register bits: j0 = bit mask, entry of bit r = slot + rank of r in mask
   IK_RXM_ADJ = 15,  // adjoint of IK_RXM: all bits share gslot/gscale
   IK_DIAG_ADJ = 16, // IK_GRADDIAG then IK_DIAG of the same group, fused
@@ -65,6 +67,7 @@ enum : int8_t {
   MT_DIAGTAB = 6, // phases exp(-i s theta/2 (T - 2m)), m = 0..T  (T+1 entries)
   MT_NOISE = 7,   // 1 entry: selected Pauli code in .x
   MT_QUARTER = 8, // quarter phases (i^{s m}), m = 0..T  (T+1 entries; s = +1 for S, -1 for S^dagger)
+  MT_CHAN = 9,    // 2 entries (a, b), (c, d) read from a channel-shaped 4x4 pool matrix
 };
 
 struct DevInstr {  // 16 bytes

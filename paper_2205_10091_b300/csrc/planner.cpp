@@ -513,9 +513,14 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
         in.j0 = (int8_t)jof[tb[g.p0]];
         switch (g.kind) {
           case TC_OP_U2:
-            in.kind = IK_MAT4;
             in.j1 = (int8_t)jof[tb[g.p1]];
-            in.slot = add_mat(MT_U2, g, 16);
+            if (g.chan) {
+              in.kind = IK_CHAN;
+              in.slot = add_mat(MT_CHAN, g, 2);
+            } else {
+              in.kind = IK_MAT4;
+              in.slot = add_mat(MT_U2, g, 16);
+            }
             break;
           case TC_OP_U1:
             in.kind = IK_MAT2;

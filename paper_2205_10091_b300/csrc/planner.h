@@ -21,6 +21,7 @@ struct HGate {
   bool diag = false;
   bool sign_mode = false;  // CZ
   bool quarter = false;    // S (scale +1) or S^dagger (scale -1) on p0: phase i^{scale * bit}
+  bool chan = false;       // U2 whose pool matrix has the Pauli-channel superoperator shape
 };
 
 // Rewrite every RX(a) as S^dagger RY(a) S (an exact identity).  The S phases

@@ -147,6 +147,12 @@ __device__ void build_mat(const DevMat& m, V* tab, const double* th, const doubl
           t[r * d + c] = mk<V>((S)re, (S)(m.adj ? -im : im));
         }
     } break;
+    case MT_CHAN: {
+      // (a, b) on the (00, 11) block, (c, d) on the (01, 10) block of the 4x4
+      auto re = [&](int r, int col) { return pool[2 * (m.pool + 4 * r + col)]; };
+      t[0] = mk<V>((S)re(0, 0), (S)re(0, 3));
+      t[1] = mk<V>((S)re(1, 1), (S)re(1, 2));
+    } break;
     case MT_DIAGTAB: {
       // phase(m) = exp(-i (ang/2) (T - 2m))
       for (int j = 0; j <= m.T; ++j) {
@@ -636,6 +642,40 @@ __device__ __forceinline__ void mat4_dispatch(V (&A)[1 << RB], int j0, int j1, c
 #undef TC_M4
 }
 
+// Pauli-channel superoperator on register bits (J0, J1): with the index
+// 2 b(J0) + b(J1), x00' = a x00 + b x11, x11' = b x00 + a x11,
+// x01' = c x01 + d x10, x10' = d x01 + c x10 (t[0] = (a, b), t[1] = (c, d)).
+template <int RB, int J0, int J1, typename V>
+__device__ __forceinline__ void g_chan(V (&A)[1 << RB], const V* t) {
+  const V a2 = mk<V>(t[0].x, t[0].x), b2 = mk<V>(t[0].y, t[0].y), c2 = mk<V>(t[1].x, t[1].x), d2 = mk<V>(t[1].y, t[1].y);
+#pragma unroll
+  for (int i = 0; i < (1 << RB); ++i) {
+    if (i & ((1 << J0) | (1 << J1))) continue;
+    const int i00 = i, i01 = i | (1 << J1), i10 = i | (1 << J0), i11 = i | (1 << J0) | (1 << J1);
+    const V x00 = A[i00], x01 = A[i01], x10 = A[i10], x11 = A[i11];
+    A[i00] = cfma2(a2, x00, cmul_re(b2, x11));
+    A[i11] = cfma2(b2, x00, cmul_re(a2, x11));
+    A[i01] = cfma2(c2, x01, cmul_re(d2, x10));
+    A[i10] = cfma2(d2, x01, cmul_re(c2, x10));
+  }
+}
+
+template <int RB, typename V>
+__device__ __forceinline__ void chan_dispatch(V (&A)[1 << RB], int j0, int j1, const V* t) {
+  // the superoperator is symmetric under exchanging its two qubits: order the bits
+  const int lo = j0 < j1 ? j0 : j1, hi = j0 < j1 ? j1 : j0;
+#define TC_CH(a, b) \
+  case a * 8 + b:   \
+    if constexpr (b < RB) g_chan<RB, a, b>(A, t); \
+    break;
+  switch (lo * 8 + hi) {
+    TC_CH(0, 1) TC_CH(0, 2) TC_CH(0, 3) TC_CH(0, 4) TC_CH(1, 2) TC_CH(1, 3) TC_CH(1, 4) TC_CH(2, 3) TC_CH(2, 4)
+    TC_CH(3, 4)
+    default: break;
+  }
+#undef TC_CH
+}
+
 // Mean and standard error (sample std, ddof = 1, over sqrt(n)) of n doubles,
 // FP64, fixed-order reduction (one block).
 __global__ void __launch_bounds__(256) k_mean_stderr(const double* x, int n, double* out) {
@@ -1039,6 +1079,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
           TC_DISPATCH_J(RB, in.j0, (g_cnot<RB, J>(A, in.jc, cb)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_cnot<RB, J>(L, in.jc, cb)));
         } break;
+        case IK_CHAN:
+          if (!LEAN) break;
+          chan_dispatch<RB>(A, in.j0, in.j1, tab + in.slot);
+          if (MODE == KM_BWD) chan_dispatch<RB>(L, in.j0, in.j1, tab + in.slot);
+          break;
         case IK_MAT4:
           if (!FULL) break;
           mat4_dispatch<RB>(A, in.j0, in.j1, tab + in.slot);
