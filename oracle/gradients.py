@@ -25,24 +25,26 @@ from paper_2205_10091_b300 import workloads as W
 from . import statevector as sv
 
 
-def energy_of(circ: W.Circuit, theta_row, ham: W.PauliSum, shift_op: int = -1, shift: float = 0.0) -> float:
-    psi = sv.run_circuit(circ, theta_row, shift_op=shift_op, shift=shift)
+def energy_of(circ: W.Circuit, theta_row, ham: W.PauliSum, shift_op: int = -1, shift: float = 0.0,
+              status_row=None) -> float:
+    psi = sv.run_circuit(circ, theta_row, status_row=status_row, shift_op=shift_op, shift=shift)
     return sv.energy(psi, circ.n, ham)[0]
 
 
-def parameter_shift(circ: W.Circuit, theta_row, ham: W.PauliSum) -> np.ndarray:
+def parameter_shift(circ: W.Circuit, theta_row, ham: W.PauliSum, status_row=None) -> np.ndarray:
     """dE/dtheta for one parameter row by the two-term shift rule per gate
-    occurrence (valid for the RX, RY, RZ, RZZ family, whose generators square
-    to the identity)."""
+    occurrence (valid for the RX, RY, RZ, RZZ family and for random-axis
+    rotations, whose generators square to the identity).  ``status_row``:
+    the row's event numbers (noise outcomes and rotation axes)."""
     g = np.zeros(circ.n_params)
     for idx, op in enumerate(circ.ops):
         p = int(op["param"])
-        if p < 0:
+        if p < 0 or int(op["kind"]) == W.OP_PAULI_NOISE:
             continue
-        assert int(op["kind"]) in (W.OP_RX, W.OP_RY, W.OP_RZ, W.OP_RZZ)
+        assert int(op["kind"]) in (W.OP_RX, W.OP_RY, W.OP_RZ, W.OP_RZZ, W.OP_RSEL)
         s = float(op["scale"])
-        ep = energy_of(circ, theta_row, ham, idx, +np.pi / 2)
-        em = energy_of(circ, theta_row, ham, idx, -np.pi / 2)
+        ep = energy_of(circ, theta_row, ham, idx, +np.pi / 2, status_row)
+        em = energy_of(circ, theta_row, ham, idx, -np.pi / 2, status_row)
         g[p] += s * (ep - em) / 2.0
     return g
 

@@ -105,6 +105,16 @@ def noise_thresholds(px: float, py: float, pz: float):
     return t1, t2, t3
 
 
+def select_rotation(u: float, px: float, py: float) -> int:
+    """Generator (1, 2, 3 = X, Y, Z) of a random-axis rotation: intervals
+    [0, px), [px, px + py), [px + py, 1), left-closed as for noise outcomes."""
+    if u < px:
+        return 1
+    if u < px + py:
+        return 2
+    return 3
+
+
 def select_pauli(u: float, px: float, py: float, pz: float) -> int:
     """Outcome i (0..3 = I,X,Y,Z) of the interval containing u; intervals are
     left-closed."""
@@ -138,6 +148,17 @@ def run_circuit(circ: W.Circuit, theta_row=None, status_row=None, init_state=Non
             i = select_pauli(u, float(op["px"]), float(op["py"]), float(op["pz"]))
             if i:
                 psi = apply_1q(psi, n, int(op["q0"]), PAULI[i])
+            continue
+        if k == W.OP_RSEL:
+            # Section "Demonstration of barren plateaus": unitary_kraus over
+            # [RX, RY, RZ] picks the rotation whose interval contains u
+            u = float(status_row[e])
+            e += 1
+            g = select_rotation(u, float(op["px"]), float(op["py"]))
+            ang = float(op["scale"]) * float(theta_row[int(op["param"])]) if int(op["param"]) >= 0 else 0.0
+            if idx == shift_op:
+                ang += shift
+            psi = apply_1q(psi, n, int(op["q0"]), rotation(PAULI[g], ang))
             continue
         m = gate_matrix(op, theta_row, circ.pool, shift if idx == shift_op else 0.0)
         if m.shape[0] == 2:

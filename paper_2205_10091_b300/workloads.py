@@ -24,8 +24,8 @@ import numpy as np
 # ---------------------------------------------------------------------------
 # Op list encoding (mirrors ``tc_op`` in include/tc.h; tests check the layout)
 # ---------------------------------------------------------------------------
-OP_H, OP_X, OP_RX, OP_RY, OP_RZ, OP_RZZ, OP_CNOT, OP_CZ, OP_U1, OP_U2, OP_PAULI_NOISE = range(11)
-OP_NAMES = ["H", "X", "RX", "RY", "RZ", "RZZ", "CNOT", "CZ", "U1", "U2", "PAULI_NOISE"]
+OP_H, OP_X, OP_RX, OP_RY, OP_RZ, OP_RZZ, OP_CNOT, OP_CZ, OP_U1, OP_U2, OP_PAULI_NOISE, OP_RSEL = range(12)
+OP_NAMES = ["H", "X", "RX", "RY", "RZ", "RZZ", "CNOT", "CZ", "U1", "U2", "PAULI_NOISE", "RSEL"]
 
 INIT_ZERO, INIT_PLUS = 0, 1
 
@@ -121,6 +121,11 @@ class OpBuilder:
 
     def depolarizing(self, q, px, py, pz):
         self._add(OP_PAULI_NOISE, q, px=px, py=py, pz=pz)
+
+    def rsel(self, q, param, scale=1.0, px=1.0 / 3, py=1.0 / 3, pz=1.0 / 3):
+        """RX, RY or RZ(scale * theta[param]), chosen per row with
+        probabilities (px, py, pz) by the row's uniform number for this event."""
+        self._add(OP_RSEL, q, param=param, scale=scale, px=px, py=py, pz=pz)
 
     def build(self, n_params: int | None = None) -> Circuit:
         ops = np.array(self.rows, dtype=OP_DTYPE) if self.rows else np.zeros(0, OP_DTYPE)
@@ -403,6 +408,23 @@ def noisy16_workload(n: int = 16, layers: int = 12, p: float = 0.01, trajectorie
     circ = noisy_su2_cz_circuit(n, layers, p, rng)
     obs = [pauli_sum(n, [(1.0, {0: 3})]), pauli_sum(n, [(1.0, {i: 3, i + 1: 3}) for i in range(n - 1)])]
     return circ, trajectories, seed, obs
+
+
+def bp_workload(n: int = 10, layers: int = 10, structures: int = 100, seed: int = 1008):
+    """The gradient-variance workload of Section "Demonstration of barren
+    plateaus": per layer a random choice of RX/RY/RZ (probability 1/3 each,
+    one weight per gate, theta[i * layers + l]) on every qubit, then CZ on
+    (i, i+1); one batch row per random structure (the structure comes from
+    the row's event stream) with weights ~ U[0, 2 pi); cost <Z0 Z1>."""
+    b = OpBuilder(n, INIT_ZERO)
+    for l in range(layers):
+        for i in range(n):
+            b.rsel(i, i * layers + l)
+        for i in range(n - 1):
+            b.cz(i, i + 1)
+    circ = b.build(n * layers)
+    theta = np.random.default_rng(seed).uniform(0, 2 * np.pi, size=(structures, n * layers))
+    return circ, theta, seed, pauli_sum(n, [(1.0, {0: 3, 1: 3})])
 
 
 def brick200_workload(n: int = 200, depth: int = 8, seed: int = SEED_BRICK200):

@@ -89,3 +89,36 @@ def test_trajectory_mean_matches_density_matrix():
     for o in range(2):
         exact = N.dm_expectation(rho, n, obs[o])
         assert abs(mean[o] - exact) < 4 * se[o] + 1e-12
+
+
+def test_random_axis_rotation_selects_by_interval():
+    """unitary_kraus over [RX, RY, RZ] (Section "Demonstration of barren
+    plateaus"): u in [0, 1/3) gives RX, [1/3, 2/3) RY, [2/3, 1) RZ; each
+    case equals the fixed rotation, and the shift rule holds for it."""
+    import numpy as np
+
+    from oracle import gradients as G
+    from oracle import statevector as sv
+    from paper_2205_10091_b300 import workloads as W
+
+    rng = np.random.default_rng(5)
+    theta = rng.uniform(-3, 3, size=2)
+    for u, fixed in ((0.0, "rx"), (0.2, "rx"), (1.0 / 3, "ry"), (0.5, "ry"), (2.0 / 3, "rz"), (0.99, "rz")):
+        b = W.OpBuilder(3)
+        b.h(0)
+        b.h(1)
+        b.rsel(1, 0, scale=0.7)
+        b.cz(0, 1)
+        b.rsel(2, 1)
+        got = sv.run_circuit(b.build(2), theta, status_row=[u, 0.1])
+        f = W.OpBuilder(3)
+        f.h(0)
+        f.h(1)
+        getattr(f, fixed)(1, 0, 0.7)
+        f.cz(0, 1)
+        f.rx(2, 1)
+        np.testing.assert_allclose(got, sv.run_circuit(f.build(2), theta), atol=1e-14)
+        ham = W.pauli_sum(3, [(1.0, {1: 1}), (0.5, {1: 2, 2: 3})])
+        gs = G.parameter_shift(b.build(2), theta, ham, status_row=[u, 0.1])
+        gf = G.parameter_shift(f.build(2), theta, ham)
+        np.testing.assert_allclose(gs, gf, atol=1e-12)
