@@ -96,7 +96,11 @@ typedef enum {
   TC_OP_CZ = 7,
   TC_OP_U1 = 8,
   TC_OP_U2 = 9,
-  TC_OP_PAULI_NOISE = 10
+  TC_OP_PAULI_NOISE = 10,
+  TC_OP_RSEL = 11  /* RX, RY or RZ(scale * theta[param]) on q0, chosen per row with
+                      probabilities (px, py, pz) by the row's number for this event
+                      (unitary_kraus over rotations, Section "Demonstration of
+                      barren plateaus"); events are numbered with the noise events */
 } tc_opkind;
 
 /* One gate.  56 bytes, naturally aligned (the Python binding mirrors it). */
@@ -108,7 +112,7 @@ typedef struct {
   double scale;  /* angle = scale * theta[param] */
   int32_t mat;   /* U1/U2: offset (complex entries) into the matrix pool */
   int32_t pad;
-  double px, py, pz; /* PAULI_NOISE probabilities */
+  double px, py, pz; /* PAULI_NOISE probabilities; RSEL: probabilities of RX, RY, RZ (sum 1) */
 } tc_op;
 
 typedef struct {

@@ -99,6 +99,9 @@ bool build_dm_ops(int n, const tc_op* ops, int n_ops, const double* pool, int n_
         out.push_back(s);
         continue;
       }
+      case TC_OP_RSEL:
+        err = "op " + std::to_string(i) + ": random-axis rotations draw per row; not a density-matrix op";
+        return false;
       default:
         err = "op " + std::to_string(i) + ": unknown kind";
         return false;

@@ -46,12 +46,13 @@ enum : int8_t {
   IK_RY_ADJ = 11,   // same for RY (planner-internal: emitted as IK_RYM_ADJ)
   IK_CHAN = 12,     // Pauli-channel superoperator on register bits (j0, j1): real 2x2 blocks on
                     // (00, 11) with table[slot] = (a, b) and on (01, 10) with table[slot + 1] = (c, d)
-  // 13: unused
+  IK_RSEL = 13,     // random-axis rotation: the row's 2x2 matrix at table[slot..slot+3], axis (1..3) in table[slot+4].x
   IK_RXM = 14,      // RX on several register bits: j0 = bit mask, entry of bit r = slot + rank of r in mask
   IK_RXM_ADJ = 15,  // adjoint of IK_RXM: all bits share gslot/gscale
   IK_DIAG_ADJ = 16, // IK_GRADDIAG then IK_DIAG of the same group, fused
   IK_RYM = 17,      // RY on the register bits of mask j0; bit r's kRYEntries entries at slot + kRYEntries * rank
   IK_RYM_ADJ = 18,  // adjoint of IK_RYM (gslot < 0: a fixed-angle rotation, uncompute only)
+  IK_RSEL_ADJ = 19, // adjoint step of IK_RSEL: gslot += gscale * Im<lam|G|psi> for the row's axis G, then U^dagger
 };
 
 constexpr int kLocalSlots = 32;  // gradient slots a pass accumulates per thread before one reduction
@@ -68,6 +69,7 @@ enum : int8_t {
   MT_NOISE = 7,   // 1 entry: selected Pauli code in .x
   MT_QUARTER = 8, // quarter phases (i^{s m}), m = 0..T  (T+1 entries; s = +1 for S, -1 for S^dagger)
   MT_CHAN = 9,    // 2 entries (a, b), (c, d) read from a channel-shaped 4x4 pool matrix
+  MT_RSEL = 10,   // 5 entries: the row's rotation matrix (2x2) and its axis code
 };
 
 struct DevInstr {  // 16 bytes

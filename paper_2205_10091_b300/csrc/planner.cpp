@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cmath>
 #include <map>
 #include <numeric>
 #include <tuple>
@@ -32,7 +33,7 @@ bool normalise_ops(int n_user, int N, const tc_op* ops, int n_ops, int n_params,
       err = "op " + std::to_string(i) + ": " + m;
       return false;
     };
-    if (o.kind < TC_OP_H || o.kind > TC_OP_PAULI_NOISE) return bad("unknown kind");
+    if (o.kind < TC_OP_H || o.kind > TC_OP_RSEL) return bad("unknown kind");
     const bool two = o.kind == TC_OP_RZZ || o.kind == TC_OP_CNOT || o.kind == TC_OP_CZ || o.kind == TC_OP_U2;
     if (o.q0 < 0 || o.q0 >= n_user) return bad("q0 out of range");
     if (two && (o.q1 < 0 || o.q1 >= n_user || o.q1 == o.q0)) return bad("q1 out of range or equal to q0");
@@ -40,7 +41,8 @@ bool normalise_ops(int n_user, int N, const tc_op* ops, int n_ops, int n_params,
     g.kind = o.kind;
     g.p0 = N - 1 - o.q0;
     g.p1 = two ? N - 1 - o.q1 : -1;
-    const bool rot = o.kind == TC_OP_RX || o.kind == TC_OP_RY || o.kind == TC_OP_RZ || o.kind == TC_OP_RZZ;
+    const bool rot = o.kind == TC_OP_RX || o.kind == TC_OP_RY || o.kind == TC_OP_RZ || o.kind == TC_OP_RZZ ||
+                     o.kind == TC_OP_RSEL;
     if (rot) {
       if (o.param < -1 || o.param >= n_params) return bad("param out of range");
       if (!std::isfinite(o.scale)) return bad("scale not finite");
@@ -57,6 +59,14 @@ bool normalise_ops(int n_user, int N, const tc_op* ops, int n_ops, int n_params,
       g.t1 = 1.0 - (o.px + o.py + o.pz);
       g.t2 = g.t1 + o.px;
       g.t3 = g.t2 + o.py;
+      g.noise_event = ev++;
+    }
+    if (o.kind == TC_OP_RSEL) {
+      if (!(o.px >= 0 && o.py >= 0 && o.pz >= 0) || std::fabs(o.px + o.py + o.pz - 1.0) > 1e-9)
+        return bad("rotation probabilities must be >= 0 and sum to 1");
+      // interval ends for [RX, RY, RZ], left-closed
+      g.t1 = o.px;
+      g.t2 = o.px + o.py;
       g.noise_event = ev++;
     }
     g.diag = o.kind == TC_OP_RZ || o.kind == TC_OP_RZZ || o.kind == TC_OP_CZ;
@@ -427,7 +437,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
       m.scale = g.scale;
       m.pool = g.pool;
       m.dst = sc.table_total + table;
-      if (type == MT_NOISE) {
+      if (type == MT_NOISE || type == MT_RSEL) {
         m.T = g.noise_event;
         m.t1 = g.t1;
         m.t2 = g.t2;
@@ -535,6 +545,16 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
           case TC_OP_PAULI_NOISE:
             in.kind = IK_PAULI;
             in.slot = add_mat(MT_NOISE, g, 1);
+            break;
+          case TC_OP_RSEL:
+            in.slot = add_mat(MT_RSEL, g, 5);
+            if (adjoint && g.param >= 0) {
+              in.kind = IK_RSEL_ADJ;
+              in.gslot = (int16_t)slot_of(g.param);
+              in.gscale = (float)g.scale;
+            } else {
+              in.kind = IK_RSEL;
+            }
             break;
           case TC_OP_RX:
           case TC_OP_RY: {

@@ -147,6 +147,31 @@ __device__ void build_mat(const DevMat& m, V* tab, const double* th, const doubl
           t[r * d + c] = mk<V>((S)re, (S)(m.adj ? -im : im));
         }
     } break;
+    case MT_RSEL: {
+      // the row's axis from its number for this event; U(a) = exp(-i a G / 2)
+      // (the angle is already negated for an adjoint table)
+      const double u = noise_uniform(a, row, m.T);
+      const int ax = u < m.t1 ? 1 : u < m.t2 ? 2 : 3;  // X, Y, Z
+      double s, c;
+      sincos(0.5 * ang, &s, &c);
+      if (ax == 1) {
+        t[0] = mk<V>((S)c, (S)0);
+        t[1] = mk<V>((S)0, (S)-s);
+        t[2] = mk<V>((S)0, (S)-s);
+        t[3] = mk<V>((S)c, (S)0);
+      } else if (ax == 2) {
+        t[0] = mk<V>((S)c, (S)0);
+        t[1] = mk<V>((S)-s, (S)0);
+        t[2] = mk<V>((S)s, (S)0);
+        t[3] = mk<V>((S)c, (S)0);
+      } else {
+        t[0] = mk<V>((S)c, (S)-s);
+        t[1] = mk<V>((S)0, (S)0);
+        t[2] = mk<V>((S)0, (S)0);
+        t[3] = mk<V>((S)c, (S)s);
+      }
+      t[4] = mk<V>((S)ax, (S)0);
+    } break;
     case MT_CHAN: {
       // (a, b) on the (00, 11) block, (c, d) on the (01, 10) block of the 4x4
       auto re = [&](int r, int col) { return pool[2 * (m.pool + 4 * r + col)]; };
@@ -487,6 +512,21 @@ __device__ __forceinline__ decltype(V::x) g_adj(V (&P)[1 << RB], V (&L)[1 << RB]
     }
   }
   return (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
+// Sum over pairs of Im<lam|Z|psi> = Im(conj(l0) p0) - Im(conj(l1) p1) on register bit J.
+template <int RB, int J, typename V>
+__device__ __forceinline__ decltype(V::x) g_zgrad(const V (&P)[1 << RB], const V (&L)[1 << RB]) {
+  using S = decltype(V::x);
+  S a0 = 0, a1 = 0;
+#pragma unroll
+  for (int i = 0; i < (1 << RB); ++i) {
+    if (i & (1 << J)) continue;
+    const V p0 = P[i], p1 = P[i | (1 << J)], l0 = L[i], l1 = L[i | (1 << J)];
+    a0 = fma(l0.x, p0.y, fma(-l0.y, p0.x, a0));
+    a1 = fma(l1.x, p1.y, fma(-l1.y, p1.x, a1));
+  }
+  return a0 - a1;
 }
 
 // Running scale of complex64 tangent-form RY: every such gate multiplies the
@@ -1078,6 +1118,28 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
           const uint32_t cb = (m.g >> in.pos) & 1u;
           TC_DISPATCH_J(RB, in.j0, (g_cnot<RB, J>(A, in.jc, cb)));
           if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_cnot<RB, J>(L, in.jc, cb)));
+        } break;
+        case IK_RSEL:
+          if (!LEAN) break;
+          TC_DISPATCH_J(RB, in.j0, (g_mat2<RB, J>(A, tab + in.slot)));
+          if (MODE == KM_BWD) TC_DISPATCH_J(RB, in.j0, (g_mat2<RB, J>(L, tab + in.slot)));
+          break;
+        case IK_RSEL_ADJ: {
+          if (MODE != KM_BWD || !LEAN) break;
+          // gradient with the row's axis, then U^dagger (the adjoint table) on psi and lam
+          const int ax = (int)tab[in.slot + 4].x;
+          const V one = mk<V>((T)1, (T)0);
+          T acc = 0;
+          if (ax == 1) {
+            TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, true>(A, L, one, false)));
+          } else if (ax == 2) {
+            TC_DISPATCH_J(RB, in.j0, (acc = g_adj<RB, J, false>(A, L, one, false)));
+          } else {
+            TC_DISPATCH_J(RB, in.j0, (acc = g_zgrad<RB, J>(A, L)));
+          }
+          TC_DISPATCH_J(RB, in.j0, (g_mat2<RB, J>(A, tab + in.slot)));
+          TC_DISPATCH_J(RB, in.j0, (g_mat2<RB, J>(L, tab + in.slot)));
+          add_grad(in.gslot, acc * sq(sc + sl) * (T)in.gscale);
         } break;
         case IK_CHAN:
           if (!LEAN) break;
