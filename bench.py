@@ -423,6 +423,18 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
                                "z0": float(vals_dm[0].item()), "sum_zz": float(vals_dm[1].item()),
                                "plan": {k: v for k, v in dmc.info().items() if k in ("fwd_passes", "fwd_stages")}}
     del rho
+    # ---- gradient variance over random structures: 10 qubits x 10 layers ----
+    cbp, thbp, seedbp, hbp = W.bp_workload()
+    cb = nt.Circuit(cbp)
+    Hbp = nt.Hamiltonian(hbp)
+    d_bp = torch.as_tensor(thbp, device="cuda")
+    e_bp = torch.empty(thbp.shape[0], dtype=torch.float64, device="cuda")
+    g_bp = torch.empty(thbp.shape, dtype=torch.float64, device="cuda")
+    ms_bp = _time_cuda(lambda: cb.expect_grad(d_bp, Hbp, seed=seedbp, energy=e_bp, grad=g_bp), 50)
+    out["bp10_gradient_variance"] = {
+        "ms_per_run": ms_bp, "qubits": cbp.n, "layers": 10, "structures": int(thbp.shape[0]),
+        "var_dtheta0": float(g_bp[:, 0].var(unbiased=False).item()),
+        "mean_var_over_params": float(g_bp.var(dim=0, unbiased=False).mean().item())}
     # ---- many-term Pauli sum: 12-qubit, 1390-term chemistry-shaped H ------
     hc = W.chem_pauli_sum(12)
     Hc = nt.Hamiltonian(hc)

@@ -364,7 +364,8 @@ typedef struct {
   int32_t n_cone_gates;
   int32_t cone_lo, cone_hi; /* qubit span of the light cone */
   int32_t n_inputs;         /* input tensors of the doubled network */
-  int32_t reserved[4];
+  int32_t n_active;         /* qubits with ket/bra chains in the network */
+  int32_t reserved[3];
 } tc_path_info;
 TC_API tc_status tc_tn_lightcone_create(int n_qubits, const int32_t* gate_qubits, int n_gates,
                                         const int32_t* z_qubits, int n_z, int rank_cap, const int32_t* path,
@@ -372,6 +373,41 @@ TC_API tc_status tc_tn_lightcone_create(int n_qubits, const int32_t* gate_qubits
 TC_API tc_status tc_tn_info(const tc_tn* t, tc_path_info* out);
 TC_API tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out, void* stream);
 TC_API void tc_tn_destroy(tc_tn* t);
+
+/*
+ * tc_tn_circuit_create — plan <init| U^dagger P U |init> of a parameterised
+ * circuit as one closed tensor network (Section "Custom contraction
+ * settings": the expectation of one Pauli string contracted as a single
+ * network, two-qubit gates split in two tensors, the default greedy path).
+ *   n_qubits, init, ops, n_ops, n_params, const_mats, n_mats
+ *                as tc_circuit_create (host, copied); ops of kind H, X, RX,
+ *                RY, RZ, RZZ, CNOT, CZ, U1, U2 (others: TC_E_UNSUPPORTED)
+ *   pauli        host [n_qubits] codes 0..3 = I, X, Y, Z (copied; at least
+ *                one non-identity)
+ *   prune        0 = every op and qubit enters the network; 1 = the ops in
+ *                the backward causal cone of the string; 2 = the same with
+ *                diagonal gates (RZ, RZZ, CZ, diagonal U1/U2) dropped where
+ *                they commute with the Heisenberg-evolved string (exact)
+ *   split        1 = RZZ, CZ and CNOT enter as two rank-3 tensors joined by
+ *                a dimension-2 bond (their operator-Schmidt decomposition);
+ *                0 = as one rank-4 tensor
+ *   rank_cap, path, n_path_steps   as tc_tn_lightcone_create
+ * The network holds ket and bra (complex-conjugated) copies of the kept
+ * ops, the initial vectors and the string's Pauli matrices; qubits carrying
+ * the identity join their ket and bra legs.  Host only.
+ *
+ * tc_tn_circuit_expect — contract B instances (one parameter row each).
+ *   d_params  device [B][n_params] float32
+ *   d_out     device [B][2] doubles: Re and Im of <P> per row
+ * Tensor entries are evaluated on the device from each row's angles (FP32),
+ * then contracted step by step (complex GEMMs, FP32 accumulate) in one CUDA
+ * graph.  Plans from tc_tn_lightcone_create are refused (TC_E_INVALID) and
+ * vice versa.
+ */
+TC_API tc_status tc_tn_circuit_create(int n_qubits, tc_init init, const tc_op* ops, int n_ops, int n_params,
+                                      const double* const_mats, int n_mats, const uint8_t* pauli, int prune,
+                                      int split, int rank_cap, const int32_t* path, int n_path_steps, tc_tn** out);
+TC_API tc_status tc_tn_circuit_expect(tc_tn* t, int B, const float* d_params, double* d_out, void* stream);
 
 /*
  * Serving loop (continuous batching of circuit-evaluation requests).

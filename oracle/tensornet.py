@@ -11,18 +11,27 @@ conjugated bra gates) whose value does not depend on the contraction path.
   at a time, then <O>.
 * ``window_statevector_expectation``: every gate inside a qubit window wider
   than the cone (pins the cone: must give the same scalar).
+* ``circuit_window_expectation``: <P> of a parameterised op-list circuit
+  over a qubit window: every op inside the window applied to a dense FP64
+  window state, ops touching the outside dropped.  Exact whenever every
+  dropped op commutes with the Heisenberg-evolved string at its position
+  (outside its support, or diagonal against diagonal support), which holds
+  for the contraction testbed with the window n//2 - d - 1 .. n//2 + d + 1.
 * ``network_expectation`` + ``contract``: the doubled network contracted
   pairwise with np.einsum along any given path (pins path independence and
   agreement with the state vector on tiny circuits).
 
 Pinned by tests/test_oracle_tensornet.py (state vector == network on tiny
 brickworks along two different paths; cone == window; cone of a brickwork
-has the expected gate count).
+has the expected gate count; the circuit window equals the full state
+vector on circuits small enough to simulate whole, and a window narrower
+than the string's support does not).
 """
 from __future__ import annotations
 
 import numpy as np
 
+from paper_2205_10091_b300 import workloads as W
 from . import statevector as sv
 
 PZ = sv.PZ
@@ -69,6 +78,24 @@ def window_statevector_expectation(gates, obs_qubits, lo, hi):
     """<Z..Z> with every gate whose qubits lie in [lo, hi] applied."""
     inside = [g for g in gates if lo <= g[0] <= hi and lo <= g[1] <= hi]
     return _local_statevector_expectation(inside, obs_qubits, range(lo, hi + 1))
+
+
+def circuit_window_expectation(circ: W.Circuit, theta_row, pauli: dict, lo: int, hi: int) -> complex:
+    """<P> for the Pauli string ``pauli`` ({qubit: 1..3 = X, Y, Z}) with
+    the ops of ``circ`` that lie inside [lo, hi] applied to the window."""
+    ops = circ.ops
+    q1 = ops["q1"]
+    inside = (ops["q0"] >= lo) & (ops["q0"] <= hi) & ((q1 < 0) | ((q1 >= lo) & (q1 <= hi)))
+    sub = ops[inside].copy()
+    sub["q0"] -= lo
+    sub["q1"] = np.where(sub["q1"] >= 0, sub["q1"] - lo, -1)
+    m = hi - lo + 1
+    psi = sv.run_circuit(W.Circuit(m, sub, circ.n_params, circ.pool, circ.init), theta_row)
+    phi = psi
+    for q, c in pauli.items():
+        assert lo <= q <= hi
+        phi = sv.apply_1q(phi, m, q - lo, sv.PAULI[c])
+    return complex(np.vdot(psi, phi))
 
 
 def network_expectation(n, gates, obs_qubits):

@@ -12,6 +12,7 @@
 #include "tn.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <map>
 #include <set>
@@ -31,6 +32,194 @@ struct Ten {
 int64_t pow2(int r) { return (int64_t)1 << r; }
 
 }  // namespace
+
+// Pairwise path over a closed network whose every label joins exactly two
+// tensors (all index dimensions 2).  T holds the input tensors (P.inputs
+// already carries their offsets); steps, gather tables, arena layout and the
+// path metrics are appended to P.  Without a user path the greedy rule picks
+// the connected pair minimising size(out) - size(a) - size(b), ties to the
+// smallest tensor ids, skipping pairs whose result exceeds rank_cap; with
+// no connected pair left, disconnected parts are joined by outer products.
+bool tn_plan_path(std::vector<Ten>& T, int rank_cap, const int32_t* path, int n_path, TnPlan& P, std::string& err) {
+  const int n_inputs = (int)T.size();
+  int max_label = -1;
+  for (const auto& t : T)
+    for (int l : t.labels) max_label = std::max(max_label, l);
+  // holders[l] = the two tensors carrying label l
+  std::vector<std::array<int, 2>> holders((size_t)(max_label + 1), std::array<int, 2>{-1, -1});
+  for (int i = 0; i < n_inputs; ++i)
+    for (int l : T[i].labels) {
+      auto& h = holders[l];
+      if (h[0] < 0) {
+        h[0] = i;
+      } else if (h[1] < 0 && h[0] != i) {
+        h[1] = i;
+      } else {
+        err = "label " + std::to_string(l) + " is not shared by exactly two tensors";
+        return false;
+      }
+    }
+  for (int l = 0; l <= max_label; ++l)
+    if (holders[l][0] >= 0 && holders[l][1] < 0) {
+      err = "network is not closed (label " + std::to_string(l) + " is open)";
+      return false;
+    }
+  std::vector<int> live(n_inputs);
+  for (int i = 0; i < n_inputs; ++i) live[i] = i;
+  auto split_labels = [&](const Ten& a, const Ten& b, std::vector<int>& fa, std::vector<int>& sh,
+                          std::vector<int>& fb) {
+    fa.clear();
+    sh.clear();
+    fb.clear();
+    for (int l : a.labels)
+      (std::find(b.labels.begin(), b.labels.end(), l) != b.labels.end() ? sh : fa).push_back(l);
+    for (int l : b.labels)
+      if (std::find(a.labels.begin(), a.labels.end(), l) == a.labels.end()) fb.push_back(l);
+  };
+  std::vector<std::pair<int, int>> pairs;  // tensor ids of a user path
+  if (path) {
+    std::vector<int> list = live;
+    for (int s = 0; s < n_path; ++s) {
+      int i = path[2 * s], j = path[2 * s + 1];
+      if (i == j || i < 0 || j < 0 || i >= (int)list.size() || j >= (int)list.size()) {
+        err = "path step " + std::to_string(s) + " out of range";
+        return false;
+      }
+      if (i > j) std::swap(i, j);
+      const int a = list[i], b = list[j];
+      list.erase(list.begin() + j);
+      list.erase(list.begin() + i);
+      list.push_back(n_inputs + (int)pairs.size());
+      pairs.push_back({a, b});
+    }
+    if (list.size() != 1) {
+      err = "path does not contract the network to one tensor";
+      return false;
+    }
+  }
+  int64_t tab_total = (int64_t)P.tables.size();
+  std::vector<int64_t> ten_off(n_inputs);
+  for (int i = 0; i < n_inputs; ++i) ten_off[i] = P.inputs[i].off;
+  int64_t arena = P.in_total;
+  size_t pi = 0;
+  std::vector<int> fa, sh, fb;
+  while (live.size() > 1) {
+    int best_a = -1, best_b = -1;
+    if (path) {
+      best_a = pairs[pi].first;
+      best_b = pairs[pi].second;
+      ++pi;
+    } else {
+      int64_t best_cost = 0;
+      bool found = false, connected = false;
+      for (int x : live)
+        for (int l : T[x].labels) {
+          const int y = holders[l][0] == x ? holders[l][1] : holders[l][0];
+          if (y <= x) continue;  // each connected pair once, from its smaller id
+          connected = true;
+          split_labels(T[x], T[y], fa, sh, fb);
+          const int r = (int)(fa.size() + fb.size());
+          if (r > rank_cap) continue;
+          const int64_t cost = pow2(r) - pow2((int)T[x].labels.size()) - pow2((int)T[y].labels.size());
+          if (!found || cost < best_cost || (cost == best_cost && (x < best_a || (x == best_a && y < best_b)))) {
+            found = true;
+            best_cost = cost;
+            best_a = x;
+            best_b = y;
+          }
+        }
+      if (!found && !connected) {
+        // disconnected components: once each is contracted, join the two
+        // smallest tensors by an outer product (scalars in a closed network)
+        int best_r = 0;
+        for (size_t x = 0; x < live.size(); ++x)
+          for (size_t y = x + 1; y < live.size(); ++y) {
+            const int a = std::min(live[x], live[y]), b = std::max(live[x], live[y]);
+            split_labels(T[a], T[b], fa, sh, fb);
+            if (!sh.empty()) continue;
+            const int r = (int)(fa.size() + fb.size());
+            if (r > rank_cap) continue;
+            if (!found || r < best_r || (r == best_r && (a < best_a || (a == best_a && b < best_b)))) {
+              found = true;
+              best_r = r;
+              best_a = a;
+              best_b = b;
+            }
+          }
+      }
+      if (!found) {
+        err = "no contraction within the rank cap";
+        return false;
+      }
+    }
+    split_labels(T[best_a], T[best_b], fa, sh, fb);
+    const int rc = (int)(fa.size() + fb.size());
+    if (rc > rank_cap) {
+      err = "path step exceeds the rank cap";
+      return false;
+    }
+    TnStep st{};
+    st.a = best_a;
+    st.b = best_b;
+    st.c = (int)T.size();
+    st.M = (int)pow2((int)fa.size());
+    st.K = (int)pow2((int)sh.size());
+    st.N = (int)pow2((int)fb.size());
+    if ((st.M + 31) / 32 > 65535 || (st.N + 31) / 32 > 65535) {
+      err = "path step too large for one launch (free rank above 21 on one side)";
+      return false;
+    }
+    // index tables: bit of label l in a tensor = rank - 1 - position
+    auto bitpos = [](const Ten& t, int l) {
+      const int p = (int)(std::find(t.labels.begin(), t.labels.end(), l) - t.labels.begin());
+      return (int)t.labels.size() - 1 - p;
+    };
+    auto table = [&](const Ten& t, const std::vector<int>& ls) {
+      const int64_t off = tab_total;
+      const int nb = (int)ls.size();
+      for (int64_t v = 0; v < pow2(nb); ++v) {
+        int32_t idx = 0;
+        for (int u = 0; u < nb; ++u)
+          if ((v >> (nb - 1 - u)) & 1) idx |= 1 << bitpos(t, ls[u]);
+        P.tables.push_back(idx);
+      }
+      tab_total += pow2(nb);
+      return (int32_t)off;
+    };
+    st.fa = table(T[best_a], fa);
+    st.sa = table(T[best_a], sh);
+    st.sb = table(T[best_b], sh);
+    st.fb = table(T[best_b], fb);
+    st.a_off = ten_off[best_a];
+    st.b_off = ten_off[best_b];
+    st.c_off = arena;
+    ten_off.push_back(arena);
+    arena += (int64_t)st.M * st.N;
+    P.flops += (double)st.M * st.K * st.N;
+    P.write += (double)st.M * st.N;
+    P.size = std::max(P.size, (double)st.M * st.N);
+    P.max_rank = std::max(P.max_rank, rc);
+    Ten c;
+    c.labels = fa;
+    c.labels.insert(c.labels.end(), fb.begin(), fb.end());
+    for (int l : c.labels) {
+      auto& h = holders[l];
+      h[h[0] == best_a || h[0] == best_b ? 0 : 1] = st.c;
+    }
+    T.push_back(c);
+    P.steps.push_back(st);
+    live.erase(std::remove(live.begin(), live.end(), best_a), live.end());
+    live.erase(std::remove(live.begin(), live.end(), best_b), live.end());
+    live.push_back(st.c);
+  }
+  if (!T[live[0]].labels.empty()) {
+    err = "network is not closed";
+    return false;
+  }
+  P.arena_total = arena;
+  P.result_off = P.steps.empty() ? 0 : P.steps.back().c_off;
+  return true;
+}
 
 bool tn_build_lightcone(int n_qubits, const int32_t* gate_q, int n_gates, const int32_t* z_q, int n_z, int rank_cap,
                         const int32_t* path, int n_path, TnPlan& P, std::string& err) {
@@ -112,140 +301,173 @@ bool tn_build_lightcone(int n_qubits, const int32_t* gate_q, int n_gates, const 
           if (l == bra[q]) l = ket[q];
     }
   }
-  const int n_inputs = (int)T.size();
+  return tn_plan_path(T, rank_cap, path, n_path, P, err);
+}
 
-  // ---- path -----------------------------------------------------------------
-  std::vector<int> live(n_inputs);
-  for (int i = 0; i < n_inputs; ++i) live[i] = i;
-  auto out_labels = [&](const Ten& a, const Ten& b, std::vector<int>& fa, std::vector<int>& sh, std::vector<int>& fb) {
-    fa.clear();
-    sh.clear();
-    fb.clear();
-    for (int l : a.labels)
-      (std::find(b.labels.begin(), b.labels.end(), l) != b.labels.end() ? sh : fa).push_back(l);
-    for (int l : b.labels)
-      if (std::find(a.labels.begin(), a.labels.end(), l) == a.labels.end()) fb.push_back(l);
+// Circuit network <init| K^dagger P K |init> for a Pauli string P, K the ops
+// that survive pruning (Section "Custom contraction settings": the testbed
+// expectation computed as one network, two-qubit gates split in two tensors).
+//   prune 0  every op and qubit (the whole doubled network)
+//   prune 1  backward causal cone of P in circuit order
+//   prune 2  cone with commuting diagonal gates removed: walking back from P
+//            in the Heisenberg picture, each qubit's support is none, diagonal
+//            (only I/Z factors) or full.  A diagonal gate commutes with the
+//            operator unless one of its qubits is full, so it drops out
+//            exactly; a kept diagonal gate makes its idle qubits diagonal (it
+//            multiplies X/Y factors by Z on the partner).  A non-diagonal gate
+//            on a supported qubit makes its qubits full.
+//   split 1  RZZ, CZ and CNOT enter as two rank-3 tensors joined by a bond
+//            of dimension 2 (their operator-Schmidt rank), else as one 4x4.
+bool tn_build_circuit(int n, int init, const tc_op* ops, int n_ops, int n_params, const double* mats, int n_mats,
+                      const uint8_t* pauli, int prune, int split, int rank_cap, const int32_t* path, int n_path,
+                      TnPlan& P, std::string& err) {
+  P = TnPlan{};
+  P.circuit = true;
+  P.n_qubits = n;
+  P.n_params = n_params;
+  auto is_diag_mat = [&](int off, int dim) {
+    for (int r = 0; r < dim; ++r)
+      for (int c = 0; c < dim; ++c)
+        if (r != c && (mats[2 * (off + r * dim + c)] != 0.0 || mats[2 * (off + r * dim + c) + 1] != 0.0)) return false;
+    return true;
   };
-  std::vector<std::pair<int, int>> pairs;  // tensor ids
-  if (path) {
-    std::vector<int> list = live;
-    for (int s = 0; s < n_path; ++s) {
-      int i = path[2 * s], j = path[2 * s + 1];
-      if (i == j || i < 0 || j < 0 || i >= (int)list.size() || j >= (int)list.size()) {
-        err = "path step " + std::to_string(s) + " out of range";
-        return false;
-      }
-      if (i > j) std::swap(i, j);
-      const int a = list[i], b = list[j];
-      list.erase(list.begin() + j);
-      list.erase(list.begin() + i);
-      list.push_back((int)T.size() + (int)pairs.size());
-      pairs.push_back({a, b});
-      // placeholder tensor to keep ids aligned; labels filled below
-    }
-    if (list.size() != 1) {
-      err = "path does not contract the network to one tensor";
+  std::vector<char> two(n_ops), diag(n_ops);
+  for (int i = 0; i < n_ops; ++i) {
+    const tc_op& o = ops[i];
+    const bool q2 = o.kind == TC_OP_RZZ || o.kind == TC_OP_CNOT || o.kind == TC_OP_CZ || o.kind == TC_OP_U2;
+    if (o.kind < TC_OP_H || o.kind > TC_OP_U2) {
+      err = "op " + std::to_string(i) + ": kind not supported by tensor-network plans (noise and random-axis "
+            "rotations need the state-vector engine)";
       return false;
     }
-  }
-  int64_t tab_total = 0;
-  std::vector<int64_t> ten_off(n_inputs);
-  for (int i = 0; i < n_inputs; ++i) ten_off[i] = P.inputs[i].off;
-  int64_t arena = P.in_total;
-  size_t pi = 0;
-  while (live.size() > 1) {
-    int best_a = -1, best_b = -1;
-    if (path) {
-      best_a = pairs[pi].first;
-      best_b = pairs[pi].second;
-      ++pi;
-    } else {
-      // greedy: connected pair minimising size(out) - size(a) - size(b); ties -> smallest ids
-      int64_t best_cost = 0;
-      bool found = false;
-      std::vector<int> fa, sh, fb;
-      for (size_t x = 0; x < live.size(); ++x)
-        for (size_t y = x + 1; y < live.size(); ++y) {
-          const Ten& A = T[live[x]];
-          const Ten& B = T[live[y]];
-          out_labels(A, B, fa, sh, fb);
-          if (sh.empty()) continue;
-          const int r = (int)(fa.size() + fb.size());
-          if (r > rank_cap) continue;
-          const int64_t cost = pow2(r) - pow2((int)A.labels.size()) - pow2((int)B.labels.size());
-          const int ia = std::min(live[x], live[y]), ib = std::max(live[x], live[y]);
-          if (!found || cost < best_cost || (cost == best_cost && (ia < best_a || (ia == best_a && ib < best_b)))) {
-            found = true;
-            best_cost = cost;
-            best_a = ia;
-            best_b = ib;
-          }
-        }
-      if (!found) {
-        err = "no contraction within the rank cap (or the network is disconnected)";
-        return false;
-      }
-    }
-    std::vector<int> fa, sh, fb;
-    out_labels(T[best_a], T[best_b], fa, sh, fb);
-    const int rc = (int)(fa.size() + fb.size());
-    if (rc > rank_cap) {
-      err = "path step exceeds the rank cap";
+    if (o.q0 < 0 || o.q0 >= n || (q2 && (o.q1 < 0 || o.q1 >= n || o.q1 == o.q0))) {
+      err = "op " + std::to_string(i) + ": qubit out of range";
       return false;
     }
-    TnStep st{};
-    st.a = best_a;
-    st.b = best_b;
-    st.c = (int)T.size();
-    st.M = (int)pow2((int)fa.size());
-    st.K = (int)pow2((int)sh.size());
-    st.N = (int)pow2((int)fb.size());
-    // index tables: bit of label l in a tensor = rank - 1 - position
-    auto bitpos = [](const Ten& t, int l) {
-      const int p = (int)(std::find(t.labels.begin(), t.labels.end(), l) - t.labels.begin());
-      return (int)t.labels.size() - 1 - p;
-    };
-    auto table = [&](const Ten& t, const std::vector<int>& ls) {
-      const int64_t off = tab_total;
-      const int nb = (int)ls.size();
-      for (int64_t v = 0; v < pow2(nb); ++v) {
-        int32_t idx = 0;
-        for (int u = 0; u < nb; ++u)
-          if ((v >> (nb - 1 - u)) & 1) idx |= 1 << bitpos(t, ls[u]);
-        P.tables.push_back(idx);
-      }
-      tab_total += pow2(nb);
-      return (int32_t)off;
-    };
-    st.fa = table(T[best_a], fa);
-    st.sa = table(T[best_a], sh);
-    st.sb = table(T[best_b], sh);
-    st.fb = table(T[best_b], fb);
-    st.a_off = ten_off[best_a];
-    st.b_off = ten_off[best_b];
-    st.c_off = arena;
-    ten_off.push_back(arena);
-    arena += (int64_t)st.M * st.N;
-    P.flops += (double)st.M * st.K * st.N;
-    P.write += (double)st.M * st.N;
-    P.size = std::max(P.size, (double)st.M * st.N);
-    P.max_rank = std::max(P.max_rank, rc);
-    Ten c;
-    c.labels = fa;
-    c.labels.insert(c.labels.end(), fb.begin(), fb.end());
-    T.push_back(c);
-    P.steps.push_back(st);
-    live.erase(std::remove(live.begin(), live.end(), best_a), live.end());
-    live.erase(std::remove(live.begin(), live.end(), best_b), live.end());
-    live.push_back(st.c);
+    if (o.param >= n_params || o.param < -1) {
+      err = "op " + std::to_string(i) + ": parameter index out of range";
+      return false;
+    }
+    const int dim = o.kind == TC_OP_U1 ? 2 : 4;
+    if ((o.kind == TC_OP_U1 || o.kind == TC_OP_U2) && (o.mat < 0 || (int64_t)o.mat + dim * dim > n_mats || !mats)) {
+      err = "op " + std::to_string(i) + ": matrix offset out of range";
+      return false;
+    }
+    two[i] = q2;
+    diag[i] = o.kind == TC_OP_RZ || o.kind == TC_OP_RZZ || o.kind == TC_OP_CZ ||
+              ((o.kind == TC_OP_U1 || o.kind == TC_OP_U2) && is_diag_mat(o.mat, dim));
   }
-  if (!T[live[0]].labels.empty()) {
-    err = "network is not closed";
+  std::vector<int> sup(n, 0);  // 0 none, 1 diagonal, 2 full
+  bool any = false;
+  for (int q = 0; q < n; ++q) {
+    if (pauli[q] > 3) {
+      err = "Pauli code out of range";
+      return false;
+    }
+    sup[q] = pauli[q] == 0 ? 0 : (pauli[q] == 3 ? 1 : 2);
+    any = any || pauli[q] != 0;
+  }
+  if (!any) {
+    err = "empty observable";
     return false;
   }
-  P.arena_total = arena;
-  P.result_off = P.steps.empty() ? 0 : P.steps.back().c_off;
-  return true;
+  std::vector<char> keep(n_ops, 0);
+  if (prune == 0) {
+    std::fill(keep.begin(), keep.end(), 1);
+    for (int q = 0; q < n; ++q) sup[q] = std::max(sup[q], 1);
+  } else {
+    for (int i = n_ops - 1; i >= 0; --i) {
+      const tc_op& o = ops[i];
+      const int a = o.q0, b = two[i] ? o.q1 : o.q0;
+      if (prune == 1) {
+        if (sup[a] || sup[b]) {
+          keep[i] = 1;
+          sup[a] = sup[b] = 2;
+        }
+      } else if (diag[i]) {
+        if (sup[a] == 2 || sup[b] == 2) {
+          keep[i] = 1;
+          sup[a] = std::max(sup[a], 1);
+          sup[b] = std::max(sup[b], 1);
+        }
+      } else if (sup[a] || sup[b]) {
+        keep[i] = 1;
+        sup[a] = sup[b] = 2;
+      }
+    }
+  }
+  P.cone_lo = n;
+  P.cone_hi = -1;
+  for (int q = 0; q < n; ++q)
+    if (sup[q]) {
+      P.cone_lo = std::min(P.cone_lo, q);
+      P.cone_hi = std::max(P.cone_hi, q);
+      ++P.n_active;
+    }
+  for (int i = 0; i < n_ops; ++i) {
+    const tc_op& o = ops[i];
+    P.ops.push_back(TnOp{o.kind, o.param, (float)o.scale, o.mat});
+    if (keep[i]) P.cone.push_back(i);
+  }
+  if (mats)
+    for (int i = 0; i < 2 * n_mats; ++i) P.mats.push_back((float)mats[i]);
+
+  // ---- doubled network ------------------------------------------------------
+  std::vector<Ten> T;
+  int next_label = 0;
+  std::vector<int> ket(n, -1), bra(n, -1);
+  auto add_input = [&](int kind, int gate, int conj, std::vector<int> labels) {
+    TnInput in{};
+    in.kind = kind;
+    in.gate = gate;
+    in.conj = conj;
+    in.rank = (int)labels.size();
+    in.off = (int32_t)P.in_total;
+    P.in_total += pow2(in.rank);
+    P.inputs.push_back(in);
+    T.push_back({std::move(labels)});
+  };
+  const int vec = init == TC_INIT_PLUS ? TS_PLUS : TS_ZERO;
+  for (int q = 0; q < n; ++q)
+    if (sup[q]) {
+      ket[q] = next_label++;
+      add_input(vec, -1, 0, {ket[q]});
+      bra[q] = next_label++;
+      add_input(vec, -1, 1, {bra[q]});
+    }
+  for (int i : P.cone) {
+    const tc_op& o = ops[i];
+    for (int side = 0; side < 2; ++side) {
+      std::vector<int>& ch = side ? bra : ket;
+      if (!two[i]) {
+        const int out = next_label++;
+        add_input(TS_OP1, i, side, {out, ch[o.q0]});
+        ch[o.q0] = out;
+      } else if (split && (o.kind == TC_OP_RZZ || o.kind == TC_OP_CZ || o.kind == TC_OP_CNOT)) {
+        const int k = next_label++, oa = next_label++, ob = next_label++;
+        add_input(TS_SPA, i, side, {oa, ch[o.q0], k});
+        add_input(TS_SPB, i, side, {ob, ch[o.q1], k});
+        ch[o.q0] = oa;
+        ch[o.q1] = ob;
+      } else {
+        const int oa = next_label++, ob = next_label++;
+        add_input(TS_OP2, i, side, {oa, ob, ch[o.q0], ch[o.q1]});
+        ch[o.q0] = oa;
+        ch[o.q1] = ob;
+      }
+    }
+  }
+  for (int q = 0; q < n; ++q) {
+    if (!sup[q]) continue;
+    if (pauli[q]) {
+      add_input(TS_PAULI, pauli[q], 0, {bra[q], ket[q]});
+    } else {
+      for (auto& t : T)
+        for (auto& l : t.labels)
+          if (l == bra[q]) l = ket[q];
+    }
+  }
+  return tn_plan_path(T, rank_cap, path, n_path, P, err);
 }
 
 }  // namespace tcb
@@ -260,6 +482,8 @@ void tn_release(tc_tn* t) {
   if (t->d_tables) cudaFree(t->d_tables);
   if (t->d_inputs) cudaFree(t->d_inputs);
   if (t->d_gate_q) cudaFree(t->d_gate_q);
+  if (t->d_ops) cudaFree(t->d_ops);
+  if (t->d_mats) cudaFree(t->d_mats);
   if (t->d_arena) cudaFree(t->d_arena);
 }
 }  // namespace
@@ -295,13 +519,18 @@ tc_status tc_tn_info(const tc_tn* t, tc_path_info* o) {
   o->n_cone_gates = (int32_t)t->cone.size();
   o->cone_lo = t->cone_lo;
   o->cone_hi = t->cone_hi;
+  o->n_active = t->circuit ? t->n_active : t->cone_hi - t->cone_lo + 1;
   o->n_inputs = (int32_t)t->inputs.size();
   return TC_OK;
 }
 
-tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out, void* stream) {
-  if (!t || !d_gates || !d_out) return fail(TC_E_INVALID, "NULL argument");
-  if (B <= 0) return B == 0 ? TC_OK : fail(TC_E_INVALID, "B < 0");
+}  // extern "C"
+
+namespace {
+// Uploads the plan once, sizes the arena for B instances and replays the
+// whole contraction (assembly, every path step, result) as one CUDA graph,
+// captured once per (B, source buffer, output buffer).
+tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, void* stream) {
   if (B > 65535) return fail(TC_E_UNSUPPORTED, "at most 65535 instances per call");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
@@ -321,6 +550,16 @@ tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out,
       if ((e = cudaMemcpy(t->d_gate_q, t->gate_q.data(), t->gate_q.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "tn gates copy");
     }
+    if (!t->ops.empty()) {
+      if ((e = cudaMalloc(&t->d_ops, t->ops.size() * sizeof(TnOp))) != cudaSuccess) return cuda_fail(e, "tn ops");
+      if ((e = cudaMemcpy(t->d_ops, t->ops.data(), t->ops.size() * sizeof(TnOp), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "tn ops copy");
+    }
+    if (!t->mats.empty()) {
+      if ((e = cudaMalloc(&t->d_mats, t->mats.size() * 4)) != cudaSuccess) return cuda_fail(e, "tn mats");
+      if ((e = cudaMemcpy(t->d_mats, t->mats.data(), t->mats.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "tn mats copy");
+    }
     t->uploaded = true;
   }
   if (B > t->arena_B) {
@@ -334,16 +573,14 @@ tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out,
     t->graph = nullptr;
   }
   float2* arena = (float2*)t->d_arena;
-  // the whole contraction is one CUDA graph (steps are tiny and launch-bound);
-  // it is captured once per (B, input, output) and replayed on `stream`
-  if (!t->graph || t->graph_B != B || t->graph_gates != d_gates || t->graph_out != d_out) {
+  if (!t->graph || t->graph_B != B || t->graph_gates != d_src || t->graph_out != d_out) {
     if (t->graph) cudaGraphExecDestroy(t->graph);
     t->graph = nullptr;
     cudaStream_t cap;
     if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
     cudaGraph_t g;
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = tn_launch_assemble(*t, B, d_gates, arena, cap);
+    if (e == cudaSuccess) e = tn_launch_assemble(*t, B, d_src, arena, cap);
     for (size_t i = 0; e == cudaSuccess && i < t->steps.size(); ++i) e = tn_launch_step(*t, t->steps[i], B, arena, cap);
     if (e == cudaSuccess) e = tn_launch_result(*t, B, arena, d_out, cap);
     cudaError_t e2 = cudaStreamEndCapture(cap, &g);
@@ -358,11 +595,53 @@ tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out,
       return cuda_fail(e, "tn graph capture");
     }
     t->graph_B = B;
-    t->graph_gates = d_gates;
+    t->graph_gates = d_src;
     t->graph_out = d_out;
   }
   if ((e = cudaGraphLaunch(t->graph, s)) != cudaSuccess) return cuda_fail(e, "tn graph launch");
   return TC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out, void* stream) {
+  if (!t || !d_gates || !d_out) return fail(TC_E_INVALID, "NULL argument");
+  if (t->circuit) return fail(TC_E_INVALID, "plan was built from a circuit: use tc_tn_circuit_expect");
+  if (B <= 0) return B == 0 ? TC_OK : fail(TC_E_INVALID, "B < 0");
+  return tn_run(t, B, d_gates, d_out, stream);
+}
+
+tc_status tc_tn_circuit_create(int n_qubits, tc_init init, const tc_op* ops, int n_ops, int n_params,
+                               const double* const_mats, int n_mats, const uint8_t* pauli, int prune, int split,
+                               int rank_cap, const int32_t* path, int n_path_steps, tc_tn** out) {
+  if (!out) return fail(TC_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_qubits < 1 || n_ops < 0 || (n_ops > 0 && !ops) || !pauli || n_params < 0 || n_mats < 0)
+    return fail(TC_E_INVALID, "bad sizes or NULL arrays");
+  if (init != TC_INIT_ZERO && init != TC_INIT_PLUS) return fail(TC_E_INVALID, "init must be TC_INIT_ZERO or TC_INIT_PLUS");
+  if (prune < 0 || prune > 2 || split < 0 || split > 1) return fail(TC_E_INVALID, "prune must be 0..2, split 0..1");
+  if (rank_cap < 1 || rank_cap > 26) return fail(TC_E_INVALID, "rank_cap must be in 1..26");
+  if (path && n_path_steps < 0) return fail(TC_E_INVALID, "n_path_steps < 0");
+  auto* t = new tc_tn();
+  std::string err;
+  if (!tn_build_circuit(n_qubits, (int)init, ops, n_ops, n_params, const_mats, n_mats, pauli, prune, split, rank_cap,
+                        path, n_path_steps, *t, err)) {
+    delete t;
+    return fail(err.rfind("op ", 0) == 0 && err.find("not supported") != std::string::npos ? TC_E_UNSUPPORTED
+                                                                                          : TC_E_INVALID,
+                err);
+  }
+  *out = t;
+  return TC_OK;
+}
+
+tc_status tc_tn_circuit_expect(tc_tn* t, int B, const float* d_params, double* d_out, void* stream) {
+  if (!t || !d_out) return fail(TC_E_INVALID, "NULL argument");
+  if (!t->circuit) return fail(TC_E_INVALID, "plan is a light-cone gate network: use tc_contract_path");
+  if (t->n_params > 0 && !d_params) return fail(TC_E_INVALID, "d_params is NULL");
+  if (B <= 0) return B == 0 ? TC_OK : fail(TC_E_INVALID, "B < 0");
+  return tn_run(t, B, d_params, d_out, stream);
 }
 
 void tc_tn_destroy(tc_tn* t) {

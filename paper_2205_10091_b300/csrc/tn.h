@@ -11,13 +11,35 @@
 namespace tcb {
 
 // Input tensor slot of the doubled network <0|U^dagger O U|0>.
-enum : int32_t { TS_KET = 0, TS_BRA = 1, TS_ZERO = 2, TS_Z = 3 };
+//   TS_KET / TS_BRA   per-instance 4x4 gate matrix (light-cone plans), labels (o0, o1, i0, i1)
+//   TS_ZERO / TS_PLUS initial one-qubit vector |0> or |+>
+//   TS_Z              Z observable, labels (bra, ket)
+//   TS_PAULI          Pauli observable of code `gate` (1..3 = X, Y, Z), labels (bra, ket)
+//   TS_OP1            one-qubit gate of op `gate`, labels (out, in)
+//   TS_OP2            two-qubit gate of op `gate`, labels (o0, o1, i0, i1)
+//   TS_SPA / TS_SPB   the q0 / q1 half of a two-qubit gate of operator-Schmidt
+//                     rank 2 (RZZ, CZ, CNOT), labels (out, in, k)
+// Circuit-network tensors on the bra side carry conj = 1 (complex conjugate).
+enum : int32_t {
+  TS_KET = 0, TS_BRA = 1, TS_ZERO = 2, TS_Z = 3, TS_PLUS = 4, TS_PAULI = 5,
+  TS_OP1 = 6, TS_OP2 = 7, TS_SPA = 8, TS_SPB = 9
+};
 
 struct TnInput {
   int32_t kind;   // TS_*
-  int32_t gate;   // gate index for TS_KET / TS_BRA
+  int32_t gate;   // gate index (TS_KET / TS_BRA), op index (TS_OP*, TS_SP*) or Pauli code
   int32_t off;    // offset (complex entries) in the per-instance input buffer
   int32_t rank;
+  int32_t conj;   // 1: complex-conjugate the entries (bra side of a circuit network)
+  int32_t pad;
+};
+
+// Device copy of one circuit op for the circuit-network assembly kernel.
+struct TnOp {
+  int32_t kind;   // tc_opkind
+  int32_t param;  // -1 = angle 0
+  float scale;
+  int32_t mat;    // offset (complex entries) into the plan's matrix pool
 };
 
 // One pairwise contraction: C[i][j] = sum_k A[fa[i] + sa[k]] * B[sb[k] + fb[j]],
@@ -44,12 +66,21 @@ struct TnPlan {
   int64_t result_off = 0;
   double flops = 0, write = 0, size = 0;  // path metrics (complex MACs, elements, elements)
   int max_rank = 0;
+  // circuit networks (tc_tn_circuit_create): the ops whose values the
+  // assembly kernel evaluates from each instance's parameters
+  bool circuit = false;
+  int n_params = 0;
+  std::vector<TnOp> ops;
+  std::vector<float> mats;              // complex pool as interleaved floats
+  int n_active = 0;                     // qubits with ket/bra chains
   // device state
   bool uploaded = false;
   int device = -1;
   int32_t* d_tables = nullptr;
   TnInput* d_inputs = nullptr;
   int32_t* d_gate_q = nullptr;
+  TnOp* d_ops = nullptr;
+  float* d_mats = nullptr;
   void* d_arena = nullptr;  // float2 [B][arena_total]
   int arena_B = 0;
   cudaGraphExec_t graph = nullptr;
@@ -61,7 +92,13 @@ struct TnPlan {
 bool tn_build_lightcone(int n_qubits, const int32_t* gate_q, int n_gates, const int32_t* z_q, int n_z, int rank_cap,
                         const int32_t* path, int n_path, TnPlan& P, std::string& err);
 
-cudaError_t tn_launch_assemble(const TnPlan& P, int B, const float* d_gates, float2* arena, cudaStream_t s);
+bool tn_build_circuit(int n_qubits, int init, const tc_op* ops, int n_ops, int n_params, const double* mats,
+                      int n_mats, const uint8_t* pauli, int prune, int split, int rank_cap, const int32_t* path,
+                      int n_path, TnPlan& P, std::string& err);
+
+// d_src: [B][n_gates][16] complex64 gates (light-cone plans) or [B][n_params]
+// float parameters (circuit networks)
+cudaError_t tn_launch_assemble(const TnPlan& P, int B, const float* d_src, float2* arena, cudaStream_t s);
 cudaError_t tn_launch_step(const TnPlan& P, const TnStep& st, int B, float2* arena, cudaStream_t s);
 cudaError_t tn_launch_result(const TnPlan& P, int B, const float2* arena, double* d_out, cudaStream_t s);
 

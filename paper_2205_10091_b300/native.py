@@ -76,7 +76,7 @@ class tc_grad_options(C.Structure):
 class tc_path_info(C.Structure):
     _fields_ = [("flops", C.c_double), ("cmacs", C.c_double), ("write", C.c_double), ("size", C.c_double),
                 ("n_steps", C.c_int32), ("max_rank", C.c_int32), ("n_cone_gates", C.c_int32), ("cone_lo", C.c_int32),
-                ("cone_hi", C.c_int32), ("n_inputs", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("cone_hi", C.c_int32), ("n_inputs", C.c_int32), ("n_active", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class tc_server_options(C.Structure):
@@ -138,6 +138,10 @@ SIGNATURES = {
     "tc_tn_info": (C.c_int, [C.c_void_p, C.POINTER(tc_path_info)]),
     "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_tn_destroy": (None, [C.c_void_p]),
+    "tc_tn_circuit_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                       C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                       C.POINTER(C.c_void_p)]),
+    "tc_tn_circuit_expect": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_mean_stderr": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tc_server_create": (C.c_int, [C.POINTER(tc_server_options), C.POINTER(C.c_void_p)]),
     "tc_submit": (C.c_int, [C.c_void_p, C.POINTER(tc_request), C.POINTER(C.c_uint64)]),
@@ -372,6 +376,53 @@ class LightCone:
         if out is None:
             out = torch.empty((B, 2), dtype=torch.float64, device="cuda")
         _check(lib().tc_contract_path(self.h, B, _ptr(d_gates), _ptr(out), _stream(stream)))
+        return out
+
+
+class CircuitNetwork:
+    """<P> of a parameterised circuit contracted as one tensor network
+    (tc_tn_circuit_create / tc_tn_circuit_expect).  ``pauli``: {qubit: code}
+    with codes 1..3 = X, Y, Z; ``prune``: 0 whole network, 1 causal cone,
+    2 cone without commuting diagonal gates; ``split``: rank-2 gates (RZZ, CZ,
+    CNOT) as two tensors."""
+
+    def __init__(self, circ: W.Circuit, pauli: dict, prune: int = 2, split: bool = True, rank_cap: int = 18,
+                 path=None):
+        ops = np.ascontiguousarray(circ.ops, dtype=W.OP_DTYPE)
+        pool = np.ascontiguousarray(np.stack([circ.pool.real, circ.pool.imag], -1).ravel(), dtype=np.float64)
+        codes = np.zeros(circ.n, dtype=np.uint8)
+        for q, c in pauli.items():
+            codes[q] = c
+        pth = None if path is None else np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1, 2))
+        h = C.c_void_p()
+        _check(lib().tc_tn_circuit_create(circ.n, circ.init, ops.ctypes.data_as(C.c_void_p), len(ops), circ.n_params,
+                                          pool.ctypes.data_as(C.c_void_p) if len(circ.pool) else None,
+                                          len(circ.pool), codes.ctypes.data_as(C.c_void_p), prune, int(split),
+                                          rank_cap, None if pth is None else pth.ctypes.data_as(C.c_void_p),
+                                          0 if pth is None else len(pth), C.byref(h)))
+        self.h = h
+        self.n_params = circ.n_params
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.tc_tn_destroy(h)
+            self.h = None
+
+    def info(self) -> dict:
+        o = tc_path_info()
+        _check(lib().tc_tn_info(self.h, C.byref(o)))
+        return {f: getattr(o, f) for f, _ in tc_path_info._fields_ if f != "reserved"}
+
+    def expect(self, d_params, B: int | None = None, out=None, stream=None):
+        """d_params: CUDA float32 [B][n_params]; returns CUDA float64 [B][2] (Re, Im)."""
+        import torch
+
+        if B is None:
+            B = d_params.shape[0]
+        if out is None:
+            out = torch.empty((B, 2), dtype=torch.float64, device="cuda")
+        _check(lib().tc_tn_circuit_expect(self.h, B, _ptr(d_params), _ptr(out), _stream(stream)))
         return out
 
 

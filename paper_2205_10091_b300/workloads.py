@@ -427,6 +427,22 @@ def bp_workload(n: int = 10, layers: int = 10, structures: int = 100, seed: int 
     return circ, theta, seed, pauli_sum(n, [(1.0, {0: 3, 1: 3})])
 
 
+def example_block_circuit(n: int = 40, d: int = 6) -> Circuit:
+    """The contraction testbed of Section "Custom contraction settings": d
+    layers, each exp(i t Z_i Z_{i+1}) along the chain i = 0..n-2 followed by
+    RX on every qubit, on |0...0>.  Weights: theta[2 j n + i] for the ZZ gate
+    (i, i+1) of layer j, theta[(2 j + 1) n + i] for RX on qubit i; the paper
+    sets all 2 d n of them to one.  exp(i t ZZ) = RZZ(-2 t), hence scale -2.
+    The observable is Z on qubit n // 2."""
+    b = OpBuilder(n, INIT_ZERO)
+    for j in range(d):
+        for i in range(n - 1):
+            b.rzz(i, i + 1, 2 * j * n + i, scale=-2.0)
+        for i in range(n):
+            b.rx(i, (2 * j + 1) * n + i)
+    return b.build(2 * d * n)
+
+
 def brick200_workload(n: int = 200, depth: int = 8, seed: int = SEED_BRICK200):
     rng = np.random.default_rng(seed)
     gates = brickwork_u4(n, depth, rng)

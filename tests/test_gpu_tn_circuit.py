@@ -1,0 +1,119 @@
+"""GPU parity for circuit tensor networks (tc_tn_circuit_create /
+tc_tn_circuit_expect, Section "Custom contraction settings") against the
+oracle's dense FP64 state vector (whole register, or a window wider than the
+string's support for the 40-qubit testbed)."""
+import numpy as np
+import pytest
+
+from oracle import statevector as sv
+from oracle import tensornet as T
+from paper_2205_10091_b300 import native as nt
+from paper_2205_10091_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# FP32 tensors and FP32-accumulated GEMMs over a few hundred (small
+# networks) to ~1500 (whole 40-qubit network) steps of unit-norm factors
+TOL_SMALL = 2e-5
+TOL_WHOLE = 2e-4
+
+
+def _random_circuit(n, n_ops, rng, init):
+    b = W.OpBuilder(n, init)
+    p = 0
+    for _ in range(n_ops):
+        k = rng.integers(0, 10)
+        q0, q1 = (int(x) for x in rng.choice(n, 2, replace=False))
+        if k == 0:
+            b.h(q0)
+        elif k == 1:
+            b.x(q0)
+        elif k in (2, 3, 4):
+            (b.rx, b.ry, b.rz)[k - 2](q0, p % 9, scale=float(rng.choice([1.0, -0.5, 2.0])))
+            p += 1
+        elif k == 5:
+            b.rzz(q0, q1, p % 9, scale=-2.0)
+            p += 1
+        elif k == 6:
+            b.cnot(q0, q1)
+        elif k == 7:
+            b.cz(q0, q1)
+        elif k == 8:
+            b.unitary1(q0, W.haar_unitary(2, rng))
+        else:
+            b.unitary2(q0, q1, W.haar_unitary(4, rng))
+    return b.build(9)
+
+
+def _params(theta):
+    import torch
+
+    return torch.as_tensor(np.asarray(theta, np.float32), device="cuda")
+
+
+@pytest.mark.parametrize("prune", [0, 1, 2])
+@pytest.mark.parametrize("split", [False, True])
+@pytest.mark.parametrize("init", [W.INIT_ZERO, W.INIT_PLUS])
+def test_random_circuits_match_statevector(prune, split, init):
+    rng = np.random.default_rng(100 + 10 * prune + 2 * int(split) + init)
+    n = 7
+    for trial in range(3):
+        circ = _random_circuit(n, 40, rng, init)
+        qs = rng.choice(n, int(rng.integers(1, 4)), replace=False)
+        pauli = {int(q): int(rng.integers(1, 4)) for q in qs}
+        theta = rng.uniform(-3, 3, size=(3, circ.n_params))
+        net = nt.CircuitNetwork(circ, pauli, prune=prune, split=split, rank_cap=26)
+        out = net.expect(_params(theta)).cpu().numpy()
+        for b in range(3):
+            psi = sv.run_circuit(circ, theta[b].astype(np.float32).astype(np.float64))
+            ref = complex(*sv.energy(psi, n, W.pauli_sum(n, [(1.0, pauli)])))
+            assert abs(out[b, 0] - ref.real) <= TOL_SMALL
+            assert abs(out[b, 1] - ref.imag) <= TOL_SMALL
+
+
+def _testbed_rows(circ, B, seed):
+    rng = np.random.default_rng(seed)
+    theta = rng.uniform(-1.5, 1.5, size=(B, circ.n_params))
+    theta[0] = 1.0  # the paper's weights: all ones
+    return theta.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("prune,split,tol", [(2, True, TOL_SMALL), (2, False, TOL_SMALL), (0, True, TOL_WHOLE)])
+def test_example_block_40_matches_window_oracle(prune, split, tol):
+    n, d, c = 40, 6, 20
+    circ = W.example_block_circuit(n, d)
+    theta = _testbed_rows(circ, 3, 41)
+    net = nt.CircuitNetwork(circ, {c: 3}, prune=prune, split=split, rank_cap=26)
+    out = net.expect(_params(theta)).cpu().numpy()
+    for b in range(3):
+        ref = T.circuit_window_expectation(circ, theta[b], {c: 3}, c - d - 1, c + d + 1)
+        assert abs(out[b, 0] - ref.real) <= tol
+        assert abs(out[b, 1]) <= tol
+
+
+def test_example_block_batched_rows_sampled():
+    # the bench launch: many weight rows of the 40-qubit testbed in one graph
+    n, d, c = 40, 6, 20
+    circ = W.example_block_circuit(n, d)
+    B = 1024
+    theta = _testbed_rows(circ, B, 42)
+    net = nt.CircuitNetwork(circ, {c: 3}, prune=2, split=True)
+    out = net.expect(_params(theta)).cpu().numpy()
+    for b in (0, 1, 517, B - 1):
+        ref = T.circuit_window_expectation(circ, theta[b], {c: 3}, c - d - 1, c + d + 1)
+        assert abs(out[b, 0] - ref.real) <= TOL_SMALL
+    # a second call on the same buffers replays the captured graph
+    out2 = net.expect(_params(theta)).cpu().numpy()
+    assert np.array_equal(out, out2)
+
+
+def test_mixed_pauli_string_on_testbed():
+    n, d = 40, 6
+    circ = W.example_block_circuit(n, d)
+    theta = _testbed_rows(circ, 2, 43)
+    pauli = {19: 1, 20: 2, 22: 3}
+    net = nt.CircuitNetwork(circ, pauli, prune=2, split=True)
+    out = net.expect(_params(theta)).cpu().numpy()
+    for b in range(2):
+        ref = T.circuit_window_expectation(circ, theta[b], pauli, 19 - d - 1, 22 + d + 1)
+        assert abs(out[b, 0] - ref.real) <= TOL_SMALL and abs(out[b, 1] - ref.imag) <= TOL_SMALL

@@ -69,3 +69,46 @@ def test_example_block_shaped_metrics_reported():
     info = nt.LightCone(n, [(a, b) for a, b, _ in gates], (20,)).info()
     assert 0 < math.log10(info["flops"]) < 10
     assert math.log2(info["size"]) <= 18
+
+
+def test_example_block_commuting_cone_shape():
+    # Section "Custom contraction settings" testbed, n = 40, d = 6, <Z_20>.
+    # Walking back from Z_20, layer j (0-based) keeps RX on 2 (5 - j) + 1
+    # qubits and the 2 (5 - j) + 2 ZZ gates touching them; the first layer's
+    # ZZ gates leave qubits 14 and 26 with diagonal support only.
+    c = W.example_block_circuit(40, 6)
+    net = nt.CircuitNetwork(c, {20: 3}, prune=2, split=True)
+    info = net.info()
+    assert info["n_cone_gates"] == 36 + 42
+    assert (info["cone_lo"], info["cone_hi"], info["n_active"]) == (14, 26, 13)
+    # 13 x (|0> ket + bra) + 2 x (36 RX + 42 x 2 halves) + Z
+    assert info["n_inputs"] == 26 + 2 * (36 + 84) + 1
+    assert info["n_steps"] == info["n_inputs"] - 1
+    unsplit = nt.CircuitNetwork(c, {20: 3}, prune=2, split=False).info()
+    assert unsplit["n_inputs"] == 26 + 2 * (36 + 42) + 1
+
+
+def test_example_block_whole_network_and_causal_cone():
+    c = W.example_block_circuit(40, 6)
+    whole = nt.CircuitNetwork(c, {20: 3}, prune=0, split=True, rank_cap=26).info()
+    assert whole["n_cone_gates"] == len(c.ops) and whole["n_active"] == 40
+    cone = nt.CircuitNetwork(c, {20: 3}, prune=1, split=True, rank_cap=26).info()
+    # in circuit order the chain ZZ(i, i+1), i = 0..38, drags every qubit left of 20 into the cone
+    assert (cone["cone_lo"], cone["cone_hi"]) == (0, 26)
+    comm = nt.CircuitNetwork(c, {20: 3}, prune=2).info()
+    assert comm["cmacs"] < cone["cmacs"] < whole["cmacs"]
+
+
+def test_circuit_network_rejects_bad_input():
+    b = W.OpBuilder(4)
+    b.rx(0, 0)
+    b.depolarizing(1, 0.1, 0.1, 0.1)
+    with pytest.raises(nt.TcError) as e:
+        nt.CircuitNetwork(b.build(), {0: 3})
+    assert e.value.status == nt.TC_E_UNSUPPORTED
+    b = W.OpBuilder(4)
+    b.rx(0, 0)
+    with pytest.raises(nt.TcError):
+        nt.CircuitNetwork(b.build(), {})
+    with pytest.raises(nt.TcError):
+        nt.CircuitNetwork(b.build(), {0: 3}, prune=3)
