@@ -384,6 +384,37 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
         "log10_flops": float(np.log10(info["flops"])), "log2_size": float(np.log2(info["size"])),
         "log2_write": float(np.log2(info["write"])), "steps": info["n_steps"], "cone_gates": info["n_cone_gates"]}
     del gb, ob
+    # ---- contraction testbed: 40 qubits, 6 layers of ZZ + RX, <Z_20> -------
+    cb40 = W.example_block_circuit(40, 6)
+    paths = {}
+    for name, kw in (("whole_network_greedy", dict(prune=0, rank_cap=26)),
+                     ("whole_network_best_of_16", dict(prune=0, rank_cap=26, greedy_trials=16)),
+                     ("causal_cone_greedy", dict(prune=1, rank_cap=26)),
+                     ("commuting_cone_greedy", dict(prune=2)),
+                     ("commuting_cone_best_of_64", dict(prune=2, greedy_trials=64))):
+        pi = nt.CircuitNetwork(cb40, {20: 3}, split=True, **kw).info()
+        paths[name] = {"log10_flops_2_per_cmac": float(np.log10(2 * pi["cmacs"])),
+                       "log2_size": float(np.log2(pi["size"])), "log2_write": float(np.log2(pi["write"])),
+                       "steps": pi["n_steps"], "kept_ops": pi["n_cone_gates"], "qubits": pi["n_active"]}
+    net40 = nt.CircuitNetwork(cb40, {20: 3}, split=True, prune=2, greedy_trials=64)
+    th1 = torch.ones((1, cb40.n_params), dtype=torch.float32, device="cuda")
+    o40 = torch.empty((1, 2), dtype=torch.float64, device="cuda")
+    ms40 = _time_cuda(lambda: net40.expect(th1, out=o40), 200)
+    B40 = 1024
+    th40 = torch.as_tensor(np.random.default_rng(1009).uniform(-1.5, 1.5, (B40, cb40.n_params)).astype(np.float32),
+                           device="cuda")
+    o40b = torch.empty((B40, 2), dtype=torch.float64, device="cuda")
+    ms40b = _time_cuda(lambda: net40.expect(th40, out=o40b), 20)
+    whole = nt.CircuitNetwork(cb40, {20: 3}, split=True, prune=0, rank_cap=26, greedy_trials=16)
+    o40w = torch.empty((1, 2), dtype=torch.float64, device="cuda")
+    ms40w = _time_cuda(lambda: whole.expect(th1, out=o40w), 20)
+    out["example_block40_tn"] = {
+        "z20_all_ones": float(o40[0, 0].item()), "z20_whole_network": float(o40w[0, 0].item()),
+        "us_per_contraction": ms40 * 1e3, "batched_contractions_per_s": B40 / (ms40b / 1e3), "batch": B40,
+        "us_per_whole_network_contraction": ms40w * 1e3,
+        "paper_default_row": {"log10_flops": 7.373, "log2_size": 12, "log2_write": 20.171},
+        "paths": paths}
+    del net40, whole
     # ---- noisy 16-qubit trajectories ---------------------------------------
     circ, n_traj, seed, obs = W.noisy16_workload()
     c = nt.Circuit(circ)

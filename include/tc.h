@@ -365,7 +365,11 @@ typedef struct {
   int32_t cone_lo, cone_hi; /* qubit span of the light cone */
   int32_t n_inputs;         /* input tensors of the doubled network */
   int32_t n_active;         /* qubits with ket/bra chains in the network */
-  int32_t reserved[3];
+  int32_t fused;            /* executor: 1 = one launch for the whole contraction, live tensors in
+                               shared memory (when smem_bytes <= 200 KiB); 0 = one GEMM launch per
+                               step, replayed as a CUDA graph */
+  int32_t smem_bytes;       /* bytes of live tensors per instance under the liveness layout */
+  int32_t fused_groups;     /* barriers of the fused launch: groups of independent steps */
 } tc_path_info;
 TC_API tc_status tc_tn_lightcone_create(int n_qubits, const int32_t* gate_qubits, int n_gates,
                                         const int32_t* z_qubits, int n_z, int rank_cap, const int32_t* path,
@@ -392,6 +396,10 @@ TC_API void tc_tn_destroy(tc_tn* t);
  *                a dimension-2 bond (their operator-Schmidt decomposition);
  *                0 = as one rank-4 tensor
  *   rank_cap, path, n_path_steps   as tc_tn_lightcone_create
+ *   greedy_trials  without a path: 0 or 1 = the deterministic greedy path;
+ *                k > 1 = the cheapest (FLOPs, then WRITE) of it and k - 1
+ *                randomised greedy runs whose pair costs carry seeded Gumbel
+ *                noise (deterministic for a given k)
  * The network holds ket and bra (complex-conjugated) copies of the kept
  * ops, the initial vectors and the string's Pauli matrices; qubits carrying
  * the identity join their ket and bra legs.  Host only.
@@ -406,7 +414,8 @@ TC_API void tc_tn_destroy(tc_tn* t);
  */
 TC_API tc_status tc_tn_circuit_create(int n_qubits, tc_init init, const tc_op* ops, int n_ops, int n_params,
                                       const double* const_mats, int n_mats, const uint8_t* pauli, int prune,
-                                      int split, int rank_cap, const int32_t* path, int n_path_steps, tc_tn** out);
+                                      int split, int rank_cap, int greedy_trials, const int32_t* path,
+                                      int n_path_steps, tc_tn** out);
 TC_API tc_status tc_tn_circuit_expect(tc_tn* t, int B, const float* d_params, double* d_out, void* stream);
 
 /*

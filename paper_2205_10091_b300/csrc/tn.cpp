@@ -15,6 +15,7 @@
 #include <array>
 #include <cmath>
 #include <map>
+#include <random>
 #include <set>
 #include <string>
 
@@ -40,8 +41,11 @@ int64_t pow2(int r) { return (int64_t)1 << r; }
 // the connected pair minimising size(out) - size(a) - size(b), ties to the
 // smallest tensor ids, skipping pairs whose result exceeds rank_cap; with
 // no connected pair left, disconnected parts are joined by outer products.
-bool tn_plan_path(std::vector<Ten>& T, int rank_cap, const int32_t* path, int n_path, TnPlan& P, std::string& err) {
+bool tn_plan_once(std::vector<Ten>& T, int rank_cap, const int32_t* path, int n_path, double temp, uint64_t seed,
+                  TnPlan& P, std::string& err) {
   const int n_inputs = (int)T.size();
+  std::mt19937_64 rng(seed);
+  std::uniform_real_distribution<double> uni(1e-300, 1.0);
   int max_label = -1;
   for (const auto& t : T)
     for (int l : t.labels) max_label = std::max(max_label, l);
@@ -110,7 +114,7 @@ bool tn_plan_path(std::vector<Ten>& T, int rank_cap, const int32_t* path, int n_
       best_b = pairs[pi].second;
       ++pi;
     } else {
-      int64_t best_cost = 0;
+      double best_cost = 0;
       bool found = false, connected = false;
       for (int x : live)
         for (int l : T[x].labels) {
@@ -120,7 +124,11 @@ bool tn_plan_path(std::vector<Ten>& T, int rank_cap, const int32_t* path, int n_
           split_labels(T[x], T[y], fa, sh, fb);
           const int r = (int)(fa.size() + fb.size());
           if (r > rank_cap) continue;
-          const int64_t cost = pow2(r) - pow2((int)T[x].labels.size()) - pow2((int)T[y].labels.size());
+          const int64_t c = pow2(r) - pow2((int)T[x].labels.size()) - pow2((int)T[y].labels.size());
+          double cost = (double)c;
+          if (temp > 0) {  // randomised trial: Gumbel noise on a log-scaled cost
+            cost = (c < 0 ? -1.0 : 1.0) * std::log2(1.0 + std::fabs((double)c)) - temp * std::log(-std::log(uni(rng)));
+          }
           if (!found || cost < best_cost || (cost == best_cost && (x < best_a || (x == best_a && y < best_b)))) {
             found = true;
             best_cost = cost;
@@ -221,6 +229,184 @@ bool tn_plan_path(std::vector<Ten>& T, int rank_cap, const int32_t* path, int n_
   return true;
 }
 
+// Layout for the fused executor.  Steps are grouped by tree level (see
+// tn.h); live tensors get offsets first-fit: inputs first, then per group the
+// results of all its steps while every operand of the group is still live,
+// then the group's operands are released (the root result stays).
+void tn_layout_fused(TnPlan& P) {
+  const int n_inputs = (int)P.inputs.size();
+  const int n_steps = (int)P.steps.size();
+  const int n_ten = n_inputs + n_steps;
+  std::vector<int64_t> off(n_ten, -1), size(n_ten, 0);
+  std::vector<std::pair<int64_t, int64_t>> live;  // (offset, size), sorted by offset
+  int64_t peak = 0;
+  auto place = [&](int id, int64_t sz) {
+    int64_t at = 0;
+    size_t pos = 0;
+    for (; pos < live.size(); ++pos) {
+      if (live[pos].first - at >= sz) break;
+      at = std::max(at, live[pos].first + live[pos].second);
+    }
+    live.insert(live.begin() + pos, {at, sz});
+    off[id] = at;
+    size[id] = sz;
+    peak = std::max(peak, at + sz);
+  };
+  auto release = [&](int id) {
+    for (size_t i = 0; i < live.size(); ++i)
+      if (live[i].first == off[id] && live[i].second == size[id]) {
+        live.erase(live.begin() + i);
+        return;
+      }
+  };
+  auto lg = [](int64_t x) {
+    int r = 0;
+    while (((int64_t)1 << r) < x) ++r;
+    return r;
+  };
+  auto tab_len = [](int g) {
+    return g <= kTnFullTabBits ? (1 << g) : (1 << ((g + 1) / 2)) + (1 << (g - (g + 1) / 2));
+  };
+  // levels
+  std::vector<int> lvl_t(n_ten, 0), lvl(n_steps);
+  for (int s = 0; s < n_steps; ++s) {
+    const TnStep& st = P.steps[s];
+    lvl[s] = 1 + std::max(lvl_t[st.a], lvl_t[st.b]);
+    lvl_t[st.c] = lvl[s];
+  }
+  std::vector<int> order(n_steps);
+  for (int s = 0; s < n_steps; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lvl[x] < lvl[y]; });
+  auto tpo_of = [](const TnStep& st) {
+    int t = kTnFusedThreads / std::max(1, st.M * st.N);
+    t = std::max(1, std::min(32, t));
+    while (t > st.K) t >>= 1;
+    return t;
+  };
+  auto step_tabs = [&](const TnStep& st) {
+    return tab_len(lg(st.M)) + 2 * tab_len(lg(st.K)) + tab_len(lg(st.N));
+  };
+  for (int i = 0; i < n_inputs; ++i) place(i, pow2(P.inputs[i].rank));
+  P.fblob.clear();
+  P.fblob_ok = true;
+  P.n_groups = 0;
+  std::vector<size_t> starts;
+  size_t g0 = 0;
+  while (g0 < order.size()) {
+    // a group: consecutive steps of one level while the block fits
+    size_t g1 = g0;
+    int len = kTnGHdr;
+    while (g1 < order.size() && lvl[order[g1]] == lvl[order[g0]]) {
+      const int add = kTnSRec + step_tabs(P.steps[order[g1]]);
+      if (g1 > g0 && len + add > kTnBlobMax) break;
+      len += add;
+      ++g1;
+    }
+    if (len > kTnBlobMax) P.fblob_ok = false;
+    // steps of the group sorted by tpo so a warp never mixes tpo values
+    std::vector<int> gs(order.begin() + g0, order.begin() + g1);
+    std::stable_sort(gs.begin(), gs.end(),
+                     [&](int x, int y) { return tpo_of(P.steps[x]) < tpo_of(P.steps[y]); });
+    for (int s : gs) place(P.steps[s].c, (int64_t)P.steps[s].M * P.steps[s].N);
+    const size_t gstart = P.fblob.size();
+    starts.push_back(gstart);
+    P.fblob.resize(gstart + kTnGHdr + kTnSRec * gs.size(), 0);
+    int64_t items = 0;
+    int prev_tpo = -1;
+    for (size_t q = 0; q < gs.size(); ++q) {
+      const TnStep& st = P.steps[gs[q]];
+      const int tpo = tpo_of(st);
+      if (tpo != prev_tpo) items = (items + 31) / 32 * 32;  // a warp never spans two tpo values
+      prev_tpo = tpo;
+      const int lgM = lg(st.M), lgK = lg(st.K), lgN = lg(st.N);
+      if (lgM > 16 || lgK > 16 || lgN > 16) P.fblob_ok = false;
+      int32_t* rec = P.fblob.data() + gstart + kTnGHdr + kTnSRec * q;
+      rec[0] = (int32_t)items;
+      rec[1] = st.M;
+      rec[2] = st.K;
+      rec[3] = st.N;
+      rec[4] = lgM;
+      rec[5] = lgK;
+      rec[6] = lgN;
+      rec[7] = tpo;
+      rec[8] = (int32_t)off[st.a];
+      rec[9] = (int32_t)off[st.b];
+      rec[10] = (int32_t)off[st.c];
+      rec[11] = (int32_t)(P.fblob.size() - gstart);
+      auto split = [&](int32_t tab, int g) {
+        if (g <= kTnFullTabBits) {
+          for (int v = 0; v < (1 << g); ++v) P.fblob.push_back(P.tables[tab + v]);
+          return;
+        }
+        const int lo = (g + 1) / 2, hi = g - lo;
+        for (int v = 0; v < (1 << lo); ++v) P.fblob.push_back(P.tables[tab + v]);
+        for (int v = 0; v < (1 << hi); ++v) P.fblob.push_back(P.tables[tab + ((int64_t)v << lo)]);
+      };
+      split(st.fa, lgM);
+      split(st.sa, lgK);
+      split(st.sb, lgK);
+      split(st.fb, lgN);
+      items += (int64_t)st.M * st.N * tpo;
+      if ((int64_t)st.M * st.N * tpo > (1 << 26)) P.fblob_ok = false;
+    }
+    items = (items + 31) / 32 * 32;
+    P.fblob[gstart + 0] = (int32_t)gs.size();
+    P.fblob[gstart + 1] = (int32_t)std::min<int64_t>(items, INT32_MAX);
+    for (int s : gs) {
+      release(P.steps[s].a);
+      release(P.steps[s].b);
+    }
+    ++P.n_groups;
+    g0 = g1;
+  }
+  starts.push_back(P.fblob.size());
+  for (size_t i = 0; i + 1 < starts.size(); ++i) {
+    const int32_t len = (int32_t)(starts[i + 1] - starts[i]);
+    if (len > kTnBlobMax) P.fblob_ok = false;
+    P.fblob[starts[i] + 2] = len;
+    if (i > 0) P.fblob[starts[i - 1] + 3] = len;
+  }
+  P.in_soff.assign(n_inputs, 0);
+  for (int i = 0; i < n_inputs; ++i) P.in_soff[i] = (int32_t)off[i];
+  P.smem_entries = peak;
+  P.result_soff = n_steps == 0 ? 0 : (int32_t)off[P.steps.back().c];
+}
+
+// Path for T: the user's, else the deterministic greedy path, else (trials >
+// 1) the cheapest of that and trials - 1 randomised greedy runs (costs
+// perturbed by Gumbel noise, seeds 1..trials-1), by FLOPs then WRITE.
+bool tn_plan_path(std::vector<Ten>& T, int rank_cap, const int32_t* path, int n_path, int trials, TnPlan& P,
+                  std::string& err) {
+  if (path || trials <= 1) {
+    if (!tn_plan_once(T, rank_cap, path, n_path, 0.0, 0, P, err)) return false;
+    tn_layout_fused(P);
+    return true;
+  }
+  TnPlan best;
+  bool have = false;
+  std::string first_err;
+  for (int t = 0; t < trials; ++t) {
+    std::vector<Ten> Tt = T;
+    TnPlan Pt = P;
+    std::string e;
+    if (!tn_plan_once(Tt, rank_cap, nullptr, 0, t == 0 ? 0.0 : 1.0, (uint64_t)t, Pt, e)) {
+      if (first_err.empty()) first_err = e;
+      continue;
+    }
+    if (!have || Pt.flops < best.flops || (Pt.flops == best.flops && Pt.write < best.write)) {
+      best = std::move(Pt);
+      have = true;
+    }
+  }
+  if (!have) {
+    err = first_err;
+    return false;
+  }
+  P = std::move(best);
+  tn_layout_fused(P);
+  return true;
+}
+
 bool tn_build_lightcone(int n_qubits, const int32_t* gate_q, int n_gates, const int32_t* z_q, int n_z, int rank_cap,
                         const int32_t* path, int n_path, TnPlan& P, std::string& err) {
   P = TnPlan{};
@@ -301,7 +487,7 @@ bool tn_build_lightcone(int n_qubits, const int32_t* gate_q, int n_gates, const 
           if (l == bra[q]) l = ket[q];
     }
   }
-  return tn_plan_path(T, rank_cap, path, n_path, P, err);
+  return tn_plan_path(T, rank_cap, path, n_path, 1, P, err);
 }
 
 // Circuit network <init| K^dagger P K |init> for a Pauli string P, K the ops
@@ -319,8 +505,8 @@ bool tn_build_lightcone(int n_qubits, const int32_t* gate_q, int n_gates, const 
 //   split 1  RZZ, CZ and CNOT enter as two rank-3 tensors joined by a bond
 //            of dimension 2 (their operator-Schmidt rank), else as one 4x4.
 bool tn_build_circuit(int n, int init, const tc_op* ops, int n_ops, int n_params, const double* mats, int n_mats,
-                      const uint8_t* pauli, int prune, int split, int rank_cap, const int32_t* path, int n_path,
-                      TnPlan& P, std::string& err) {
+                      const uint8_t* pauli, int prune, int split, int rank_cap, int trials, const int32_t* path,
+                      int n_path, TnPlan& P, std::string& err) {
   P = TnPlan{};
   P.circuit = true;
   P.n_qubits = n;
@@ -467,7 +653,7 @@ bool tn_build_circuit(int n, int init, const tc_op* ops, int n_ops, int n_params
           if (l == bra[q]) l = ket[q];
     }
   }
-  return tn_plan_path(T, rank_cap, path, n_path, P, err);
+  return tn_plan_path(T, rank_cap, path, n_path, trials, P, err);
 }
 
 }  // namespace tcb
@@ -484,6 +670,8 @@ void tn_release(tc_tn* t) {
   if (t->d_gate_q) cudaFree(t->d_gate_q);
   if (t->d_ops) cudaFree(t->d_ops);
   if (t->d_mats) cudaFree(t->d_mats);
+  if (t->d_fblob) cudaFree(t->d_fblob);
+  if (t->d_in_soff) cudaFree(t->d_in_soff);
   if (t->d_arena) cudaFree(t->d_arena);
 }
 }  // namespace
@@ -520,6 +708,9 @@ tc_status tc_tn_info(const tc_tn* t, tc_path_info* o) {
   o->cone_lo = t->cone_lo;
   o->cone_hi = t->cone_hi;
   o->n_active = t->circuit ? t->n_active : t->cone_hi - t->cone_lo + 1;
+  o->fused = tn_fused_ok(*t) ? 1 : 0;
+  o->smem_bytes = (int32_t)std::min<int64_t>(t->smem_entries * 8, INT32_MAX);
+  o->fused_groups = t->n_groups;
   o->n_inputs = (int32_t)t->inputs.size();
   return TC_OK;
 }
@@ -527,9 +718,10 @@ tc_status tc_tn_info(const tc_tn* t, tc_path_info* o) {
 }  // extern "C"
 
 namespace {
-// Uploads the plan once, sizes the arena for B instances and replays the
-// whole contraction (assembly, every path step, result) as one CUDA graph,
-// captured once per (B, source buffer, output buffer).
+// Uploads the plan once.  A plan whose live tensors fit in shared memory runs
+// as one fused launch; otherwise the arena is sized for B instances and the
+// whole contraction (assembly, every path step, result) replays as one CUDA
+// graph, captured once per (B, source buffer, output buffer).
 tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, void* stream) {
   if (B > 65535) return fail(TC_E_UNSUPPORTED, "at most 65535 instances per call");
   cudaStream_t s = (cudaStream_t)stream;
@@ -560,7 +752,22 @@ tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, void* strea
       if ((e = cudaMemcpy(t->d_mats, t->mats.data(), t->mats.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(e, "tn mats copy");
     }
+    if (tn_fused_ok(*t)) {
+      if ((e = cudaMalloc(&t->d_fblob, t->fblob.size() * 4)) != cudaSuccess) return cuda_fail(e, "tn fused steps");
+      if ((e = cudaMemcpy(t->d_fblob, t->fblob.data(), t->fblob.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "tn fused steps copy");
+      if ((e = cudaMalloc(&t->d_in_soff, t->in_soff.size() * 4)) != cudaSuccess) return cuda_fail(e, "tn offsets");
+      if ((e = cudaMemcpy(t->d_in_soff, t->in_soff.data(), t->in_soff.size() * 4, cudaMemcpyHostToDevice)) !=
+          cudaSuccess)
+        return cuda_fail(e, "tn offsets copy");
+    }
     t->uploaded = true;
+  }
+  if (tn_fused_ok(*t)) {
+    const int grid = tn_fused_grid(*t, B);
+    if (grid < 1) return fail(TC_E_CUDA, "tn fused launch: no valid grid");
+    if ((e = tn_launch_fused(*t, B, d_src, d_out, grid, s)) != cudaSuccess) return cuda_fail(e, "tn fused launch");
+    return TC_OK;
   }
   if (B > t->arena_B) {
     if (t->d_arena) cudaFree(t->d_arena);
@@ -614,7 +821,7 @@ tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out,
 
 tc_status tc_tn_circuit_create(int n_qubits, tc_init init, const tc_op* ops, int n_ops, int n_params,
                                const double* const_mats, int n_mats, const uint8_t* pauli, int prune, int split,
-                               int rank_cap, const int32_t* path, int n_path_steps, tc_tn** out) {
+                               int rank_cap, int greedy_trials, const int32_t* path, int n_path_steps, tc_tn** out) {
   if (!out) return fail(TC_E_INVALID, "out is NULL");
   *out = nullptr;
   if (n_qubits < 1 || n_ops < 0 || (n_ops > 0 && !ops) || !pauli || n_params < 0 || n_mats < 0)
@@ -622,11 +829,12 @@ tc_status tc_tn_circuit_create(int n_qubits, tc_init init, const tc_op* ops, int
   if (init != TC_INIT_ZERO && init != TC_INIT_PLUS) return fail(TC_E_INVALID, "init must be TC_INIT_ZERO or TC_INIT_PLUS");
   if (prune < 0 || prune > 2 || split < 0 || split > 1) return fail(TC_E_INVALID, "prune must be 0..2, split 0..1");
   if (rank_cap < 1 || rank_cap > 26) return fail(TC_E_INVALID, "rank_cap must be in 1..26");
+  if (greedy_trials < 0 || greedy_trials > 4096) return fail(TC_E_INVALID, "greedy_trials must be in 0..4096");
   if (path && n_path_steps < 0) return fail(TC_E_INVALID, "n_path_steps < 0");
   auto* t = new tc_tn();
   std::string err;
   if (!tn_build_circuit(n_qubits, (int)init, ops, n_ops, n_params, const_mats, n_mats, pauli, prune, split, rank_cap,
-                        path, n_path_steps, *t, err)) {
+                        greedy_trials, path, n_path_steps, *t, err)) {
     delete t;
     return fail(err.rfind("op ", 0) == 0 && err.find("not supported") != std::string::npos ? TC_E_UNSUPPORTED
                                                                                           : TC_E_INVALID,

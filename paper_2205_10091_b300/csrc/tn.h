@@ -52,6 +52,32 @@ struct TnStep {
   int64_t a_off, b_off, c_off;  // offsets (complex entries) of the operands in the per-instance arena
 };
 
+// Fused executor blob: the path's steps grouped by level of the contraction
+// tree (a step's level is one more than its operands'), steps of one level
+// being independent; a level too large for one staged block is cut into
+// several groups run one after another.  Per group:
+//   header (kTnGHdr ints): {n_steps, n_items, len, next_len, 0...}
+//   per step (kTnSRec ints): {item0, M, K, N, lgM, lgK, lgN, tpo, a, b, c, tab}
+//     item0 = first work item of the step (work items: M N tpo, each run of
+//     equal tpo padded to a warp), a, b, c = live-tensor offsets (complex
+//     entries), tab = offset of the step's tables from the group start
+//   tables: per step fa, sa, sb, fb; an index set of g <= 8 bits as one full
+//     table, a wider one split in two levels: lo = the lowest (g + 1) / 2
+//     bits, table(v) = lo[v & (2^lo - 1)] + hi[v >> lo] (the bits scatter to
+//     disjoint positions, so the parts add)
+constexpr int kTnGHdr = 8;
+constexpr int kTnFullTabBits = 8;
+// Threads of a fused-executor CTA (work items of a group are spread over them).
+constexpr int kTnFusedThreads = 1024;
+constexpr int kTnSRec = 12;
+// Longest group block staged in shared memory (ints).
+constexpr int kTnBlobMax = 3072;
+
+// Largest live-tensor layout the fused executor keeps in shared memory
+// (bytes per CTA; the two staged step blocks take 2 x kTnBlobMax ints more).
+constexpr int kTnFusedSmemMax = 200 * 1024;
+
+
 struct TnPlan {
   int n_qubits = 0;
   int n_gates = 0;
@@ -73,6 +99,13 @@ struct TnPlan {
   std::vector<TnOp> ops;
   std::vector<float> mats;              // complex pool as interleaved floats
   int n_active = 0;                     // qubits with ket/bra chains
+  // fused executor layout
+  std::vector<int32_t> fblob;           // group blocks (see kTnGHdr)
+  int n_groups = 0;
+  bool fblob_ok = false;                // every group within kTnBlobMax
+  std::vector<int32_t> in_soff;         // shared-memory offset of each input tensor
+  int64_t smem_entries = 0;
+  int32_t result_soff = 0;
   // device state
   bool uploaded = false;
   int device = -1;
@@ -81,6 +114,8 @@ struct TnPlan {
   int32_t* d_gate_q = nullptr;
   TnOp* d_ops = nullptr;
   float* d_mats = nullptr;
+  int32_t* d_fblob = nullptr;
+  int32_t* d_in_soff = nullptr;
   void* d_arena = nullptr;  // float2 [B][arena_total]
   int arena_B = 0;
   cudaGraphExec_t graph = nullptr;
@@ -93,13 +128,19 @@ bool tn_build_lightcone(int n_qubits, const int32_t* gate_q, int n_gates, const 
                         const int32_t* path, int n_path, TnPlan& P, std::string& err);
 
 bool tn_build_circuit(int n_qubits, int init, const tc_op* ops, int n_ops, int n_params, const double* mats,
-                      int n_mats, const uint8_t* pauli, int prune, int split, int rank_cap, const int32_t* path,
-                      int n_path, TnPlan& P, std::string& err);
+                      int n_mats, const uint8_t* pauli, int prune, int split, int rank_cap, int trials,
+                      const int32_t* path, int n_path, TnPlan& P, std::string& err);
 
 // d_src: [B][n_gates][16] complex64 gates (light-cone plans) or [B][n_params]
 // float parameters (circuit networks)
 cudaError_t tn_launch_assemble(const TnPlan& P, int B, const float* d_src, float2* arena, cudaStream_t s);
 cudaError_t tn_launch_step(const TnPlan& P, const TnStep& st, int B, float2* arena, cudaStream_t s);
+// The whole contraction of B instances in one launch (one CTA per instance,
+// grid-stride) with every live tensor in shared memory; taken when the
+// plan's layout fits (else one GEMM launch per step, replayed as a graph).
+bool tn_fused_ok(const TnPlan& P);
+int tn_fused_grid(const TnPlan& P, int B);
+cudaError_t tn_launch_fused(const TnPlan& P, int B, const float* d_src, double* d_out, int grid, cudaStream_t s);
 cudaError_t tn_launch_result(const TnPlan& P, int B, const float2* arena, double* d_out, cudaStream_t s);
 
 }  // namespace tcb

@@ -173,6 +173,158 @@ __global__ void k_tn_result(const float2* arena, int64_t arena_total, int64_t of
   }
 }
 
+// Fused executor: one CTA per instance (grid-stride over instances) runs the
+// assembly and the whole path with all live tensors in shared memory.  The path runs group by group (independent
+// steps of one tree level, see tn.h), one barrier per group; the group's work
+// items are spread over the CTA's threads.  A step computes
+// C[e] = sum_k A[fa(i) + sa(k)] B[sb(k) + fb(j)], e = i N + j, with tpo
+// items per output (a power of two <= 32: small results with long sums
+// spread the sum over lanes and reduce by shuffles).  Group blocks are staged
+// in a double-buffered shared slot: the next block is loaded into registers
+// before the current group computes and stored after it.
+constexpr int kFusedThreads = kTnFusedThreads;
+constexpr int kFusedPf = (kTnBlobMax + kFusedThreads - 1) / kFusedThreads;
+
+__device__ __forceinline__ int tn_tab(const int32_t* t, int lg, int v) {
+  if (lg <= kTnFullTabBits) return t[v];
+  const int lo = (lg + 1) >> 1;
+  return t[v & ((1 << lo) - 1)] + t[(1 << lo) + (v >> lo)];
+}
+
+__device__ __forceinline__ int tn_tab_len(int lg) {
+  if (lg <= kTnFullTabBits) return 1 << lg;
+  const int lo = (lg + 1) >> 1;
+  return (1 << lo) + (1 << (lg - lo));
+}
+
+template <bool CIRCUIT>
+__global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __restrict__ inputs,
+                                                            const int32_t* __restrict__ in_soff, int n_inputs,
+                                                            const int32_t* __restrict__ blob, int n_groups,
+                                                            const float* __restrict__ src, int n_src,
+                                                            const TnOp* __restrict__ ops,
+                                                            const float* __restrict__ mats, int result_soff, int B,
+                                                            double* __restrict__ out) {
+  extern __shared__ float2 sm[];
+  __shared__ int32_t tb[2][kTnBlobMax];
+  const int tid = threadIdx.x;
+  for (int b = blockIdx.x; b < B; b += gridDim.x) {
+    // ---- group 0's block, and the inputs: one warp per tensor, a lane per entry
+    const int len0 = n_groups > 0 ? __ldg(blob + 2) : 0;
+    for (int i = tid; i < len0; i += kFusedThreads) tb[0][i] = __ldg(blob + i);
+    for (int t = tid >> 5; t < n_inputs; t += kFusedThreads / 32) {
+      const TnInput in = inputs[t];
+      const int e = tid & 31;
+      if (e < (1 << in.rank)) {
+        float2 v;
+        if (CIRCUIT) {
+          v = tn_circuit_entry(in, e, ops, mats, src + (size_t)b * n_src);
+          if (in.conj) v.y = -v.y;
+        } else if (in.kind == TS_KET || in.kind == TS_BRA) {
+          const float* g = src + ((size_t)b * n_src + in.gate) * 32;
+          v = make_float2(g[2 * e], in.kind == TS_BRA ? -g[2 * e + 1] : g[2 * e + 1]);
+        } else if (in.kind == TS_ZERO) {
+          v = make_float2(e == 0 ? 1.f : 0.f, 0.f);
+        } else {  // TS_Z
+          v = make_float2(e == 0 ? 1.f : (e == 3 ? -1.f : 0.f), 0.f);
+        }
+        sm[in_soff[t] + e] = v;
+      }
+    }
+    __syncthreads();
+    // ---- path, group by group ------------------------------------------------
+    int off = 0;
+    for (int gi = 0; gi < n_groups; ++gi) {
+      const int32_t* g = tb[gi & 1];
+      const int n_st = g[0], n_items = g[1], len = g[2];
+      const int nlen = gi + 1 < n_groups ? g[3] : 0;
+      int32_t pf[kFusedPf];
+#pragma unroll
+      for (int r = 0; r < kFusedPf; ++r) {
+        const int i = tid + r * kFusedThreads;
+        pf[r] = i < nlen ? __ldg(blob + off + len + i) : 0;
+      }
+      const int32_t* recs = g + kTnGHdr;
+      for (int base = 0; base < n_items; base += kFusedThreads) {
+        const int w = base + tid;
+        int lo = 0, hi = n_st - 1;  // last step whose first item is <= w
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (recs[mid * kTnSRec] <= w) lo = mid; else hi = mid - 1;
+        }
+        const int32_t* r = recs + lo * kTnSRec;
+        const int M = r[1], K = r[2], N = r[3], lgM = r[4], lgK = r[5], lgN = r[6], tpo = r[7];
+        const int local = w - r[0];
+        const int e = local >> (__ffs(tpo) - 1), part = local & (tpo - 1);
+        const int32_t* fa = g + r[11];
+        const int32_t* sa = fa + tn_tab_len(lgM);
+        const int32_t* sb = sa + tn_tab_len(lgK);
+        const int32_t* fb = sb + tn_tab_len(lgK);
+        float2 acc = make_float2(0.f, 0.f);
+        const bool valid = e < M * N;
+        if (valid) {
+          const float2* Ar = sm + r[8] + tn_tab(fa, lgM, e >> lgN);
+          const float2* Bc = sm + r[9] + tn_tab(fb, lgN, e & (N - 1));
+          for (int k = part; k < K; k += tpo) {
+            const float2 a = Ar[tn_tab(sa, lgK, k)];
+            const float2 c = Bc[tn_tab(sb, lgK, k)];
+            acc.x = fmaf(a.x, c.x, fmaf(-a.y, c.y, acc.x));
+            acc.y = fmaf(a.x, c.y, fmaf(a.y, c.x, acc.y));
+          }
+        }
+        // tpo is uniform over a warp: runs of equal tpo are padded to 32 items
+        for (int o = tpo >> 1; o > 0; o >>= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (valid && part == 0) sm[r[10] + e] = acc;
+      }
+      // the other slot held the previous group's block, which no thread reads any more
+      int32_t* nb = tb[(gi + 1) & 1];
+#pragma unroll
+      for (int r = 0; r < kFusedPf; ++r) {
+        const int i = tid + r * kFusedThreads;
+        if (i < nlen) nb[i] = pf[r];
+      }
+      off += len;
+      __syncthreads();
+    }
+    if (tid == 0) {
+      const float2 v = sm[result_soff];
+      out[2 * b] = (double)v.x;
+      out[2 * b + 1] = (double)v.y;
+    }
+    __syncthreads();
+  }
+}
+
+bool tn_fused_ok(const TnPlan& P) {
+  return !P.steps.empty() && P.smem_entries > 0 && P.fblob_ok && !P.fblob.empty() &&
+         P.smem_entries * 8 <= kTnFusedSmemMax;
+}
+
+int tn_fused_grid(const TnPlan& P, int B) {
+  const int smem = (int)(P.smem_entries * 8);
+  int per_sm = 0, sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  auto kern = P.circuit ? k_tn_fused<true> : k_tn_fused<false>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, smem) != cudaSuccess) return 0;
+  if (per_sm < 1) return 0;
+  return B < per_sm * sms ? B : per_sm * sms;
+}
+
+cudaError_t tn_launch_fused(const TnPlan& P, int B, const float* d_src, double* d_out, int grid, cudaStream_t s) {
+  if (!tn_fused_ok(P) || grid < 1) return cudaErrorInvalidConfiguration;
+  const int smem = (int)(P.smem_entries * 8);
+  auto kern = P.circuit ? k_tn_fused<true> : k_tn_fused<false>;
+  kern<<<grid, kFusedThreads, smem, s>>>(P.d_inputs, P.d_in_soff, (int)P.inputs.size(), P.d_fblob, P.n_groups,
+                                         d_src, P.circuit ? P.n_params : P.n_gates, P.d_ops, P.d_mats,
+                                         P.result_soff, B, d_out);
+  return cudaGetLastError();
+}
+
 cudaError_t tn_launch_assemble(const TnPlan& P, int B, const float* d_src, float2* arena, cudaStream_t s) {
   if (P.inputs.empty()) return cudaSuccess;
   dim3 grid((unsigned)P.inputs.size(), (unsigned)B);

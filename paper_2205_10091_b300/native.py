@@ -76,7 +76,8 @@ class tc_grad_options(C.Structure):
 class tc_path_info(C.Structure):
     _fields_ = [("flops", C.c_double), ("cmacs", C.c_double), ("write", C.c_double), ("size", C.c_double),
                 ("n_steps", C.c_int32), ("max_rank", C.c_int32), ("n_cone_gates", C.c_int32), ("cone_lo", C.c_int32),
-                ("cone_hi", C.c_int32), ("n_inputs", C.c_int32), ("n_active", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("cone_hi", C.c_int32), ("n_inputs", C.c_int32), ("n_active", C.c_int32), ("fused", C.c_int32),
+                ("smem_bytes", C.c_int32), ("fused_groups", C.c_int32)]
 
 
 class tc_server_options(C.Structure):
@@ -139,7 +140,7 @@ SIGNATURES = {
     "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_tn_destroy": (None, [C.c_void_p]),
     "tc_tn_circuit_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
-                                       C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                       C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                        C.POINTER(C.c_void_p)]),
     "tc_tn_circuit_expect": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_mean_stderr": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
@@ -384,10 +385,11 @@ class CircuitNetwork:
     (tc_tn_circuit_create / tc_tn_circuit_expect).  ``pauli``: {qubit: code}
     with codes 1..3 = X, Y, Z; ``prune``: 0 whole network, 1 causal cone,
     2 cone without commuting diagonal gates; ``split``: rank-2 gates (RZZ, CZ,
-    CNOT) as two tensors."""
+    CNOT) as two tensors; ``greedy_trials``: > 1 keeps the cheapest of that
+    many greedy paths (the first deterministic, the rest randomised)."""
 
     def __init__(self, circ: W.Circuit, pauli: dict, prune: int = 2, split: bool = True, rank_cap: int = 18,
-                 path=None):
+                 greedy_trials: int = 1, path=None):
         ops = np.ascontiguousarray(circ.ops, dtype=W.OP_DTYPE)
         pool = np.ascontiguousarray(np.stack([circ.pool.real, circ.pool.imag], -1).ravel(), dtype=np.float64)
         codes = np.zeros(circ.n, dtype=np.uint8)
@@ -398,7 +400,8 @@ class CircuitNetwork:
         _check(lib().tc_tn_circuit_create(circ.n, circ.init, ops.ctypes.data_as(C.c_void_p), len(ops), circ.n_params,
                                           pool.ctypes.data_as(C.c_void_p) if len(circ.pool) else None,
                                           len(circ.pool), codes.ctypes.data_as(C.c_void_p), prune, int(split),
-                                          rank_cap, None if pth is None else pth.ctypes.data_as(C.c_void_p),
+                                          rank_cap, greedy_trials,
+                                          None if pth is None else pth.ctypes.data_as(C.c_void_p),
                                           0 if pth is None else len(pth), C.byref(h)))
         self.h = h
         self.n_params = circ.n_params

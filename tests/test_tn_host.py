@@ -112,3 +112,27 @@ def test_circuit_network_rejects_bad_input():
         nt.CircuitNetwork(b.build(), {})
     with pytest.raises(nt.TcError):
         nt.CircuitNetwork(b.build(), {0: 3}, prune=3)
+
+
+def test_greedy_trials_deterministic_and_no_worse():
+    c = W.example_block_circuit(40, 6)
+    one = nt.CircuitNetwork(c, {20: 3}, prune=2, greedy_trials=1).info()
+    a = nt.CircuitNetwork(c, {20: 3}, prune=2, greedy_trials=16).info()
+    b = nt.CircuitNetwork(c, {20: 3}, prune=2, greedy_trials=16).info()
+    assert a == b
+    assert a["cmacs"] <= one["cmacs"]
+    with pytest.raises(nt.TcError):
+        nt.CircuitNetwork(c, {20: 3}, greedy_trials=-1)
+
+
+def test_executor_choice():
+    # small live sets run as one fused launch; the whole 40-qubit network and
+    # the 200-qubit light cone (live tensors above 200 KiB) as per-step GEMMs
+    c = W.example_block_circuit(40, 6)
+    fused = nt.CircuitNetwork(c, {20: 3}, prune=2).info()
+    assert fused["fused"] == 1 and 0 < fused["smem_bytes"] <= 200 * 1024
+    assert 0 < fused["fused_groups"] < fused["n_steps"]
+    whole = nt.CircuitNetwork(c, {20: 3}, prune=0, rank_cap=26).info()
+    assert whole["fused"] == 0 and whole["smem_bytes"] > 200 * 1024
+    n, gates, obs = W.brick200_workload()
+    assert nt.LightCone(n, [(a, b) for a, b, _ in gates], obs).info()["fused"] == 0
