@@ -7,13 +7,18 @@ uses two other routes so that neither can hide a mistake in the other:
   and a = s*theta_k, dE/da = [E(a + pi/2) - E(a - pi/2)] / 2 exactly, and
   dE/dtheta_k sums s * dE/da over every occurrence of theta_k (shared angles
   such as one g_l over a whole RZZ layer);
-* central finite differences with step h in FP64.
+* central finite differences with step h in FP64;
+* state derivatives by the product rule (generator inserted after each gate
+  occurrence) and the quantum geometric tensor built from them.
 
 Pinned by tests/test_oracle_gradients.py: the batched-VQE toy of Section
 "Batched VQE" (closed form cos(w1), gradient (0, -sin w1)), the vvag toy of
 Section "vmap and vectorized_value_and_grad" (summed-over-batch gradient),
 agreement of the two routes, and TFIM closed forms (zero gradient at zero
-angles).  Batch semantics (Section "vmap and vectorized_value_and_grad"):
+angles); the state derivatives against central differences of the state,
+and the geometric tensor against closed forms (one qubit RY then RZ: the
+Bloch-sphere metric diag(1/4, sin^2(a)/4); a global-phase parameter gives a
+zero row).  Batch semantics (Section "vmap and vectorized_value_and_grad"):
 with argnums == vectorized_argnums each row gets its own gradient; the
 summed variant is the sum over rows.
 """
@@ -62,3 +67,42 @@ def finite_difference(circ: W.Circuit, theta_row, ham: W.PauliSum, h: float = 1e
         tm[k] -= h
         g[k] = (energy_of(circ, tp, ham) - energy_of(circ, tm, ham)) / (2.0 * h)
     return g
+
+
+_GENERATOR = {W.OP_RX: 1, W.OP_RY: 2, W.OP_RZ: 3}  # Pauli code of G in exp(-i a G / 2)
+
+
+def state_derivatives(circ: W.Circuit, theta_row) -> np.ndarray:
+    """[n_params][2^n]: d|psi>/d theta_p by the product rule, one gate
+    occurrence at a time: for an occurrence exp(-i a G / 2), a = s theta_p,
+    the term is U_after (-i s / 2) G U_upto |psi_0>, the generator applied
+    right after the gate (the two commute).  RZZ has G = Z (x) Z."""
+    n = circ.n
+    theta_row = np.asarray(theta_row, np.float64)
+    out = np.zeros((circ.n_params, 2 ** n), np.complex128)
+    for idx, op in enumerate(circ.ops):
+        p = int(op["param"])
+        if p < 0:
+            continue
+        k = int(op["kind"])
+        assert k in (W.OP_RX, W.OP_RY, W.OP_RZ, W.OP_RZZ), "state derivatives need RX/RY/RZ/RZZ gates"
+        head = W.Circuit(n, circ.ops[:idx + 1], circ.n_params, circ.pool, circ.init)
+        psi = sv.run_circuit(head, theta_row)
+        if k == W.OP_RZZ:
+            psi = sv.apply_1q(psi, n, int(op["q0"]), sv.PZ)
+            psi = sv.apply_1q(psi, n, int(op["q1"]), sv.PZ)
+        else:
+            psi = sv.apply_1q(psi, n, int(op["q0"]), sv.PAULI[_GENERATOR[k]])
+        psi = psi * (-0.5j * float(op["scale"]))
+        tail = W.Circuit(n, circ.ops[idx + 1:], circ.n_params, circ.pool, circ.init)
+        out[p] += sv.run_circuit(tail, theta_row, init_state=psi)
+    return out
+
+
+def quantum_geometric_tensor(circ: W.Circuit, theta_row) -> np.ndarray:
+    """G_ij = <d_i psi|d_j psi> - <d_i psi|psi><psi|d_j psi> (Section
+    "Quantum Fisher Information"); the QFI is 4 Re G."""
+    psi = sv.run_circuit(circ, theta_row)
+    d = state_derivatives(circ, theta_row)
+    ov = d.conj() @ psi  # <d_i psi|psi>
+    return d.conj() @ d.T - np.outer(ov, ov.conj())

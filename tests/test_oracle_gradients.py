@@ -71,3 +71,60 @@ def test_summed_batch_gradient_is_row_sum():
         e = np.zeros(4)
         e[k] = h
         assert abs((tot(e) - tot(-e)) / (2 * h) - rows[:, k].sum()) < 1e-8
+
+
+def _qgt_circuit(rng, n=4):
+    b = W.OpBuilder(n)
+    for q in range(n):
+        b.ry(q, q)
+    for q in range(n - 1):
+        b.rzz(q, q + 1, n, scale=-2.0)  # one shared angle over the chain
+    b.cnot(0, 2)
+    for q in range(n):
+        b.rx(q, n + 1 + q % 2, scale=0.5)
+    b.rz(1, 0)  # theta_0 also drives a second gate
+    return b.build()
+
+
+def test_state_derivatives_match_finite_differences():
+    rng = np.random.default_rng(77)
+    circ = _qgt_circuit(rng)
+    theta = rng.uniform(-2, 2, circ.n_params)
+    d = G.state_derivatives(circ, theta)
+    h = 1e-6
+    for p in range(circ.n_params):
+        tp, tm = theta.copy(), theta.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (sv.run_circuit(circ, tp) - sv.run_circuit(circ, tm)) / (2 * h)
+        assert np.abs(d[p] - fd).max() < 1e-8
+
+
+def test_qgt_bloch_sphere_closed_form():
+    # RZ(b) RY(a) |0>: the Fubini-Study metric is diag(1/4, sin^2(a) / 4)
+    b = W.OpBuilder(1)
+    b.ry(0, 0)
+    b.rz(0, 1)
+    circ = b.build()
+    for a, bb in [(0.3, -1.1), (1.9, 0.4), (np.pi / 2, 2.0)]:
+        g = G.quantum_geometric_tensor(circ, [a, bb])
+        assert np.allclose(g.real, [[0.25, 0.0], [0.0, np.sin(a) ** 2 / 4]], atol=1e-14)
+        assert np.allclose(g, g.conj().T, atol=1e-14)
+
+
+def test_qgt_global_phase_parameter_is_zero():
+    # RZ on |0> only multiplies by a phase: <d psi|d psi> = |<psi|d psi>|^2
+    b = W.OpBuilder(2)
+    b.rz(0, 0)
+    b.ry(1, 1)
+    g = G.quantum_geometric_tensor(b.build(), [0.7, 0.2])
+    assert np.abs(g[0]).max() < 1e-14 and np.abs(g[:, 0]).max() < 1e-14
+    assert abs(g[1, 1] - 0.25) < 1e-14
+
+
+def test_qgt_positive_semidefinite_and_hermitian():
+    rng = np.random.default_rng(78)
+    circ = _qgt_circuit(rng)
+    g = G.quantum_geometric_tensor(circ, rng.uniform(-2, 2, circ.n_params))
+    assert np.allclose(g, g.conj().T, atol=1e-13)
+    assert np.linalg.eigvalsh(g).min() > -1e-12
