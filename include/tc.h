@@ -323,6 +323,28 @@ TC_API tc_status tc_profile_begin(void);
 TC_API tc_status tc_profile_end(tc_kernel_stat* out, int max_out, int* n_out);
 
 /*
+ * tc_qgt — quantum geometric tensor of each row's state (Section "Quantum
+ * Fisher Information"):
+ *   G_ij = <d_i psi|d_j psi> - <d_i psi|psi><psi|d_j psi>
+ * with d_i = d / d theta_i; the quantum Fisher information is 4 Re G and the
+ * natural gradient solves (4 Re G) x = grad.
+ *   d_params  device [B][n_params] doubles
+ *   d_out     device [B][n_params][n_params][2] doubles (Re, Im of G; Hermitian)
+ * Every RX/RY/RZ/RZZ occurrence k (angle s_k theta_p) contributes
+ * (s_k / 2) |psi_k> to d_p|psi>, |psi_k> being the state with that
+ * occurrence's angle advanced by pi (the derivative of exp(-i a G / 2) is
+ * half of exp(-i (a + pi) G / 2)).  Per row the library evaluates the S =
+ * occurrences + 1 states with the forward tile passes, their Gram matrix
+ * <psi_k|psi_l> with a tiled kernel (products in the circuit's precision over
+ * chunks of 2048 amplitudes, FP64 sums) and folds occurrences onto
+ * parameters.  Scratch: S states + S x S complex doubles per row, rows
+ * chunked by the circuit's memory budget (default half the free memory);
+ * TC_E_NOMEM if one row does not fit.  Circuits with noise or random-axis
+ * rotations and density-matrix circuits: TC_E_UNSUPPORTED.
+ */
+TC_API tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, void* stream);
+
+/*
  * Light-cone tensor-network contraction (Section "Tensor network engine",
  * Section "Custom contraction settings", Table "contractor").
  *

@@ -71,6 +71,12 @@ tc_circuit::~tc_circuit() {
     dev_free(d_csr_slots);
   }
   dev_free(ws);
+  delete qgt_sub;
+  dev_free(d_qgt_occ_param);
+  dev_free(d_qgt_occ_c);
+  dev_free(d_qgt_off);
+  dev_free(d_qgt_occ);
+  dev_free(qgt_ws);
 }
 
 namespace {
@@ -344,6 +350,7 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
   c->init = init;
   c->n_ops = n_ops;
   c->n_params = n_params;
+  if (n_ops > 0) c->ops_in.assign(ops, ops + n_ops);
   if (opt) c->opt = *opt;
   const bool dbl = dtype == TC_C128;
   auto pick = [&](int want, int dflt, int maxk) {

@@ -109,5 +109,17 @@ struct tc_circuit {
   void* ws = nullptr;
   size_t ws_bytes = 0;
 
+  // geometric tensor (tc_qgt): the op list as given, and a companion circuit
+  // with one parameter per parameterised gate occurrence (built on first use)
+  std::vector<tc_op> ops_in;
+  tc_circuit* qgt_sub = nullptr;
+  int qgt_occ = 0;                 // parameterised gate occurrences
+  int* d_qgt_occ_param = nullptr;  // [occ] parameter of each occurrence
+  double* d_qgt_occ_c = nullptr;   // [occ] scale / 2
+  int* d_qgt_off = nullptr;        // [n_params + 1] CSR parameter -> occurrences
+  int* d_qgt_occ = nullptr;        // [occ]
+  void* qgt_ws = nullptr;
+  size_t qgt_ws_bytes = 0;
+
   ~tc_circuit();
 };

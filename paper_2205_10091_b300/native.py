@@ -139,6 +139,7 @@ SIGNATURES = {
     "tc_tn_info": (C.c_int, [C.c_void_p, C.POINTER(tc_path_info)]),
     "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_tn_destroy": (None, [C.c_void_p]),
+    "tc_qgt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tc_tn_circuit_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                        C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                        C.POINTER(C.c_void_p)]),
@@ -285,6 +286,17 @@ class Circuit:
         B = states.shape[0]
         s, w, T = ham.args()
         _check(lib().tc_expect_pauli_sum_noalloc(self.h, _ptr(states), B, s, w, T, _ptr(out), _stream(stream)))
+        return out
+
+    def qgt(self, params, out=None, stream=None):
+        """Quantum geometric tensor G_ij = <d_i psi|d_j psi> - <d_i psi|psi><psi|d_j psi>
+        per row: CUDA complex128 [B][P][P] (the QFI is 4 G.real)."""
+        import torch
+
+        B = params.shape[0]
+        if out is None:
+            out = torch.empty((B, self.n_params, self.n_params), dtype=torch.complex128, device="cuda")
+        _check(lib().tc_qgt(self.h, _ptr(params), B, _ptr(out), _stream(stream)))
         return out
 
     def expect_grad(self, params, ham: Hamiltonian, seed: int = 0, energy=None, grad=None, max_rows: int = 0,

@@ -1,0 +1,82 @@
+"""GPU parity for the quantum geometric tensor (tc_qgt, Section "Quantum
+Fisher Information") against the oracle's product-rule state derivatives."""
+import numpy as np
+import pytest
+
+from oracle import gradients as G
+from paper_2205_10091_b300 import native as nt
+from paper_2205_10091_b300 import workloads as W
+
+from gpu_util import cuda_params
+
+pytestmark = pytest.mark.gpu
+
+# G_ij sums c_k c_l <psi_k|psi_l> over the occurrences k of i and l of j
+# (c = s / 2), minus a product of two such sums: an overlap error delta
+# becomes at most 2 W_i W_j delta, W_i = sum_k |c_k|.  delta: complex64
+# states (FP32 gates, ~1e-6 per overlap of unit vectors) / complex128.
+DELTA = {nt.TC_C64: 2e-6, nt.TC_C128: 2e-12}
+
+
+def _tol(circ, dtype):
+    w = np.zeros(circ.n_params)
+    for op in circ.ops:
+        if int(op["param"]) >= 0:
+            w[int(op["param"])] += abs(float(op["scale"])) / 2
+    return 2 * DELTA[dtype] * max(1.0, w.max()) ** 2
+
+
+def _circuit(n, rng, layers=2):
+    b = W.OpBuilder(n, W.INIT_ZERO if n % 2 else W.INIT_PLUS)
+    p = 0
+    for _ in range(layers):
+        for q in range(n):
+            b.ry(q, p + q % 3, scale=float(rng.choice([1.0, -0.5, 2.0])))
+        p += 3
+        for q in range(n - 1):
+            b.rzz(q, q + 1, p, scale=-2.0)  # one angle over the chain
+        b.cnot(0, n - 1)
+        b.unitary1(1, W.haar_unitary(2, rng))
+        for q in range(0, n, 2):
+            b.rx(q, p + 1)
+        b.rz(n // 2, p + 2)
+        p += 3
+    return b.build(p + 1)  # the last parameter drives no gate: zero row and column
+
+
+@pytest.mark.parametrize("dtype", [nt.TC_C64, nt.TC_C128])
+@pytest.mark.parametrize("n", [3, 10, 12])
+def test_qgt_matches_oracle(n, dtype):
+    rng = np.random.default_rng(900 + n)
+    circ = _circuit(n, rng)
+    B = 3
+    theta = rng.uniform(-2.5, 2.5, size=(B, circ.n_params))
+    c = nt.Circuit(circ, dtype=dtype)
+    g = c.qgt(cuda_params(theta)).cpu().numpy()
+    for b in range(B):
+        ref = G.quantum_geometric_tensor(circ, theta[b])
+        assert np.abs(g[b] - ref).max() <= _tol(circ, dtype)
+        assert np.abs(g[b, -1]).max() == 0 and np.abs(g[b, :, -1]).max() == 0
+
+
+def test_qgt_tfim_rows_chunked():
+    circ, theta, _ = W.tfim_workload(10, 2, 4)
+    # a budget below two rows' scratch forces one row per chunk
+    c = nt.Circuit(circ, mem_budget_bytes=1 << 20)
+    g = c.qgt(cuda_params(theta)).cpu().numpy()
+    for b in range(4):
+        assert np.abs(g[b] - G.quantum_geometric_tensor(circ, theta[b])).max() <= _tol(circ, nt.TC_C64)
+
+
+def test_qgt_unsupported_and_empty():
+    b = W.OpBuilder(4)
+    b.ry(0, 0)
+    b.depolarizing(1, 0.1, 0.1, 0.1)
+    c = nt.Circuit(b.build())
+    with pytest.raises(nt.TcError) as e:
+        c.qgt(cuda_params(np.zeros((1, 1))))
+    assert e.value.status == nt.TC_E_UNSUPPORTED
+    b = W.OpBuilder(4)
+    b.h(0)
+    c = nt.Circuit(b.build(2))  # parameters that drive no gate
+    assert np.abs(c.qgt(cuda_params(np.ones((2, 2)))).cpu().numpy()).max() == 0
