@@ -466,6 +466,20 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
         "ms_per_run": ms_bp, "qubits": cbp.n, "layers": 10, "structures": int(thbp.shape[0]),
         "var_dtheta0": float(g_bp[:, 0].var(unbiased=False).item()),
         "mean_var_over_params": float(g_bp.var(dim=0, unbiased=False).mean().item())}
+    # ---- quantum geometric tensor (QFI = 4 Re G) of the TFIM ansatz -------
+    qgt = {}
+    for nq, Bq in ((20, 2), (12, 64)):
+        cq_circ, thq, _ = W.tfim_workload(nq, 10, Bq)
+        cq = nt.Circuit(cq_circ)
+        d_thq = torch.as_tensor(thq, device="cuda")
+        gq = torch.empty((Bq, cq_circ.n_params, cq_circ.n_params), dtype=torch.complex128, device="cuda")
+        msq = _time_cuda(lambda: cq.qgt(d_thq, out=gq), 3 if nq == 20 else 10, warm=1)
+        occ = int(np.count_nonzero(cq_circ.ops["param"] >= 0))
+        qgt[f"tfim{nq}_l10"] = {"rows": Bq, "ms_per_row": msq / Bq, "params": cq_circ.n_params,
+                                "gate_occurrences": occ, "states_per_row": occ + 1,
+                                "qfi00_row0": float(4 * gq[0, 0, 0].real.item())}
+        del cq, gq
+    out["qgt_tfim"] = qgt
     # ---- many-term Pauli sum: 12-qubit, 1390-term chemistry-shaped H ------
     hc = W.chem_pauli_sum(12)
     Hc = nt.Hamiltonian(hc)
@@ -515,7 +529,7 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
 def _traffic(kernel: str):
     """DRAM bytes per full-size launch of `kernel` from the committed ncu
     summary (profiles/traffic_<kernel>.txt, 'key: value' lines), or None when
-    the kernel sources changed since the counters were taken."""
+    the tile-pass sources changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", f"traffic_{kernel}.txt")
     if not os.path.exists(path):
         return None
@@ -533,15 +547,18 @@ def _traffic(kernel: str):
         return None
 
 
+# the sources that define the tile-pass kernels and the plans they run
+TILE_PASS_SOURCES = ("plan.h", "planner.cpp", "planner.h", "sv_kernels.cu", "sv_kernels.cuh")
+
+
 def _source_hash() -> str:
     import hashlib
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2205_10091_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(fh.read())
+    for f in TILE_PASS_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
