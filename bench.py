@@ -176,6 +176,29 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def rank_workload(rank: int):
+    """Each rank's own batch of parameter rows (weak scaling: rows are
+    independent problems, no data-path collective)."""
+    return W.tfim_workload(N_QUBITS, LAYERS, BATCH, seed=W.SEED_TFIM20 + rank)
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's time (the job's time), identical on every rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(rows_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job rows per second: every rank's rows over the slowest rank's time."""
+    return world * rows_per_rank / (ms / 1e3)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -194,7 +217,7 @@ def run_gpu(args):
             dist.barrier()
 
     # each rank owns an independent batch of parameter sets (weak scaling)
-    circ, theta, ham = W.tfim_workload(N_QUBITS, LAYERS, BATCH, seed=W.SEED_TFIM20 + rank)
+    circ, theta, ham = rank_workload(rank)
     c = nt.Circuit(circ)
     H = nt.Hamiltonian(ham)
     B, P = theta.shape
@@ -223,12 +246,8 @@ def run_gpu(args):
     prof = nt.profile_end()
     clk = clocks.stop()
     barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * B / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    value = job_rate(B, world, ms)
 
     # ---- end to end through host buffers -------------------------------------
     h_theta = torch.as_tensor(theta).pin_memory()
@@ -250,12 +269,8 @@ def run_gpu(args):
         h_g.copy_(grad, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms_e2e], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = {"value": world * B / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h_theta.numel() * 8),
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
+    e2e = {"value": job_rate(B, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": int(h_theta.numel() * 8),
            "d2h_bytes_per_step": int((h_e.numel() + h_g.numel()) * 8)}
 
     # ---- plain per-circuit path: one row, unfused sweeps, forward + energy ----

@@ -1,0 +1,50 @@
+"""bench.py's multi-rank host logic on two gloo ranks (CPU): each rank owns
+different rows, the job time is the slowest rank's, and the rate counts every
+rank's rows."""
+import os
+import socket
+import sys
+
+import numpy as np
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    _, theta, _ = bench.rank_workload(rank)
+    ms = bench.max_over_ranks(10.0 + 5.0 * rank, world, "cpu")
+    q.put((rank, float(theta[0, 0]), theta.shape[0], ms, bench.job_rate(theta.shape[0], world, ms)))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, t0, b0, ms0, v0), (r1, t1, b1, ms1, v1) = res
+    assert t0 != t1  # independent rows per rank
+    assert ms0 == ms1 == 15.0  # the slowest rank's time on both ranks
+    assert np.isclose(v0, 2 * b0 / 0.015) and v0 == v1
