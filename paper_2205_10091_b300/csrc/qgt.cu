@@ -124,13 +124,248 @@ __global__ void __launch_bounds__(256) k_gram(const typename Cplx<R>::T* __restr
     }
 }
 
-// M(k, l) from the computed triangle of tiles: M(l, k) = conj(M(k, l))
-__device__ __forceinline__ double2 gram_at(const double* Mr, int S, int k, int l) {
-  if (k / kGramTile <= l / kGramTile) return make_double2(Mr[((size_t)k * S + l) * 2], Mr[((size_t)k * S + l) * 2 + 1]);
+// ---------------------------------------------------------------------------
+// Tensor-core Gram for complex64 states (tcgen05, kind::tf32, cta_group::1).
+// With the state rows interleaved as real vectors a = (re_0, im_0, re_1, ...),
+// Re <psi_k|psi_l> = a_k . a_l and Im <psi_k|psi_l> = a_k . b_l with
+// b = (im_0, -re_0, im_1, -re_1, ...): two real GEMMs D = A B^T over K = 2L.
+// Operands split x = hi + lo, hi = tf32(x): A B = A_hi B_hi + A_hi B_lo +
+// A_lo B_hi.  The tensor core's FP32 accumulation is not round-to-nearest
+// (its error grows with the chain length: measured 3e-3 on G over 4096
+// amplitudes, 3e-5 over 64), so each stage's MMAs start a fresh TMEM
+// accumulator and every thread adds its 64 accumulator values into FP32
+// registers (round-to-nearest) after the stage; FP64 atomics combine the
+// CTAs.  One CTA: 128 x 128 outputs (state rows k of tile kt by rows l of
+// tile lt), Re and Im in TMEM columns [0, 128) and [128, 256), over kTcChunk
+// amplitudes.  The raw amplitudes of stage s + 1 (16 per row of the 256 rows)
+// are copied global -> shared with cp.async while stage s is converted and
+// multiplied.  Per stage all threads convert the raw amplitudes into the
+// operand tiles (hi and lo of A, B1 = a, B2 = b) in the K-major no-swizzle
+// layout (8-row x 16-byte core matrices, K-adjacent core matrices kTcLBO
+// bytes apart, 8-row groups kTcSBO bytes apart), one thread issues the 24
+// MMAs and commits them to an mbarrier that every thread waits on (bounded).
+constexpr int kTcThreads = 512;
+constexpr int kTcTile = 128;                      // rows per side = TMEM lanes
+constexpr int kTcKA = 16;                         // amplitudes per stage
+constexpr int kTcK = 2 * kTcKA;                   // TF32 elements per stage
+constexpr int kTcLBO = 128;                       // bytes between K-adjacent core matrices
+constexpr int kTcSBO = (kTcK / 4) * 128;          // bytes between 8-row groups
+constexpr int kTcTileBytes = kTcTile * kTcK * 4;  // one operand tile (16 KiB)
+constexpr int kTcRawBytes = 2 * kTcTile * kTcKA * 8;  // one stage's raw amplitudes (32 KiB)
+constexpr int kTcSmem = 6 * kTcTileBytes + 2 * kTcRawBytes;  // tiles + double-buffered raw stage
+constexpr int kTcChunk = 4096;                    // amplitudes per CTA
+constexpr int kTcCols = 256;                      // TMEM columns: Re then Im
+constexpr long long kTcSpin = 1ll << 20;          // bounded mbarrier waits
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, N = M = 128
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcTile >> 3) << 17) |
+                              ((uint32_t)(kTcTile >> 4) << 24);
+
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((kTcLBO >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((kTcSBO >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version; base offset 0, no swizzle
+  return d;
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc));
+}
+
+// bounded wait for the phase of the given parity; false on timeout
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < kTcSpin; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 16-byte asynchronous copy global -> shared; zero-fills when !valid
+__device__ __forceinline__ void tc_cp16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restrict__ states, int S, int64_t L,
+                                                           int ntile, double* __restrict__ M, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t tc_smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  int pair = blockIdx.x, kt = 0;
+  while (pair >= ntile - kt) {
+    pair -= ntile - kt;
+    ++kt;
+  }
+  const int lt = kt + pair;
+  const int r = blockIdx.z;
+  const int64_t x0 = (int64_t)blockIdx.y * kTcChunk;
+  const int64_t x1 = x0 + kTcChunk < L ? x0 + kTcChunk : L;
+  const float2* base = states + (size_t)r * S * L;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // accumulator share: TMEM lanes 32 (warp % 4).. (rows k), 64 columns
+  // starting at 64 (warp / 4): Re columns [0, 128), then Im
+  const int lg = warp & 3, part = warp >> 2;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tc_smem);
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+  if (warp == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tacc = tmem_base;
+  const uint32_t tmine = tacc + ((uint32_t)(32 * lg) << 16) + (uint32_t)(64 * part);
+  float acc[64];
+#pragma unroll
+  for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+  uint32_t parity = 0;
+  bool ok = true;
+  // raw stage layout: [operand][row][8 amplitude pairs], pair p of a row stored
+  // at slot p ^ (row % 8) (so both the copy mapping below, row-major for
+  // coalesced global reads, and the conversion mapping, rows fastest, hit
+  // distinct shared-memory banks)
+  const uint32_t raw0 = sbase + 6 * kTcTileBytes;
+  auto prefetch = [&](int64_t xs, int buf) {
+#pragma unroll
+    for (int q = 0; q < 1024 / kTcThreads; ++q) {
+      const int e = tid + kTcThreads * q;
+      const int row = e >> 3, c4 = e & 7;
+      const int64_t x = xs + 2 * c4;
+      const int ka = kt * kTcTile + row, kb = lt * kTcTile + row;
+      const uint32_t d = raw0 + (uint32_t)(buf * kTcRawBytes + row * (kTcKA * 8) + ((c4 ^ (row & 7)) * 16));
+      const bool va = ka < S && x < x1, vb = kb < S && x < x1;
+      tc_cp16(d, va ? (const void*)(base + (size_t)ka * L + x) : (const void*)base, va);
+      tc_cp16(d + kTcRawBytes / 2, vb ? (const void*)(base + (size_t)kb * L + x) : (const void*)base, vb);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  prefetch(x0, 0);
+  int buf = 0;
+  for (int64_t xs = x0; xs < x1 && ok; xs += kTcKA, buf ^= 1) {
+    if (xs + kTcKA < x1) {
+      prefetch(xs + kTcKA, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();  // the stage's raw amplitudes, copied by all threads
+    // ---- convert the raw amplitudes into the operand tiles (rows fastest:
+    // a warp's 16-byte tile stores cover the 8 row slots of a core matrix)
+#pragma unroll
+    for (int q = 0; q < 1024 / kTcThreads; ++q) {
+      const int e = tid + kTcThreads * q;  // 0..1023
+      const int row = e & (kTcTile - 1), c4 = e >> 7;
+      const uint32_t off = (uint32_t)((row >> 3) * kTcSBO + c4 * kTcLBO + (row & 7) * 16);
+      const uint8_t* rp = tc_smem + 6 * kTcTileBytes + buf * kTcRawBytes + row * (kTcKA * 8) + ((c4 ^ (row & 7)) * 16);
+      const float4 va = *reinterpret_cast<const float4*>(rp);
+      const float4 vb = *reinterpret_cast<const float4*>(rp + kTcRawBytes / 2);
+      const float4 ah = make_float4(tf32_rna(va.x), tf32_rna(va.y), tf32_rna(va.z), tf32_rna(va.w));
+      const float4 al = make_float4(va.x - ah.x, va.y - ah.y, va.z - ah.z, va.w - ah.w);
+      const float4 bh = make_float4(tf32_rna(vb.x), tf32_rna(vb.y), tf32_rna(vb.z), tf32_rna(vb.w));
+      const float4 bl = make_float4(vb.x - bh.x, vb.y - bh.y, vb.z - bh.z, vb.w - bh.w);
+      *reinterpret_cast<float4*>(tc_smem + 0 * kTcTileBytes + off) = ah;
+      *reinterpret_cast<float4*>(tc_smem + 1 * kTcTileBytes + off) = al;
+      *reinterpret_cast<float4*>(tc_smem + 2 * kTcTileBytes + off) = bh;
+      *reinterpret_cast<float4*>(tc_smem + 3 * kTcTileBytes + off) = bl;
+      // b = (im, -re) per amplitude; rounding to TF32 commutes with this
+      *reinterpret_cast<float4*>(tc_smem + 4 * kTcTileBytes + off) = make_float4(bh.y, -bh.x, bh.w, -bh.z);
+      *reinterpret_cast<float4*>(tc_smem + 5 * kTcTileBytes + off) = make_float4(bl.y, -bl.x, bl.w, -bl.z);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // also orders the previous stage's TMEM reads before these MMAs overwrite it
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int ks = 0; ks < kTcK / 8; ++ks) {  // 8 TF32 = two core matrices along K per MMA
+        const uint32_t o = (uint32_t)(ks * 2 * kTcLBO);
+        const uint64_t ah = tc_sdesc(sbase + 0 * kTcTileBytes + o), al = tc_sdesc(sbase + 1 * kTcTileBytes + o);
+        const uint64_t bh = tc_sdesc(sbase + 2 * kTcTileBytes + o), bl = tc_sdesc(sbase + 3 * kTcTileBytes + o);
+        const uint64_t ch = tc_sdesc(sbase + 4 * kTcTileBytes + o), cl = tc_sdesc(sbase + 5 * kTcTileBytes + o);
+        const uint32_t first = ks == 0 ? 0u : 1u;  // a fresh accumulator every stage
+        tc_mma(tacc, ah, bh, first);
+        tc_mma(tacc, ah, bl, 1u);
+        tc_mma(tacc, al, bh, 1u);
+        tc_mma(tacc + kTcTile, ah, ch, first);
+        tc_mma(tacc + kTcTile, ah, cl, 1u);
+        tc_mma(tacc + kTcTile, al, ch, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                   : "memory");
+    }
+    ok = tc_wait(bar, parity);
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t v[32];
+        tc_ld32(tmine + 32 * h, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[32 * h + j] += __uint_as_float(v[j]);
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!ok) {
+    if (tid == 0) atomicExch(err, 1);
+    tc_wait(bar, parity ^ 1u);  // let the committed MMAs finish before TMEM is freed
+  } else {
+    const int k = kt * kTcTile + 32 * lg + lane;
+    const int comp = part >> 1, l0 = lt * kTcTile + 64 * (part & 1);
+    if (k < S) {
+#pragma unroll
+      for (int j = 0; j < 64; ++j)
+        if (l0 + j < S) atomicAdd(M + (((size_t)r * S + k) * S + l0 + j) * 2 + comp, (double)acc[j]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(kTcCols));
+}
+
+// M(k, l) from the computed triangle of tiles (tile = rows per tile side):
+// M(l, k) = conj(M(k, l))
+__device__ __forceinline__ double2 gram_at(const double* Mr, int S, int tile, int k, int l) {
+  if (k / tile <= l / tile) return make_double2(Mr[((size_t)k * S + l) * 2], Mr[((size_t)k * S + l) * 2 + 1]);
   return make_double2(Mr[((size_t)l * S + k) * 2], -Mr[((size_t)l * S + k) * 2 + 1]);
 }
 
-__global__ void k_qgt_fold(const double* __restrict__ M, int S, const int* __restrict__ off,
+__global__ void k_qgt_fold(const double* __restrict__ M, int S, int tile, const int* __restrict__ off,
                            const int* __restrict__ occ, const double* __restrict__ occ_c, int P, int rows,
                            double* __restrict__ out) {
   const int64_t total = (int64_t)rows * P * P;
@@ -144,19 +379,19 @@ __global__ void k_qgt_fold(const double* __restrict__ M, int S, const int* __res
     for (int a = off[i]; a < off[i + 1]; ++a) {
       const int k = occ[a];
       const double ck = occ_c[k];
-      const double2 mk = gram_at(Mr, S, k, last);  // <psi_k|psi>
+      const double2 mk = gram_at(Mr, S, tile, k, last);  // <psi_k|psi>
       ur += ck * mk.x;
       ui += ck * mk.y;
       for (int b = off[j]; b < off[j + 1]; ++b) {
         const int l = occ[b];
-        const double2 m = gram_at(Mr, S, k, l);
+        const double2 m = gram_at(Mr, S, tile, k, l);
         gr += ck * occ_c[l] * m.x;
         gi += ck * occ_c[l] * m.y;
       }
     }
     for (int b = off[j]; b < off[j + 1]; ++b) {
       const int l = occ[b];
-      const double2 m = gram_at(Mr, S, last, l);  // <psi|psi_l>
+      const double2 m = gram_at(Mr, S, tile, last, l);  // <psi|psi_l>
       vr += occ_c[l] * m.x;
       vi += occ_c[l] * m.y;
     }
@@ -261,10 +496,19 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
   void* states = w;
   double* th = (double*)(w + al((size_t)S * L * amp) * chunk);
   double* M = (double*)((char*)th + al((size_t)S * Pp * 8) * chunk);
-  const int ntile = (S + kGramTile - 1) / kGramTile;
-  const int64_t nchunk = (L + kGramChunk - 1) / kGramChunk;
+  // complex64: tensor-core Gram (128-row tiles); complex128: FP64 CUDA-core Gram
+  const bool tc = c->dtype == TC_C64;
+  const int tile = tc ? kTcTile : kGramTile;
+  const int ntile = (S + tile - 1) / tile;
+  const int64_t nchunk = (L + (tc ? kTcChunk : kGramChunk) - 1) / (tc ? kTcChunk : kGramChunk);
   if (nchunk > 65535) return fail(TC_E_UNSUPPORTED, "too many qubits for the Gram kernel");
+  int* d_err = (int*)(w + row_bytes * chunk);  // in the workspace's slack
   cudaError_t e;
+  if (tc) {
+    if ((e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem)) != cudaSuccess)
+      return cuda_fail(e, "gram smem");
+    if ((e = cudaMemsetAsync(d_err, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "memset");
+  }
   for (int r0 = 0; r0 < B; r0 += chunk) {
     const int rows = std::min(chunk, B - r0);
     if (Pp > 0) {
@@ -280,19 +524,26 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
     for (int r = 0; r < rows; r += 65535) {
       const int rr = std::min(65535, rows - r);
       dim3 grid((unsigned)(ntile * (ntile + 1) / 2), (unsigned)nchunk, (unsigned)rr);
-      if (c->dtype == TC_C128)
+      if (tc)
+        k_gram_tc<<<grid, kTcThreads, kTcSmem, s>>>((const float2*)states + (size_t)r * S * L, S, L, ntile,
+                                             M + (size_t)r * S * S * 2, d_err);
+      else
         k_gram<double><<<grid, 256, 0, s>>>((const double2*)states + (size_t)r * S * L, S, L, ntile,
                                             M + (size_t)r * S * S * 2);
-      else
-        k_gram<float><<<grid, 256, 0, s>>>((const float2*)states + (size_t)r * S * L, S, L, ntile,
-                                           M + (size_t)r * S * S * 2);
       if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gram");
     }
     const int64_t tot = (int64_t)rows * P * P;
     const int g = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
-    k_qgt_fold<<<g, 256, 0, s>>>(M, S, c->d_qgt_off, c->d_qgt_occ, c->d_qgt_occ_c, P, rows,
+    k_qgt_fold<<<g, 256, 0, s>>>(M, S, tile, c->d_qgt_off, c->d_qgt_occ, c->d_qgt_occ_c, P, rows,
                                  d_out + (size_t)r0 * P * P * 2);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "geometric tensor fold");
+  }
+  if (tc) {  // the tensor-core Gram's bounded waits report through a flag
+    int h_err = 0;
+    if ((e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+      return cuda_fail(e, "gram status");
+    if (h_err) return fail(TC_E_TIMEOUT, "tensor-core Gram: an MMA completion wait timed out");
   }
   return TC_OK;
 }
