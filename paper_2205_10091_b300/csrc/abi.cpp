@@ -71,7 +71,11 @@ tc_circuit::~tc_circuit() {
     dev_free(d_csr_slots);
   }
   dev_free(ws);
-  delete qgt_sub;
+  for (auto& g : qgt_groups) {
+    delete g.seg;
+    delete g.suffix;
+  }
+  dev_free(d_qgt_pauli);
   dev_free(d_qgt_occ_param);
   dev_free(d_qgt_occ_c);
   dev_free(d_qgt_off);

@@ -109,15 +109,24 @@ struct tc_circuit {
   void* ws = nullptr;
   size_t ws_bytes = 0;
 
-  // geometric tensor (tc_qgt): the op list as given, and a companion circuit
-  // with one parameter per parameterised gate occurrence (built on first use)
+  // geometric tensor (tc_qgt): the op list as given and its plan (built on
+  // first use): occurrence groups that share a generator insertion point, the
+  // circuit segments between the points and the suffix after each point
   std::vector<tc_op> ops_in;
-  tc_circuit* qgt_sub = nullptr;
-  int qgt_occ = 0;                 // parameterised gate occurrences
-  int* d_qgt_occ_param = nullptr;  // [occ] parameter of each occurrence
+  struct QgtGroup {
+    int point = 0;            // insertion point (op index)
+    int first = 0, count = 0; // state slots [first, first + count)
+    tc_circuit* seg = nullptr;    // ops from the previous point to this one (nullptr if none)
+    tc_circuit* suffix = nullptr; // ops from this point to the end (nullptr if none)
+  };
+  std::vector<QgtGroup> qgt_groups;
+  bool qgt_ready = false;
+  int qgt_occ = 0;                 // parameterised gate occurrences (state slots before the last)
+  int* d_qgt_occ_param = nullptr;  // [occ] parameter of each slot's occurrence
   double* d_qgt_occ_c = nullptr;   // [occ] scale / 2
-  int* d_qgt_off = nullptr;        // [n_params + 1] CSR parameter -> occurrences
+  int* d_qgt_off = nullptr;        // [n_params + 1] CSR parameter -> slots
   int* d_qgt_occ = nullptr;        // [occ]
+  uint32_t* d_qgt_pauli = nullptr; // [occ][3] generator: flip mask, sign mask, number of Y
   void* qgt_ws = nullptr;
   size_t qgt_ws_bytes = 0;
 

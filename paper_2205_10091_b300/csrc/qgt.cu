@@ -6,11 +6,19 @@
 // d/da exp(-i a G / 2) = (-i/2) G exp(-i a G / 2) = (1/2) exp(-i (a + pi) G / 2).
 // So d|psi>/d theta_p = sum over the occurrences k of p of c_k |psi_k>, with
 // c_k = s_k / 2 and |psi_k> the circuit's state with occurrence k's angle
-// advanced by pi.  Per batch row the engine runs the occurrences' S - 1
-// shifted states and the unshifted state as S rows of a companion circuit
-// that gives every occurrence its own parameter (the forward tile passes),
-// a Gram kernel forms M_kl = <psi_k|psi_l>, and a fold kernel sums
-// G_ij = sum_{k in i, l in j} c_k c_l M_kl - u_i conj(u_j), u_i = sum_k c_k M_{k,S-1}.
+// advanced by pi, which is -i times the state with the Pauli generator G_k
+// inserted right after the gate; the phase cancels in G, so the engine uses
+// the insertion states chi_k.  An insertion moves right past every later gate
+// that commutes with G_k (disjoint qubits; diagonal gates for Z-type G; RX
+// after X, RY after Y; a CNOT's control for Z, its target for X), and the
+// occurrences are grouped by a common insertion point (fewest points
+// stabbing the intervals).  Per group: the segment of the circuit up to the
+// point advances each row's prefix state phi, the group's states are G_k phi,
+// and the suffix after the point runs on them, all with the circuit's own
+// parameters (so diagonal gates sharing an angle stay grouped).  The last
+// slot holds the unshifted state.  A Gram kernel forms M_kl = <chi_k|chi_l>,
+// and a fold kernel sums G_ij = sum_{k in i, l in j} c_k c_l M_kl - u_i v_j,
+// u_i = sum_k c_k M_{k,S-1}, v_j = sum_l c_l M_{S-1,l}.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,18 +46,42 @@ struct Cplx<double> {
   using T = double2;
 };
 
-// theta'[(r S + t)][k] = s_k theta[r][p_k] + (t == k ? pi : 0), t = S - 1 unshifted
-__global__ void k_qgt_params(const double* __restrict__ theta, int P, const int* __restrict__ occ_param,
-                             const double* __restrict__ occ_c, int Pp, int rows, double* __restrict__ out) {
-  const int S = Pp + 1;
-  const int64_t total = (int64_t)rows * S * Pp;
+// out[(t R + r)][p] = theta[r][p] for t < count: the row's parameters for
+// each of its states in a group
+__global__ void k_qgt_rep(const double* __restrict__ theta, int P, int R, int count, double* __restrict__ out) {
+  const int64_t total = (int64_t)count * R * P;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e % Pp);
-    const int64_t rt = e / Pp;
-    const int t = (int)(rt % S);
-    const int64_t r = rt / S;
-    double v = 2.0 * occ_c[k] * theta[r * P + occ_param[k]];
-    if (t == k) v += 3.14159265358979323846;
+    const int p = (int)(e % P);
+    const int r = (int)((e / P) % R);
+    out[e] = theta[(size_t)r * P + p];
+  }
+}
+
+// out[(t R + r)][x] = (G_t phi_r)[x] for the group's slots t < count (the
+// last slot of the last group takes phi itself: pauli entry = 0, 0, 0).
+// G = (-i)^{#Y} (-1)^{popc(x & sign)} applied to phi[x ^ flip] (qubit q is
+// bit n - 1 - q; X and Y flip, Z and Y give the sign).
+template <typename C2>
+__global__ void k_qgt_pauli(const C2* __restrict__ phi, int R, int64_t L, const uint32_t* __restrict__ pauli,
+                            int count, C2* __restrict__ out) {
+  const int64_t total = (int64_t)count * R * L;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = e % L;
+    const int64_t tr = e / L;
+    const int r = (int)(tr % R);
+    const int t = (int)(tr / R);
+    const uint32_t flip = pauli[3 * t], sign = pauli[3 * t + 1], ny = pauli[3 * t + 2];
+    C2 v = phi[(size_t)r * L + (x ^ (int64_t)flip)];
+    if (__popc((uint32_t)x & sign) & 1) {
+      v.x = -v.x;
+      v.y = -v.y;
+    }
+    switch (ny & 3) {  // multiply by (-i)^ny
+      case 1: { const auto re = v.x; v.x = v.y; v.y = -re; } break;
+      case 2: v.x = -v.x; v.y = -v.y; break;
+      case 3: { const auto re = v.x; v.x = -v.y; v.y = re; } break;
+      default: break;
+    }
     out[e] = v;
   }
 }
@@ -58,7 +90,7 @@ __global__ void k_qgt_params(const double* __restrict__ theta, int P, const int*
 // chunk, for the tile pair (kt <= lt) of blockIdx.x; 4 x 4 outputs a thread.
 template <typename R>
 __global__ void __launch_bounds__(256) k_gram(const typename Cplx<R>::T* __restrict__ states, int S, int64_t L,
-                                              int ntile, double* __restrict__ M) {
+                                              int64_t kstride, int ntile, double* __restrict__ M) {
   using C2 = typename Cplx<R>::T;
   __shared__ C2 As[kGramX][kGramTile + 1];
   __shared__ C2 Bs[kGramX][kGramTile + 1];
@@ -72,7 +104,7 @@ __global__ void __launch_bounds__(256) k_gram(const typename Cplx<R>::T* __restr
   const int r = blockIdx.z;
   const int64_t x0 = (int64_t)blockIdx.y * kGramChunk;
   const int64_t x1 = x0 + kGramChunk < L ? x0 + kGramChunk : L;
-  const C2* base = states + (size_t)r * S * L;
+  const C2* base = states + (size_t)r * L;  // state slot k of row r at base + k kstride
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   R ar[4][4], ai[4][4];
 #pragma unroll
@@ -89,8 +121,8 @@ __global__ void __launch_bounds__(256) k_gram(const typename Cplx<R>::T* __restr
       C2 z;
       z.x = R(0);
       z.y = R(0);
-      As[xx][kk] = (ka < S && x < x1) ? base[(size_t)ka * L + x] : z;
-      Bs[xx][kk] = (kb < S && x < x1) ? base[(size_t)kb * L + x] : z;
+      As[xx][kk] = (ka < S && x < x1) ? base[(size_t)ka * kstride + x] : z;
+      Bs[xx][kk] = (kb < S && x < x1) ? base[(size_t)kb * kstride + x] : z;
     }
     __syncthreads();
 #pragma unroll 4
@@ -214,7 +246,8 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restrict__ states, int S, int64_t L,
-                                                           int ntile, double* __restrict__ M, int* __restrict__ err) {
+                                                           int64_t kstride, int ntile, double* __restrict__ M,
+                                                           int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -227,7 +260,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
   const int r = blockIdx.z;
   const int64_t x0 = (int64_t)blockIdx.y * kTcChunk;
   const int64_t x1 = x0 + kTcChunk < L ? x0 + kTcChunk : L;
-  const float2* base = states + (size_t)r * S * L;
+  const float2* base = states + (size_t)r * L;  // state slot k of row r at base + k kstride
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // accumulator share: TMEM lanes 32 (warp % 4).. (rows k), 64 columns
   // starting at 64 (warp / 4): Re columns [0, 128), then Im
@@ -267,8 +300,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
       const int ka = kt * kTcTile + row, kb = lt * kTcTile + row;
       const uint32_t d = raw0 + (uint32_t)(buf * kTcRawBytes + row * (kTcKA * 8) + ((c4 ^ (row & 7)) * 16));
       const bool va = ka < S && x < x1, vb = kb < S && x < x1;
-      tc_cp16(d, va ? (const void*)(base + (size_t)ka * L + x) : (const void*)base, va);
-      tc_cp16(d + kTcRawBytes / 2, vb ? (const void*)(base + (size_t)kb * L + x) : (const void*)base, vb);
+      tc_cp16(d, va ? (const void*)(base + (size_t)ka * kstride + x) : (const void*)base, va);
+      tc_cp16(d + kTcRawBytes / 2, vb ? (const void*)(base + (size_t)kb * kstride + x) : (const void*)base, vb);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
@@ -408,51 +441,149 @@ using namespace tcb;
 
 namespace {
 
+bool diag_op(const tc_op& o, const std::vector<double>& pool) {
+  if (o.kind == TC_OP_RZ || o.kind == TC_OP_RZZ || o.kind == TC_OP_CZ) return true;
+  if (o.kind != TC_OP_U1 && o.kind != TC_OP_U2) return false;
+  const int d = o.kind == TC_OP_U1 ? 2 : 4;
+  for (int r = 0; r < d; ++r)
+    for (int c = 0; c < d; ++c)
+      if (r != c && (pool[2 * ((size_t)o.mat + r * d + c)] != 0.0 || pool[2 * ((size_t)o.mat + r * d + c) + 1] != 0.0))
+        return false;
+  return true;
+}
+
+bool two_qubit(const tc_op& o) {
+  return o.kind == TC_OP_RZZ || o.kind == TC_OP_CNOT || o.kind == TC_OP_CZ || o.kind == TC_OP_U2;
+}
+
+// Does op o commute with the generator (Pauli code on qubits g0 and g1, g1 = -1 if none)?
+bool commutes(const tc_op& o, int code, int g0, int g1, const std::vector<double>& pool) {
+  const int a = o.q0, b = two_qubit(o) ? o.q1 : -1;
+  auto on = [&](int q) { return q >= 0 && (q == g0 || q == g1); };
+  if (!on(a) && !on(b)) return true;  // disjoint qubits
+  if (code == 3 && diag_op(o, pool)) return true;
+  if (g1 < 0) {  // one-qubit generator on g0
+    if (code == 1 && b < 0 && (o.kind == TC_OP_RX || o.kind == TC_OP_X)) return true;
+    if (code == 2 && b < 0 && o.kind == TC_OP_RY) return true;
+    if (o.kind == TC_OP_CNOT && ((code == 3 && g0 == a) || (code == 1 && g0 == b))) return true;
+  }
+  return false;
+}
+
 tc_status qgt_prepare(tc_circuit* c) {
-  if (c->qgt_sub) return TC_OK;
-  std::vector<tc_op> ops = c->ops_in;
-  std::vector<int> occ_param;
-  std::vector<double> occ_c;
-  for (auto& o : ops) {
+  if (c->qgt_ready) return TC_OK;
+  const std::vector<tc_op>& ops = c->ops_in;
+  const int n_ops = (int)ops.size();
+  struct Occ {
+    int op, param, lo, hi;  // insertion point interval [lo, hi]
+    double chalf;
+    uint32_t flip, sign, ny;
+  };
+  std::vector<Occ> occ;
+  for (int i = 0; i < n_ops; ++i) {
+    const tc_op& o = ops[i];
     if (o.kind == TC_OP_PAULI_NOISE || o.kind == TC_OP_RSEL)
       return fail(TC_E_UNSUPPORTED, "geometric tensor of circuits with noise or random-axis rotations");
     const bool rot = o.kind == TC_OP_RX || o.kind == TC_OP_RY || o.kind == TC_OP_RZ || o.kind == TC_OP_RZZ;
     if (o.param < 0 || !rot) continue;
-    occ_param.push_back(o.param);
-    occ_c.push_back(0.5 * o.scale);
-    o.param = (int32_t)occ_param.size() - 1;
-    o.scale = 1.0;
+    const int code = o.kind == TC_OP_RX ? 1 : o.kind == TC_OP_RY ? 2 : 3;
+    const int g1 = o.kind == TC_OP_RZZ ? o.q1 : -1;
+    int j = i + 1;
+    while (j < n_ops && commutes(ops[j], code, o.q0, g1, c->pool)) ++j;
+    Occ k{};
+    k.op = i;
+    k.param = o.param;
+    k.lo = i + 1;
+    k.hi = j;
+    k.chalf = 0.5 * o.scale;
+    const uint32_t m0 = 1u << (c->n - 1 - o.q0), m1 = g1 >= 0 ? 1u << (c->n - 1 - g1) : 0u;
+    k.flip = code == 3 ? 0u : m0;
+    k.sign = code == 1 ? 0u : (m0 | m1);
+    k.ny = code == 2 ? 1u : 0u;
+    occ.push_back(k);
   }
-  const int Pp = (int)occ_param.size();
-  std::vector<double> pool = c->pool;
-  tc_circuit* sub = nullptr;
-  tc_status st = tc_circuit_create(c->n, c->dtype, c->init, ops.data(), (int)ops.size(), Pp,
-                                   pool.empty() ? nullptr : pool.data(), (int)(pool.size() / 2), &c->opt, &sub);
-  if (st != TC_OK) return st;
-  // parameter -> occurrences (CSR)
-  std::vector<int> off(c->n_params + 1, 0), occ(Pp);
-  for (int k = 0; k < Pp; ++k) off[occ_param[k] + 1]++;
+  // fewest insertion points: greedy by interval end
+  std::vector<int> order(occ.size());
+  for (size_t i = 0; i < occ.size(); ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return occ[x].hi < occ[y].hi; });
+  std::vector<int> point_of(occ.size(), -1);
+  std::vector<int> points;
+  for (int k : order) {
+    if (point_of[k] >= 0) continue;
+    const int p = occ[k].hi;
+    points.push_back(p);
+    for (size_t m = 0; m < occ.size(); ++m)
+      if (point_of[m] < 0 && occ[m].lo <= p && occ[m].hi >= p) point_of[m] = p;
+  }
+  std::sort(points.begin(), points.end());
+  // slots in point order
+  std::vector<int> slot_occ;
+  std::vector<tc_circuit::QgtGroup> groups;
+  int prev = 0;
+  auto make = [&](int from, int to, tc_circuit** out) -> tc_status {
+    *out = nullptr;
+    if (to <= from) return TC_OK;
+    return tc_circuit_create(c->n, c->dtype, c->init, ops.data() + from, to - from, c->n_params,
+                             c->pool.empty() ? nullptr : c->pool.data(), (int)(c->pool.size() / 2), &c->opt, out);
+  };
+  tc_status st = TC_OK;
+  for (int p : points) {
+    tc_circuit::QgtGroup g;
+    g.point = p;
+    g.first = (int)slot_occ.size();
+    for (size_t m = 0; m < occ.size(); ++m)
+      if (point_of[m] == p) slot_occ.push_back((int)m);
+    g.count = (int)slot_occ.size() - g.first;
+    if ((st = make(prev, p, &g.seg)) != TC_OK || (st = make(p, n_ops, &g.suffix)) != TC_OK) {
+      delete g.seg;
+      delete g.suffix;
+      break;
+    }
+    groups.push_back(g);
+    prev = p;
+  }
+  if (st != TC_OK) {
+    for (auto& g : groups) {
+      delete g.seg;
+      delete g.suffix;
+    }
+    return st;
+  }
+  const int Pp = (int)slot_occ.size();
+  std::vector<int> occ_param(std::max(Pp, 1), 0), off(c->n_params + 1, 0), list(std::max(Pp, 1), 0);
+  std::vector<double> occ_c(std::max(Pp, 1), 0.0);
+  std::vector<uint32_t> pauli(3 * (size_t)(Pp + 1), 0u);  // + the unshifted slot (identity)
+  for (int t = 0; t < Pp; ++t) {
+    const Occ& k = occ[slot_occ[t]];
+    occ_param[t] = k.param;
+    occ_c[t] = k.chalf;
+    pauli[3 * t] = k.flip;
+    pauli[3 * t + 1] = k.sign;
+    pauli[3 * t + 2] = k.ny;
+    off[k.param + 1]++;
+  }
   for (int p = 0; p < c->n_params; ++p) off[p + 1] += off[p];
   {
     std::vector<int> fill(off.begin(), off.end() - 1);
-    for (int k = 0; k < Pp; ++k) occ[fill[occ_param[k]]++] = k;
-  }
-  if (occ.empty()) occ.push_back(0);
-  if (occ_param.empty()) {
-    occ_param.push_back(0);
-    occ_c.push_back(0.0);
+    for (int t = 0; t < Pp; ++t) list[fill[occ_param[t]]++] = t;
   }
   cudaError_t e;
   if ((e = dev_upload(occ_param, &c->d_qgt_occ_param)) != cudaSuccess ||
       (e = dev_upload(occ_c, &c->d_qgt_occ_c)) != cudaSuccess || (e = dev_upload(off, &c->d_qgt_off)) != cudaSuccess ||
-      (e = dev_upload(occ, &c->d_qgt_occ)) != cudaSuccess) {
-    delete sub;
+      (e = dev_upload(list, &c->d_qgt_occ)) != cudaSuccess || (e = dev_upload(pauli, &c->d_qgt_pauli)) != cudaSuccess) {
+    for (auto& g : groups) {
+      delete g.seg;
+      delete g.suffix;
+    }
     return cuda_fail(e, "geometric tensor tables");
   }
-  c->qgt_sub = sub;
+  c->qgt_groups = groups;
   c->qgt_occ = Pp;
+  c->qgt_ready = true;
   return TC_OK;
 }
+
+int grid_for(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 148 * 16)); }
 
 }  // namespace
 
@@ -469,23 +600,31 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
   cudaStream_t s = (cudaStream_t)stream;
   const int P = c->n_params, Pp = c->qgt_occ, S = Pp + 1;
   const int64_t L = (int64_t)1 << c->n;
-  const size_t amp = c->dtype == TC_C128 ? 16 : 8;
+  cudaError_t e;
+  if (Pp == 0) {  // no parameter drives a gate
+    if ((e = cudaMemsetAsync(d_out, 0, (size_t)B * P * P * 16, s)) != cudaSuccess) return cuda_fail(e, "memset");
+    return TC_OK;
+  }
+  const bool dbl = c->dtype == TC_C128;
+  const size_t amp = dbl ? 16 : 8;
+  int maxc = 0;
+  for (const auto& g : c->qgt_groups) maxc = std::max(maxc, g.count + 1);
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  // per row: S states, S x P' shifted parameters, S x S Gram matrix
-  const size_t row_bytes = al((size_t)S * L * amp) + al((size_t)S * Pp * 8) + al((size_t)S * S * 16);
+  // per row: S states, the prefix state, replicated parameters, the Gram matrix
+  const size_t row_bytes = al((size_t)S * L * amp) + al((size_t)L * amp) + al((size_t)maxc * P * 8) + al((size_t)S * S * 16);
   int64_t cap = c->opt.mem_budget_bytes;
   if (cap <= 0) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     cap = (int64_t)((double)(fr + c->qgt_ws_bytes) * 0.5);
   }
-  const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(B, cap / (int64_t)row_bytes));
+  const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(B, 65535), cap / (int64_t)row_bytes));
   const size_t need = row_bytes * chunk + 1024;
   if (need > c->qgt_ws_bytes) {
     dev_free(c->qgt_ws);
     c->qgt_ws = nullptr;
     c->qgt_ws_bytes = 0;
-    cudaError_t e = cudaMalloc(&c->qgt_ws, need);
+    e = cudaMalloc(&c->qgt_ws, need);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(TC_E_NOMEM, "geometric tensor workspace (" + std::to_string(need >> 20) + " MiB)");
@@ -493,49 +632,62 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
     c->qgt_ws_bytes = need;
   }
   char* w = (char*)c->qgt_ws;
-  void* states = w;
-  double* th = (double*)(w + al((size_t)S * L * amp) * chunk);
-  double* M = (double*)((char*)th + al((size_t)S * Pp * 8) * chunk);
+  char* states = w;                                              // [S][R][L], slot-major
+  char* phi = states + al((size_t)S * L * amp) * chunk;         // [R][L]
+  double* th = (double*)(phi + al((size_t)L * amp) * chunk);   // [count][R][P]
+  double* M = (double*)((char*)th + al((size_t)maxc * P * 8) * chunk);
+  int* d_err = (int*)(w + row_bytes * chunk);                  // in the workspace's slack
   // complex64: tensor-core Gram (128-row tiles); complex128: FP64 CUDA-core Gram
-  const bool tc = c->dtype == TC_C64;
+  const bool tc = !dbl;
   const int tile = tc ? kTcTile : kGramTile;
   const int ntile = (S + tile - 1) / tile;
   const int64_t nchunk = (L + (tc ? kTcChunk : kGramChunk) - 1) / (tc ? kTcChunk : kGramChunk);
   if (nchunk > 65535) return fail(TC_E_UNSUPPORTED, "too many qubits for the Gram kernel");
-  int* d_err = (int*)(w + row_bytes * chunk);  // in the workspace's slack
-  cudaError_t e;
   if (tc) {
     if ((e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem)) != cudaSuccess)
       return cuda_fail(e, "gram smem");
     if ((e = cudaMemsetAsync(d_err, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "memset");
   }
+  const int ng = (int)c->qgt_groups.size();
   for (int r0 = 0; r0 < B; r0 += chunk) {
-    const int rows = std::min(chunk, B - r0);
-    if (Pp > 0) {
-      const int64_t tot = (int64_t)rows * S * Pp;
-      const int g = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
-      k_qgt_params<<<g, 256, 0, s>>>(d_params + (size_t)r0 * P, P, c->d_qgt_occ_param, c->d_qgt_occ_c, Pp, rows, th);
-      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "geometric tensor parameters");
-    }
-    if ((st = tc_apply_layers(c->qgt_sub, Pp > 0 ? th : nullptr, rows * S, nullptr, 0, nullptr, 0, states, s)) !=
-        TC_OK)
-      return st;
-    if ((e = cudaMemsetAsync(M, 0, (size_t)rows * S * S * 16, s)) != cudaSuccess) return cuda_fail(e, "memset");
-    for (int r = 0; r < rows; r += 65535) {
-      const int rr = std::min(65535, rows - r);
-      dim3 grid((unsigned)(ntile * (ntile + 1) / 2), (unsigned)nchunk, (unsigned)rr);
-      if (tc)
-        k_gram_tc<<<grid, kTcThreads, kTcSmem, s>>>((const float2*)states + (size_t)r * S * L, S, L, ntile,
-                                             M + (size_t)r * S * S * 2, d_err);
+    const int R = std::min(chunk, B - r0);
+    const double* th_rows = d_params + (size_t)r0 * P;
+    const int64_t slot_bytes = (int64_t)R * L * (int64_t)amp;  // one slot of every row
+    for (int gi = 0; gi < ng; ++gi) {
+      const auto& g = c->qgt_groups[gi];
+      // advance the prefix state to this group's insertion point
+      if (g.seg) {
+        if ((st = tc_apply_layers(g.seg, th_rows, R, gi == 0 ? nullptr : phi, 0, nullptr, 0, phi, s)) != TC_OK)
+          return st;
+      } else if (gi == 0) {
+        return fail(TC_E_INVALID, "geometric tensor plan: no prefix before the first insertion point");
+      }
+      // the group's states (plus the unshifted state after the last group)
+      const int cnt = g.count + (gi == ng - 1 ? 1 : 0);
+      char* dst = states + (int64_t)g.first * slot_bytes;
+      const uint32_t* pz = c->d_qgt_pauli + 3 * (size_t)g.first;
+      if (dbl)
+        k_qgt_pauli<double2><<<grid_for((int64_t)cnt * R * L), 256, 0, s>>>((const double2*)phi, R, L, pz, cnt,
+                                                                            (double2*)dst);
       else
-        k_gram<double><<<grid, 256, 0, s>>>((const double2*)states + (size_t)r * S * L, S, L, ntile,
-                                            M + (size_t)r * S * S * 2);
-      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gram");
+        k_qgt_pauli<float2><<<grid_for((int64_t)cnt * R * L), 256, 0, s>>>((const float2*)phi, R, L, pz, cnt,
+                                                                           (float2*)dst);
+      if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "geometric tensor states");
+      if (g.suffix) {
+        k_qgt_rep<<<grid_for((int64_t)cnt * R * P), 256, 0, s>>>(th_rows, P, R, cnt, th);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "geometric tensor parameters");
+        if ((st = tc_apply_layers(g.suffix, th, cnt * R, dst, 0, nullptr, 0, dst, s)) != TC_OK) return st;
+      }
     }
-    const int64_t tot = (int64_t)rows * P * P;
-    const int g = (int)std::min<int64_t>((tot + 255) / 256, 148 * 16);
-    k_qgt_fold<<<g, 256, 0, s>>>(M, S, tile, c->d_qgt_off, c->d_qgt_occ, c->d_qgt_occ_c, P, rows,
-                                 d_out + (size_t)r0 * P * P * 2);
+    if ((e = cudaMemsetAsync(M, 0, (size_t)R * S * S * 16, s)) != cudaSuccess) return cuda_fail(e, "memset");
+    dim3 grid((unsigned)(ntile * (ntile + 1) / 2), (unsigned)nchunk, (unsigned)R);
+    if (tc)
+      k_gram_tc<<<grid, kTcThreads, kTcSmem, s>>>((const float2*)states, S, L, (int64_t)R * L, ntile, M, d_err);
+    else
+      k_gram<double><<<grid, 256, 0, s>>>((const double2*)states, S, L, (int64_t)R * L, ntile, M);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gram");
+    k_qgt_fold<<<grid_for((int64_t)R * P * P), 256, 0, s>>>(M, S, tile, c->d_qgt_off, c->d_qgt_occ, c->d_qgt_occ_c,
+                                                             P, R, d_out + (size_t)r0 * P * P * 2);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "geometric tensor fold");
   }
   if (tc) {  // the tensor-core Gram's bounded waits report through a flag

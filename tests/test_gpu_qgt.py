@@ -80,3 +80,29 @@ def test_qgt_unsupported_and_empty():
     b.h(0)
     c = nt.Circuit(b.build(2))  # parameters that drive no gate
     assert np.abs(c.qgt(cuda_params(np.ones((2, 2)))).cpu().numpy()).max() == 0
+
+
+@pytest.mark.parametrize("dtype", [nt.TC_C64, nt.TC_C128])
+def test_qgt_commuting_insertions(dtype):
+    # generators that move past commuting gates before their insertion point
+    rng = np.random.default_rng(931)
+    n = 5
+    b = W.OpBuilder(n, W.INIT_PLUS)
+    b.rx(2, 0)
+    b.cnot(4, 2)          # X on the target commutes
+    b.rx(2, 0, scale=-0.5)  # same axis
+    b.rz(1, 1)
+    b.cnot(1, 3)          # Z on the control commutes
+    b.unitary1(1, np.diag(np.exp(1j * rng.uniform(0, 6, 2))))  # diagonal U1
+    b.rzz(0, 1, 2)
+    b.unitary2(0, 1, np.diag(np.exp(1j * rng.uniform(0, 6, 4))))  # diagonal U2
+    b.cz(0, 3)
+    b.ry(3, 3)
+    b.ry(3, 3, scale=2.0)
+    b.h(0)                # stops Z-type generators on qubit 0
+    b.rz(4, 1)            # the last gate: its generator moves to the end
+    circ = b.build()
+    theta = rng.uniform(-2.5, 2.5, size=(2, circ.n_params))
+    g = nt.Circuit(circ, dtype=dtype).qgt(cuda_params(theta)).cpu().numpy()
+    for r in range(2):
+        assert np.abs(g[r] - G.quantum_geometric_tensor(circ, theta[r])).max() <= _tol(circ, dtype)
