@@ -331,15 +331,19 @@ TC_API tc_status tc_profile_end(tc_kernel_stat* out, int max_out, int* n_out);
  *   d_params  device [B][n_params] doubles
  *   d_out     device [B][n_params][n_params][2] doubles (Re, Im of G; Hermitian)
  * Every RX/RY/RZ/RZZ occurrence k (angle s_k theta_p) contributes
- * (s_k / 2) |psi_k> to d_p|psi>, |psi_k> being the state with that
- * occurrence's angle advanced by pi (the derivative of exp(-i a G / 2) is
- * half of exp(-i (a + pi) G / 2)).  Per row the library evaluates the S =
- * occurrences + 1 states with the forward tile passes, their Gram matrix
- * <psi_k|psi_l> with a tiled kernel (products in the circuit's precision over
- * chunks of 2048 amplitudes, FP64 sums) and folds occurrences onto
- * parameters.  Scratch: S states + S x S complex doubles per row, rows
- * chunked by the circuit's memory budget (default half the free memory);
- * TC_E_NOMEM if one row does not fit.  Circuits with noise or random-axis
+ * (-i s_k / 2) |chi_k> to d_p|psi>, chi_k being the state with the gate's
+ * Pauli generator inserted right after it.  An insertion moves past later
+ * gates that commute with it, occurrences sharing an insertion point form a
+ * group, and per group the library runs the circuit's own ops after the
+ * point on the generator-multiplied prefix states (forward tile passes);
+ * the S = occurrences + 1 states of a row (the last unshifted) then go
+ * through a Gram kernel <chi_k|chi_l> (complex64: tcgen05 tensor cores,
+ * TF32 operands split hi + lo, FP32 sums per 16 amplitudes, FP64 across;
+ * complex128: FP64 CUDA cores) and a fold onto parameters.  Scratch: S + 1
+ * states and S x S complex doubles per row, rows chunked by the circuit's
+ * memory budget (default half the free memory); TC_E_NOMEM if one row does
+ * not fit, TC_E_TIMEOUT if a tensor-core completion wait ran out (bounded
+ * waits; the call then synchronises its stream).  Circuits with noise or random-axis
  * rotations and density-matrix circuits: TC_E_UNSUPPORTED.
  */
 TC_API tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, void* stream);
