@@ -383,7 +383,7 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
     del stb, d_thb
     # ---- light-cone TN, 200-qubit brickwork depth 8, <Z99 Z100> -----------
     n, gates, zq = W.brick200_workload()
-    lc = nt.LightCone(n, [(a, b) for a, b, _ in gates], zq)
+    lc = nt.LightCone(n, [(a, b) for a, b, _ in gates], zq, greedy_trials=64)
     g1 = torch.as_tensor(np.stack([u for (_, _, u) in gates])[None].astype(np.complex64), device="cuda")
     o1 = torch.empty((1, 2), dtype=torch.float64, device="cuda")
     ms_tn = _time_cuda(lambda: lc.contract(g1, out=o1), 200)

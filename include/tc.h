@@ -360,6 +360,11 @@ TC_API tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_
  *   z_qubits     host [n_z] qubits of the Z observable (copied)
  *   rank_cap     largest rank an intermediate tensor may have (every index
  *                has dimension 2)
+ *   greedy_trials  without a path: 0 or 1 = the deterministic greedy path;
+ *                k > 1 = the best of it and k - 1 randomised greedy runs
+ *                (seeded Gumbel noise on the pair costs): plans whose live
+ *                tensors fit the one-launch fused executor first, then fewer
+ *                FLOPs, then less WRITE (deterministic for a given k)
  *   path         NULL = greedy path found on the host; else an
  *                opt_einsum-style list of n_path_steps position pairs over
  *                the plan's input tensors (operands removed, result appended)
@@ -398,8 +403,8 @@ typedef struct {
   int32_t fused_groups;     /* barriers of the fused launch: groups of independent steps */
 } tc_path_info;
 TC_API tc_status tc_tn_lightcone_create(int n_qubits, const int32_t* gate_qubits, int n_gates,
-                                        const int32_t* z_qubits, int n_z, int rank_cap, const int32_t* path,
-                                        int n_path_steps, tc_tn** out);
+                                        const int32_t* z_qubits, int n_z, int rank_cap, int greedy_trials,
+                                        const int32_t* path, int n_path_steps, tc_tn** out);
 TC_API tc_status tc_tn_info(const tc_tn* t, tc_path_info* out);
 TC_API tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out, void* stream);
 TC_API void tc_tn_destroy(tc_tn* t);
@@ -422,10 +427,7 @@ TC_API void tc_tn_destroy(tc_tn* t);
  *                a dimension-2 bond (their operator-Schmidt decomposition);
  *                0 = as one rank-4 tensor
  *   rank_cap, path, n_path_steps   as tc_tn_lightcone_create
- *   greedy_trials  without a path: 0 or 1 = the deterministic greedy path;
- *                k > 1 = the cheapest (FLOPs, then WRITE) of it and k - 1
- *                randomised greedy runs whose pair costs carry seeded Gumbel
- *                noise (deterministic for a given k)
+ *   greedy_trials  as tc_tn_lightcone_create
  * The network holds ket and bra (complex-conjugated) copies of the kept
  * ops, the initial vectors and the string's Pauli matrices; qubits carrying
  * the identity join their ket and bra legs.  Host only.

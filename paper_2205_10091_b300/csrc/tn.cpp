@@ -373,8 +373,9 @@ void tn_layout_fused(TnPlan& P) {
 }
 
 // Path for T: the user's, else the deterministic greedy path, else (trials >
-// 1) the cheapest of that and trials - 1 randomised greedy runs (costs
-// perturbed by Gumbel noise, seeds 1..trials-1), by FLOPs then WRITE.
+// 1) the best of that and trials - 1 randomised greedy runs (costs perturbed
+// by Gumbel noise, seeds 1..trials-1): plans whose live tensors fit the fused
+// executor first, then fewer FLOPs, then less WRITE.
 bool tn_plan_path(std::vector<Ten>& T, int rank_cap, const int32_t* path, int n_path, int trials, TnPlan& P,
                   std::string& err) {
   if (path || trials <= 1) {
@@ -393,7 +394,10 @@ bool tn_plan_path(std::vector<Ten>& T, int rank_cap, const int32_t* path, int n_
       if (first_err.empty()) first_err = e;
       continue;
     }
-    if (!have || Pt.flops < best.flops || (Pt.flops == best.flops && Pt.write < best.write)) {
+    tn_layout_fused(Pt);
+    const bool fits = tn_fused_ok(Pt), best_fits = have && tn_fused_ok(best);
+    if (!have || (fits && !best_fits) ||
+        (fits == best_fits && (Pt.flops < best.flops || (Pt.flops == best.flops && Pt.write < best.write)))) {
       best = std::move(Pt);
       have = true;
     }
@@ -403,12 +407,11 @@ bool tn_plan_path(std::vector<Ten>& T, int rank_cap, const int32_t* path, int n_
     return false;
   }
   P = std::move(best);
-  tn_layout_fused(P);
   return true;
 }
 
 bool tn_build_lightcone(int n_qubits, const int32_t* gate_q, int n_gates, const int32_t* z_q, int n_z, int rank_cap,
-                        const int32_t* path, int n_path, TnPlan& P, std::string& err) {
+                        int trials, const int32_t* path, int n_path, TnPlan& P, std::string& err) {
   P = TnPlan{};
   P.n_qubits = n_qubits;
   P.n_gates = n_gates;
@@ -487,7 +490,7 @@ bool tn_build_lightcone(int n_qubits, const int32_t* gate_q, int n_gates, const 
           if (l == bra[q]) l = ket[q];
     }
   }
-  return tn_plan_path(T, rank_cap, path, n_path, 1, P, err);
+  return tn_plan_path(T, rank_cap, path, n_path, trials, P, err);
 }
 
 // Circuit network <init| K^dagger P K |init> for a Pauli string P, K the ops
@@ -679,7 +682,8 @@ void tn_release(tc_tn* t) {
 extern "C" {
 
 tc_status tc_tn_lightcone_create(int n_qubits, const int32_t* gate_qubits, int n_gates, const int32_t* z_qubits,
-                                 int n_z, int rank_cap, const int32_t* path, int n_path_steps, tc_tn** out) {
+                                 int n_z, int rank_cap, int greedy_trials, const int32_t* path, int n_path_steps,
+                                 tc_tn** out) {
   if (!out) return fail(TC_E_INVALID, "out is NULL");
   *out = nullptr;
   if (n_qubits < 2 || n_gates < 0 || (n_gates > 0 && !gate_qubits) || n_z < 1 || !z_qubits)
@@ -687,7 +691,12 @@ tc_status tc_tn_lightcone_create(int n_qubits, const int32_t* gate_qubits, int n
   if (rank_cap < 1 || rank_cap > 26) return fail(TC_E_INVALID, "rank_cap must be in 1..26");
   auto* t = new tc_tn();
   std::string err;
-  if (!tn_build_lightcone(n_qubits, gate_qubits, n_gates, z_qubits, n_z, rank_cap, path, n_path_steps, *t, err)) {
+  if (greedy_trials < 0 || greedy_trials > 4096) {
+    delete t;
+    return fail(TC_E_INVALID, "greedy_trials must be in 0..4096");
+  }
+  if (!tn_build_lightcone(n_qubits, gate_qubits, n_gates, z_qubits, n_z, rank_cap, greedy_trials, path, n_path_steps,
+                          *t, err)) {
     delete t;
     return fail(TC_E_INVALID, err);
   }

@@ -125,7 +125,7 @@ struct TnPlan {
 };
 
 bool tn_build_lightcone(int n_qubits, const int32_t* gate_q, int n_gates, const int32_t* z_q, int n_z, int rank_cap,
-                        const int32_t* path, int n_path, TnPlan& P, std::string& err);
+                        int trials, const int32_t* path, int n_path, TnPlan& P, std::string& err);
 
 bool tn_build_circuit(int n_qubits, int init, const tc_op* ops, int n_ops, int n_params, const double* mats,
                       int n_mats, const uint8_t* pauli, int prune, int split, int rank_cap, int trials,

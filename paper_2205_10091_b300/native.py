@@ -134,7 +134,7 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p]),
     "tc_expect_pauli_sum_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                               C.c_void_p, C.c_void_p]),
-    "tc_tn_lightcone_create": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+    "tc_tn_lightcone_create": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                          C.c_int, C.POINTER(C.c_void_p)]),
     "tc_tn_info": (C.c_int, [C.c_void_p, C.POINTER(tc_path_info)]),
     "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -358,13 +358,13 @@ class DensityMatrixCircuit(Circuit):
 class LightCone:
     """Light-cone tensor-network plan for <Z..Z> of a two-qubit-gate circuit."""
 
-    def __init__(self, n_qubits: int, gate_qubits, z_qubits, rank_cap: int = 18, path=None):
+    def __init__(self, n_qubits: int, gate_qubits, z_qubits, rank_cap: int = 18, path=None, greedy_trials: int = 1):
         gq = np.ascontiguousarray(np.asarray(gate_qubits, dtype=np.int32).reshape(-1, 2))
         zq = np.ascontiguousarray(np.asarray(z_qubits, dtype=np.int32))
         pth = None if path is None else np.ascontiguousarray(np.asarray(path, dtype=np.int32).reshape(-1, 2))
         h = C.c_void_p()
         _check(lib().tc_tn_lightcone_create(n_qubits, gq.ctypes.data_as(C.c_void_p), len(gq),
-                                            zq.ctypes.data_as(C.c_void_p), len(zq), rank_cap,
+                                            zq.ctypes.data_as(C.c_void_p), len(zq), rank_cap, greedy_trials,
                                             None if pth is None else pth.ctypes.data_as(C.c_void_p),
                                             0 if pth is None else len(pth), C.byref(h)))
         self.h = h

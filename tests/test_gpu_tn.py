@@ -18,12 +18,25 @@ def _gates_tensor(gate_lists):
     return torch.as_tensor(arr, device="cuda")
 
 
-def test_brick200_depth8_zz_vs_oracle():
+@pytest.mark.parametrize("trials", [1, 64])  # per-step graph / fused executor
+def test_brick200_depth8_zz_vs_oracle(trials):
     n, gates, obs = W.brick200_workload()
-    lc = nt.LightCone(n, [(a, b) for a, b, _ in gates], obs)
+    lc = nt.LightCone(n, [(a, b) for a, b, _ in gates], obs, greedy_trials=trials)
+    assert lc.info()["fused"] == (1 if trials > 1 else 0)
     out = lc.contract(_gates_tensor([gates])).cpu().numpy()
     ref = T.cone_statevector_expectation(gates, obs)
     assert abs(out[0, 0] - ref.real) <= TOL_ZZ and abs(out[0, 1]) <= TOL_ZZ
+
+
+def test_brick200_seed_batch_fused_sampled():
+    # the bench launch: 1024 seeds of the 200-qubit brickwork in one fused launch
+    n, gates0, obs = W.brick200_workload()
+    lc = nt.LightCone(n, [(a, b) for a, b, _ in gates0], obs, greedy_trials=64)
+    gl = [W.brickwork_u4(n, 8, np.random.default_rng(s)) for s in range(1024)]
+    out = lc.contract(_gates_tensor(gl)).cpu().numpy()
+    for b in (0, 1, 511, 1023):
+        ref = T.cone_statevector_expectation(gl[b], obs)
+        assert abs(out[b, 0] - ref.real) <= TOL_ZZ
 
 
 def test_batch_of_seeds_each_matches():
