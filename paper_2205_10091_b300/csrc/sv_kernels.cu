@@ -53,6 +53,15 @@ __device__ __forceinline__ V cmac2(V m0, V x0, V m1, V x1) {
   r.y = fma(m0.x, x0.y, fma(m0.y, x0.x, fma(m1.x, x1.y, m1.y * x1.x)));
   return r;
 }
+// complex64: the same m0 x0 + m1 x1 as four packed FP32x2 operations,
+// (re, im) * m.re + (-im, re) * m.im per term
+template <>
+__device__ __forceinline__ float2 cmac2(float2 m0, float2 x0, float2 m1, float2 x1) {
+  float2 r = __fmul2_rn(make_float2(m0.x, m0.x), x0);
+  r = __ffma2_rn(make_float2(-m0.y, m0.y), make_float2(x0.y, x0.x), r);
+  r = __ffma2_rn(make_float2(m1.x, m1.x), x1, r);
+  return __ffma2_rn(make_float2(-m1.y, m1.y), make_float2(x1.y, x1.x), r);
+}
 template <typename V>
 __device__ __forceinline__ V cmul(V a, V b) {
   V r;
