@@ -184,9 +184,10 @@ constexpr int kTcLBO = 128;                       // bytes between K-adjacent co
 constexpr int kTcSBO = (kTcK / 4) * 128;          // bytes between 8-row groups
 constexpr int kTcTileBytes = kTcTile * kTcK * 4;  // one operand tile (16 KiB)
 constexpr int kTcRawBytes = 2 * kTcTile * kTcKA * 8;  // one stage's raw amplitudes (32 KiB)
-constexpr int kTcSmem = 6 * kTcTileBytes + 2 * kTcRawBytes;  // tiles + double-buffered raw stage
+constexpr int kTcSetBytes = 6 * kTcTileBytes;            // one stage's operand tiles (96 KiB)
+constexpr int kTcSmem = 2 * kTcSetBytes + kTcRawBytes;   // two tile sets + the raw stage (224 KiB)
 constexpr int kTcChunk = 4096;                    // amplitudes per CTA
-constexpr int kTcCols = 256;                      // TMEM columns: Re then Im
+constexpr int kTcCols = 512;                      // TMEM: two accumulators of Re then Im columns
 constexpr long long kTcSpin = 1ll << 20;          // bounded mbarrier waits
 
 // instruction descriptor: D = F32, A = B = TF32, both K-major, N = M = 128
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
                                                            int64_t kstride, int ntile, double* __restrict__ M,
                                                            int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   int pair = blockIdx.x, kt = 0;
   while (pair >= ntile - kt) {
@@ -260,123 +261,147 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
   const int r = blockIdx.z;
   const int64_t x0 = (int64_t)blockIdx.y * kTcChunk;
   const int64_t x1 = x0 + kTcChunk < L ? x0 + kTcChunk : L;
+  const int nst = (int)((x1 - x0 + kTcKA - 1) / kTcKA);
   const float2* base = states + (size_t)r * L;  // state slot k of row r at base + k kstride
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // accumulator share: TMEM lanes 32 (warp % 4).. (rows k), 64 columns
   // starting at 64 (warp / 4): Re columns [0, 128), then Im
   const int lg = warp & 3, part = warp >> 2;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tc_smem);
-  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
+  const uint32_t bar1 = (uint32_t)__cvta_generic_to_shared(&mbar[1]);
   if (warp == 0) {
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tacc = tmem_base;
-  const uint32_t tmine = tacc + ((uint32_t)(32 * lg) << 16) + (uint32_t)(64 * part);
+  const uint32_t tmine = ((uint32_t)(32 * lg) << 16) + (uint32_t)(64 * part);
   float acc[64];
 #pragma unroll
   for (int j = 0; j < 64; ++j) acc[j] = 0.f;
-  uint32_t parity = 0;
+  uint32_t parity0 = 0, parity1 = 0;
+  bool pending0 = false, pending1 = false;  // a commit not yet waited for
   bool ok = true;
   // raw stage layout: [operand][row][8 amplitude pairs], pair p of a row stored
   // at slot p ^ (row % 8) (so both the copy mapping below, row-major for
   // coalesced global reads, and the conversion mapping, rows fastest, hit
   // distinct shared-memory banks)
-  const uint32_t raw0 = sbase + 6 * kTcTileBytes;
-  auto prefetch = [&](int64_t xs, int buf) {
+  const uint32_t raw0 = sbase + 2 * kTcSetBytes;
+  auto prefetch = [&](int64_t xs) {
 #pragma unroll
     for (int q = 0; q < 1024 / kTcThreads; ++q) {
       const int e = tid + kTcThreads * q;
       const int row = e >> 3, c4 = e & 7;
       const int64_t x = xs + 2 * c4;
       const int ka = kt * kTcTile + row, kb = lt * kTcTile + row;
-      const uint32_t d = raw0 + (uint32_t)(buf * kTcRawBytes + row * (kTcKA * 8) + ((c4 ^ (row & 7)) * 16));
+      const uint32_t d = raw0 + (uint32_t)(row * (kTcKA * 8) + ((c4 ^ (row & 7)) * 16));
       const bool va = ka < S && x < x1, vb = kb < S && x < x1;
       tc_cp16(d, va ? (const void*)(base + (size_t)ka * kstride + x) : (const void*)base, va);
       tc_cp16(d + kTcRawBytes / 2, vb ? (const void*)(base + (size_t)kb * kstride + x) : (const void*)base, vb);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  prefetch(x0, 0);
-  int buf = 0;
-  for (int64_t xs = x0; xs < x1 && ok; xs += kTcKA, buf ^= 1) {
-    if (xs + kTcKA < x1) {
-      prefetch(xs + kTcKA, buf ^ 1);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
+  // add the accumulator of stage set `set` into the registers once its MMAs completed
+  auto drain = [&](int set) -> bool {
+    const bool done = set ? tc_wait(bar1, parity1) : tc_wait(bar0, parity0);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!done) return false;
+    if (set) {
+      parity1 ^= 1u;
+      pending1 = false;
     } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      parity0 ^= 1u;
+      pending0 = false;
     }
-    __syncthreads();  // the stage's raw amplitudes, copied by all threads
-    // ---- convert the raw amplitudes into the operand tiles (rows fastest:
-    // a warp's 16-byte tile stores cover the 8 row slots of a core matrix)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint32_t v[32];
+      tc_ld32(tacc + (uint32_t)(set * 2 * kTcTile) + tmine + 32 * h, v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[32 * h + j] += __uint_as_float(v[j]);
+    }
+    return true;
+  };
+  prefetch(x0);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  int issued = 0;  // stages whose MMAs were committed
+  for (int st = 0; st < nst && ok; ++st) {
+    const int set = st & 1;
+    uint8_t* tiles = tc_smem + set * kTcSetBytes;
+    // ---- convert the raw amplitudes into this stage's operand tiles (rows
+    // fastest: a warp's 16-byte tile stores cover the 8 row slots of a core matrix)
 #pragma unroll
     for (int q = 0; q < 1024 / kTcThreads; ++q) {
       const int e = tid + kTcThreads * q;  // 0..1023
       const int row = e & (kTcTile - 1), c4 = e >> 7;
       const uint32_t off = (uint32_t)((row >> 3) * kTcSBO + c4 * kTcLBO + (row & 7) * 16);
-      const uint8_t* rp = tc_smem + 6 * kTcTileBytes + buf * kTcRawBytes + row * (kTcKA * 8) + ((c4 ^ (row & 7)) * 16);
+      const uint8_t* rp = tc_smem + 2 * kTcSetBytes + row * (kTcKA * 8) + ((c4 ^ (row & 7)) * 16);
       const float4 va = *reinterpret_cast<const float4*>(rp);
       const float4 vb = *reinterpret_cast<const float4*>(rp + kTcRawBytes / 2);
       const float4 ah = make_float4(tf32_rna(va.x), tf32_rna(va.y), tf32_rna(va.z), tf32_rna(va.w));
       const float4 al = make_float4(va.x - ah.x, va.y - ah.y, va.z - ah.z, va.w - ah.w);
       const float4 bh = make_float4(tf32_rna(vb.x), tf32_rna(vb.y), tf32_rna(vb.z), tf32_rna(vb.w));
       const float4 bl = make_float4(vb.x - bh.x, vb.y - bh.y, vb.z - bh.z, vb.w - bh.w);
-      *reinterpret_cast<float4*>(tc_smem + 0 * kTcTileBytes + off) = ah;
-      *reinterpret_cast<float4*>(tc_smem + 1 * kTcTileBytes + off) = al;
-      *reinterpret_cast<float4*>(tc_smem + 2 * kTcTileBytes + off) = bh;
-      *reinterpret_cast<float4*>(tc_smem + 3 * kTcTileBytes + off) = bl;
+      *reinterpret_cast<float4*>(tiles + 0 * kTcTileBytes + off) = ah;
+      *reinterpret_cast<float4*>(tiles + 1 * kTcTileBytes + off) = al;
+      *reinterpret_cast<float4*>(tiles + 2 * kTcTileBytes + off) = bh;
+      *reinterpret_cast<float4*>(tiles + 3 * kTcTileBytes + off) = bl;
       // b = (im, -re) per amplitude; rounding to TF32 commutes with this
-      *reinterpret_cast<float4*>(tc_smem + 4 * kTcTileBytes + off) = make_float4(bh.y, -bh.x, bh.w, -bh.z);
-      *reinterpret_cast<float4*>(tc_smem + 5 * kTcTileBytes + off) = make_float4(bl.y, -bl.x, bl.w, -bl.z);
+      *reinterpret_cast<float4*>(tiles + 4 * kTcTileBytes + off) = make_float4(bh.y, -bh.x, bh.w, -bh.z);
+      *reinterpret_cast<float4*>(tiles + 5 * kTcTileBytes + off) = make_float4(bl.y, -bl.x, bl.w, -bl.z);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // also orders the previous stage's TMEM reads before these MMAs overwrite it
+    __syncthreads();  // tiles complete; the raw stage is free
+    if (st + 1 < nst) prefetch(x0 + (int64_t)(st + 1) * kTcKA);
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t tb = sbase + (uint32_t)(set * kTcSetBytes);
+      const uint32_t dre = tacc + (uint32_t)(set * 2 * kTcTile), dim = dre + kTcTile;
 #pragma unroll
       for (int ks = 0; ks < kTcK / 8; ++ks) {  // 8 TF32 = two core matrices along K per MMA
         const uint32_t o = (uint32_t)(ks * 2 * kTcLBO);
-        const uint64_t ah = tc_sdesc(sbase + 0 * kTcTileBytes + o), al = tc_sdesc(sbase + 1 * kTcTileBytes + o);
-        const uint64_t bh = tc_sdesc(sbase + 2 * kTcTileBytes + o), bl = tc_sdesc(sbase + 3 * kTcTileBytes + o);
-        const uint64_t ch = tc_sdesc(sbase + 4 * kTcTileBytes + o), cl = tc_sdesc(sbase + 5 * kTcTileBytes + o);
+        const uint64_t ah = tc_sdesc(tb + 0 * kTcTileBytes + o), al = tc_sdesc(tb + 1 * kTcTileBytes + o);
+        const uint64_t bh = tc_sdesc(tb + 2 * kTcTileBytes + o), bl = tc_sdesc(tb + 3 * kTcTileBytes + o);
+        const uint64_t ch = tc_sdesc(tb + 4 * kTcTileBytes + o), cl = tc_sdesc(tb + 5 * kTcTileBytes + o);
         const uint32_t first = ks == 0 ? 0u : 1u;  // a fresh accumulator every stage
-        tc_mma(tacc, ah, bh, first);
-        tc_mma(tacc, ah, bl, 1u);
-        tc_mma(tacc, al, bh, 1u);
-        tc_mma(tacc + kTcTile, ah, ch, first);
-        tc_mma(tacc + kTcTile, ah, cl, 1u);
-        tc_mma(tacc + kTcTile, al, ch, 1u);
+        tc_mma(dre, ah, bh, first);
+        tc_mma(dre, ah, bl, 1u);
+        tc_mma(dre, al, bh, 1u);
+        tc_mma(dim, ah, ch, first);
+        tc_mma(dim, ah, cl, 1u);
+        tc_mma(dim, al, ch, 1u);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       set ? bar1 : bar0)
                    : "memory");
     }
-    ok = tc_wait(bar, parity);
-    parity ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (ok) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        uint32_t v[32];
-        tc_ld32(tmine + 32 * h, v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc[32 * h + j] += __uint_as_float(v[j]);
-      }
-    }
+    ++issued;
+    if (set) pending1 = true; else pending0 = true;
+    // the previous stage's accumulator (its MMAs overlapped this stage's conversion)
+    if (st > 0) ok = drain(set ^ 1);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();  // TMEM reads done before that accumulator is reused; next raw stage visible
   }
+  if (ok && issued > 0) ok = drain((issued - 1) & 1);
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
-    tc_wait(bar, parity ^ 1u);  // let the committed MMAs finish before TMEM is freed
+    // let any committed MMAs finish (bounded) before TMEM is freed
+    if (pending0) tc_wait(bar0, parity0);
+    if (pending1) tc_wait(bar1, parity1);
   } else {
     const int k = kt * kTcTile + 32 * lg + lane;
     const int comp = part >> 1, l0 = lt * kTcTile + 64 * (part & 1);
