@@ -376,6 +376,7 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
   for (auto& g : c->gates)
     if (g.noise_event >= 0) c->n_noise++;
   c->gates_orig = c->gates;
+  c->gates = fold_noise_into_u1(c->gates);
   if (dtype == TC_C64) c->gates = rewrite_rx_frames(c->gates, c->N);
   c->pool.assign(pool, pool + 2 * (size_t)n_pool);
   // 4x4 matrices of the Pauli-channel superoperator shape (real, two symmetric

@@ -90,10 +90,12 @@ struct DevMat {
   double scale;
   int32_t pool;    // MT_U1/MT_U2 offset (complex entries) into the pool
   int32_t dst;     // entry offset in the per-row table array of the schedule
-  int32_t T;       // MT_DIAGTAB: number of terms; MT_NOISE: event index
-  int32_t pad2;
-  double t1, t2, t3;  // MT_NOISE: interval ends of I, X, Y (left-closed)
+  int32_t T;       // MT_DIAGTAB: number of terms; MT_NOISE, MT_RSEL: event index; MT_U1: event folded before (-1 none)
+  int32_t T2;      // MT_U1: event folded after the matrix (-1 none)
+  double t1, t2, t3;  // MT_NOISE (and MT_U1's event before): interval ends of I, X, Y (left-closed)
+  double u1, u2, u3;  // MT_U1's event after: interval ends of I, X, Y
 };
+static_assert(sizeof(DevMat) == 80, "DevMat layout");
 
 // A diagonal group: m(x) = sum_e popc(op_e(x) & mask_e), with
 //   op_e(x) = x ^ (x >> d_e)   (ZZ pairs at distance d_e; d_e = 0 means x: single Z)

@@ -76,6 +76,40 @@ bool normalise_ops(int n_user, int N, const tc_op* ops, int n_ops, int n_params,
   return true;
 }
 
+std::vector<HGate> fold_noise_into_u1(const std::vector<HGate>& gates) {
+  const int n = (int)gates.size();
+  std::vector<HGate> g = gates;
+  std::vector<char> gone(n, 0);
+  auto touches = [&](int i, int p) { return g[i].p0 == p || g[i].p1 == p; };
+  auto foldable = [&](int i) { return g[i].kind == TC_OP_U1 && !g[i].diag; };
+  for (int i = 0; i < n; ++i) {
+    if (g[i].kind != TC_OP_PAULI_NOISE) continue;
+    const int p = g[i].p0;
+    int prev = -1, next = -1;
+    for (int j = i - 1; j >= 0 && prev < 0; --j)
+      if (touches(j, p)) prev = j;
+    for (int j = i + 1; j < n && next < 0; ++j)
+      if (touches(j, p)) next = j;
+    if (prev >= 0 && foldable(prev) && g[prev].post_ev < 0) {
+      g[prev].post_ev = g[i].noise_event;
+      g[prev].post_t[0] = g[i].t1;
+      g[prev].post_t[1] = g[i].t2;
+      g[prev].post_t[2] = g[i].t3;
+      gone[i] = 1;
+    } else if (next >= 0 && foldable(next) && g[next].pre_ev < 0) {
+      g[next].pre_ev = g[i].noise_event;
+      g[next].pre_t[0] = g[i].t1;
+      g[next].pre_t[1] = g[i].t2;
+      g[next].pre_t[2] = g[i].t3;
+      gone[i] = 1;
+    }
+  }
+  std::vector<HGate> out;
+  for (int i = 0; i < n; ++i)
+    if (!gone[i]) out.push_back(g[i]);
+  return out;
+}
+
 std::vector<HGate> rewrite_rx_frames(const std::vector<HGate>& gates, int N) {
   std::vector<HGate> out;
   std::vector<char> frame(N, 0);
@@ -442,6 +476,16 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
         m.t1 = g.t1;
         m.t2 = g.t2;
         m.t3 = g.t3;
+      }
+      if (type == MT_U1) {
+        m.T = g.pre_ev;
+        m.t1 = g.pre_t[0];
+        m.t2 = g.pre_t[1];
+        m.t3 = g.pre_t[2];
+        m.T2 = g.post_ev;
+        m.u1 = g.post_t[0];
+        m.u2 = g.post_t[1];
+        m.u3 = g.post_t[2];
       }
       A.mats.push_back(m);
       const int local = table;

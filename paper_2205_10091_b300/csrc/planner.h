@@ -22,7 +22,19 @@ struct HGate {
   bool sign_mode = false;  // CZ
   bool quarter = false;    // S (scale +1) or S^dagger (scale -1) on p0: phase i^{scale * bit}
   bool chan = false;       // U2 whose pool matrix has the Pauli-channel superoperator shape
+  // U1 with Pauli-noise events folded in (fold_noise_into_u1): the row's
+  // outcome of event pre_ev acts before the matrix, of post_ev after it
+  int pre_ev = -1, post_ev = -1;
+  double pre_t[3] = {0, 0, 0}, post_t[3] = {0, 0, 0};
 };
+
+// Fold each Pauli-noise event into the non-diagonal U1 on the same qubit
+// right before it (or, failing that, right after it) when no other gate or
+// event touches that qubit in between: the row's Pauli then multiplies the
+// row's 2x2 matrix when the gate tables are built, and the event costs no
+// instruction.  Events keep their numbers (the random streams do not change);
+// events with no such neighbour stay as they are.
+std::vector<HGate> fold_noise_into_u1(const std::vector<HGate>& gates);
 
 // Rewrite every RX(a) as S^dagger RY(a) S (an exact identity).  The S phases
 // are diagonal, commute with every diagonal gate and cancel between two RX on

@@ -146,9 +146,64 @@ __device__ void build_mat(const DevMat& m, V* tab, const double* th, const doubl
         if (m.type == MT_RY) t[1] = mk<V>((S)0, (S)0);
       }
     } break;
-    case MT_U1:
+    case MT_U1: {
+      // P_after M P_before with the row's outcomes of the folded noise events
+      // (I, X, Y, Z; the same selection as MT_NOISE), then the adjoint if asked
+      double re[4], im[4];
+      for (int e = 0; e < 4; ++e) {
+        re[e] = pool[2 * (m.pool + e)];
+        im[e] = pool[2 * (m.pool + e) + 1];
+      }
+      auto pick = [&](int ev, double t1, double t2, double t3) {
+        if (ev < 0) return 0;
+        const double u = noise_uniform(a, row, ev);
+        return u < t1 ? 0 : u < t2 ? 1 : u < t3 ? 2 : 3;
+      };
+      auto swap_e = [&](int x, int y) {
+        const double r = re[x], i = im[x];
+        re[x] = re[y];
+        im[x] = im[y];
+        re[y] = r;
+        im[y] = i;
+      };
+      auto times_i = [&](int e, double sgn) {  // entry *= sgn * i
+        const double r = re[e];
+        re[e] = -sgn * im[e];
+        im[e] = sgn * r;
+      };
+      const int wb = pick(m.T, m.t1, m.t2, m.t3), wa = pick(m.T2, m.u1, m.u2, m.u3);
+      if (wb == 1 || wb == 2) {  // M X: swap columns; M Y = [[i b, -i a], [i d, -i c]]
+        swap_e(0, 1);
+        swap_e(2, 3);
+        if (wb == 2) {
+          times_i(0, 1.0);
+          times_i(2, 1.0);
+          times_i(1, -1.0);
+          times_i(3, -1.0);
+        }
+      } else if (wb == 3) {  // M Z: negate column 1
+        re[1] = -re[1], im[1] = -im[1], re[3] = -re[3], im[3] = -im[3];
+      }
+      if (wa == 1 || wa == 2) {  // X M: swap rows; Y M = [[-i c, -i d], [i a, i b]]
+        swap_e(0, 2);
+        swap_e(1, 3);
+        if (wa == 2) {
+          times_i(0, -1.0);
+          times_i(1, -1.0);
+          times_i(2, 1.0);
+          times_i(3, 1.0);
+        }
+      } else if (wa == 3) {  // Z M: negate row 1
+        re[2] = -re[2], im[2] = -im[2], re[3] = -re[3], im[3] = -im[3];
+      }
+      for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) {
+          const int src = m.adj ? (c * 2 + r) : (r * 2 + c);
+          t[r * 2 + c] = mk<V>((S)re[src], (S)(m.adj ? -im[src] : im[src]));
+        }
+    } break;
     case MT_U2: {
-      const int d = m.type == MT_U1 ? 2 : 4;
+      const int d = 4;
       for (int r = 0; r < d; ++r)
         for (int c = 0; c < d; ++c) {
           const int src = m.adj ? (c * d + r) : (r * d + c);

@@ -7,7 +7,7 @@ from oracle import statevector as sv
 from paper_2205_10091_b300 import native as nt
 from paper_2205_10091_b300 import workloads as W
 
-from gpu_util import TOL_AMP_C64
+from gpu_util import TOL_AMP_C64, assert_energy_close, assert_grad_close, cuda_params
 
 pytestmark = pytest.mark.gpu
 
@@ -82,3 +82,41 @@ def test_noisy16_full_size_sampled_trajectories():
             assert abs(vals[o][b] - ref[o]) <= 1e-5 * max(1.0, abs(ref[o])), (b, o, vals[o][b], ref[o])
     est = [nt.mean_stderr(torch.as_tensor(v, device="cuda")).cpu().numpy() for v in vals]
     assert 0 < est[0][1] < 0.05 and 0 < est[1][1] < 0.2
+
+
+@pytest.mark.parametrize("dtype", [nt.TC_C64, nt.TC_C128])
+def test_folded_noise_gradients_per_trajectory(dtype):
+    # noise events next to a U1 on their qubit are folded into its per-row
+    # matrix (after it, or before the next one); the rest stay instructions
+    from oracle import gradients as G
+    from oracle import noise as N
+
+    rng = np.random.default_rng(4242)
+    n = 5
+    b = W.OpBuilder(n)
+    for q in range(n):
+        b.unitary1(q, W.haar_unitary(2, rng))
+        b.depolarizing(q, 0.2, 0.15, 0.25)          # after the U1: folded after it
+    for q in range(n - 1):
+        b.cz(q, q + 1)
+        b.depolarizing(q, 0.1, 0.3, 0.2)            # before the next U1 on q: folded before it
+    for q in range(n):
+        b.unitary1(q, W.haar_unitary(2, rng))
+        b.ry(q, q % 3)
+    b.depolarizing(2, 0.3, 0.3, 0.3)                # next to RY only: stays an instruction
+    circ = b.build(3)
+    ham = W.random_pauli_sum(n, 5, rng)
+    B, seed = 6, 77
+    theta = rng.uniform(-2, 2, size=(B, circ.n_params))
+    c = nt.Circuit(circ, dtype=dtype)
+    e, g = c.expect_grad(cuda_params(theta), nt.Hamiltonian(ham), seed=seed)
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    status = N.status_from_seed(seed, B, circ.n_noise)
+    for r in range(B):
+        e_ref = sv.energy(sv.run_circuit(circ, theta[r], status_row=status[r]), n, ham)[0]
+        g_ref = G.parameter_shift(circ, theta[r], ham, status_row=status[r])
+        if dtype == nt.TC_C128:
+            assert abs(e[r] - e_ref) <= 1e-11 and np.abs(g[r] - g_ref).max() <= 1e-10
+        else:
+            assert_energy_close(e[r:r + 1], [e_ref])
+            assert_grad_close(g[r], g_ref)
