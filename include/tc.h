@@ -136,7 +136,9 @@ typedef struct {
   int32_t bwd_stages;
   int32_t tile_qubits_fwd;
   int32_t tile_qubits_bwd;
-  int32_t reserved[5];
+  int32_t fwd_instrs;  /* gate instructions over forward passes (diagonal groups count once) */
+  int32_t bwd_instrs;
+  int32_t reserved[3];
 } tc_plan_info;
 
 typedef struct tc_circuit tc_circuit;

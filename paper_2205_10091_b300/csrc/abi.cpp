@@ -485,6 +485,13 @@ tc_status tc_circuit_info(const tc_circuit* c, tc_plan_info* o) {
   o->bwd_stages = c->bwd.n_stages;
   o->tile_qubits_fwd = c->k_fwd;
   o->tile_qubits_bwd = c->k_bwd;
+  auto instrs = [&](const Schedule& sc) {
+    int n = 0;
+    for (int p = sc.first_pass; p < sc.first_pass + sc.n_passes; ++p) n += c->A.passes[p].n_instr;
+    return n;
+  };
+  o->fwd_instrs = instrs(c->fwd);
+  o->bwd_instrs = instrs(c->bwd);
   return TC_OK;
 }
 

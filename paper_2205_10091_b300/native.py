@@ -65,7 +65,9 @@ class tc_plan_info(C.Structure):
         ("bwd_stages", C.c_int32),
         ("tile_qubits_fwd", C.c_int32),
         ("tile_qubits_bwd", C.c_int32),
-        ("reserved", C.c_int32 * 5),
+        ("fwd_instrs", C.c_int32),
+        ("bwd_instrs", C.c_int32),
+        ("reserved", C.c_int32 * 3),
     ]
 
 

@@ -89,3 +89,25 @@ def test_bad_sizes_rejected():
     assert nt.lib().tc_circuit_create(0, 0, 0, None, 0, 0, None, 0, None, C.byref(h)) == nt.TC_E_INVALID
     assert nt.lib().tc_circuit_create(31, 0, 0, None, 0, 0, None, 0, None, C.byref(h)) == nt.TC_E_INVALID
     assert nt.lib().tc_circuit_create(4, 7, 0, None, 0, 0, None, 0, None, C.byref(h)) == nt.TC_E_INVALID
+
+
+def test_noise_events_next_to_u1_fold_into_its_matrix():
+    # an event right after a U1 on its qubit (or right before the next one)
+    # costs no instruction; one next to an RY stays an instruction
+    rng = np.random.default_rng(3)
+    b = W.OpBuilder(12)
+    b.unitary1(0, W.haar_unitary(2, rng))
+    b.depolarizing(0, 0.1, 0.1, 0.1)   # after U1 on 0: folded
+    b.depolarizing(1, 0.1, 0.1, 0.1)   # before U1 on 1: folded
+    b.unitary1(1, W.haar_unitary(2, rng))
+    b.ry(2, 0)
+    b.depolarizing(2, 0.1, 0.1, 0.1)   # next to RY: stays
+    noisy = nt.Circuit(b.build(1)).info()
+    b = W.OpBuilder(12)
+    b.unitary1(0, W.haar_unitary(2, rng))
+    b.unitary1(1, W.haar_unitary(2, rng))
+    b.ry(2, 0)
+    plain = nt.Circuit(b.build(1)).info()
+    assert noisy["n_noise"] == 3
+    assert noisy["fwd_instrs"] == plain["fwd_instrs"] + 1
+    assert noisy["bwd_instrs"] == plain["bwd_instrs"] + 1
