@@ -334,6 +334,10 @@ def run_gpu(args):
 # ---------------------------------------------------------------------------
 # the other hot-path workloads (bounded, rank 0 at N=1)
 # ---------------------------------------------------------------------------
+# FP32 FMA rate of this B300 measured by a CUDA-core FMA probe (34 T lane-FMA/s)
+FP32_TFLOPS_PROBE = 68.0
+
+
 def _time_cuda(fn, reps: int, warm: int = 3) -> float:
     """Mean ms per call of fn() on the current stream (CUDA events)."""
     import torch
@@ -445,8 +449,13 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
             nt.mean_stderr(v, out=e)
 
     ms_tr = _time_cuda(traj, 5, warm=2)
+    ms_ap = _time_cuda(lambda: c.apply(None, n_traj, seed=seed, out=sts), 5, warm=2)
+    # algorithmic arithmetic: a generic 2x2 complex gate is 14 real FLOP per amplitude
+    flop = int(np.count_nonzero(circ.ops["kind"] == W.OP_U1)) * 14 * (1 << circ.n) * n_traj
     out["noisy16_trajectories"] = {
         "trajectories_per_s": n_traj / (ms_tr / 1e3), "ms_per_run": ms_tr, "trajectories": n_traj,
+        "ms_forward": ms_ap, "forward_tflops": flop / (ms_ap / 1e3) / 1e12,
+        "fp32_frac": flop / (ms_ap / 1e3) / 1e12 / FP32_TFLOPS_PROBE,
         "z0": [float(x) for x in ests[0].tolist()], "sum_zz": [float(x) for x in ests[1].tolist()]}
     del sts
     torch.cuda.synchronize()
