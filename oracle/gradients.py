@@ -106,3 +106,11 @@ def quantum_geometric_tensor(circ: W.Circuit, theta_row) -> np.ndarray:
     d = state_derivatives(circ, theta_row)
     ov = d.conj() @ psi  # <d_i psi|psi>
     return d.conj() @ d.T - np.outer(ov, ov.conj())
+
+
+def natural_gradient(qgt, grad, eps: float) -> np.ndarray:
+    """x solving (4 Re G + eps I) x = grad (Section "Quantum Fisher
+    Information": the natural gradient solves the QFI system; eps > 0 is a
+    Tikhonov shift that makes the positive semidefinite QFI invertible)."""
+    qfi = 4.0 * np.asarray(qgt).real
+    return np.linalg.solve(qfi + eps * np.eye(qfi.shape[0]), np.asarray(grad, np.float64))

@@ -128,3 +128,15 @@ def test_qgt_positive_semidefinite_and_hermitian():
     g = G.quantum_geometric_tensor(circ, rng.uniform(-2, 2, circ.n_params))
     assert np.allclose(g, g.conj().T, atol=1e-13)
     assert np.linalg.eigvalsh(g).min() > -1e-12
+
+
+def test_natural_gradient_bloch_closed_form():
+    # 4 Re G = diag(1, sin^2 a) for RZ(b) RY(a)|0>: x_i = g_i / (qfi_ii + eps)
+    b = W.OpBuilder(1)
+    b.ry(0, 0)
+    b.rz(0, 1)
+    circ = b.build()
+    a, eps = 0.8, 1e-3
+    g = np.array([0.3, -0.7])
+    x = G.natural_gradient(G.quantum_geometric_tensor(circ, [a, 0.4]), g, eps)
+    assert np.allclose(x, [0.3 / (1 + eps), -0.7 / (np.sin(a) ** 2 + eps)], rtol=1e-12)
