@@ -351,6 +351,22 @@ TC_API tc_status tc_profile_end(tc_kernel_stat* out, int max_out, int* n_out);
 TC_API tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, void* stream);
 
 /*
+ * tc_natural_gradient — x = (4 Re G + eps I)^-1 grad per row (Section "Quantum
+ * Fisher Information": the natural gradient solves the QFI system).
+ *   d_qgt   device [B][P][P][2] doubles: tc_qgt's output
+ *   d_grad  device [B][P] doubles (e.g. tc_expect_grad's gradients)
+ *   eps     Tikhonov shift, > 0 (the QFI is only positive semidefinite)
+ *   d_out   device [B][P] doubles
+ * One CTA per row: Cholesky factorisation in shared memory (FP64) of the
+ * symmetric matrix given by the lower triangle (i >= j) of 4 Re G + eps I,
+ * and two triangular solves.  P <= 128 (else TC_E_UNSUPPORTED).  A row whose matrix
+ * is not positive definite gets NaN and the call returns TC_E_INVALID; the
+ * call synchronises its stream to read that status.
+ */
+TC_API tc_status tc_natural_gradient(const double* d_qgt, const double* d_grad, int B, int P, double eps,
+                                     double* d_out, void* stream);
+
+/*
  * Light-cone tensor-network contraction (Section "Tensor network engine",
  * Section "Custom contraction settings", Table "contractor").
  *

@@ -458,6 +458,65 @@ __global__ void k_qgt_fold(const double* __restrict__ M, int S, int tile, const 
   }
 }
 
+// Natural gradient: x = (4 Re G + eps I)^-1 grad per row.  One CTA per row:
+// the matrix in shared memory (FP64), Cholesky A = L L^T in place on the lower
+// triangle (column by column: pivot, scale the column, update the trailing
+// lower triangle), then L y = grad and L^T x = y by one warp with shuffle-
+// reduced dot products.  A pivot that is not positive marks the row bad
+// (status flag) and its output NaN.
+constexpr int kNgMaxP = 128;
+__device__ int g_ng_bad;
+
+__global__ void __launch_bounds__(256) k_natgrad(const double* __restrict__ qgt, const double* __restrict__ grad,
+                                                 int P, double eps, double* __restrict__ out) {
+  extern __shared__ double ng[];
+  double* A = ng;          // P x P, row-major
+  double* y = ng + P * P;  // P
+  __shared__ int bad;
+  const int r = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  const double* Gr = qgt + (size_t)r * P * P * 2;
+  for (int e = tid; e < P * P; e += nt) A[e] = 4.0 * Gr[2 * e] + ((e / P) == (e % P) ? eps : 0.0);
+  for (int i = tid; i < P; i += nt) y[i] = grad[(size_t)r * P + i];
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < P; ++j) {
+    if (tid == 0) {
+      const double d = A[j * P + j];
+      if (!(d > 0.0)) bad = 1;
+      A[j * P + j] = d > 0.0 ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double djj = A[j * P + j];
+    for (int i = j + 1 + tid; i < P; i += nt) A[i * P + j] /= djj;
+    __syncthreads();
+    const int m = P - j - 1;
+    for (int e = tid; e < m * m; e += nt) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k <= i) A[i * P + k] -= A[i * P + j] * A[k * P + j];
+    }
+    __syncthreads();
+  }
+  if (tid < 32) {
+    for (int i = 0; i < P; ++i) {  // L y = grad
+      double sdot = 0.0;
+      for (int k = lane; k < i; k += 32) sdot += A[i * P + k] * y[k];
+      for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+      if (lane == 0) y[i] = (y[i] - sdot) / A[i * P + i];
+      __syncwarp();
+    }
+    for (int i = P - 1; i >= 0; --i) {  // L^T x = y
+      double sdot = 0.0;
+      for (int k = i + 1 + lane; k < P; k += 32) sdot += A[k * P + i] * y[k];
+      for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+      if (lane == 0) y[i] = (y[i] - sdot) / A[i * P + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < P; i += nt) out[(size_t)r * P + i] = bad ? __longlong_as_double(0x7ff8000000000000ll) : y[i];
+  if (tid == 0 && bad) atomicExch(&g_ng_bad, 1);
+}
+
 }  // namespace
 
 }  // namespace tcb
@@ -722,6 +781,35 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
       return cuda_fail(e, "gram status");
     if (h_err) return fail(TC_E_TIMEOUT, "tensor-core Gram: an MMA completion wait timed out");
   }
+  return TC_OK;
+}
+
+tc_status tc_natural_gradient(const double* d_qgt, const double* d_grad, int B, int P, double eps, double* d_out,
+                              void* stream) {
+  if (!d_qgt || !d_grad || !d_out) return fail(TC_E_INVALID, "NULL argument");
+  if (B < 0 || P < 1) return fail(TC_E_INVALID, "B < 0 or P < 1");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(TC_E_INVALID, "eps must be positive and finite");
+  if (P > kNgMaxP) return fail(TC_E_UNSUPPORTED, "natural gradient for more than 128 parameters");
+  if (B == 0) return TC_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int smem = (P * P + P) * 8;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_natgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+    return cuda_fail(e, "natural gradient smem");
+  void* flag = nullptr;
+  if ((e = cudaGetSymbolAddress(&flag, g_ng_bad)) != cudaSuccess) return cuda_fail(e, "natural gradient status");
+  if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "memset");
+  for (int r0 = 0; r0 < B; r0 += 65535) {
+    const int rows = std::min(65535, B - r0);
+    k_natgrad<<<rows, 256, smem, s>>>(d_qgt + (size_t)r0 * P * P * 2, d_grad + (size_t)r0 * P, P, eps,
+                                      d_out + (size_t)r0 * P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "natural gradient");
+  }
+  int h = 0;
+  if ((e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(e, "natural gradient status");
+  if (h) return fail(TC_E_INVALID, "natural gradient: 4 Re G + eps I is not positive definite for some row (NaN)");
   return TC_OK;
 }
 

@@ -142,6 +142,8 @@ SIGNATURES = {
     "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_tn_destroy": (None, [C.c_void_p]),
     "tc_qgt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "tc_natural_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p,
+                                      C.c_void_p]),
     "tc_tn_circuit_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                        C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                        C.POINTER(C.c_void_p)]),
@@ -204,6 +206,18 @@ def profile_end() -> dict:
     _check(lib().tc_profile_end(arr, 16, C.byref(n)))
     return {KERNEL_KINDS[arr[i].kind]: {"launches": arr[i].launches, "ms": arr[i].total_ms,
                                         "algo_bytes": arr[i].algo_bytes} for i in range(min(n.value, 16))}
+
+
+def natural_gradient(qgt, grad, eps: float, out=None, stream=None):
+    """x = (4 Re G + eps I)^-1 grad per row on the device: qgt CUDA complex128
+    [B][P][P] (Circuit.qgt), grad CUDA float64 [B][P]; returns CUDA float64 [B][P]."""
+    import torch
+
+    B, P = grad.shape
+    if out is None:
+        out = torch.empty((B, P), dtype=torch.float64, device="cuda")
+    _check(lib().tc_natural_gradient(_ptr(qgt), _ptr(grad), B, P, C.c_double(eps), _ptr(out), _stream(stream)))
+    return out
 
 
 def mean_stderr(x, out=None, stream=None):

@@ -106,3 +106,34 @@ def test_qgt_commuting_insertions(dtype):
     g = nt.Circuit(circ, dtype=dtype).qgt(cuda_params(theta)).cpu().numpy()
     for r in range(2):
         assert np.abs(g[r] - G.quantum_geometric_tensor(circ, theta[r])).max() <= _tol(circ, dtype)
+
+
+def test_natural_gradient_solve_and_pipeline():
+    import torch
+
+    circ, theta, ham = W.tfim_workload(10, 2, 3)
+    c = nt.Circuit(circ)
+    d = cuda_params(theta)
+    q = c.qgt(d)
+    _, grad = c.expect_grad(d, nt.Hamiltonian(ham))
+    eps = 0.05
+    x = nt.natural_gradient(q, grad, eps).cpu().numpy()
+    qn, gn = q.cpu().numpy(), grad.cpu().numpy()
+    for r in range(3):
+        # the solve itself, on the same inputs (FP64 Cholesky vs LAPACK); the
+        # device reads the lower triangle of 4 Re G (complex64 makes it
+        # symmetric only to rounding)
+        low = np.tril(4.0 * qn[r].real)
+        ref = np.linalg.solve(low + np.tril(low, -1).T + eps * np.eye(low.shape[0]), gn[r])
+        assert np.abs(x[r] - ref).max() <= 1e-9 * max(1.0, np.abs(ref).max())
+        # the whole pipeline against the oracle's tensor and parameter-shift gradient
+        ref_o = G.natural_gradient(G.quantum_geometric_tensor(circ, theta[r]),
+                                   G.parameter_shift(circ, theta[r], ham), eps)
+        assert np.abs(x[r] - ref_o).max() <= 1e-2 * max(1.0, np.abs(ref_o).max())
+    with pytest.raises(nt.TcError):
+        nt.natural_gradient(q, grad, 0.0)
+    bad = torch.zeros((1, 2, 2), dtype=torch.complex128, device="cuda")
+    bad[0, 0, 0] = -1.0
+    with pytest.raises(nt.TcError) as e:
+        nt.natural_gradient(bad, torch.ones((1, 2), dtype=torch.float64, device="cuda"), 1e-3)
+    assert e.value.status == nt.TC_E_INVALID
