@@ -48,3 +48,17 @@ def test_two_gloo_ranks():
     assert t0 != t1  # independent rows per rank
     assert ms0 == ms1 == 15.0  # the slowest rank's time on both ranks
     assert np.isclose(v0, 2 * b0 / 0.015) and v0 == v1
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import argparse
+
+    import bench
+
+    monkeypatch.setenv("RANK", "1")
+    called = []
+    monkeypatch.setattr(bench, "oracle_step_seconds", lambda *a, **k: called.append(1) or (0.0, 0.0))
+    args = argparse.Namespace(gpus=2, steps=1, warmup=0)
+    assert bench.run_reference(args) == 0
+    assert not called and capsys.readouterr().out == ""
