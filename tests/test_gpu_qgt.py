@@ -137,3 +137,20 @@ def test_natural_gradient_solve_and_pipeline():
     with pytest.raises(nt.TcError) as e:
         nt.natural_gradient(bad, torch.ones((1, 2), dtype=torch.float64, device="cuda"), 1e-3)
     assert e.value.status == nt.TC_E_INVALID
+
+
+def test_qgt_full_size_tfim20_closed_form_at_zero_angles():
+    # the bench's 20-qubit, 10-layer ansatz at theta = 0: every gate is the
+    # identity on |+>^20, d_l psi = -(i/2) sum_j Z_j Z_{j+1} psi for a ZZ-layer
+    # angle and -(i/2) sum_j X_j psi = -10 i psi for an RX-layer angle, so
+    # 4 Re G = Var(sum_j Z_j Z_{j+1}) = 19 between any two ZZ-layer angles and 0
+    # elsewhere (X-sum acts as a scalar on |+>^20), and Im G = 0
+    circ, _, _ = W.tfim_workload(20, 10, 1)
+    c = nt.Circuit(circ)
+    g = c.qgt(cuda_params(np.zeros((1, circ.n_params)))).cpu().numpy()[0]
+    qfi = 4 * g.real
+    ref = np.zeros_like(qfi)
+    ref[0::2, 0::2] = 19.0
+    tol = 4 * _tol(circ, nt.TC_C64)
+    assert np.abs(qfi - ref).max() <= tol
+    assert np.abs(g.imag).max() <= tol
