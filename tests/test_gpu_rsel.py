@@ -84,3 +84,16 @@ def test_bp_workload_rows_match_oracle():
     for b in range(theta.shape[0]):
         assert_energy_close(e[b:b + 1], [sv.energy(sv.run_circuit(circ, theta[b], status_row=status[b]), 6, ham)[0]])
         assert_grad_close(g[b], G.parameter_shift(circ, theta[b], ham, status_row=status[b]))
+
+
+def test_bp_workload_full_size_sampled_rows():
+    # the bench launch: 10 qubits x 10 layers, 100 structures in one call
+    circ, theta, seed, ham = W.bp_workload()
+    c = nt.Circuit(circ)
+    e, g = c.expect_grad(cuda_params(theta), nt.Hamiltonian(ham), seed=seed)
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    status = N.status_from_seed(seed, theta.shape[0], _n_events(circ))
+    for b in (0, 57, 99):
+        e_ref = sv.energy(sv.run_circuit(circ, theta[b], status_row=status[b]), circ.n, ham)[0]
+        assert_energy_close(e[b:b + 1], [e_ref])
+        assert_grad_close(g[b], G.parameter_shift(circ, theta[b], ham, status_row=status[b]))
