@@ -324,6 +324,9 @@ __device__ __forceinline__ Map<RB> stage_map(const DevStage& st, uint32_t tid, u
   return m;
 }
 
+// bit i set when register bit r of amplitude i is set (i < 32)
+__constant__ uint32_t kRegBitPattern[5] = {0xaaaaaaaau, 0xccccccccu, 0xf0f0f0f0u, 0xff00ff00u, 0xffff0000u};
+
 template <int RB>
 __device__ __forceinline__ uint32_t offg(const Map<RB>& m, int i) {
   uint32_t o = 0;
@@ -1027,6 +1030,48 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
           const T ws = (__popc(xp & ht.sm) & 1) ? -w : w;
           const T hr = (ht.ny == 0) ? ws : (ht.ny == 2) ? -ws : (T)0;
           const T hi = (ht.ny == 1) ? ws : (ht.ny == 3) ? -ws : (T)0;
+          const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
+          L[i].x += vr;
+          L[i].y += vi;
+          eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
+        }
+        continue;
+      }
+      if (fl.n_terms <= 4) {
+        // up to four terms: each term's sign over this thread's amplitudes is
+        // XOR-linear in the index, a base parity (the thread's fixed bits)
+        // times a pattern over the register bits, built once per term
+        const uint32_t gb = m.g ^ fl.f;
+        uint32_t pat[4];
+        T wre[4], wim[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          pat[q] = 0u;
+          wre[q] = (T)0;
+          wim[q] = (T)0;
+          if (q < fl.n_terms) {
+            const DevHTerm ht = tt0[q];
+            uint32_t pq = (__popc(gb & ht.sm) & 1) ? 0xffffffffu : 0u;
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+              if (__popc(m.ro[r] & ht.sm) & 1) pq ^= kRegBitPattern[r];
+            pat[q] = pq;
+            const T w = (T)ht.w;
+            wre[q] = ht.ny == 0 ? w : (ht.ny == 2 ? -w : (T)0);
+            wim[q] = ht.ny == 1 ? w : (ht.ny == 3 ? -w : (T)0);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          const V pp = sm0[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
+          T hr = 0, hi = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const bool neg = (pat[q] >> i) & 1u;
+            hr += neg ? -wre[q] : wre[q];
+            hi += neg ? -wim[q] : wim[q];
+          }
+          // (P psi)_x = h(x ^ f) psi_{x ^ f}
           const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
           L[i].x += vr;
           L[i].y += vi;
