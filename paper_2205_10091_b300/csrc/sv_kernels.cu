@@ -1079,24 +1079,44 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
         }
         continue;
       }
+      // more terms: the same in chunks of four
+      const uint32_t gb = m.g ^ fl.f;
+      for (int q0 = 0; q0 < fl.n_terms; q0 += 4) {
+        uint32_t pat[4];
+        T wre[4], wim[4];
 #pragma unroll
-      for (int i = 0; i < R; ++i) {
-        const uint32_t xp = (m.g | offg(m, i)) ^ fl.f;
-        const V pp = sm0[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
-        T hr = 0, hi = 0;
-        for (int q = 0; q < fl.n_terms; ++q) {
-          const DevHTerm ht = tt0[q];
-          const T w = (__popc(xp & ht.sm) & 1) ? -(T)ht.w : (T)ht.w;
-          if (ht.ny == 0) hr += w;
-          else if (ht.ny == 1) hi += w;
-          else if (ht.ny == 2) hr -= w;
-          else hi -= w;
+        for (int q = 0; q < 4; ++q) {
+          pat[q] = 0u;
+          wre[q] = (T)0;
+          wim[q] = (T)0;
+          if (q0 + q < fl.n_terms) {
+            const DevHTerm ht = tt0[q0 + q];
+            uint32_t pq = (__popc(gb & ht.sm) & 1) ? 0xffffffffu : 0u;
+#pragma unroll
+            for (int r = 0; r < RB; ++r)
+              if (__popc(m.ro[r] & ht.sm) & 1) pq ^= kRegBitPattern[r];
+            pat[q] = pq;
+            const T w = (T)ht.w;
+            wre[q] = ht.ny == 0 ? w : (ht.ny == 2 ? -w : (T)0);
+            wim[q] = ht.ny == 1 ? w : (ht.ny == 3 ? -w : (T)0);
+          }
         }
-        // (P psi)_x = h(x ^ f) psi_{x ^ f}
-        const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
-        L[i].x += vr;
-        L[i].y += vi;
-        eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          const V pp = sm0[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
+          T hr = 0, hi = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const bool neg = (pat[q] >> i) & 1u;
+            hr += neg ? -wre[q] : wre[q];
+            hi += neg ? -wim[q] : wim[q];
+          }
+          // (P psi)_x = h(x ^ f) psi_{x ^ f}
+          const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
+          L[i].x += vr;
+          L[i].y += vi;
+          eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
+        }
       }
     }
     if ((sp.flags & PF_LAM_STORE) && lam && a.store_lambda && nch == 1) store_regs<RB>(L, lam, m);
