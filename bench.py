@@ -377,11 +377,20 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
             c.expect(st, H, out=e)
 
     ms1 = _time_cuda(one, 200)
+    # per-call latency: CUDA events around each call, median of 1000
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(1000)]
+    for e0, e1 in ev:
+        e0.record()
+        one()
+        e1.record()
+    torch.cuda.synchronize()
+    med1 = float(np.median([e0.elapsed_time(e1) for e0, e1 in ev]))
     Bb = 65536
     d_thb = torch.as_tensor(np.tile(theta, (Bb, 1)), device="cuda")
     stb = torch.empty((Bb, 1 << 10), dtype=torch.complex128, device="cuda")
     msb = _time_cuda(lambda: c.apply(d_thb, Bb, out=stb), 5, warm=2)
     out["hea10_c128"] = {"us_per_circuit_state_and_2_observables": ms1 * 1e3,
+                         "us_median_of_1000": med1 * 1e3,
                          "batched_states_per_s": Bb / (msb / 1e3), "batch": Bb,
                          "zz01": float(e_out[0].item()), "x5": float(e_out[1].item())}
     del stb, d_thb
