@@ -543,19 +543,25 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
             while time.monotonic() - t0 < ta:
                 pass
             ids.append((srv.submit(cc, th, hh), ta))
-        lat, last = [], 0.0
+        lat, svc, last = [], [], 0.0
         for rid, ta in ids:
             r = srv.wait(rid, timeout_s=600)
             lat.append(r["t_done"] - (t0 + ta))
+            svc.append(r["t_done"] - r["t_start"])
             last = max(last, r["t_done"] - t0)
         stt = srv.stats()
         srv.close()
         lat = np.asarray(lat)
         serv[f"{rate:g}_per_s"] = {"requests": len(lat), "p50_ms": float(np.percentile(lat, 50) * 1e3),
                                   "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                                  "completed_per_s": len(lat) / last, "peak_inflight": stt["peak_inflight"]}
+                                  "completed_per_s": len(lat) / last, "peak_inflight": stt["peak_inflight"],
+                                  "mean_admitted_to_done_ms": float(np.mean(svc) * 1e3)}
+    # offered load against the saturated throughput (the highest completion rate seen)
+    cap = max(v["completed_per_s"] for v in serv.values())
+    for k, v in serv.items():
+        v["rho_offered_over_capacity"] = float(k.split("_")[0]) / cap
     out["qaoa_serving"] = {"n_qubits": "8..26 (even)", "layers": "1..6", "arrivals": "Poisson",
-                           "seconds_per_rate": serve_seconds, "by_offered_rate": serv}
+                           "seconds_per_rate": serve_seconds, "capacity_per_s": cap, "by_offered_rate": serv}
     return out
 
 
