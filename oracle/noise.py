@@ -2,10 +2,10 @@
 
 * ``philox4x32_10``: the counter-based generator of Salmon, Moraes, Dror and
   Shaw ("Parallel random numbers: as easy as 1, 2, 3", SC'11), written from
-  its published definition.  PARITY UNPINNED for absolute correctness: no
-  published known-answer vector is available here, so the generator is
-  pinned only by uniformity/independence statistics and by bit-equality
-  with the engine's own independent implementation.
+  its published definition; pinned by the algorithm's published
+  known-answer vectors (tests/golden/philox4x32_10_kat.txt), by
+  uniformity/independence statistics, and by bit-equality with the engine's
+  own independent implementation.
 * Trajectory selection follows Section "Externalizing the randomness": the
   uniform number u picks the outcome whose interval contains it; intervals
   are contiguous with lengths proportional to the probabilities, in the

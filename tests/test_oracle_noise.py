@@ -1,4 +1,5 @@
 """Pins for the oracle's trajectory machinery (CPU only)."""
+import os
 import numpy as np
 import pytest
 
@@ -122,3 +123,14 @@ def test_random_axis_rotation_selects_by_interval():
         gs = G.parameter_shift(b.build(2), theta, ham, status_row=[u, 0.1])
         gf = G.parameter_shift(f.build(2), theta, ham)
         np.testing.assert_allclose(gs, gf, atol=1e-12)
+
+
+def test_philox_known_answer_vectors():
+    # published known-answer vectors of Philox4x32-10 (tests/golden/philox4x32_10_kat.txt)
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        got = N.philox4x32_10(tuple(v[0:4]), tuple(v[4:6]))
+        assert [int(x) for x in got] == v[6:10]
