@@ -109,68 +109,127 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# oracle (CPU) legs
+# oracle (CPU) legs: the FP64 numpy oracle in worker processes (spawn start
+# method, one BLAS thread each), never inside a timed GPU region
 # ---------------------------------------------------------------------------
-def oracle_step_seconds(circ, theta_row, ham, n_fd_params: int):
-    """Time the FP64 oracle on one row: forward + energy, then central
-    differences on `n_fd_params` parameters; returns (t_forward, t_per_param)."""
-    from oracle import gradients as G
-    from oracle import statevector as sv
-
-    t0 = time.perf_counter()
-    sv.energy(sv.run_circuit(circ, theta_row), circ.n, ham)
-    t1 = time.perf_counter()
-    G.finite_difference(circ, theta_row, ham, h=1e-5, params=list(range(n_fd_params)))
-    t2 = time.perf_counter()
-    return t1 - t0, (t2 - t1) / max(n_fd_params, 1)
+# the oracle is memory-bound (numpy einsum over 16 MiB complex128 states), so
+# more processes than this add little on the host; the reference arm's
+# steps use fewer still, so that K + W steps end within a few minutes
+MAX_ORACLE_WORKERS = 8
+REFERENCE_STEP_ROWS = 2
 
 
-def _limit_threads():
+def host_info() -> dict:
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or None}
+
+
+def _worker_init():
+    global _WORKER_LIMIT
     try:
         from threadpoolctl import threadpool_limits
 
-        return threadpool_limits(1)
+        _WORKER_LIMIT = threadpool_limits(1)
     except Exception:  # pragma: no cover
-        import contextlib
-
-        return contextlib.nullcontext()
+        _WORKER_LIMIT = None
 
 
-def cpu_baseline(circ, theta, ham) -> dict:
-    with _limit_threads():
-        tf, tp = oracle_step_seconds(circ, theta[0], ham, n_fd_params=2)
-    per_eval = tf + tp * circ.n_params
-    return {"value": 1.0 / per_eval, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"1 row of the workload: FP64 numpy forward+energy ({tf:.2f} s) and central differences "
-                       f"on 2 of {circ.n_params} parameters ({tp:.2f} s each), extrapolated to all "
-                       f"{circ.n_params} parameters; 1 thread")}
+def oracle_pool(workers: int):
+    import multiprocessing as mp
+
+    return mp.get_context("spawn").Pool(workers, initializer=_worker_init)
+
+
+def tfim_energy_task(args):
+    """Oracle energy of one TFIM row, optionally with theta[k] shifted by h:
+    returns (energy, seconds)."""
+    from oracle import statevector as sv
+
+    n, layers, batch, seed, row, k, h = args
+    circ, theta, ham = W.tfim_workload(n, layers, batch, seed)
+    th = theta[row].copy()
+    if k >= 0:
+        th[k] += h
+    t0 = time.perf_counter()
+    e = sv.energy(sv.run_circuit(circ, th), n, ham)[0]
+    return e, time.perf_counter() - t0
+
+
+def oracle_rows_wall(pool, workers: int, seed: int, first_row: int = 0):
+    """Forward + energy of `workers` rows, one per worker, in parallel: wall seconds."""
+    tasks = [(N_QUBITS, LAYERS, BATCH, seed, (first_row + i) % BATCH, -1, 0.0) for i in range(workers)]
+    t0 = time.perf_counter()
+    pool.map(tfim_energy_task, tasks, chunksize=1)
+    return time.perf_counter() - t0
+
+
+def _evals_per_grad() -> int:
+    # central differences: the energy plus two shifted energies per parameter
+    return 2 * 2 * LAYERS + 1
+
+
+def cpu_baseline(pool, workers: int) -> dict:
+    wall = oracle_rows_wall(pool, workers, W.SEED_TFIM20)
+    value = workers / (wall * _evals_per_grad())
+    hi = host_info()
+    return {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", **hi,
+            "sample": (f"{workers} rows of the workload, FP64 numpy forward+energy, one row per process "
+                       f"({workers} spawn processes x 1 thread on {hi['nproc']} host cores): {wall:.2f} s wall; "
+                       f"energy+gradient by central differences costs {_evals_per_grad()} such evaluations "
+                       f"per row, so value = rows / (wall x {_evals_per_grad()}) (extrapolated)")}
 
 
 def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
         return 0
-    circ, theta, ham = W.tfim_workload(N_QUBITS, LAYERS, BATCH)
-    with _limit_threads():
+    workers = min(os.cpu_count() or 1, REFERENCE_STEP_ROWS)
+    with oracle_pool(workers) as pool:
         for w in range(args.warmup):
-            oracle_step_seconds(circ, theta[w % BATCH], ham, n_fd_params=1)
-        per = []
-        for k in range(args.steps):
-            tf, tp = oracle_step_seconds(circ, theta[k % BATCH], ham, n_fd_params=1)
-            per.append(tf + tp * circ.n_params)
-    per_eval = float(np.mean(per))
-    value = 1.0 / per_eval
-    sample = (f"per step 1 row: FP64 numpy forward+energy and central differences on 1 of {circ.n_params} "
-              f"parameters, extrapolated to all; 1 thread")
+            oracle_rows_wall(pool, workers, W.SEED_TFIM20, first_row=w * workers)
+        walls = [oracle_rows_wall(pool, workers, W.SEED_TFIM20, first_row=(args.warmup + k) * workers)
+                 for k in range(args.steps)]
+    wall = float(np.mean(walls))
+    value = workers / (wall * _evals_per_grad())
+    hi = host_info()
+    sample = (f"each step: FP64 numpy forward+energy of {workers} rows of the workload, one per process "
+              f"({workers} spawn processes x 1 thread on {hi['nproc']} host cores); ms_per_step is that "
+              f"measured wall time.  value extrapolates: energy+gradient by central differences costs "
+              f"{_evals_per_grad()} forward+energy evaluations per row")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "layers": LAYERS, "batch_per_gpu": BATCH},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample, **hi},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
     return 0
+
+
+def headline_errors(pool, energy, grad, seed: int, rows=(0, 517, 1023), grad_samples=((517, 3), (1023, 18)),
+                    h: float = 1e-4) -> dict:
+    """Sampled rows of the timed batch against the FP64 oracle: energies, and
+    gradient entries by central differences (run in the oracle pool)."""
+    tasks = [(N_QUBITS, LAYERS, BATCH, seed, r, -1, 0.0) for r in rows]
+    for r, k in grad_samples:
+        tasks += [(N_QUBITS, LAYERS, BATCH, seed, r, k, h), (N_QUBITS, LAYERS, BATCH, seed, r, k, -h)]
+    res = [e for e, _ in pool.map(tfim_energy_task, tasks, chunksize=1)]
+    e_ref = res[:len(rows)]
+    fd = [(res[len(rows) + 2 * i] - res[len(rows) + 2 * i + 1]) / (2 * h) for i in range(len(grad_samples))]
+    de = [abs(float(energy[r]) - e_ref[i]) for i, r in enumerate(rows)]
+    dg = [abs(float(grad[r, k]) - fd[i]) for i, (r, k) in enumerate(grad_samples)]
+    return {"energy_max_abs": max(de), "energy_rows": list(rows), "energy_tol": "1e-5 max(|E|, 1)",
+            "grad_max_abs": max(dg), "grad_samples": [list(x) for x in grad_samples],
+            "grad_ref": f"central differences, h = {h:g}", "grad_tol": "1e-4 max(|g|_inf, 1)"}
 
 
 # ---------------------------------------------------------------------------
@@ -215,6 +274,13 @@ def run_gpu(args):
     def barrier():
         if world > 1:
             dist.barrier()
+
+    # the oracle's worker processes (rank 0 at N=1 only): spawned, outside
+    # every timed region
+    pool, workers = None, 0
+    if world == 1 and not args.no_oracle:
+        workers = min(os.cpu_count() or 1, MAX_ORACLE_WORKERS)
+        pool = oracle_pool(workers)
 
     # each rank owns an independent batch of parameter sets (weak scaling)
     circ, theta, ham = rank_workload(rank)
@@ -288,6 +354,12 @@ def run_gpu(args):
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / n_plain
 
+    # ---- FP64 norm check of every row's final state (after the timed region) --
+    st_all = c.apply(d_theta, B)
+    norm_dev = float((c.norms(st_all) - 1.0).abs().max().item())
+    del st_all
+    torch.cuda.synchronize()
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -321,10 +393,17 @@ def run_gpu(args):
                        "ms_per_eval": plain_ms, "what": "unfused: one HBM sweep per gate, one per Pauli term"},
         "clocks": clk,
     }
+    err = {"norm_max_dev": norm_dev, "norm_rows": B, "norm_tol": 1e-5}
+    if pool is not None:
+        err.update(headline_errors(pool, energy.cpu().numpy(), grad.cpu().numpy(), W.SEED_TFIM20 + rank))
+    out["err_vs_oracle"] = err
     if world == 1 and not args.no_extra:
-        out["workloads"] = extra_workloads()
-    if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(circ, theta, ham)
+        out["workloads"] = extra_workloads(check=not args.no_oracle)
+    if pool is not None and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(pool, workers)
+    if pool is not None:
+        pool.close()
+        pool.join()
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
@@ -355,13 +434,22 @@ def _time_cuda(fn, reps: int, warm: int = 3) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: float = 2.0) -> dict:
+def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: float = 2.0,
+                    check: bool = True) -> dict:
+    """Each block times one workload of the hot path and, with check=True,
+    states the error of sampled results against the FP64 oracle
+    (`err_vs_oracle`, computed after the timing)."""
     import time
 
     import torch
 
     from paper_2205_10091_b300 import native as nt
 
+    if check:
+        from oracle import gradients as G
+        from oracle import noise as NZ
+        from oracle import statevector as sv
+        from oracle import tensornet as T
     out = {}
     # ---- HEA-10, complex128: one circuit, state + two observables ----------
     circ, theta, obs = W.hea10_workload()
@@ -393,6 +481,13 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
                          "us_median_of_1000": med1 * 1e3,
                          "batched_states_per_s": Bb / (msb / 1e3), "batch": Bb,
                          "zz01": float(e_out[0].item()), "x5": float(e_out[1].item())}
+    if check:
+        ref = sv.run_circuit(circ, theta[0])
+        got = st[0].cpu().numpy()
+        out["hea10_c128"]["err_vs_oracle"] = {
+            "amp_max_abs": float(np.abs(got - ref).max()), "amp_tol": 1e-12,
+            "obs_max_abs": max(abs(float(e_out[i].item()) - sv.energy(ref, 10, o)[0]) for i, o in enumerate(obs)),
+            "batched_amp_max_abs": float(np.abs(stb[Bb - 1].cpu().numpy() - ref).max())}
     del stb, d_thb
     # ---- light-cone TN, 200-qubit brickwork depth 8, <Z99 Z100> -----------
     n, gates, zq = W.brick200_workload()
@@ -406,7 +501,25 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
     ob = torch.empty((Bt, 2), dtype=torch.float64, device="cuda")
     ms_tnb = _time_cuda(lambda: lc.contract(gb, out=ob), 20)
     info = lc.info()
+    tn_err = None
+    if check:
+        seeds = (0, 511, 1023)
+        d_b = [abs(float(ob[sd, 0].item()) - T.cone_statevector_expectation(
+            W.brickwork_u4(n, 8, np.random.default_rng(sd)), zq).real) for sd in seeds]
+        tn_err = {"zz_abs": abs(float(o1[0, 0].item()) - T.cone_statevector_expectation(gates, zq).real),
+                  "batched_zz_max_abs": max(d_b), "batched_seeds": list(seeds), "tol": 1e-5,
+                  "oracle": "FP64 state vector of the 16-qubit light cone"}
+    modes = {}
+    for mname, prec in (("tf32x3", nt.TC_TN_TF32X3), ("bf16x6", nt.TC_TN_BF16X6)):
+        om = torch.empty((1, 2), dtype=torch.float64, device="cuda")
+        ms_m = _time_cuda(lambda: lc.contract(g1, out=om, precision=prec), 50)
+        modes[mname] = {"us_per_contraction": ms_m * 1e3, "tc_steps": lc.info()["tc_steps"],
+                        "zz_abs_err_vs_oracle": (abs(float(om[0, 0].item()) -
+                                                     T.cone_statevector_expectation(gates, zq).real)
+                                                 if check else None)}
     out["brick200_lightcone_tn"] = {
+        "err_vs_oracle": tn_err,
+        "precision_modes": modes,
         "zz": float(o1[0, 0].item()), "us_per_contraction": ms_tn * 1e3,
         "batched_contractions_per_s": Bt / (ms_tnb / 1e3), "batch_seeds": Bt,
         "log10_flops": float(np.log10(info["flops"])), "log2_size": float(np.log2(info["size"])),
@@ -436,10 +549,37 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
     whole = nt.CircuitNetwork(cb40, {20: 3}, split=True, prune=0, rank_cap=26, greedy_trials=16)
     o40w = torch.empty((1, 2), dtype=torch.float64, device="cuda")
     ms40w = _time_cuda(lambda: whole.expect(th1, out=o40w), 20)
+    # the whole network per precision mode: one instance, and 1024 weight rows per launch
+    Bw = 1024
+    thw = th40[:Bw].contiguous()
+    ref_w = (T.circuit_window_expectation(cb40, np.ones(cb40.n_params), {20: 3}, 13, 27).real if check else None)
+    wmodes = {}
+    for mname, prec in (("fp32", nt.TC_TN_FP32), ("tf32x3", nt.TC_TN_TF32X3), ("bf16x6", nt.TC_TN_BF16X6)):
+        o1m = torch.empty((1, 2), dtype=torch.float64, device="cuda")
+        obm = torch.empty((Bw, 2), dtype=torch.float64, device="cuda")
+        ms1m = _time_cuda(lambda: whole.expect(th1, out=o1m, precision=prec), 20)
+        msbm = _time_cuda(lambda: whole.expect(thw, out=obm, precision=prec), 5, warm=2)
+        wi = whole.info()
+        wmodes[mname] = {"us_per_contraction": ms1m * 1e3, "batched_contractions_per_s": Bw / (msbm / 1e3),
+                         "batch": Bw, "tc_steps": wi["tc_steps"] if prec else 0,
+                         "tflops_batched": 8 * wi["cmacs"] * Bw / (msbm / 1e3) / 1e12,
+                         "z20_abs_err_vs_oracle": abs(float(o1m[0, 0].item()) - ref_w) if check else None}
+    eb_err = None
+    if check:
+        win = lambda th: T.circuit_window_expectation(cb40, th, {20: 3}, 13, 27).real  # noqa: E731
+        ref1 = win(np.ones(cb40.n_params))
+        th40h = th40.cpu().numpy().astype(np.float64)
+        eb_err = {"z20_abs": abs(float(o40[0, 0].item()) - ref1),
+                  "z20_whole_network_abs": abs(float(o40w[0, 0].item()) - ref1),
+                  "batched_max_abs": max(abs(float(o40b[b, 0].item()) - win(th40h[b])) for b in (0, 1023)),
+                  "oracle": "FP64 state vector of qubits 13..27 (exact: the gates outside commute with the "
+                            "evolved Z_20)"}
     out["example_block40_tn"] = {
+        "err_vs_oracle": eb_err,
         "z20_all_ones": float(o40[0, 0].item()), "z20_whole_network": float(o40w[0, 0].item()),
         "us_per_contraction": ms40 * 1e3, "batched_contractions_per_s": B40 / (ms40b / 1e3), "batch": B40,
         "us_per_whole_network_contraction": ms40w * 1e3,
+        "whole_network_precision_modes": wmodes,
         "paper_default_row": {"log10_flops": 7.373, "log2_size": 12, "log2_write": 20.171},
         "paths": paths}
     del net40, whole
@@ -461,7 +601,17 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
     ms_ap = _time_cuda(lambda: c.apply(None, n_traj, seed=seed, out=sts), 5, warm=2)
     # algorithmic arithmetic: a generic 2x2 complex gate is 14 real FLOP per amplitude
     flop = int(np.count_nonzero(circ.ops["kind"] == W.OP_U1)) * 14 * (1 << circ.n) * n_traj
+    nz_err = None
+    if check:
+        kk = 4
+        ex = NZ.trajectory_expectations(circ, NZ.status_from_seed(seed, kk, circ.n_noise), obs)
+        nz_err = {"per_trajectory_max_abs": max(abs(float(vals[o][b].item()) - ex[b][o])
+                                                for b in range(kk) for o in range(len(obs))),
+                  "trajectories": kk, "tol": 1e-5,
+                  "oracle": "exact FP64 state of each trajectory under the same Philox outcomes",
+                  "norm_max_dev": float((c.norms(sts[:256]) - 1.0).abs().max().item())}
     out["noisy16_trajectories"] = {
+        "err_vs_oracle": nz_err,
         "trajectories_per_s": n_traj / (ms_tr / 1e3), "ms_per_run": ms_tr, "trajectories": n_traj,
         "ms_forward": ms_ap, "forward_tflops": flop / (ms_ap / 1e3) / 1e12,
         "fp32_frac": flop / (ms_ap / 1e3) / 1e12 / FP32_TFLOPS_PROBE,
@@ -483,7 +633,10 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
             dmc.expect(rho, H, out=v)
 
     ms_dm = _time_cuda(dm_run, 20)
-    out["dm12_noisy_exact"] = {"ms_per_run": ms_dm, "qubits": ndm, "layers": ldm, "p": 0.01,
+    out["dm12_noisy_exact"] = {"err_vs_oracle": None if not check else
+                               "not checked here: the oracle's dense density matrix is run at 2..7 qubits in "
+                               "the parity tests",
+                               "ms_per_run": ms_dm, "qubits": ndm, "layers": ldm, "p": 0.01,
                                "z0": float(vals_dm[0].item()), "sum_zz": float(vals_dm[1].item()),
                                "plan": {k: v for k, v in dmc.info().items() if k in ("fwd_passes", "fwd_stages")}}
     del rho
@@ -495,7 +648,20 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
     e_bp = torch.empty(thbp.shape[0], dtype=torch.float64, device="cuda")
     g_bp = torch.empty(thbp.shape, dtype=torch.float64, device="cuda")
     ms_bp = _time_cuda(lambda: cb.expect_grad(d_bp, Hbp, seed=seedbp, energy=e_bp, grad=g_bp), 50)
+    bp_err = None
+    if check:
+        n_ev = int(np.count_nonzero((cbp.ops["kind"] == W.OP_PAULI_NOISE) | (cbp.ops["kind"] == W.OP_RSEL)))
+        stat = NZ.status_from_seed(seedbp, thbp.shape[0], n_ev)
+        de, dg = [], []
+        for b in (0, 57):
+            de.append(abs(float(e_bp[b].item()) - sv.energy(sv.run_circuit(cbp, thbp[b], status_row=stat[b]),
+                                                               cbp.n, hbp)[0]))
+            dg.append(float(np.abs(g_bp[b].cpu().numpy()
+                                   - G.parameter_shift(cbp, thbp[b], hbp, status_row=stat[b])).max()))
+        bp_err = {"energy_max_abs": max(de), "grad_max_abs": max(dg), "rows": [0, 57],
+                  "grad_ref": "parameter shift per gate occurrence"}
     out["bp10_gradient_variance"] = {
+        "err_vs_oracle": bp_err,
         "ms_per_run": ms_bp, "qubits": cbp.n, "layers": 10, "structures": int(thbp.shape[0]),
         "var_dtheta0": float(g_bp[:, 0].var(unbiased=False).item()),
         "mean_var_over_params": float(g_bp.var(dim=0, unbiased=False).mean().item())}
@@ -511,6 +677,11 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
         qgt[f"tfim{nq}_l10"] = {"rows": Bq, "ms_per_row": msq / Bq, "params": cq_circ.n_params,
                                 "gate_occurrences": occ, "states_per_row": occ + 1,
                                 "qfi00_row0": float(4 * gq[0, 0, 0].real.item())}
+        if check and nq == 12:
+            ref = G.quantum_geometric_tensor(cq_circ, thq[0])
+            qgt[f"tfim{nq}_l10"]["err_vs_oracle"] = {
+                "G_max_abs": float(np.abs(gq[0].cpu().numpy() - ref).max()), "G_max_abs_ref": float(np.abs(ref).max()),
+                "row": 0, "oracle": "product-rule state derivatives, FP64"}
         del cq, gq
     out["qgt_tfim"] = qgt
     # ---- many-term Pauli sum: 12-qubit, 1390-term chemistry-shaped H ------
@@ -526,9 +697,13 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
         ec = torch.empty(Bc, dtype=torch.float64, device="cuda")
         msc = _time_cuda(lambda: cc.expect(stc, Hc, out=ec), 50 if Bc == 1 else 10)
         chem[f"b{Bc}"] = {"us_per_call": msc * 1e3, "states_per_s": Bc / (msc / 1e3)}
+        if check:
+            x0 = xs[0].astype(np.complex64).astype(np.complex128)
+            chem[f"b{Bc}"]["err_vs_oracle"] = {"energy_abs_row0": abs(float(ec[0].item()) - sv.energy(x0, 12, hc)[0])}
     out["chem12_pauli_sum"] = chem
     # ---- QAOA serving: Poisson arrivals, continuous admission ---------------
     serv = {}
+    sampled = []
     for rate in serve_rates:
         reqs = W.qaoa_stream(rate_hz=rate, duration_s=serve_seconds)
         prep = [(W.qaoa_circuit(r.n, r.edges, r.p), r.theta, W.zz_on_edges(r.n, r.edges), r.t_arrive)
@@ -544,11 +719,13 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
                 pass
             ids.append((srv.submit(cc, th, hh), ta))
         lat, svc, last = [], [], 0.0
-        for rid, ta in ids:
+        for i, (rid, ta) in enumerate(ids):
             r = srv.wait(rid, timeout_s=600)
             lat.append(r["t_done"] - (t0 + ta))
             svc.append(r["t_done"] - r["t_start"])
             last = max(last, r["t_done"] - t0)
+            if check and len(sampled) < 3 and prep[i][0].n <= 14:
+                sampled.append((prep[i], r))
         stt = srv.stats()
         srv.close()
         lat = np.asarray(lat)
@@ -562,6 +739,15 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
         v["rho_offered_over_capacity"] = float(k.split("_")[0]) / cap
     out["qaoa_serving"] = {"n_qubits": "8..26 (even)", "layers": "1..6", "arrivals": "Poisson",
                            "seconds_per_rate": serve_seconds, "capacity_per_s": cap, "by_offered_rate": serv}
+    if check and sampled:
+        de, dg = [], []
+        for (cc, th, hh, _), r in sampled:
+            thr = np.asarray(th, dtype=np.float64).ravel()
+            de.append(abs(r["energy"] - sv.energy(sv.run_circuit(cc, thr), cc.n, hh)[0]))
+            dg.append(float(np.abs(r["grad"] - G.finite_difference(cc, thr, hh, h=1e-5)).max()))
+        out["qaoa_serving"]["err_vs_oracle"] = {"energy_max_abs": max(de), "grad_max_abs": max(dg),
+                                                "requests": len(sampled), "qubits": [p[0][0].n for p in sampled],
+                                                "grad_ref": "central differences, h = 1e-5"}
     return out
 
 
@@ -609,6 +795,7 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other hot-path workloads")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle checks and the CPU baseline")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

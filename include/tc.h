@@ -165,6 +165,24 @@ TC_API void tc_circuit_destroy(tc_circuit* c);
 TC_API tc_status tc_circuit_info(const tc_circuit* c, tc_plan_info* out);
 
 /*
+ * tc_pauli_sum_info — host-only plan of a Pauli sum (structures and weights
+ * as in tc_expect_pauli_sum) for this circuit's width: the number of
+ * Pauli-sum passes (sweeps over the state), how many of them are paired
+ * passes (flip masks wider than a tile), the flip-mask groups and the
+ * diagonal entries.  Touches no device.
+ */
+typedef struct {
+  int32_t passes;
+  int32_t paired_passes;
+  int32_t flip_groups;
+  int32_t diag_entries;
+  int32_t tile_qubits;
+  int32_t reserved[3];
+} tc_pauli_sum_plan_info;
+TC_API tc_status tc_pauli_sum_info(const tc_circuit* c, const uint8_t* structures, const double* weights, int T,
+                                   tc_pauli_sum_plan_info* out);
+
+/*
  * tc_apply_layers — |psi_b> = U(theta_b)|psi_0> for every batch row b
  * (Section "Basic circuits and outputs", batched as in Section "Batched
  * circuits").
@@ -197,8 +215,15 @@ TC_API tc_status tc_apply_layers(const tc_circuit* c, const double* d_params, in
  *   structures    host [T][n] bytes in {0,1,2,3} (copied)
  *   weights       host [T] doubles (copied)
  *   d_energy_out  device [B] doubles (written)
- * Scratch: one double per (row, shared-memory tile) inside the circuit's
- * workspace.  Reductions: FP32/FP64 partial sums per tile, FP64 across tiles.
+ * Any Pauli structure is accepted.  A group whose flip mask fits one
+ * shared-memory tile (with the three lowest index bits every tile holds) is
+ * evaluated inside that tile; a wider group runs in a paired pass, in which
+ * one CTA holds tile t and tile t ^ f_out (f_out: the group's flip bits
+ * outside the tile) and evaluates both; groups with the same f_out share a
+ * paired pass.  Each pass reads every amplitude once.
+ * Scratch: one double per (row, pass, shared-memory tile) inside the
+ * circuit's workspace.  Reductions: FP32/FP64 partial sums per tile, FP64
+ * across tiles.
  */
 TC_API tc_status tc_expect_pauli_sum(tc_circuit* c, const void* d_states, int B, const uint8_t* structures,
                               const double* weights, int T, double* d_energy_out, void* stream);
@@ -274,6 +299,18 @@ TC_API tc_status tc_dm_expect_pauli_sum(tc_circuit* c, const void* d_rho, int B,
                                         const double* weights, int T, double* d_out, void* stream);
 
 /*
+ * tc_state_norms — d_norm2_out[b] = sum_x |psi_b(x)|^2 for B states of the
+ * circuit's width and dtype (d_states: device [B][2^n] interleaved complex,
+ * 16-byte aligned; d_norm2_out: device [B] doubles).  Squares and sums in FP64
+ * with a fixed-order reduction (the same result for a row alone or in a
+ * batch): the norm-preservation check of a simulated state (unitary gates keep
+ * ||psi|| = 1), the one place besides the energy reduction where the
+ * complex64 path uses FP64.  Uses the circuit's workspace (one double per row
+ * and block); calls on one circuit must not overlap.
+ */
+TC_API tc_status tc_state_norms(tc_circuit* c, const void* d_states, int B, double* d_norm2_out, void* stream);
+
+/*
  * tc_mean_stderr — d_out[0] = mean of d_x[0..n), d_out[1] = its standard
  * error (sample standard deviation with ddof = 1, over sqrt(n)), in FP64 with
  * a fixed-order reduction: the Monte Carlo estimate over trajectories
@@ -294,9 +331,17 @@ TC_API tc_status tc_mean_stderr(const double* d_x, int n, double* d_out, void* s
  *     plus one double per (row, Pauli-sum pass, tile).  A call that needs
  *     more returns TC_E_INVALID before touching the GPU; call with fewer rows.
  *   - It calls no cudaMalloc, cudaFree or other allocating routine.  The
- *     plan is copied in with cudaMemcpyAsync from host memory.
+ *     plan is copied in with cudaMemcpyAsync from pageable host memory; the
+ *     CUDA runtime may stage such a copy before the call returns, so the call
+ *     can wait on the host for the copy engine (it does not wait for the
+ *     stream's earlier work).
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress).  That lookup loads the library's module with
+ *     the array on the device, which may allocate device memory; make one
+ *     warm-up call (B = 0 is enough, with valid pointers) per device before
+ *     any fixed reservation or allocator callback, and before any stream
+ *     capture.  The address is cached per device index: do not use the
+ *     library on a device after a cudaDeviceReset there.
  *   - Every call shares the array and overwrites what it uses; calls that
  *     overlap on the GPU (other streams, other host threads) race.
  */
@@ -361,7 +406,9 @@ TC_API tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_
  * symmetric matrix given by the lower triangle (i >= j) of 4 Re G + eps I,
  * and two triangular solves.  P <= 128 (else TC_E_UNSUPPORTED).  A row whose matrix
  * is not positive definite gets NaN and the call returns TC_E_INVALID; the
- * call synchronises its stream to read that status.
+ * call synchronises its stream and reads the first element of every output
+ * row to find out (the status lives in this call's own output, so calls on
+ * other streams or threads do not interfere).
  */
 TC_API tc_status tc_natural_gradient(const double* d_qgt, const double* d_grad, int B, int P, double eps,
                                      double* d_out, void* stream);
@@ -397,10 +444,15 @@ TC_API tc_status tc_natural_gradient(const double* d_qgt, const double* d_grad, 
  *   d_gates  device [B][n_gates][16] complex64 (interleaved floats): the
  *            4x4 gate matrices of every gate of the circuit (cone gates used)
  *   d_out    device [B][2] doubles: the complex scalar of each instance
- * Each path step is one complex GEMM (FP32 accumulate) whose operand index
- * permutation is folded into precomputed gather tables; the whole sequence
- * is captured once as a CUDA graph and replayed.  Scratch (inputs and all
- * intermediates of B instances) is owned by the plan.
+ *   precision  tc_tn_precision (below): FP32 CUDA cores, or split TF32 /
+ *            BF16 tensor cores for the steps above the plan's threshold
+ * Each path step is one complex GEMM whose operand index permutation is
+ * folded into precomputed gather tables; the whole sequence is captured once
+ * (per batch size, buffers and precision) as a CUDA graph and replayed.
+ * Scratch (inputs and all intermediates of B instances) is owned by the plan.
+ * A tensor-core step whose bounded wait ran out sets the plan's error word;
+ * the library reads it back after the call and the next call on the plan
+ * returns TC_E_TIMEOUT.
  */
 typedef struct tc_tn tc_tn;
 typedef struct {
@@ -419,12 +471,37 @@ typedef struct {
                                step, replayed as a CUDA graph */
   int32_t smem_bytes;       /* bytes of live tensors per instance under the liveness layout */
   int32_t fused_groups;     /* barriers of the fused launch: groups of independent steps */
+  int32_t tc_steps;         /* steps the split-precision modes run on tensor cores (current threshold) */
+  double tc_cmacs;          /* complex multiply-adds of those steps per instance */
 } tc_path_info;
+
+/*
+ * Precision of a contraction's dense steps (Section "Tensor network engine":
+ * the pairwise contractions are matrix products):
+ *   TC_TN_FP32    every step on CUDA cores, FP32 products and sums;
+ *   TC_TN_TF32X3  steps of at least the plan's threshold of complex
+ *                 multiply-adds (tc_tn_set_tc_threshold; default 32768) on the
+ *                 tensor cores: operands split x = hi + lo, hi = tf32(x),
+ *                 products hi hi + hi lo + lo hi (tcgen05 kind::tf32), FP32
+ *                 accumulation rounded to nearest every 16 complex k;
+ *   TC_TN_BF16X6  the same steps with x = h + m + l in bfloat16 and the six
+ *                 products above 2^-24 relative weight (kind::f16).
+ * Smaller steps run on CUDA cores in every mode.  A plan whose steps all fall
+ * below the threshold runs as in TC_TN_FP32 (fused launch when it fits).
+ */
+typedef enum { TC_TN_FP32 = 0, TC_TN_TF32X3 = 1, TC_TN_BF16X6 = 2 } tc_tn_precision;
 TC_API tc_status tc_tn_lightcone_create(int n_qubits, const int32_t* gate_qubits, int n_gates,
                                         const int32_t* z_qubits, int n_z, int rank_cap, int greedy_trials,
                                         const int32_t* path, int n_path_steps, tc_tn** out);
 TC_API tc_status tc_tn_info(const tc_tn* t, tc_path_info* out);
-TC_API tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out, void* stream);
+TC_API tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, tc_tn_precision precision, double* d_out,
+                                  void* stream);
+/*
+ * tc_tn_set_tc_threshold — complex multiply-adds per instance from which a
+ * step runs on the tensor cores in TC_TN_TF32X3 / TC_TN_BF16X6 (>= 0; 0 puts
+ * every step with K >= 2 there).  Host only.
+ */
+TC_API tc_status tc_tn_set_tc_threshold(tc_tn* t, double min_cmacs);
 TC_API void tc_tn_destroy(tc_tn* t);
 
 /*
@@ -454,15 +531,16 @@ TC_API void tc_tn_destroy(tc_tn* t);
  *   d_params  device [B][n_params] float32
  *   d_out     device [B][2] doubles: Re and Im of <P> per row
  * Tensor entries are evaluated on the device from each row's angles (FP32),
- * then contracted step by step (complex GEMMs, FP32 accumulate) in one CUDA
- * graph.  Plans from tc_tn_lightcone_create are refused (TC_E_INVALID) and
+ * then contracted along the path in the given precision (as
+ * tc_contract_path).  Plans from tc_tn_lightcone_create are refused (TC_E_INVALID) and
  * vice versa.
  */
 TC_API tc_status tc_tn_circuit_create(int n_qubits, tc_init init, const tc_op* ops, int n_ops, int n_params,
                                       const double* const_mats, int n_mats, const uint8_t* pauli, int prune,
                                       int split, int rank_cap, int greedy_trials, const int32_t* path,
                                       int n_path_steps, tc_tn** out);
-TC_API tc_status tc_tn_circuit_expect(tc_tn* t, int B, const float* d_params, double* d_out, void* stream);
+TC_API tc_status tc_tn_circuit_expect(tc_tn* t, int B, const float* d_params, tc_tn_precision precision,
+                                      double* d_out, void* stream);
 
 /*
  * Serving loop (continuous batching of circuit-evaluation requests).

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtc_b300.so")
 
-SOURCES = ["sv_kernels.cu", "planner.cpp", "abi.cpp", "noalloc.cu", "tn.cpp", "tn_kernels.cu", "qgt.cu", "server.cpp", "dm.cpp",
+SOURCES = ["sv_kernels.cu", "planner.cpp", "abi.cpp", "noalloc.cu", "tn.cpp", "tn_kernels.cu", "tn_tc.cu", "qgt.cu", "server.cpp", "dm.cpp",
            "dm_kernels.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

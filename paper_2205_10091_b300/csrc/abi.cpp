@@ -1,5 +1,6 @@
 // C-ABI entry points of libtc_b300.so (declared in include/tc.h).
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -495,6 +496,22 @@ tc_status tc_circuit_info(const tc_circuit* c, tc_plan_info* o) {
   return TC_OK;
 }
 
+tc_status tc_pauli_sum_info(const tc_circuit* c, const uint8_t* structures, const double* weights, int T,
+                            tc_pauli_sum_plan_info* o) {
+  if (!c || !o) return fail(TC_E_INVALID, "NULL argument");
+  if (T < 0 || (T > 0 && (!structures || !weights))) return fail(TC_E_INVALID, "bad Pauli sum");
+  HamPlan H;
+  std::string err;
+  if (!build_hamiltonian(c->n, c->N, c->k_ham, structures, weights, T, H, err)) return fail(TC_E_INVALID, err);
+  memset(o, 0, sizeof(*o));
+  o->passes = (int)H.passes.size();
+  for (const auto& P : H.passes) o->paired_passes += P.pair_fout ? 1 : 0;
+  o->flip_groups = (int)H.hflips.size();
+  o->diag_entries = (int)H.hdiag.size();
+  o->tile_qubits = c->k_ham;
+  return TC_OK;
+}
+
 tc_status tc_apply_layers(const tc_circuit* cc, const double* d_params, int B, const void* d_init, uint64_t seed,
                           const float* d_status, int64_t row_offset, void* d_states_out, void* stream) {
   tc_circuit* c = const_cast<tc_circuit*>(cc);
@@ -647,6 +664,33 @@ tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, const ui
     }
     TC_CHECK_CUDA(launch_plain_term(is_dbl(c), d_states_work, c->N, B, f, sm, ny & 3, weights[t], d_energy_out, s),
                   "plain term");
+  }
+  return TC_OK;
+}
+
+tc_status tc_state_norms(tc_circuit* c, const void* d_states, int B, double* d_norm2_out, void* stream) {
+  if (!c || !d_states || !d_norm2_out) return fail(TC_E_INVALID, "NULL argument");
+  if (B < 0) return fail(TC_E_INVALID, "B < 0");
+  if (B == 0) return TC_OK;
+  const bool dbl = is_dbl(c);
+  // 16-byte words per row: 2^n (complex128) or 2^(n-1) (complex64)
+  const size_t words = ((size_t)1 << c->n) >> (dbl ? 0 : 1);
+  if (words == 0 || ((uintptr_t)d_states & 15)) return fail(TC_E_INVALID, "states must be 16-byte aligned, n >= 1");
+  // blocks per row from the width alone (at least 8192 words = 128 KiB each,
+  // at most 256), so a row's summation order does not depend on B
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)(words / 8192), 256));
+  const int chunk = std::min(B, 65535);
+  tc_status st = ensure_ws(c, (size_t)chunk * nblk * sizeof(double) + 256);
+  if (st != TC_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t rb = ((size_t)1 << c->n) * amp_bytes(c);
+  for (int r0 = 0; r0 < B; r0 += chunk) {
+    const int rows = std::min(chunk, B - r0);
+    TC_CHECK_CUDA(launch_norm2(dbl, (const char*)d_states + (size_t)r0 * rb, c->n, rows, nblk, (double*)c->ws, s),
+                  "norm");
+    TC_CHECK_CUDA(launch_finalize((double*)c->ws, nblk, 1, nullptr, 0, 1, nullptr, nullptr, 0, rows,
+                                  d_norm2_out + r0, nullptr, s),
+                  "finalize");
   }
   return TC_OK;
 }

@@ -28,7 +28,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Device address of the scratch array for the current device.  In host code
 // `g_noalloc_scratch` is only a host-side stand-in for the symbol, never a
 // device address; the real address comes from cudaGetSymbolAddress, taken
-// once per device with that device current (on the first call there).
+// once per device with that device current (on the first call there).  The
+// cached address belongs to the device's primary context: the library must
+// not be used on a device after cudaDeviceReset there.
 tc_status scratch_for_device(int dev, void** out) {
   std::lock_guard<std::mutex> lk(g_setup_mu);
   if (!g_scratch_ptr[dev]) {
@@ -51,6 +53,17 @@ extern "C" tc_status tc_expect_pauli_sum_noalloc(const tc_circuit* c, const void
   if (B < 0 || T < 0) return fail(TC_E_INVALID, "B < 0 or T < 0");
   if (T > 0 && (!structures || !weights)) return fail(TC_E_INVALID, "structures/weights are NULL");
   if (c->N != c->n) return fail(TC_E_UNSUPPORTED, "the allocation-free entry point needs n >= 10");
+
+  // Set-up comes before the B == 0 return, so that a call with no rows can
+  // serve as the warm-up: the first lookup on a device loads this file's
+  // module, and with it the scratch array, which may allocate device memory.
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(TC_E_UNSUPPORTED, "device index beyond 63");
+  void* base = nullptr;
+  tc_status st = scratch_for_device(dev, &base);
+  if (st != TC_OK) return st;
   if (B == 0) return TC_OK;
 
   // compile the Pauli sum on the host (host memory only)
@@ -71,13 +84,6 @@ extern "C" tc_status tc_expect_pauli_sum_noalloc(const tc_circuit* c, const void
                                   " bytes of scratch; the fixed limit is " + std::to_string(kScratchBytes) +
                                   " (use fewer rows per call)");
 
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= kMaxDevices) return fail(TC_E_UNSUPPORTED, "device index beyond 63");
-  void* base = nullptr;
-  tc_status st = scratch_for_device(dev, &base);
-  if (st != TC_OK) return st;
   char* sc = (char*)base;
   cudaStream_t s = (cudaStream_t)stream;
 

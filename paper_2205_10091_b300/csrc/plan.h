@@ -194,6 +194,16 @@ struct DevPass {
   int32_t n_hflip, hflip_off;
   int32_t n_hterm, hterm_off;  // this pass's terms (contiguous), staged in shared memory with its groups
   int32_t epart_index;  // which energy partial this pass writes
+  // Paired Pauli-sum pass (flip masks wider than a tile): every group of the
+  // pass flips the same fixed bits pair_fout, so tile t's partners all lie in
+  // tile t ^ pair_fout.  One CTA owns both tiles of a pair (the one whose
+  // tile-index bit pair_bit is 0 and its partner), stages both in shared
+  // memory and writes lambda and the energy partial of each.  pair_fout = 0:
+  // an ordinary pass.
+  uint32_t pair_fout;      // global positions
+  uint32_t pair_fout_idx;  // the same bits as CTA tile-index bits
+  int32_t pair_bit;        // highest bit of pair_fout_idx
+  int32_t pad_pair;
 };
 
 }  // namespace tcb

@@ -747,30 +747,16 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
     for (auto& e : ents) diag.push_back(e);
   }
   // ---- passes ---------------------------------------------------------------
+  // A group whose flip mask fits one tile together with the positions every
+  // tile holds goes into an ordinary pass (its partners sit in the same tile).
+  // A wider group goes into a paired pass: the tile takes as many of its flip
+  // bits as fit, and the rest (f_out) pair each tile with tile ^ f_out.
   std::vector<std::pair<uint32_t, std::vector<DevHTerm>>> groups(flips.begin(), flips.end());
+  std::vector<int> narrow, wide;
+  for (size_t g = 0; g < groups.size(); ++g)
+    (popc(io_low | groups[g].first) <= k ? narrow : wide).push_back((int)g);
   std::vector<bool> done(groups.size(), false);
-  size_t n_done = 0;
-  bool first = true;
-  while (first || n_done < groups.size()) {
-    uint32_t tile = io_low;
-    std::vector<int> mine;
-    // the pass stages its diagonal entries, groups and terms in shared memory
-    size_t staged = first ? sizeof(DevHDiag) * diag.size() : 0;
-    for (size_t g = 0; g < groups.size(); ++g) {
-      if (done[g]) continue;
-      const size_t gb = sizeof(DevHFlip) + sizeof(DevHTerm) * groups[g].second.size();
-      if (!mine.empty() && staged + gb > (size_t)kHamStageBytes) continue;
-      if (popc(tile | groups[g].first) <= k) {
-        tile |= groups[g].first;
-        mine.push_back((int)g);
-        staged += gb;
-      }
-    }
-    if (!first && mine.empty()) {
-      err = "a Pauli term flips more qubits than one shared-memory tile holds";
-      return false;
-    }
-    for (int p = 0; popc(tile) < k && p < N; ++p) tile |= bit(p);
+  auto emit = [&](uint32_t tile, const std::vector<int>& mine, bool with_diag, bool lam_load, uint32_t fout) {
     DevPass P{};
     P.k = k;
     P.nfix = N - k;
@@ -783,13 +769,16 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
           P.pos[j] = (uint8_t)p;
           tbit[p] = j++;
         } else {
+          if (fout & bit(p)) P.pair_fout_idx |= 1u << f;
           P.fixpos[f++] = (uint8_t)p;
         }
       }
     }
     fill_fix_runs(P);
-    P.flags = first ? PF_LAM_STORE : (PF_LAM_LOAD | PF_LAM_STORE);
-    if (first) {
+    P.pair_fout = fout;
+    P.pair_bit = fout ? 31 - __builtin_clz(P.pair_fout_idx) : 0;
+    P.flags = lam_load ? (PF_LAM_LOAD | PF_LAM_STORE) : PF_LAM_STORE;
+    if (with_diag) {
       P.hdiag_off = (int)H.hdiag.size();
       P.n_hdiag = (int)diag.size();
       for (auto& d : diag) H.hdiag.push_back(d);
@@ -802,19 +791,75 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
       fl.f = groups[g].first;
       uint32_t ft = 0;
       for (int p = 0; p < N; ++p)
-        if (fl.f & bit(p)) ft |= 1u << tbit[p];
+        if (fl.f & tile & bit(p)) ft |= 1u << tbit[p];
       fl.f_tile = ft;
       fl.term_off = (int)H.hterms.size();
       fl.n_terms = (int)groups[g].second.size();
       for (auto& t : groups[g].second) H.hterms.push_back(t);
       H.hflips.push_back(fl);
       done[g] = true;
-      n_done++;
     }
     P.n_hterm = (int)H.hterms.size() - P.hterm_off;
     P.epart_index = (int)H.passes.size();
     H.passes.push_back(P);
+  };
+  auto fill_tile = [&](uint32_t tile) {
+    for (int p = 0; popc(tile) < k && p < N; ++p) tile |= bit(p);
+    return tile;
+  };
+  // ordinary passes; the first one always exists (it starts lambda and holds
+  // the diagonal terms)
+  size_t n_left = narrow.size();
+  bool first = true;
+  while (first || n_left > 0) {
+    uint32_t tile = io_low;
+    std::vector<int> mine;
+    // the pass stages its diagonal entries, groups and terms in shared memory
+    size_t staged = first ? sizeof(DevHDiag) * diag.size() : 0;
+    for (int g : narrow) {
+      if (done[g]) continue;
+      const size_t gb = sizeof(DevHFlip) + sizeof(DevHTerm) * groups[g].second.size();
+      if (!mine.empty() && staged + gb > (size_t)kHamStageBytes) continue;
+      if (popc(tile | groups[g].first) <= k) {
+        tile |= groups[g].first;
+        mine.push_back(g);
+        staged += gb;
+      }
+    }
+    if (!first && mine.empty()) {
+      err = "internal: a tile-sized flip group did not fit an empty pass";
+      return false;
+    }
+    for (int g : mine) done[g] = true;
+    n_left -= mine.size();
+    emit(fill_tile(tile), mine, first, !first, 0u);
     first = false;
+  }
+  // paired passes.  Groups g with the same f_g & ~tile share a pass, which
+  // holds when the tile contains every bit where f_g differs from the first
+  // open group's f0.  So the tile starts with the positions every tile holds
+  // and takes, group by group, the differing bits while they fit; the rest of
+  // the tile is filled from the lowest positions.  f_out = f0 & ~tile is not
+  // empty: f0 does not fit one tile with the fixed positions.
+  for (size_t wi = 0; wi < wide.size(); ++wi) {
+    const int g0 = wide[wi];
+    if (done[g0]) continue;
+    const uint32_t f0 = groups[g0].first;
+    uint32_t tile = io_low;
+    std::vector<int> mine{g0};
+    size_t staged = sizeof(DevHFlip) + sizeof(DevHTerm) * groups[g0].second.size();
+    for (size_t wj = wi + 1; wj < wide.size(); ++wj) {
+      const int g = wide[wj];
+      if (done[g]) continue;
+      const uint32_t d = (groups[g].first ^ f0) & ~tile;
+      const size_t gb = sizeof(DevHFlip) + sizeof(DevHTerm) * groups[g].second.size();
+      if (popc(tile | d) > k || staged + gb > (size_t)kHamStageBytes) continue;
+      tile |= d;
+      mine.push_back(g);
+      staged += gb;
+    }
+    tile = fill_tile(tile);
+    emit(tile, mine, false, true, f0 & ~tile);
   }
   return true;
 }

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "tcgen05.cuh"
 
 namespace tcb {
 
@@ -190,61 +191,13 @@ constexpr int kTcChunk = 4096;                    // amplitudes per CTA
 constexpr int kTcCols = 512;                      // TMEM: two accumulators of Re then Im columns
 constexpr long long kTcSpin = 1ll << 20;          // bounded mbarrier waits
 
-// instruction descriptor: D = F32, A = B = TF32, both K-major, N = M = 128
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcTile >> 3) << 17) |
-                              ((uint32_t)(kTcTile >> 4) << 24);
+constexpr uint32_t kTcIdesc = tc_idesc(kTcFmtTF32, kTcTile, kTcTile);
 
-__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((kTcLBO >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((kTcSBO >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version; base offset 0, no swizzle
-  return d;
-}
-
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr) { return tc_smem_desc(saddr, kTcLBO, kTcSBO); }
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc));
+  tc_mma_tf32(d, a, b, kTcIdesc, acc);
 }
-
-// bounded wait for the phase of the given parity; false on timeout
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
-  for (long long i = 0; i < kTcSpin; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// 16-byte asynchronous copy global -> shared; zero-fills when !valid
-__device__ __forceinline__ void tc_cp16(uint32_t dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-}
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) { return mbar_wait(bar, parity, kTcSpin); }
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restrict__ states, int S, int64_t L,
                                                            int64_t kstride, int ntile, double* __restrict__ M,
@@ -305,8 +258,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
       const int ka = kt * kTcTile + row, kb = lt * kTcTile + row;
       const uint32_t d = raw0 + (uint32_t)(row * (kTcKA * 8) + ((c4 ^ (row & 7)) * 16));
       const bool va = ka < S && x < x1, vb = kb < S && x < x1;
-      tc_cp16(d, va ? (const void*)(base + (size_t)ka * kstride + x) : (const void*)base, va);
-      tc_cp16(d + kTcRawBytes / 2, vb ? (const void*)(base + (size_t)kb * kstride + x) : (const void*)base, vb);
+      cp_async16(d, va ? (const void*)(base + (size_t)ka * kstride + x) : (const void*)base, va);
+      cp_async16(d + kTcRawBytes / 2, vb ? (const void*)(base + (size_t)kb * kstride + x) : (const void*)base, vb);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
@@ -325,7 +278,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       uint32_t v[32];
-      tc_ld32(tacc + (uint32_t)(set * 2 * kTcTile) + tmine + 32 * h, v);
+      tmem_ld32(tacc + (uint32_t)(set * 2 * kTcTile) + tmine + 32 * h, v);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc[32 * h + j] += __uint_as_float(v[j]);
@@ -465,8 +418,6 @@ __global__ void k_qgt_fold(const double* __restrict__ M, int S, int tile, const 
 // reduced dot products.  A pivot that is not positive marks the row bad
 // (status flag) and its output NaN.
 constexpr int kNgMaxP = 128;
-__device__ int g_ng_bad;
-
 __global__ void __launch_bounds__(256) k_natgrad(const double* __restrict__ qgt, const double* __restrict__ grad,
                                                  int P, double eps, double* __restrict__ out) {
   extern __shared__ double ng[];
@@ -514,7 +465,6 @@ __global__ void __launch_bounds__(256) k_natgrad(const double* __restrict__ qgt,
   }
   __syncthreads();
   for (int i = tid; i < P; i += nt) out[(size_t)r * P + i] = bad ? __longlong_as_double(0x7ff8000000000000ll) : y[i];
-  if (tid == 0 && bad) atomicExch(&g_ng_bad, 1);
 }
 
 }  // namespace
@@ -796,20 +746,23 @@ tc_status tc_natural_gradient(const double* d_qgt, const double* d_grad, int B, 
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_natgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
     return cuda_fail(e, "natural gradient smem");
-  void* flag = nullptr;
-  if ((e = cudaGetSymbolAddress(&flag, g_ng_bad)) != cudaSuccess) return cuda_fail(e, "natural gradient status");
-  if ((e = cudaMemsetAsync(flag, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "memset");
   for (int r0 = 0; r0 < B; r0 += 65535) {
     const int rows = std::min(65535, B - r0);
     k_natgrad<<<rows, 256, smem, s>>>(d_qgt + (size_t)r0 * P * P * 2, d_grad + (size_t)r0 * P, P, eps,
                                       d_out + (size_t)r0 * P);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "natural gradient");
   }
-  int h = 0;
-  if ((e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+  // status per call, from this call's own output: a row whose matrix is not
+  // positive definite is all NaN, so its first element tells (one strided copy)
+  std::vector<double> first(B);
+  if ((e = cudaMemcpy2DAsync(first.data(), sizeof(double), d_out, (size_t)P * sizeof(double), sizeof(double), B,
+                             cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return cuda_fail(e, "natural gradient status");
-  if (h) return fail(TC_E_INVALID, "natural gradient: 4 Re G + eps I is not positive definite for some row (NaN)");
+  for (int r = 0; r < B; ++r)
+    if (std::isnan(first[r]))
+      return fail(TC_E_INVALID, "natural gradient: 4 Re G + eps I is not positive definite for row " +
+                                    std::to_string(r) + " (or its inputs hold NaN); that row is NaN");
   return TC_OK;
 }
 

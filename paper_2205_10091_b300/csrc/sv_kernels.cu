@@ -815,6 +815,47 @@ cudaError_t launch_mean_stderr(const double* x, int n, double* out, cudaStream_t
   return cudaGetLastError();
 }
 
+// Squared norm of each state, FP64 accumulation: block (b, row) sums |psi_x|^2
+// over its contiguous slice of the row (16-byte loads: two complex64 or one
+// complex128 amplitude each) into part[row][b].
+__global__ void __launch_bounds__(256) k_norm2(const void* __restrict__ psi, int dbl, int n_qubits, int nblk,
+                                               double* __restrict__ part) {
+  const int row = blockIdx.y;
+  const size_t words = ((size_t)1 << n_qubits) >> (dbl ? 0 : 1);  // 16-byte words per row
+  const size_t per = (words + nblk - 1) / nblk;
+  const size_t lo = per * blockIdx.x, hi = lo + per < words ? lo + per : words;
+  const float4* f4 = (const float4*)psi + (size_t)row * words;
+  const double2* d2 = (const double2*)psi + (size_t)row * words;
+  double acc = 0.0;
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    if (dbl) {
+      const double2 v = d2[i];
+      acc = fma(v.x, v.x, fma(v.y, v.y, acc));
+    } else {
+      const float4 v = f4[i];
+      const double a = v.x, b = v.y, c = v.z, d = v.w;
+      acc = fma(a, a, fma(b, b, fma(c, c, fma(d, d, acc))));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[(size_t)row * nblk + blockIdx.x] = t;
+  }
+}
+
+cudaError_t launch_norm2(bool dbl, const void* psi, int n_qubits, int rows, int nblk, double* part, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  if (rows > 65535 || nblk < 1) return cudaErrorInvalidConfiguration;
+  k_norm2<<<dim3((unsigned)nblk, (unsigned)rows), 256, 0, s>>>(psi, dbl ? 1 : 0, n_qubits, nblk, part);
+  return cudaGetLastError();
+}
+
 // Warp reduction in the working precision, then FP64 (T -> double).
 template <typename S>
 __device__ __forceinline__ double warp_sum(S v) {
@@ -895,8 +936,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
   const uint32_t tid = threadIdx.x;
   const int nwarps = blockDim.x >> 5;
   const int warp = tid >> 5, lane = tid & 31;
-  const int row = (int)(blockIdx.x >> sp.nfix);
-  const uint32_t tile = blockIdx.x & ((1u << sp.nfix) - 1u);
+  // a paired Pauli-sum pass runs one CTA per tile pair: the CTA index skips
+  // tile-index bit pair_bit, which is 0 on the CTA's own tile
+  const bool paired = MODE == KM_HAM && sp.pair_fout != 0u;
+  const int cbits = sp.nfix - (paired ? 1 : 0);
+  const int row = (int)(blockIdx.x >> cbits);
+  uint32_t tile = blockIdx.x & ((1u << cbits) - 1u);
+  if (paired) tile = ((tile >> sp.pair_bit) << (sp.pair_bit + 1)) | (tile & ((1u << sp.pair_bit) - 1u));
   uint32_t base = 0;
   for (int q = 0; q < sp.n_fixruns; ++q) {
     const DevRun u = sp.fixrun[q];
@@ -910,7 +956,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
   const int tsize = 1 << k;
   V* sm0 = (V*)smem_raw;
   V* sm1 = sm0 + tsize;
-  V* tab = sm0 + (MODE == KM_BWD ? 2 * tsize : tsize);
+  V* tab = sm0 + ((MODE == KM_BWD || paired) ? 2 * tsize : tsize);
   DevInstr* ins = (DevInstr*)(tab + ((sp.table_size + 1) & ~1));
   DevStage* sst = (DevStage*)(ins + sp.n_instr);
   DevDiag* dgs = (DevDiag*)(sst + (MODE == KM_HAM ? 0 : sp.n_stages));
@@ -922,16 +968,21 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
 
   if (MODE == KM_HAM) {
     // ---------------- lambda (+)= H psi, energy partial -------------------
+    // Ordinary pass: one side, the CTA's tile, whose partners x ^ f lie in the
+    // same tile.  Paired pass: side 0 is the CTA's tile t (in sm0), side 1 its
+    // partner t ^ pair_fout (in sm1); each side reads its partners from the
+    // other side's copy.
     int8_t S[RB];
 #pragma unroll
     for (int r = 0; r < RB; ++r) S[r] = (int8_t)(k - RB + r);
-    const Map<RB> m = make_map<RB>(sp, S, tid, base);
-    load_regs<RB>(A, psi, m);
-    if ((sp.flags & PF_LAM_LOAD) && lam) {
-      load_regs<RB>(L, lam, m);
+    const Map<RB> m0 = make_map<RB>(sp, S, tid, base);
+    if (paired) {
+      const Map<RB> m1 = make_map<RB>(sp, S, tid, base ^ sp.pair_fout);
+      load_regs<RB>(L, psi, m1);
+      load_regs<RB>(A, psi, m0);
+      smem_write<RB>(L, sm1, m1);
     } else {
-#pragma unroll
-      for (int i = 0; i < R; ++i) L[i] = mk<V>((T)0, (T)0);
+      load_regs<RB>(A, psi, m0);
     }
     // energy-only calls split the pass's flip groups over gridDim.y blocks;
     // the diagonal terms go to the first of them
@@ -946,7 +997,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
       const DevHFlip last = a.hflips[sp.hflip_off + g_hi - 1];
       term_hi = last.term_off + last.n_terms;
     }
-    DevHDiag* hds = (DevHDiag*)(red + nwarps);
+    DevHDiag* hds = (DevHDiag*)(red + 2 * nwarps);
     DevHFlip* hfs = (DevHFlip*)(hds + n_diag_here);
     DevHTerm* hts = (DevHTerm*)(hfs + (g_hi - g_lo));
     {
@@ -957,176 +1008,190 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
       stage(hfs, a.hflips + sp.hflip_off + g_lo, (g_hi - g_lo) * (int)sizeof(DevHFlip));
       stage(hts, a.hterms + term_lo, (term_hi - term_lo) * (int)sizeof(DevHTerm));
     }
-    smem_write<RB>(A, sm0, m);
+    smem_write<RB>(A, sm0, m0);
     __syncthreads();
-    T eacc = 0;
-    {
-      // diagonal terms: the count (or parity) is XOR-linear in the index, so
-      // it is walked in Gray-code order over the registers
-      V e2 = mk<V>((T)0, (T)0);
-      for (int e = 0; e < n_diag_here; ++e) {
-        const DevHDiag hd = hds[e];
-        const T w = (T)hd.w;
-        const uint32_t dd = hd.cnt < 0 ? 0u : hd.d;
-        auto op = [&](uint32_t x) { return (dd == 0 ? x : (x ^ (x >> dd))) & hd.mask; };
-        uint32_t v = op(m.g);
-        uint32_t vr[RB];
-#pragma unroll
-        for (int r = 0; r < RB; ++r) vr[r] = op(m.ro[r]);
-        if (hd.cnt < 0) {
-#pragma unroll
-          for (int j = 0; j < R; ++j) {
-            if (j) v ^= vr[low_bit(j)];
-            const int i = j ^ (j >> 1);
-            const T h = (__popc(v) & 1) ? -w : w;
-            const V h2 = mk<V>(h, h);
-            L[i] = cfma2(h2, A[i], L[i]);
-            e2 = cfma2(cmul_re(h2, A[i]), A[i], e2);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < R; ++j) {
-            if (j) v ^= vr[low_bit(j)];
-            const int i = j ^ (j >> 1);
-            const T h = w * (T)(hd.cnt - 2 * __popc(v));
-            const V h2 = mk<V>(h, h);
-            L[i] = cfma2(h2, A[i], L[i]);
-            e2 = cfma2(cmul_re(h2, A[i]), A[i], e2);
-          }
-        }
-      }
-      eacc = e2.x + e2.y;
-    }
     // swizzled tile offsets of the register bits (the swizzle is XOR-linear)
     uint32_t srt[RB];
 #pragma unroll
-    for (int r = 0; r < RB; ++r) srt[r] = swz<V>(m.rt[r]);
-    for (int g = 0; g < g_hi - g_lo; ++g) {
-      const DevHFlip fl = hfs[g];
-      const DevHTerm* tt0 = hts + (fl.term_off - term_lo);
-      if (fl.n_terms == 1) {
-        const DevHTerm ht = tt0[0];
-        const T w = (T)ht.w;
-        if (ht.sm == 0 && ht.ny == 0) {
-          // X string: (P psi)_x = w psi_{x ^ f}; partner index walked in Gray-code order
-          uint32_t tt = swz<V>(m.t) ^ swz<V>(fl.f_tile);
-          V e2 = mk<V>((T)0, (T)0);
-          const V w2 = mk<V>(w, w);
-#pragma unroll
-          for (int j = 0; j < R; ++j) {
-            if (j) tt ^= srt[low_bit(j)];
-            const int i = j ^ (j >> 1);
-            const V pp = sm0[tt];
-            L[i] = cfma2(w2, pp, L[i]);
-            e2 = cfma2(A[i], pp, e2);
+    for (int r = 0; r < RB; ++r) srt[r] = swz<V>(m0.rt[r]);
+    const int nsides = paired ? 2 : 1;
+    for (int side = 0; side < nsides; ++side) {
+      const Map<RB> m = side ? make_map<RB>(sp, S, tid, base ^ sp.pair_fout) : m0;
+      // the tile that holds this side's partners
+      const V* smp = paired ? (side ? sm0 : sm1) : sm0;
+      if (side) smem_read<RB>(A, sm1, m);
+      if ((sp.flags & PF_LAM_LOAD) && lam) {
+        load_regs<RB>(L, lam, m);
+      } else {
+  #pragma unroll
+        for (int i = 0; i < R; ++i) L[i] = mk<V>((T)0, (T)0);
+      }
+      T eacc = 0;
+      {
+        // diagonal terms: the count (or parity) is XOR-linear in the index, so
+        // it is walked in Gray-code order over the registers
+        V e2 = mk<V>((T)0, (T)0);
+        for (int e = 0; e < n_diag_here; ++e) {
+          const DevHDiag hd = hds[e];
+          const T w = (T)hd.w;
+          const uint32_t dd = hd.cnt < 0 ? 0u : hd.d;
+          auto op = [&](uint32_t x) { return (dd == 0 ? x : (x ^ (x >> dd))) & hd.mask; };
+          uint32_t v = op(m.g);
+          uint32_t vr[RB];
+  #pragma unroll
+          for (int r = 0; r < RB; ++r) vr[r] = op(m.ro[r]);
+          if (hd.cnt < 0) {
+  #pragma unroll
+            for (int j = 0; j < R; ++j) {
+              if (j) v ^= vr[low_bit(j)];
+              const int i = j ^ (j >> 1);
+              const T h = (__popc(v) & 1) ? -w : w;
+              const V h2 = mk<V>(h, h);
+              L[i] = cfma2(h2, A[i], L[i]);
+              e2 = cfma2(cmul_re(h2, A[i]), A[i], e2);
+            }
+          } else {
+  #pragma unroll
+            for (int j = 0; j < R; ++j) {
+              if (j) v ^= vr[low_bit(j)];
+              const int i = j ^ (j >> 1);
+              const T h = w * (T)(hd.cnt - 2 * __popc(v));
+              const V h2 = mk<V>(h, h);
+              L[i] = cfma2(h2, A[i], L[i]);
+              e2 = cfma2(cmul_re(h2, A[i]), A[i], e2);
+            }
           }
-          eacc = fma(w, e2.x + e2.y, eacc);
+        }
+        eacc = e2.x + e2.y;
+      }
+      for (int g = 0; g < g_hi - g_lo; ++g) {
+        const DevHFlip fl = hfs[g];
+        const DevHTerm* tt0 = hts + (fl.term_off - term_lo);
+        if (fl.n_terms == 1) {
+          const DevHTerm ht = tt0[0];
+          const T w = (T)ht.w;
+          if (ht.sm == 0 && ht.ny == 0) {
+            // X string: (P psi)_x = w psi_{x ^ f}; partner index walked in Gray-code order
+            uint32_t tt = swz<V>(m.t) ^ swz<V>(fl.f_tile);
+            V e2 = mk<V>((T)0, (T)0);
+            const V w2 = mk<V>(w, w);
+  #pragma unroll
+            for (int j = 0; j < R; ++j) {
+              if (j) tt ^= srt[low_bit(j)];
+              const int i = j ^ (j >> 1);
+              const V pp = smp[tt];
+              L[i] = cfma2(w2, pp, L[i]);
+              e2 = cfma2(A[i], pp, e2);
+            }
+            eacc = fma(w, e2.x + e2.y, eacc);
+            continue;
+          }
+  #pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const uint32_t xp = (m.g | offg(m, i)) ^ fl.f;
+            const V pp = smp[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
+            const T ws = (__popc(xp & ht.sm) & 1) ? -w : w;
+            const T hr = (ht.ny == 0) ? ws : (ht.ny == 2) ? -ws : (T)0;
+            const T hi = (ht.ny == 1) ? ws : (ht.ny == 3) ? -ws : (T)0;
+            const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
+            L[i].x += vr;
+            L[i].y += vi;
+            eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
+          }
           continue;
         }
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const uint32_t xp = (m.g | offg(m, i)) ^ fl.f;
-          const V pp = sm0[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
-          const T ws = (__popc(xp & ht.sm) & 1) ? -w : w;
-          const T hr = (ht.ny == 0) ? ws : (ht.ny == 2) ? -ws : (T)0;
-          const T hi = (ht.ny == 1) ? ws : (ht.ny == 3) ? -ws : (T)0;
-          const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
-          L[i].x += vr;
-          L[i].y += vi;
-          eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
+        if (fl.n_terms <= 4) {
+          // up to four terms: each term's sign over this thread's amplitudes is
+          // XOR-linear in the index, a base parity (the thread's fixed bits)
+          // times a pattern over the register bits, built once per term
+          const uint32_t gb = m.g ^ fl.f;
+          uint32_t pat[4];
+          T wre[4], wim[4];
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            pat[q] = 0u;
+            wre[q] = (T)0;
+            wim[q] = (T)0;
+            if (q < fl.n_terms) {
+              const DevHTerm ht = tt0[q];
+              uint32_t pq = (__popc(gb & ht.sm) & 1) ? 0xffffffffu : 0u;
+  #pragma unroll
+              for (int r = 0; r < RB; ++r)
+                if (__popc(m.ro[r] & ht.sm) & 1) pq ^= kRegBitPattern[r];
+              pat[q] = pq;
+              const T w = (T)ht.w;
+              wre[q] = ht.ny == 0 ? w : (ht.ny == 2 ? -w : (T)0);
+              wim[q] = ht.ny == 1 ? w : (ht.ny == 3 ? -w : (T)0);
+            }
+          }
+  #pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const V pp = smp[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
+            T hr = 0, hi = 0;
+  #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const bool neg = (pat[q] >> i) & 1u;
+              hr += neg ? -wre[q] : wre[q];
+              hi += neg ? -wim[q] : wim[q];
+            }
+            // (P psi)_x = h(x ^ f) psi_{x ^ f}
+            const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
+            L[i].x += vr;
+            L[i].y += vi;
+            eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
+          }
+          continue;
         }
-        continue;
-      }
-      if (fl.n_terms <= 4) {
-        // up to four terms: each term's sign over this thread's amplitudes is
-        // XOR-linear in the index, a base parity (the thread's fixed bits)
-        // times a pattern over the register bits, built once per term
+        // more terms: the same in chunks of four
         const uint32_t gb = m.g ^ fl.f;
-        uint32_t pat[4];
-        T wre[4], wim[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          pat[q] = 0u;
-          wre[q] = (T)0;
-          wim[q] = (T)0;
-          if (q < fl.n_terms) {
-            const DevHTerm ht = tt0[q];
-            uint32_t pq = (__popc(gb & ht.sm) & 1) ? 0xffffffffu : 0u;
-#pragma unroll
-            for (int r = 0; r < RB; ++r)
-              if (__popc(m.ro[r] & ht.sm) & 1) pq ^= kRegBitPattern[r];
-            pat[q] = pq;
-            const T w = (T)ht.w;
-            wre[q] = ht.ny == 0 ? w : (ht.ny == 2 ? -w : (T)0);
-            wim[q] = ht.ny == 1 ? w : (ht.ny == 3 ? -w : (T)0);
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const V pp = sm0[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
-          T hr = 0, hi = 0;
-#pragma unroll
+        for (int q0 = 0; q0 < fl.n_terms; q0 += 4) {
+          uint32_t pat[4];
+          T wre[4], wim[4];
+  #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const bool neg = (pat[q] >> i) & 1u;
-            hr += neg ? -wre[q] : wre[q];
-            hi += neg ? -wim[q] : wim[q];
+            pat[q] = 0u;
+            wre[q] = (T)0;
+            wim[q] = (T)0;
+            if (q0 + q < fl.n_terms) {
+              const DevHTerm ht = tt0[q0 + q];
+              uint32_t pq = (__popc(gb & ht.sm) & 1) ? 0xffffffffu : 0u;
+  #pragma unroll
+              for (int r = 0; r < RB; ++r)
+                if (__popc(m.ro[r] & ht.sm) & 1) pq ^= kRegBitPattern[r];
+              pat[q] = pq;
+              const T w = (T)ht.w;
+              wre[q] = ht.ny == 0 ? w : (ht.ny == 2 ? -w : (T)0);
+              wim[q] = ht.ny == 1 ? w : (ht.ny == 3 ? -w : (T)0);
+            }
           }
-          // (P psi)_x = h(x ^ f) psi_{x ^ f}
-          const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
-          L[i].x += vr;
-          L[i].y += vi;
-          eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
-        }
-        continue;
-      }
-      // more terms: the same in chunks of four
-      const uint32_t gb = m.g ^ fl.f;
-      for (int q0 = 0; q0 < fl.n_terms; q0 += 4) {
-        uint32_t pat[4];
-        T wre[4], wim[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          pat[q] = 0u;
-          wre[q] = (T)0;
-          wim[q] = (T)0;
-          if (q0 + q < fl.n_terms) {
-            const DevHTerm ht = tt0[q0 + q];
-            uint32_t pq = (__popc(gb & ht.sm) & 1) ? 0xffffffffu : 0u;
-#pragma unroll
-            for (int r = 0; r < RB; ++r)
-              if (__popc(m.ro[r] & ht.sm) & 1) pq ^= kRegBitPattern[r];
-            pat[q] = pq;
-            const T w = (T)ht.w;
-            wre[q] = ht.ny == 0 ? w : (ht.ny == 2 ? -w : (T)0);
-            wim[q] = ht.ny == 1 ? w : (ht.ny == 3 ? -w : (T)0);
+  #pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const V pp = smp[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
+            T hr = 0, hi = 0;
+  #pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const bool neg = (pat[q] >> i) & 1u;
+              hr += neg ? -wre[q] : wre[q];
+              hi += neg ? -wim[q] : wim[q];
+            }
+            // (P psi)_x = h(x ^ f) psi_{x ^ f}
+            const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
+            L[i].x += vr;
+            L[i].y += vi;
+            eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
           }
-        }
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          const V pp = sm0[swz<V>((m.t | offt(m, i)) ^ fl.f_tile)];
-          T hr = 0, hi = 0;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const bool neg = (pat[q] >> i) & 1u;
-            hr += neg ? -wre[q] : wre[q];
-            hi += neg ? -wim[q] : wim[q];
-          }
-          // (P psi)_x = h(x ^ f) psi_{x ^ f}
-          const T vr = hr * pp.x - hi * pp.y, vi = hr * pp.y + hi * pp.x;
-          L[i].x += vr;
-          L[i].y += vi;
-          eacc = fma(A[i].x, vr, fma(A[i].y, vi, eacc));
         }
       }
+      if ((sp.flags & PF_LAM_STORE) && lam && a.store_lambda && nch == 1) store_regs<RB>(L, lam, m);
+      const double ws = warp_sum(eacc);
+      if (lane == 0) red[side * nwarps + warp] = ws;
     }
-    if ((sp.flags & PF_LAM_STORE) && lam && a.store_lambda && nch == 1) store_regs<RB>(L, lam, m);
-    const double ws = warp_sum(eacc);
-    if (lane == 0) red[warp] = ws;
     __syncthreads();
-    if (tid == 0) {
+    if (tid < nsides) {
       double s = 0;
-      for (int w = 0; w < nwarps; ++w) s += red[w];
-      a.epart[(((size_t)row * a.n_hpasses + sp.epart_index) * nch + ch) * (1u << sp.nfix) + tile] = s;
+      for (int w = 0; w < nwarps; ++w) s += red[tid * nwarps + w];
+      const uint32_t t = tid ? (tile ^ sp.pair_fout_idx) : tile;
+      a.epart[(((size_t)row * a.n_hpasses + sp.epart_index) * nch + ch) * (1u << sp.nfix) + t] = s;
     }
     return;
   }
@@ -1504,8 +1569,8 @@ size_t pass_smem_bytes(int mode, bool dbl, const DevPass& p) {
   b += (size_t)((p.n_dent + 1) & ~1) * sizeof(DevDiagEnt);
   if (mode == KM_BWD) b += (size_t)p.n_gslots * nwarps * 8;
   if (mode == KM_HAM)
-    b += (size_t)nwarps * 8 + (size_t)p.n_hdiag * sizeof(DevHDiag) + (size_t)p.n_hflip * sizeof(DevHFlip) +
-         (size_t)p.n_hterm * sizeof(DevHTerm);
+    b += (p.pair_fout ? tsize * v : 0) + (size_t)nwarps * 16 + (size_t)p.n_hdiag * sizeof(DevHDiag) +
+         (size_t)p.n_hflip * sizeof(DevHFlip) + (size_t)p.n_hterm * sizeof(DevHTerm);
   return b + 16;
 }
 
@@ -1529,7 +1594,8 @@ static cudaError_t launch_tf(const KArgs& a, const PassArgs& pa, int rows, cudaS
   if (hp.rb != RB) return cudaErrorInvalidValue;
   const unsigned threads = 1u << (hp.k - RB);
   if (threads < 32 || threads > 256) return cudaErrorInvalidConfiguration;
-  const size_t blocks = (size_t)rows << hp.nfix;
+  // a paired Pauli-sum pass runs one CTA per pair of tiles
+  const size_t blocks = (size_t)rows << (hp.nfix - ((MODE == KM_HAM && hp.pair_fout) ? 1 : 0));
   if (blocks == 0) return cudaSuccess;
   if (blocks > 0x7fffffffull) return cudaErrorInvalidConfiguration;
   const unsigned chunks = (MODE == KM_HAM && a.hchunks > 1) ? (unsigned)a.hchunks : 1u;

@@ -83,6 +83,10 @@ cudaError_t launch_pad_states(bool dbl, const void* src, void* dst, int n_user, 
 cudaError_t launch_plain_term(bool dbl, const void* psi, int N, int rows, uint32_t f, uint32_t sm, int ny,
                               double w, double* e_acc, cudaStream_t s);
 
+// Partial squared norms of `rows` states of 2^n_qubits amplitudes (user
+// layout): part[row][0..nblk) in FP64; the finalize reduction sums them.
+cudaError_t launch_norm2(bool dbl, const void* psi, int n_qubits, int rows, int nblk, double* part, cudaStream_t s);
+
 // Mean and standard error of n doubles into out[0], out[1].
 cudaError_t launch_mean_stderr(const double* x, int n, double* out, cudaStream_t s);
 

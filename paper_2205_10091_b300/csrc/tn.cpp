@@ -668,6 +668,9 @@ struct tc_tn : TnPlan {};
 namespace {
 void tn_release(tc_tn* t) {
   if (t->graph) cudaGraphExecDestroy(t->graph);
+  if (t->err_ev) cudaEventDestroy(t->err_ev);
+  if (t->h_err) cudaFreeHost(t->h_err);
+  if (t->d_err) cudaFree(t->d_err);
   if (t->d_tables) cudaFree(t->d_tables);
   if (t->d_inputs) cudaFree(t->d_inputs);
   if (t->d_gate_q) cudaFree(t->d_gate_q);
@@ -721,6 +724,20 @@ tc_status tc_tn_info(const tc_tn* t, tc_path_info* o) {
   o->smem_bytes = (int32_t)std::min<int64_t>(t->smem_entries * 8, INT32_MAX);
   o->fused_groups = t->n_groups;
   o->n_inputs = (int32_t)t->inputs.size();
+  for (const auto& st : t->steps)
+    if (tn_step_tc_eligible(st, t->tc_min_cmacs)) {
+      o->tc_steps++;
+      o->tc_cmacs += (double)st.M * st.N * st.K;
+    }
+  return TC_OK;
+}
+
+tc_status tc_tn_set_tc_threshold(tc_tn* t, double min_cmacs) {
+  if (!t) return fail(TC_E_INVALID, "NULL plan");
+  if (!(min_cmacs >= 0.0)) return fail(TC_E_INVALID, "min_cmacs must be >= 0");
+  t->tc_min_cmacs = min_cmacs;
+  if (t->graph) cudaGraphExecDestroy(t->graph);  // the next call re-captures with the new split
+  t->graph = nullptr;
   return TC_OK;
 }
 
@@ -728,13 +745,28 @@ tc_status tc_tn_info(const tc_tn* t, tc_path_info* o) {
 
 namespace {
 // Uploads the plan once.  A plan whose live tensors fit in shared memory runs
-// as one fused launch; otherwise the arena is sized for B instances and the
-// whole contraction (assembly, every path step, result) replays as one CUDA
-// graph, captured once per (B, source buffer, output buffer).
-tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, void* stream) {
+// as one fused launch (in the split-precision modes only when no step reaches
+// the tensor-core threshold); otherwise the arena is sized for B instances
+// and the whole contraction (assembly, every path step, result) replays as
+// one CUDA graph, captured once per (B, source buffer, output buffer,
+// precision).
+tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, int prec, void* stream) {
   if (B > 65535) return fail(TC_E_UNSUPPORTED, "at most 65535 instances per call");
+  if (prec != TN_FP32 && prec != TN_TF32X3 && prec != TN_BF16X6) return fail(TC_E_INVALID, "unknown precision");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
+  // an earlier call's tensor-core step reported a timed-out wait
+  if (t->err_pending && cudaEventQuery(t->err_ev) == cudaSuccess) {
+    t->err_pending = false;
+    if (*t->h_err) {
+      *t->h_err = 0;
+      if ((e = cudaMemsetAsync(t->d_err, 0, sizeof(int), s)) != cudaSuccess) return cuda_fail(e, "tn status reset");
+      return fail(TC_E_TIMEOUT, "an earlier contraction on this plan: a tensor-core step's wait timed out");
+    }
+  }
+  bool use_tc = false;
+  if (prec != TN_FP32)
+    for (const auto& st : t->steps) use_tc = use_tc || tn_step_tc_eligible(st, t->tc_min_cmacs);
   if (!t->uploaded) {
     if ((e = cudaGetDevice(&t->device)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (!t->tables.empty()) {
@@ -772,7 +804,15 @@ tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, void* strea
     }
     t->uploaded = true;
   }
-  if (tn_fused_ok(*t)) {
+  if (use_tc && !t->d_err) {
+    if ((e = cudaMalloc(&t->d_err, sizeof(int))) != cudaSuccess) return cuda_fail(e, "tn status");
+    if ((e = cudaMemset(t->d_err, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "tn status");
+    if ((e = cudaMallocHost(&t->h_err, sizeof(int))) != cudaSuccess) return cuda_fail(e, "tn status");
+    *t->h_err = 0;
+    if ((e = cudaEventCreateWithFlags(&t->err_ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "tn status event");
+  }
+  if (tn_fused_ok(*t) && !use_tc) {
     const int grid = tn_fused_grid(*t, B);
     if (grid < 1) return fail(TC_E_CUDA, "tn fused launch: no valid grid");
     if ((e = tn_launch_fused(*t, B, d_src, d_out, grid, s)) != cudaSuccess) return cuda_fail(e, "tn fused launch");
@@ -789,7 +829,7 @@ tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, void* strea
     t->graph = nullptr;
   }
   float2* arena = (float2*)t->d_arena;
-  if (!t->graph || t->graph_B != B || t->graph_gates != d_src || t->graph_out != d_out) {
+  if (!t->graph || t->graph_B != B || t->graph_gates != d_src || t->graph_out != d_out || t->graph_prec != prec) {
     if (t->graph) cudaGraphExecDestroy(t->graph);
     t->graph = nullptr;
     cudaStream_t cap;
@@ -797,7 +837,13 @@ tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, void* strea
     cudaGraph_t g;
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = tn_launch_assemble(*t, B, d_src, arena, cap);
-    for (size_t i = 0; e == cudaSuccess && i < t->steps.size(); ++i) e = tn_launch_step(*t, t->steps[i], B, arena, cap);
+    for (size_t i = 0; e == cudaSuccess && i < t->steps.size(); ++i) {
+      const TnStep& st = t->steps[i];
+      if (prec != TN_FP32 && tn_step_tc_eligible(st, t->tc_min_cmacs))
+        e = tn_launch_step_tc(*t, st, B, arena, prec, t->d_err, cap);
+      else
+        e = tn_launch_step(*t, st, B, arena, cap);
+    }
     if (e == cudaSuccess) e = tn_launch_result(*t, B, arena, d_out, cap);
     cudaError_t e2 = cudaStreamEndCapture(cap, &g);
     if (e == cudaSuccess) e = e2;
@@ -813,19 +859,28 @@ tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, void* strea
     t->graph_B = B;
     t->graph_gates = d_src;
     t->graph_out = d_out;
+    t->graph_prec = prec;
   }
   if ((e = cudaGraphLaunch(t->graph, s)) != cudaSuccess) return cuda_fail(e, "tn graph launch");
+  if (use_tc) {
+    // the error word comes back with the call's results; the next call reads it
+    if ((e = cudaMemcpyAsync(t->h_err, t->d_err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaEventRecord(t->err_ev, s)) != cudaSuccess)
+      return cuda_fail(e, "tn status copy");
+    t->err_pending = true;
+  }
   return TC_OK;
 }
 }  // namespace
 
 extern "C" {
 
-tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, double* d_out, void* stream) {
+tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, tc_tn_precision precision, double* d_out,
+                           void* stream) {
   if (!t || !d_gates || !d_out) return fail(TC_E_INVALID, "NULL argument");
   if (t->circuit) return fail(TC_E_INVALID, "plan was built from a circuit: use tc_tn_circuit_expect");
   if (B <= 0) return B == 0 ? TC_OK : fail(TC_E_INVALID, "B < 0");
-  return tn_run(t, B, d_gates, d_out, stream);
+  return tn_run(t, B, d_gates, d_out, (int)precision, stream);
 }
 
 tc_status tc_tn_circuit_create(int n_qubits, tc_init init, const tc_op* ops, int n_ops, int n_params,
@@ -853,12 +908,13 @@ tc_status tc_tn_circuit_create(int n_qubits, tc_init init, const tc_op* ops, int
   return TC_OK;
 }
 
-tc_status tc_tn_circuit_expect(tc_tn* t, int B, const float* d_params, double* d_out, void* stream) {
+tc_status tc_tn_circuit_expect(tc_tn* t, int B, const float* d_params, tc_tn_precision precision, double* d_out,
+                               void* stream) {
   if (!t || !d_out) return fail(TC_E_INVALID, "NULL argument");
   if (!t->circuit) return fail(TC_E_INVALID, "plan is a light-cone gate network: use tc_contract_path");
   if (t->n_params > 0 && !d_params) return fail(TC_E_INVALID, "d_params is NULL");
   if (B <= 0) return B == 0 ? TC_OK : fail(TC_E_INVALID, "B < 0");
-  return tn_run(t, B, d_params, d_out, stream);
+  return tn_run(t, B, d_params, d_out, (int)precision, stream);
 }
 
 void tc_tn_destroy(tc_tn* t) {

@@ -78,6 +78,13 @@ constexpr int kTnBlobMax = 3072;
 constexpr int kTnFusedSmemMax = 200 * 1024;
 
 
+// Precision of the dense path steps (tc_tn_precision): FP32 on CUDA cores, or
+// tensor cores with split operands (tn_tc.cu).
+enum : int { TN_FP32 = TC_TN_FP32, TN_TF32X3 = TC_TN_TF32X3, TN_BF16X6 = TC_TN_BF16X6 };
+// Steps of at least this many complex multiply-adds per instance go to the
+// tensor cores in the split-precision modes (tc_tn_set_tc_threshold).
+constexpr double kTnTcMinCmacs = 32768.0;
+
 struct TnPlan {
   int n_qubits = 0;
   int n_gates = 0;
@@ -120,6 +127,15 @@ struct TnPlan {
   int arena_B = 0;
   cudaGraphExec_t graph = nullptr;
   int graph_B = -1;
+  int graph_prec = -1;
+  // split-precision tensor-core steps: eligibility threshold and the
+  // device error word of their bounded waits, read back after each call
+  // (pinned h_err, event err_ev) and reported by the next call
+  double tc_min_cmacs = kTnTcMinCmacs;
+  int* d_err = nullptr;
+  int* h_err = nullptr;
+  cudaEvent_t err_ev = nullptr;
+  bool err_pending = false;
   const void* graph_gates = nullptr;
   void* graph_out = nullptr;
 };
@@ -142,5 +158,10 @@ bool tn_fused_ok(const TnPlan& P);
 int tn_fused_grid(const TnPlan& P, int B);
 cudaError_t tn_launch_fused(const TnPlan& P, int B, const float* d_src, double* d_out, int grid, cudaStream_t s);
 cudaError_t tn_launch_result(const TnPlan& P, int B, const float2* arena, double* d_out, cudaStream_t s);
+// Tensor-core step (tn_tc.cu): TF32X3 or BF16X6; the larger free side on the
+// MMA's 128 rows.  Eligible: K >= 2 and M N K >= min_cmacs.
+bool tn_step_tc_eligible(const TnStep& st, double min_cmacs);
+cudaError_t tn_launch_step_tc(const TnPlan& P, const TnStep& st, int B, float2* arena, int prec, int* d_err,
+                              cudaStream_t s);
 
 }  // namespace tcb

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libtc_b300.so")
 
 TC_OK, TC_E_INVALID, TC_E_NOMEM, TC_E_CUDA, TC_E_TIMEOUT, TC_E_UNSUPPORTED, TC_E_BUSY, TC_E_CANCELLED = range(8)
 TC_C64, TC_C128 = 0, 1
+TC_TN_FP32, TC_TN_TF32X3, TC_TN_BF16X6 = 0, 1, 2  # tc_tn_precision
 
 
 class TcError(RuntimeError):
@@ -71,6 +72,11 @@ class tc_plan_info(C.Structure):
     ]
 
 
+class tc_pauli_sum_plan_info(C.Structure):
+    _fields_ = [("passes", C.c_int32), ("paired_passes", C.c_int32), ("flip_groups", C.c_int32),
+                ("diag_entries", C.c_int32), ("tile_qubits", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
 class tc_grad_options(C.Structure):
     _fields_ = [("mode", C.c_int32), ("max_rows", C.c_int32), ("reserved", C.c_int32 * 6)]
 
@@ -79,7 +85,8 @@ class tc_path_info(C.Structure):
     _fields_ = [("flops", C.c_double), ("cmacs", C.c_double), ("write", C.c_double), ("size", C.c_double),
                 ("n_steps", C.c_int32), ("max_rank", C.c_int32), ("n_cone_gates", C.c_int32), ("cone_lo", C.c_int32),
                 ("cone_hi", C.c_int32), ("n_inputs", C.c_int32), ("n_active", C.c_int32), ("fused", C.c_int32),
-                ("smem_bytes", C.c_int32), ("fused_groups", C.c_int32)]
+                ("smem_bytes", C.c_int32), ("fused_groups", C.c_int32), ("tc_steps", C.c_int32),
+                ("tc_cmacs", C.c_double)]
 
 
 class tc_server_options(C.Structure):
@@ -126,6 +133,8 @@ SIGNATURES = {
     "tc_dm_expect_pauli_sum": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                          C.c_void_p]),
     "tc_circuit_info": (C.c_int, [C.c_void_p, C.POINTER(tc_plan_info)]),
+    "tc_pauli_sum_info": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                    C.POINTER(tc_pauli_sum_plan_info)]),
     "tc_apply_layers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64,
                                   C.c_void_p, C.c_void_p]),
     "tc_expect_pauli_sum": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
@@ -139,7 +148,8 @@ SIGNATURES = {
     "tc_tn_lightcone_create": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                          C.c_int, C.POINTER(C.c_void_p)]),
     "tc_tn_info": (C.c_int, [C.c_void_p, C.POINTER(tc_path_info)]),
-    "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "tc_tn_set_tc_threshold": (C.c_int, [C.c_void_p, C.c_double]),
     "tc_tn_destroy": (None, [C.c_void_p]),
     "tc_qgt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tc_natural_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p,
@@ -147,8 +157,9 @@ SIGNATURES = {
     "tc_tn_circuit_create": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                        C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                        C.POINTER(C.c_void_p)]),
-    "tc_tn_circuit_expect": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tc_tn_circuit_expect": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tc_mean_stderr": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "tc_state_norms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tc_server_create": (C.c_int, [C.POINTER(tc_server_options), C.POINTER(C.c_void_p)]),
     "tc_submit": (C.c_int, [C.c_void_p, C.POINTER(tc_request), C.POINTER(C.c_uint64)]),
     "tc_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(tc_result), C.c_void_p, C.c_int]),
@@ -271,6 +282,13 @@ class Circuit:
         _check(lib().tc_circuit_info(self.h, C.byref(o)))
         return {f: getattr(o, f) for f, _ in tc_plan_info._fields_ if f != "reserved"}
 
+    def pauli_sum_info(self, ham: Hamiltonian) -> dict:
+        """Host-only plan of a Pauli sum: passes, paired passes, flip groups."""
+        o = tc_pauli_sum_plan_info()
+        s, w, T = ham.args()
+        _check(lib().tc_pauli_sum_info(self.h, s, w, T, C.byref(o)))
+        return {f: getattr(o, f) for f, _ in tc_pauli_sum_plan_info._fields_ if f != "reserved"}
+
     @property
     def state_dtype(self):
         import torch
@@ -297,9 +315,20 @@ class Circuit:
         _check(lib().tc_expect_pauli_sum(self.h, _ptr(states), B, s, w, T, _ptr(out), _stream(stream)))
         return out
 
-    def expect_noalloc(self, states, ham: Hamiltonian, out, stream=None):
-        """Energies through the allocation-free entry point (`out` is caller-owned)."""
+    def norms(self, states, out=None, stream=None):
+        """||psi_b||^2 of each row (FP64 sums on the device): CUDA float64 [B]."""
+        import torch
+
         B = states.shape[0]
+        if out is None:
+            out = torch.empty(B, dtype=torch.float64, device="cuda")
+        _check(lib().tc_state_norms(self.h, _ptr(states), B, _ptr(out), _stream(stream)))
+        return out
+
+    def expect_noalloc(self, states, ham: Hamiltonian, out, stream=None, rows=None):
+        """Energies through the allocation-free entry point (`out` is caller-owned;
+        ``rows`` defaults to states.shape[0], 0 makes the per-device warm-up call)."""
+        B = states.shape[0] if rows is None else rows
         s, w, T = ham.args()
         _check(lib().tc_expect_pauli_sum_noalloc(self.h, _ptr(states), B, s, w, T, _ptr(out), _stream(stream)))
         return out
@@ -339,6 +368,46 @@ class Circuit:
         s, w, T = ham.args()
         _check(lib().tc_expect_plain(self.h, _ptr(params), B, s, w, T, _ptr(work), _ptr(energy), _stream(stream)))
         return energy
+
+
+_EXPECT_FN = None
+
+
+def _expect_fn():
+    """torch.autograd.Function over tc_expect_grad (built on first use, so
+    that importing this module does not import torch)."""
+    global _EXPECT_FN
+    if _EXPECT_FN is None:
+        import torch
+
+        class ExpectGrad(torch.autograd.Function):
+            # forward: one tc_expect_grad call (energies and per-row
+            # gradients from the adjoint sweep); backward: the cached gradient
+            # rows scaled by the incoming gradient of each energy
+            @staticmethod
+            def forward(ctx, params, circuit, ham, seed):
+                e, g = circuit.expect_grad(params.detach().to(torch.float64).contiguous(), ham, seed=seed)
+                ctx.save_for_backward(g)
+                return e
+
+            @staticmethod
+            def backward(ctx, grad_e):
+                (g,) = ctx.saved_tensors
+                return grad_e[:, None] * g, None, None, None
+
+        _EXPECT_FN = ExpectGrad
+    return _EXPECT_FN
+
+
+def expectation(circuit: "Circuit", params, ham: Hamiltonian, seed: int = 0):
+    """E_b = <psi(theta_b)|H|psi(theta_b)> for every row of ``params`` (CUDA
+    float64 [B][P]) as a differentiable torch function: the paper's
+    value_and_grad (Section "Gradients, optimization and variational
+    algorithms") with the gradient from the library's adjoint sweep.  Rows
+    are independent (vectorized_value_and_grad with argnums equal to
+    vectorized_argnums); a parameter vector shared by all rows, expanded to
+    [B][P], gets the row sum (the summed form)."""
+    return _expect_fn().apply(params, circuit, ham, seed)
 
 
 class DensityMatrixCircuit(Circuit):
@@ -397,14 +466,19 @@ class LightCone:
         _check(lib().tc_tn_info(self.h, C.byref(o)))
         return {f: getattr(o, f) for f, _ in tc_path_info._fields_ if f != "reserved"}
 
-    def contract(self, d_gates, out=None, stream=None):
+    def set_tc_threshold(self, min_cmacs: float):
+        """Steps of at least min_cmacs complex multiply-adds run on tensor cores
+        in the split-precision modes."""
+        _check(lib().tc_tn_set_tc_threshold(self.h, C.c_double(min_cmacs)))
+
+    def contract(self, d_gates, out=None, stream=None, precision: int = TC_TN_FP32):
         """d_gates: CUDA complex64 tensor [B][n_gates][4][4]; returns CUDA float64 [B][2]."""
         import torch
 
         B = d_gates.shape[0]
         if out is None:
             out = torch.empty((B, 2), dtype=torch.float64, device="cuda")
-        _check(lib().tc_contract_path(self.h, B, _ptr(d_gates), _ptr(out), _stream(stream)))
+        _check(lib().tc_contract_path(self.h, B, _ptr(d_gates), precision, _ptr(out), _stream(stream)))
         return out
 
 
@@ -445,7 +519,12 @@ class CircuitNetwork:
         _check(lib().tc_tn_info(self.h, C.byref(o)))
         return {f: getattr(o, f) for f, _ in tc_path_info._fields_ if f != "reserved"}
 
-    def expect(self, d_params, B: int | None = None, out=None, stream=None):
+    def set_tc_threshold(self, min_cmacs: float):
+        """Steps of at least min_cmacs complex multiply-adds run on tensor cores
+        in the split-precision modes."""
+        _check(lib().tc_tn_set_tc_threshold(self.h, C.c_double(min_cmacs)))
+
+    def expect(self, d_params, B: int | None = None, out=None, stream=None, precision: int = TC_TN_FP32):
         """d_params: CUDA float32 [B][n_params]; returns CUDA float64 [B][2] (Re, Im)."""
         import torch
 
@@ -453,7 +532,7 @@ class CircuitNetwork:
             B = d_params.shape[0]
         if out is None:
             out = torch.empty((B, 2), dtype=torch.float64, device="cuda")
-        _check(lib().tc_tn_circuit_expect(self.h, B, _ptr(d_params), _ptr(out), _stream(stream)))
+        _check(lib().tc_tn_circuit_expect(self.h, B, _ptr(d_params), precision, _ptr(out), _stream(stream)))
         return out
 
 

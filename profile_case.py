@@ -1,25 +1,29 @@
-"""Small, self-contained cases for ncu captures.
+"""Small, self-contained cases for ncu captures (a harness beside bench.py).
 
-    python -m paper_2205_10091_b300.profile_case --rows 32            # TFIM-20 x10 energy+gradient
-    python -m paper_2205_10091_b300.profile_case --workload noisy16   # 16-qubit noisy trajectories
-    python -m paper_2205_10091_b300.profile_case --workload hea10     # 10-qubit complex128 ansatz
-    python -m paper_2205_10091_b300.profile_case --workload qgt --qubits 16 --rows 1
+    python profile_case.py --rows 32            # TFIM-20 x10 energy+gradient
+    python profile_case.py --workload noisy16   # 16-qubit noisy trajectories
+    python profile_case.py --workload hea10     # 10-qubit complex128 ansatz
+    python profile_case.py --workload qgt --qubits 16 --rows 1
                                                           # geometric tensor of the TFIM ansatz (10 layers)
+    python profile_case.py --workload tn40 --rows 64 --precision 1
+                                                          # whole 40-qubit testbed network, tensor-core steps
 """
+import numpy as np
 import argparse
 
 import torch
 
-from . import native as nt
-from . import workloads as W
+from paper_2205_10091_b300 import native as nt
+from paper_2205_10091_b300 import workloads as W
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="tfim20", choices=["tfim20", "noisy16", "hea10", "qgt"])
+    ap.add_argument("--workload", default="tfim20", choices=["tfim20", "noisy16", "hea10", "qgt", "tn40"])
     ap.add_argument("--rows", type=int, default=32)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--qubits", type=int, default=16)
+    ap.add_argument("--precision", type=int, default=1, help="tn40: 0 FP32, 1 TF32X3, 2 BF16X6")
     args = ap.parse_args()
     if args.workload == "tfim20":
         circ, theta, ham = W.tfim_workload(20, 10, args.rows)
@@ -38,6 +42,15 @@ def main():
             vals = [c.expect(st, nt.Hamiltonian(o)) for o in obs]
         torch.cuda.synchronize()
         print("trajectories", n_traj, "plan", c.info(), "<Z0>", float(vals[0].mean()))
+    elif args.workload == "tn40":
+        circ = W.example_block_circuit(40, 6)
+        net = nt.CircuitNetwork(circ, {20: 3}, prune=0, split=True, rank_cap=26, greedy_trials=16)
+        th = torch.as_tensor(np.random.default_rng(1009).uniform(-1.5, 1.5, (args.rows, circ.n_params))
+                             .astype(np.float32), device="cuda")
+        for _ in range(args.steps):
+            out = net.expect(th, precision=args.precision)
+        torch.cuda.synchronize()
+        print("rows", args.rows, "info", net.info(), "<Z20>[0]", float(out[0, 0]))
     elif args.workload == "qgt":
         circ, theta, _ = W.tfim_workload(args.qubits, 10, args.rows)
         c = nt.Circuit(circ)

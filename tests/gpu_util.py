@@ -3,7 +3,8 @@ import numpy as np
 
 from paper_2205_10091_b300 import native as nt
 
-# tolerances (stated in the design doc): c128 amplitudes, c64 amplitudes, energies, gradients
+# tolerances: c128 amplitudes, c64 amplitudes, energies |dE| <= 1e-5 max(|E|, 1),
+# gradients max |dg| <= 1e-4 max(max |g|, 1)
 TOL_AMP_C128 = 1e-12
 TOL_AMP_C64 = 2e-6
 TOL_E_REL = 1e-5

@@ -111,3 +111,37 @@ def test_noise_events_next_to_u1_fold_into_its_matrix():
     assert noisy["n_noise"] == 3
     assert noisy["fwd_instrs"] == plain["fwd_instrs"] + 1
     assert noisy["bwd_instrs"] == plain["bwd_instrs"] + 1
+
+
+def test_pauli_sum_plan_pairs_wide_flip_masks():
+    """Flip masks wider than a tile go to paired passes; masks with the same
+    bits outside the tile share one; tile-sized masks stay in ordinary passes."""
+    n = 20
+    c = nt.Circuit(W.OpBuilder(n).build())
+    tfim = c.pauli_sum_info(nt.Hamiltonian(W.tfim_zz_x(n)))
+    assert tfim["paired_passes"] == 0 and tfim["passes"] == 2 and tfim["flip_groups"] == 20
+    xn = W.pauli_sum(n, [(1.0, {q: 1 for q in range(n)}), (0.5, {q: 2 for q in range(n)})])
+    i = c.pauli_sum_info(nt.Hamiltonian(xn))
+    # X^n and Y^n share one flip mask: one group, one paired pass (plus the first pass)
+    assert i["flip_groups"] == 1 and i["paired_passes"] == 1 and i["passes"] == 2
+    shared = W.pauli_sum(n, [(1.0, {**{q: 1 for q in range(12)}, n - 1: 2}),
+                             (1.0, {**{q: 1 for q in range(12)}, n - 2: 1}),
+                             (1.0, {**{q: 1 for q in range(12)}, n - 3: 1, n - 4: 2})])
+    i = c.pauli_sum_info(nt.Hamiltonian(shared))
+    assert i["flip_groups"] == 3 and i["paired_passes"] == 1
+    rng = np.random.default_rng(1)
+    codes = rng.choice([1, 2, 3], p=[0.4, 0.4, 0.2], size=(40, n)).astype(np.uint8)
+    i = c.pauli_sum_info(nt.Hamiltonian(W.PauliSum(codes, np.ones(40))))
+    # strings whose masks differ only in bits that fit the tile share a pass
+    assert 1 <= i["paired_passes"] <= 40 and i["passes"] == 1 + i["paired_passes"] and i["flip_groups"] == 40
+    # two wide masks (10 flipped qubits each, none among the 3 lowest index
+    # bits) that differ in 14 qubits: more than the 9 free tile bits
+    far = np.zeros((2, n), dtype=np.uint8)
+    far[0, 7:17] = 1
+    far[1, 0:10] = 1
+    i = c.pauli_sum_info(nt.Hamiltonian(W.PauliSum(far, np.ones(2))))
+    assert i["paired_passes"] == 2
+    # a whole-state tile never pairs
+    c12 = nt.Circuit(W.OpBuilder(12).build())
+    i = c12.pauli_sum_info(nt.Hamiltonian(W.pauli_sum(12, [(1.0, {q: 1 for q in range(12)})])))
+    assert i["paired_passes"] == 0

@@ -58,7 +58,31 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch, capsys):
 
     monkeypatch.setenv("RANK", "1")
     called = []
-    monkeypatch.setattr(bench, "oracle_step_seconds", lambda *a, **k: called.append(1) or (0.0, 0.0))
+    monkeypatch.setattr(bench, "oracle_pool", lambda *a, **k: called.append(1))
+    monkeypatch.setattr(bench, "oracle_rows_wall", lambda *a, **k: called.append(1) or 1.0)
     args = argparse.Namespace(gpus=2, steps=1, warmup=0)
     assert bench.run_reference(args) == 0
     assert not called and capsys.readouterr().out == ""
+
+
+def test_reference_arm_reports_measured_step_time(monkeypatch, capsys):
+    """ms_per_step is the wall time each step measured; value extrapolates the
+    gradient's cost (central differences: 2 P + 1 evaluations per row)."""
+    sys.path.insert(0, ROOT)
+    import argparse
+    import contextlib
+    import json
+
+    import bench
+
+    monkeypatch.setenv("RANK", "0")
+    walls = iter([9.0, 2.0, 4.0])  # one warm-up, two timed steps
+    monkeypatch.setattr(bench, "oracle_pool", lambda *a, **k: contextlib.nullcontext())
+    monkeypatch.setattr(bench, "oracle_rows_wall", lambda *a, **k: next(walls))
+    monkeypatch.setattr(bench.os, "cpu_count", lambda: 8)
+    assert bench.run_reference(argparse.Namespace(gpus=1, steps=2, warmup=1)) == 0
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and line["ms_per_step"] == 3000.0
+    rows = bench.REFERENCE_STEP_ROWS
+    assert np.isclose(line["value"], rows / (3.0 * (2 * 20 + 1)))
+    assert line["cpu_baseline"]["cores"] == rows and line["cpu_baseline"]["nproc"] == 8
