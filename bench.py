@@ -284,7 +284,11 @@ def run_gpu(args):
 
     # each rank owns an independent batch of parameter sets (weak scaling)
     circ, theta, ham = rank_workload(rank)
-    c = nt.Circuit(circ)
+    # the forward and adjoint passes compiled for this circuit at plan time
+    # (before any timing; the default plan-interpreting kernels with --no-specialize)
+    t_plan = time.perf_counter()
+    c = nt.Circuit(circ, specialize=not args.no_specialize)
+    t_plan = time.perf_counter() - t_plan
     H = nt.Hamiltonian(ham)
     B, P = theta.shape
     stream = torch.cuda.current_stream()
@@ -379,6 +383,8 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "c64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "layers": LAYERS, "batch_per_gpu": B,
                    "params_per_row": P, "hamiltonian_terms": int(H.T), "parallelism": f"dp{world}",
+                   "pass_kernels": "specialised at plan time" if not args.no_specialize else "plan-interpreting",
+                   "plan_seconds": t_plan,
                    "l2": "inputs larger than L2 (psi and lambda: 2 x 8 GiB per 1024 rows)"},
         "e2e": e2e,
         "gpu_launches": launches,
@@ -796,6 +802,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other hot-path workloads")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle checks and the CPU baseline")
+    ap.add_argument("--no-specialize", action="store_true",
+                    help="run the headline circuit on the plan-interpreting pass kernels")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

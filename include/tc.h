@@ -120,7 +120,11 @@ typedef struct {
   int32_t tile_qubits_bwd;  /* same for adjoint passes (0 = default) */
   int64_t mem_budget_bytes; /* scratch cap for tc_expect_grad (0 = 60% of free memory) */
   int32_t max_gates_per_pass; /* cap on non-diagonal gates fused into one pass (0 = default, <0 = none) */
-  int32_t reserved[7];
+  int32_t specialize;       /* 1 = compile the circuit's forward and adjoint passes into kernels of
+                               their own at tc_circuit_create (NVRTC, sm_103a; seconds per circuit):
+                               every plan constant is compiled in, the arithmetic is the same as the
+                               default plan-interpreting kernels; 0 = no */
+  int32_t reserved[6];
 } tc_options;
 
 /* Plan statistics, filled by tc_circuit_info. */
@@ -138,7 +142,8 @@ typedef struct {
   int32_t tile_qubits_bwd;
   int32_t fwd_instrs;  /* gate instructions over forward passes (diagonal groups count once) */
   int32_t bwd_instrs;
-  int32_t reserved[3];
+  int32_t specialized_passes; /* passes compiled into kernels of their own (tc_options.specialize) */
+  int32_t reserved[2];
 } tc_plan_info;
 
 typedef struct tc_circuit tc_circuit;

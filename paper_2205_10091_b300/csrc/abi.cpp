@@ -63,6 +63,8 @@ cudaError_t DevHam::upload(const HamPlan& H) {
 using namespace tcb;
 
 tc_circuit::~tc_circuit() {
+  for (auto l : jit_libs)
+    if (l) cudaLibraryUnload(l);
   if (uploaded && !external_dev) {
     dplan.release();
     dplain.release();
@@ -102,6 +104,19 @@ tc_status ensure_device(tc_circuit* c) {
   if ((e = dev_upload(c->pool, &c->d_pool)) != cudaSuccess) return cuda_fail(e, "pool upload");
   if ((e = dev_upload(c->csr_off, &c->d_csr_off)) != cudaSuccess) return cuda_fail(e, "csr upload");
   if ((e = dev_upload(c->csr_slots, &c->d_csr_slots)) != cudaSuccess) return cuda_fail(e, "csr upload");
+  if (!c->jit_cubins.empty()) {
+    // the specialised pass kernels of this circuit, on this device
+    c->jit_libs.assign(c->A.passes.size(), nullptr);
+    c->jit_kern.assign(c->A.passes.size(), nullptr);
+    for (const Schedule* sc : {&c->fwd, &c->bwd})
+      for (int p = sc->first_pass; p < sc->first_pass + sc->n_passes; ++p) {
+        if ((e = cudaLibraryLoadData(&c->jit_libs[p], c->jit_cubins[p].data(), nullptr, nullptr, 0, nullptr, nullptr,
+                                     0)) != cudaSuccess)
+          return cuda_fail(e, "loading a specialised pass kernel");
+        if ((e = cudaLibraryGetKernel(&c->jit_kern[p], c->jit_libs[p], jit_kernel_name(p).c_str())) != cudaSuccess)
+          return cuda_fail(e, "specialised pass kernel lookup");
+      }
+  }
   c->uploaded = true;
   return TC_OK;
 }
@@ -201,9 +216,16 @@ tc_status run_schedule(tc_circuit* c, int mode, const Schedule& sc, const PlanAr
   a.tables = tables;
   a.table_stride = sc.table_total;
   TC_CHECK_CUDA(launch_tables(is_dbl(c), a, sc.first_mat, sc.n_mats, rows, s), "gate tables");
+  // the circuit's specialised kernels run its own schedules (not the unfused baseline's)
+  const bool spec = &A == &c->A && !c->jit_kern.empty();
   for (int p = 0; p < sc.n_passes; ++p) {
     a.pass = sc.first_pass + p;
-    TC_CHECK_CUDA(launch_pass(mode, is_dbl(c), a, A.passes[a.pass], &A.stages[A.passes[a.pass].stage_off], rows, s), mode == KM_FWD ? "forward pass" : "adjoint pass");
+    if (spec)
+      TC_CHECK_CUDA(launch_pass_specialised(c->jit_kern[a.pass], mode, is_dbl(c), a, A.passes[a.pass], rows, s),
+                    mode == KM_FWD ? "forward pass (specialised)" : "adjoint pass (specialised)");
+    else
+      TC_CHECK_CUDA(launch_pass(mode, is_dbl(c), a, A.passes[a.pass], &A.stages[A.passes[a.pass].stage_off], rows, s),
+                    mode == KM_FWD ? "forward pass" : "adjoint pass");
   }
   return TC_OK;
 }
@@ -414,6 +436,13 @@ tc_status tc_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const tc
     for (int s = 0; s < (int)c->bwd.slot_param.size(); ++s) c->csr_slots[fillp[c->bwd.slot_param[s]]++] = s;
   }
   if (c->csr_slots.empty()) c->csr_slots.push_back(0);
+  if (c->opt.specialize) {
+    std::string jerr;
+    if (!jit_compile(c, c->jit_cubins, jerr, &c->jit_compile_s)) {
+      delete c;
+      return fail(TC_E_CUDA, jerr);
+    }
+  }
   *out = c;
   return TC_OK;
 }
@@ -493,6 +522,7 @@ tc_status tc_circuit_info(const tc_circuit* c, tc_plan_info* o) {
   };
   o->fwd_instrs = instrs(c->fwd);
   o->bwd_instrs = instrs(c->bwd);
+  for (const auto& cb : c->jit_cubins) o->specialized_passes += cb.empty() ? 0 : 1;
   return TC_OK;
 }
 

@@ -60,6 +60,14 @@ tc_status expect_grad_run(tc_circuit* c, const double* d_params, int B, uint64_t
 size_t plan_dev_bytes(const tc_circuit* c);
 size_t ham_dev_bytes(const HamPlan& H);
 tc_status place_plan_and_ham(tc_circuit* c, const HamPlan& H, char* base, cudaStream_t s);
+// Specialised pass kernels (jit.cpp): CUDA source of the circuit's forward and
+// adjoint passes compiled with NVRTC; kernel pass i is jit_kernel_name(i).
+bool jit_compile(const tc_circuit* c, std::vector<std::vector<char>>& cubins, std::string& err, double* seconds,
+                 const std::vector<std::string>& extra_opts = {}, std::string* log_out = nullptr);
+std::string jit_kernel_name(int pass);
+std::string jit_pass_source(const PlanArrays& A, int pass, int mode, bool dbl, bool fence);
+bool jit_compile_source(const std::string& src, std::vector<char>& cubin, std::string& err,
+                        const std::vector<std::string>& extra_opts, std::string* log_out);
 }  // namespace tcb
 
 struct tc_circuit {
@@ -104,6 +112,13 @@ struct tc_circuit {
   uint64_t hclock = 0;
   tcb::HamPlan H;     // the selected entry's plan (host copy)
   tcb::DevHam dham;   // the selected entry's device arrays (owned by hcache)
+
+  // pass kernels specialised at plan time (tc_options.specialize): per pass
+  // index of A.passes its cubin (host), library and kernel (device)
+  std::vector<std::vector<char>> jit_cubins;
+  double jit_compile_s = 0;
+  std::vector<cudaLibrary_t> jit_libs;
+  std::vector<cudaKernel_t> jit_kern;
 
   // scratch workspace
   void* ws = nullptr;

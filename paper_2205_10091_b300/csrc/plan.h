@@ -11,7 +11,18 @@
 // thread holds 2^RB amplitudes in registers ("register bits" S[0..RB-1] are
 // tile bits); stages change S through a swizzled shared-memory transpose.
 #pragma once
+#ifdef __CUDACC_RTC__
+typedef signed char int8_t;
+typedef short int16_t;
+typedef int int32_t;
+typedef long long int64_t;
+typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
+typedef unsigned int uint32_t;
+typedef unsigned long long uint64_t;
+#else
 #include <stdint.h>
+#endif
 
 namespace tcb {
 
@@ -53,6 +64,8 @@ enum : int8_t {
   IK_RYM = 17,      // RY on the register bits of mask j0; bit r's kRYEntries entries at slot + kRYEntries * rank
   IK_RYM_ADJ = 18,  // adjoint of IK_RYM (gslot < 0: a fixed-angle rotation, uncompute only)
   IK_RSEL_ADJ = 19, // adjoint step of IK_RSEL: gslot += gscale * Im<lam|G|psi> for the row's axis G, then U^dagger
+  IK_SPHASE = 20,   // quarter phases on several qubits: each amplitude times i^(s c), s = gscale (+1 or -1),
+                    // c = its 1-bits among the register bits of mask j0 and the global positions of mask slot
 };
 
 constexpr int kLocalSlots = 32;  // gradient slots a pass accumulates per thread before one reduction

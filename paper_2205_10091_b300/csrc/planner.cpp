@@ -203,6 +203,7 @@ uint32_t gate_touch(const HGate& g) { return bit(g.p0) | bit(g.p1); }
 uint32_t item_need(const Item& it, const std::vector<HGate>& gates, const int* tb) {
   if (it.group) return 0;
   const HGate& g = gates[it.gate];
+  if (g.quarter) return 0;  // a phase: register bit or thread bit alike
   if (g.kind == TC_OP_CNOT) return 1u << tb[g.p1];
   if (g.kind == TC_OP_U2) return (1u << tb[g.p0]) | (1u << tb[g.p1]);
   return 1u << tb[g.p0];
@@ -344,7 +345,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
     for (int p = 0; p < 32; ++p) last_touch[p] = -1;
     for (int gi : taken) {
       const HGate& g = gates[gi];
-      if (g.diag) {
+      if (g.diag && !g.quarter) {
         const int mode = g.sign_mode ? 1 : (g.quarter ? 2 : 0);
         auto key = std::make_tuple(mode, mode == 0 ? g.param : -1, mode == 1 ? 0.0 : g.scale);
         auto itk = open.find(key);
@@ -506,8 +507,86 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
       }
       fill_stage_runs(P, rb, ds);
       ds.instr_off = (int)A.instrs.size() - P.instr_off;
-      for (int ii : st.second) {
+      // Quarter phases (S, S^dagger of RX frames) commute with every item of
+      // the stage except non-diagonal gates on their own qubit (and another
+      // phase there), so each may sit at any insertion point between those
+      // neighbours.  The fewest points that cover every phase's interval
+      // (greedy on the interval ends) each get one IK_SPHASE per sign.
+      const std::vector<int>& sitems = st.second;
+      const int ns = (int)sitems.size();
+      std::vector<int> q_at;  // stage positions of the quarter items
+      std::vector<int> point_of;
+      {
+        auto q_of = [&](int t) -> const HGate* {
+          const Item& it = items[sitems[t]];
+          return (!it.group && gates[it.gate].quarter) ? &gates[it.gate] : nullptr;
+        };
+        auto blocks = [&](int t, int p) {
+          const Item& it = items[sitems[t]];
+          if (it.group) return false;  // diagonal groups commute with the phases
+          const HGate& g = gates[it.gate];
+          return g.p0 == p || g.p1 == p;
+        };
+        std::vector<std::pair<int, int>> iv;  // (lo, hi) insertion points of each quarter
+        for (int t = 0; t < ns; ++t) {
+          const HGate* g = q_of(t);
+          if (!g) continue;
+          int lo = t, hi = t;
+          while (lo > 0 && !blocks(lo - 1, g->p0)) --lo;
+          while (hi < ns - 1 && !blocks(hi + 1, g->p0)) ++hi;
+          q_at.push_back(t);
+          iv.push_back({lo, hi + 1});  // point t' = before item t' (ns = after the last)
+        }
+        point_of.assign(q_at.size(), -1);
+        std::vector<int> order(q_at.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return iv[a].second < iv[b].second; });
+        for (int a : order) {
+          if (point_of[a] >= 0) continue;
+          const int pt = iv[a].second;
+          for (int b : order)
+            if (point_of[b] < 0 && iv[b].first <= pt && pt <= iv[b].second) point_of[b] = pt;
+        }
+      }
+      // the phases placed at point pt, one instruction per sign (a qubit
+      // already in an instruction's masks starts a new one)
+      auto emit_point = [&](int pt) {
+        for (double sg : {1.0, -1.0}) {
+          std::vector<const HGate*> mine;
+          for (size_t a = 0; a < q_at.size(); ++a) {
+            const HGate* g = &gates[items[sitems[q_at[a]]].gate];
+            if (point_of[a] == pt && (g->scale > 0 ? 1.0 : -1.0) * (adjoint ? -1.0 : 1.0) == sg) mine.push_back(g);
+          }
+          while (!mine.empty()) {
+            DevInstr q{};
+            q.kind = IK_SPHASE;
+            q.gslot = -1;
+            q.jc = -1;
+            q.gscale = (float)sg;
+            uint32_t rmask = 0, pmask = 0, seen = 0;
+            std::vector<const HGate*> rest;
+            for (const HGate* g : mine) {
+              if (seen & bit(g->p0)) {
+                rest.push_back(g);
+                continue;
+              }
+              seen |= bit(g->p0);
+              const int r = tb[g->p0] >= 0 ? jof[tb[g->p0]] : -1;
+              if (r >= 0) rmask |= 1u << r;
+              else pmask |= bit(g->p0);
+            }
+            q.j0 = (int8_t)rmask;
+            q.slot = (int32_t)pmask;
+            A.instrs.push_back(q);
+            mine = rest;
+          }
+        }
+      };
+      for (int t = 0; t < ns; ++t) {
+        const int ii = sitems[t];
+        emit_point(t);
         const Item& it = items[ii];
+        if (!it.group && gates[it.gate].quarter) continue;
         DevInstr in{};
         in.gslot = -1;
         in.jc = -1;
@@ -620,6 +699,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
         }
         A.instrs.push_back(in);
       }
+      emit_point(ns);
       merge_rx_runs(A, P.instr_off + ds.instr_off, rb, sc.table_total);
       ds.n_instr = (int)A.instrs.size() - P.instr_off - ds.instr_off;
       A.stages.push_back(ds);
@@ -629,7 +709,7 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
       const DevInstr& in = A.instrs[i];
       if (in.kind == IK_CNOT || in.kind == IK_MAT4) P.flags |= PF_FULL;
       if (in.kind != IK_RY && in.kind != IK_RYM && in.kind != IK_RY_ADJ && in.kind != IK_RYM_ADJ &&
-          in.kind != IK_DIAG && in.kind != IK_DIAG_ADJ)
+          in.kind != IK_DIAG && in.kind != IK_DIAG_ADJ && in.kind != IK_SPHASE)
         P.flags |= PF_LEAN;
       if (in.kind == IK_DIAG || in.kind == IK_GRADDIAG || in.kind == IK_DIAG_ADJ) {
         const DevDiag& dg = A.diags[P.diag_off + in.slot];

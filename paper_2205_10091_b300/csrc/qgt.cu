@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "engine.h"
@@ -199,9 +200,11 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
 }
 __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) { return mbar_wait(bar, parity, kTcSpin); }
 
+// skip_mma (tests only): issue no MMA and no commit, so the first completion
+// wait has nothing to wait for and runs out: the bounded-wait path end to end.
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restrict__ states, int S, int64_t L,
                                                            int64_t kstride, int ntile, double* __restrict__ M,
-                                                           int* __restrict__ err) {
+                                                           int* __restrict__ err, int skip_mma) {
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();  // tiles complete; the raw stage is free
     if (st + 1 < nst) prefetch(x0 + (int64_t)(st + 1) * kTcKA);
-    if (tid == 0) {
+    if (tid == 0 && !skip_mma) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t tb = sbase + (uint32_t)(set * kTcSetBytes);
       const uint32_t dre = tacc + (uint32_t)(set * 2 * kTcTile), dim = dre + kTcTile;
@@ -346,9 +349,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
     if (st > 0) ok = drain(set ^ 1);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();  // TMEM reads done before that accumulator is reused; next raw stage visible
+    // TMEM reads done before that accumulator is reused; next raw stage
+    // visible.  A timeout seen by any thread stops the whole CTA.
+    ok = __syncthreads_and(ok) != 0;
   }
   if (ok && issued > 0) ok = drain((issued - 1) & 1);
+  ok = __syncthreads_and(ok) != 0;
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (!ok) {
     if (tid == 0) atomicExch(err, 1);
@@ -673,6 +679,10 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
   int* d_err = (int*)(w + row_bytes * chunk);                  // in the workspace's slack
   // complex64: tensor-core Gram (128-row tiles); complex128: FP64 CUDA-core Gram
   const bool tc = !dbl;
+  // tests only: TC_TEST_GRAM_SKIP_MMA=1 makes the tensor-core Gram issue no MMA,
+  // so its bounded completion wait runs out and the call reports TC_E_TIMEOUT
+  const char* skip_env = getenv("TC_TEST_GRAM_SKIP_MMA");
+  const int skip_mma = (skip_env && skip_env[0] == '1') ? 1 : 0;
   const int tile = tc ? kTcTile : kGramTile;
   const int ntile = (S + tile - 1) / tile;
   const int64_t nchunk = (L + (tc ? kTcChunk : kGramChunk) - 1) / (tc ? kTcChunk : kGramChunk);
@@ -716,7 +726,8 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
     if ((e = cudaMemsetAsync(M, 0, (size_t)R * S * S * 16, s)) != cudaSuccess) return cuda_fail(e, "memset");
     dim3 grid((unsigned)(ntile * (ntile + 1) / 2), (unsigned)nchunk, (unsigned)R);
     if (tc)
-      k_gram_tc<<<grid, kTcThreads, kTcSmem, s>>>((const float2*)states, S, L, (int64_t)R * L, ntile, M, d_err);
+      k_gram_tc<<<grid, kTcThreads, kTcSmem, s>>>((const float2*)states, S, L, (int64_t)R * L, ntile, M, d_err,
+                                                  skip_mma);
     else
       k_gram<double><<<grid, 256, 0, s>>>((const double2*)states, S, L, (int64_t)R * L, ntile, M);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gram");

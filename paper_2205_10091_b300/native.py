@@ -49,7 +49,8 @@ class tc_options(C.Structure):
         ("tile_qubits_bwd", C.c_int32),
         ("mem_budget_bytes", C.c_int64),
         ("max_gates_per_pass", C.c_int32),
-        ("reserved", C.c_int32 * 7),
+        ("specialize", C.c_int32),
+        ("reserved", C.c_int32 * 6),
     ]
 
 
@@ -68,7 +69,8 @@ class tc_plan_info(C.Structure):
         ("tile_qubits_bwd", C.c_int32),
         ("fwd_instrs", C.c_int32),
         ("bwd_instrs", C.c_int32),
-        ("reserved", C.c_int32 * 3),
+        ("specialized_passes", C.c_int32),
+        ("reserved", C.c_int32 * 2),
     ]
 
 
@@ -257,14 +259,14 @@ class Circuit:
     """Owns a tc_circuit handle compiled from a workloads.Circuit."""
 
     def __init__(self, circ: W.Circuit, dtype: int = TC_C64, tile_fwd: int = 0, tile_bwd: int = 0,
-                 mem_budget_bytes: int = 0, max_gates_per_pass: int = 0):
+                 mem_budget_bytes: int = 0, max_gates_per_pass: int = 0, specialize: bool = False):
         self.circ = circ
         self.n = circ.n
         self.dtype = dtype
         self.n_params = circ.n_params
         ops = np.ascontiguousarray(circ.ops, dtype=W.OP_DTYPE)
         pool = np.ascontiguousarray(np.stack([circ.pool.real, circ.pool.imag], -1).ravel(), dtype=np.float64)
-        opt = tc_options(tile_fwd, tile_bwd, mem_budget_bytes, max_gates_per_pass)
+        opt = tc_options(tile_fwd, tile_bwd, mem_budget_bytes, max_gates_per_pass, int(specialize))
         h = C.c_void_p()
         _check(lib().tc_circuit_create(circ.n, dtype, circ.init, ops.ctypes.data_as(C.c_void_p), len(ops),
                                        circ.n_params, pool.ctypes.data_as(C.c_void_p) if len(circ.pool) else None,

@@ -145,3 +145,36 @@ def test_pauli_sum_plan_pairs_wide_flip_masks():
     c12 = nt.Circuit(W.OpBuilder(12).build())
     i = c12.pauli_sum_info(nt.Hamiltonian(W.pauli_sum(12, [(1.0, {q: 1 for q in range(12)})])))
     assert i["paired_passes"] == 0
+
+
+@pytest.mark.parametrize("dtype", [nt.TC_C64, nt.TC_C128])
+def test_specialised_passes_compile_for_every_instruction_kind(dtype):
+    """Plan-time specialisation (NVRTC, host only) compiles the forward and
+    adjoint passes of circuits with every gate kind: rotations, H, X, CNOT,
+    CZ, RZZ at several distances, 2x2 and 4x4 matrices, a channel-shaped 4x4,
+    noise events and random-axis rotations."""
+    rng = np.random.default_rng(12)
+    b = W.OpBuilder(12)
+    for q in range(12):
+        b.ry(q, q % 5)
+    for q in range(11):
+        b.rzz(q, (q + 3) % 12, 5)
+        b.cnot(q, q + 1)
+    b.cz(0, 7)
+    b.rx(3, 6)
+    b.rz(4, 7)
+    b.h(5)
+    b.x(6)
+    b.unitary1(2, W.haar_unitary(2, rng))
+    b.unitary2(8, 9, W.haar_unitary(4, rng))
+    chan = np.diag([0.9, 0.8, 0.8, 0.9]).astype(np.complex128)
+    chan[0, 3] = chan[3, 0] = 0.1
+    chan[1, 2] = chan[2, 1] = 0.05
+    b.unitary2(10, 11, chan)
+    b.depolarizing(1, 0.1, 0.05, 0.02)
+    b.rsel(2, 8)
+    circ = b.build(9)
+    c = nt.Circuit(circ, dtype=dtype, specialize=True)
+    info = c.info()
+    assert info["specialized_passes"] == info["fwd_passes"] + info["bwd_passes"] > 0
+    assert nt.Circuit(circ, dtype=dtype).info()["specialized_passes"] == 0

@@ -154,3 +154,42 @@ def test_qgt_full_size_tfim20_closed_form_at_zero_angles():
     tol = 4 * _tol(circ, nt.TC_C64)
     assert np.abs(qfi - ref).max() <= tol
     assert np.abs(g.imag).max() <= tol
+
+
+def test_natural_gradient_pipeline_complex128_tight():
+    """The QGT -> natural-gradient pipeline in complex128 against the oracle's
+    tensor and parameter-shift gradient: every stage in FP64, so the solve's
+    result agrees to 1e-8 relative (the solve amplifies the ~1e-13 input errors
+    by the condition number of 4 Re G + eps I, below 1e4 here)."""
+    circ, theta, ham = W.tfim_workload(10, 2, 3)
+    c = nt.Circuit(circ, dtype=nt.TC_C128)
+    d = cuda_params(theta)
+    q = c.qgt(d)
+    _, grad = c.expect_grad(d, nt.Hamiltonian(ham))
+    eps = 0.05
+    x = nt.natural_gradient(q, grad, eps).cpu().numpy()
+    for r in range(3):
+        qo = G.quantum_geometric_tensor(circ, theta[r])
+        ref = G.natural_gradient(qo, G.parameter_shift(circ, theta[r], ham), eps)
+        cond = np.linalg.cond(4.0 * qo.real + eps * np.eye(qo.shape[0]))
+        assert cond < 1e4
+        assert np.abs(x[r] - ref).max() <= 1e-8 * max(1.0, np.abs(ref).max())
+
+
+def test_gram_bounded_wait_reports_timeout_and_recovers(monkeypatch):
+    """Failure detection without a fault: with TC_TEST_GRAM_SKIP_MMA=1 the
+    tensor-core Gram issues no MMA, so its first completion wait (an mbarrier
+    nothing arrives at) runs out after its bounded number of polls; the kernel
+    sets its status word, frees its tensor memory and returns, and the call
+    reports TC_E_TIMEOUT.  The context stays usable: the next call, without
+    the variable, gives the oracle's tensor."""
+    circ, theta, _ = W.tfim_workload(12, 2, 1)
+    c = nt.Circuit(circ)
+    d = cuda_params(theta)
+    monkeypatch.setenv("TC_TEST_GRAM_SKIP_MMA", "1")
+    with pytest.raises(nt.TcError) as e:
+        c.qgt(d)
+    assert e.value.status == nt.TC_E_TIMEOUT
+    monkeypatch.delenv("TC_TEST_GRAM_SKIP_MMA")
+    g = c.qgt(d).cpu().numpy()[0]
+    assert np.abs(g - G.quantum_geometric_tensor(circ, theta[0])).max() <= _tol(circ, nt.TC_C64)

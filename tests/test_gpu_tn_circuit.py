@@ -12,10 +12,16 @@ from paper_2205_10091_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# FP32 tensors and FP32-accumulated GEMMs over a few hundred (small
-# networks) to ~1500 (whole 40-qubit network) steps of unit-norm factors
+# FP32 tensors and FP32-accumulated GEMMs: each step rounds its outputs to
+# ~2^-24 relative (K terms, round to nearest, errors of either sign), and the
+# contraction of unit-norm factors keeps intermediate entries O(1), so the
+# result's error grows like sqrt(steps) 2^-24 ~ 2e-6 for the ~1500 steps of
+# the whole 40-qubit network (measured 7.5e-7): the light-cone bound 1e-5
+# covers it with margin.  The small random networks also carry Haar U(1)/U(4)
+# matrices, which the device holds in FP32 while the oracle uses the FP64
+# values (an input difference of ~1e-7 per gate), and keep the looser 2e-5.
 TOL_SMALL = 2e-5
-TOL_WHOLE = 2e-4
+TOL_WHOLE = 1e-5
 
 
 def _random_circuit(n, n_ops, rng, init):
