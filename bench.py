@@ -779,7 +779,8 @@ def _traffic(kernel: str):
 
 
 # the sources that define the tile-pass kernels and the plans they run
-TILE_PASS_SOURCES = ("plan.h", "planner.cpp", "planner.h", "sv_kernels.cu", "sv_kernels.cuh")
+TILE_PASS_SOURCES = ("plan.h", "planner.cpp", "planner.h", "sv_args.h", "sv_core.cuh", "sv_kernels.cu",
+                     "sv_kernels.cuh", "jit.cpp")
 
 
 def _source_hash() -> str:

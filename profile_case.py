@@ -24,10 +24,11 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--qubits", type=int, default=16)
     ap.add_argument("--precision", type=int, default=1, help="tn40: 0 FP32, 1 TF32X3, 2 BF16X6")
+    ap.add_argument("--specialize", action="store_true", help="tfim20: pass kernels compiled for the circuit")
     args = ap.parse_args()
     if args.workload == "tfim20":
         circ, theta, ham = W.tfim_workload(20, 10, args.rows)
-        c = nt.Circuit(circ)
+        c = nt.Circuit(circ, specialize=args.specialize)
         H = nt.Hamiltonian(ham)
         d = torch.as_tensor(theta, device="cuda")
         for _ in range(args.steps):
