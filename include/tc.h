@@ -143,7 +143,9 @@ typedef struct {
   int32_t fwd_instrs;  /* gate instructions over forward passes (diagonal groups count once) */
   int32_t bwd_instrs;
   int32_t specialized_passes; /* passes compiled into kernels of their own (tc_options.specialize) */
-  int32_t reserved[2];
+  int32_t packed_diag_groups; /* phase groups of several ZZ distances evaluated as one 64-bit
+                                 linear map per amplitude (at most 64 terms a group), both plans */
+  int32_t reserved[1];
 } tc_plan_info;
 
 typedef struct tc_circuit tc_circuit;
@@ -180,9 +182,11 @@ typedef struct {
   int32_t passes;
   int32_t paired_passes;
   int32_t flip_groups;
-  int32_t diag_entries;
+  int32_t diag_entries;       /* diagonal records (a packed group counts 1 + n_qubits_internal) */
   int32_t tile_qubits;
-  int32_t reserved[3];
+  int32_t packed_diag_groups; /* ZZ terms of one weight at three or more distances, up to 64 a group,
+                                 evaluated as one 64-bit linear map and a popcount per amplitude */
+  int32_t reserved[2];
 } tc_pauli_sum_plan_info;
 TC_API tc_status tc_pauli_sum_info(const tc_circuit* c, const uint8_t* structures, const double* weights, int T,
                                    tc_pauli_sum_plan_info* out);

@@ -523,6 +523,11 @@ tc_status tc_circuit_info(const tc_circuit* c, tc_plan_info* o) {
   o->fwd_instrs = instrs(c->fwd);
   o->bwd_instrs = instrs(c->bwd);
   for (const auto& cb : c->jit_cubins) o->specialized_passes += cb.empty() ? 0 : 1;
+  for (const Schedule* sc : {&c->fwd, &c->bwd})
+    for (int p = sc->first_pass; p < sc->first_pass + sc->n_passes; ++p) {
+      const DevPass& P = c->A.passes[p];
+      for (int d = 0; d < P.n_diag; ++d) o->packed_diag_groups += c->A.diags[P.diag_off + d].packed;
+    }
   return TC_OK;
 }
 
@@ -539,6 +544,7 @@ tc_status tc_pauli_sum_info(const tc_circuit* c, const uint8_t* structures, cons
   o->flip_groups = (int)H.hflips.size();
   o->diag_entries = (int)H.hdiag.size();
   o->tile_qubits = c->k_ham;
+  o->packed_diag_groups = H.packed_groups;
   return TC_OK;
 }
 

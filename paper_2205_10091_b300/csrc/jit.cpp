@@ -87,7 +87,7 @@ void emit_diags(std::ostringstream& o, const PlanArrays& A, const DevPass& P) {
   for (int di = 0; di < P.n_diag; ++di) {
     const DevDiag& d = A.diags[P.diag_off + di];
     o << "      case " << di << ": d.sign_mode = " << d.sign_mode << "; d.n_ent = " << d.n_ent << "; d.ent_off = "
-      << d.ent_off << "; d.T = " << d.T << "; d.tab = " << d.tab << "; break;\n";
+      << d.ent_off << "; d.T = " << d.T << "; d.tab = " << d.tab << "; d.packed = " << d.packed << "; break;\n";
   }
   o << "      default: break;\n    }\n    return d;\n  }\n";
   o << "  __host__ __device__ static constexpr tcb::DevDiagEnt dent(int i) {\n    tcb::DevDiagEnt e{};\n"

@@ -114,13 +114,18 @@ static_assert(sizeof(DevMat) == 80, "DevMat layout");
 //   op_e(x) = x ^ (x >> d_e)   (ZZ pairs at distance d_e; d_e = 0 means x: single Z)
 //   op_e(x) = x & (x >> d_e)   (CZ pairs) when `sign_mode`.
 // Phase mode: amplitude *= table[tab + m]; sign mode: amplitude *= (-1)^m.
+// Packed form (packed = 1, phase mode, at most 64 terms): the n_ent = N
+// entries are 64-bit column words, col(p) = (mask << 32) | d, bit k of col(p)
+// set when term k acts on position p; the term parities of index x are the
+// XOR of col(p) over x's set bits p (a linear map over GF(2)), and m(x) is
+// their popcount.
 struct DevDiag {
   int32_t sign_mode;
   int32_t n_ent;
   int32_t ent_off;  // into DevDiagEnt array
   int32_t T;        // number of Z / ZZ terms (generator G(x) = T - 2 m(x))
   int32_t tab;      // table slot (phase mode)
-  int32_t pad;
+  int32_t packed;   // 1: the entries are column words (above)
 };
 struct DevDiagEnt {
   uint32_t d;
@@ -155,6 +160,9 @@ static_assert(sizeof(DevDiagEnt) == 8, "DevDiagEnt layout");
 // Pauli-sum terms, compiled per Hamiltonian.
 //  Diagonal terms: value(x) = w * (cnt - 2 popc((x ^ (x >> d)) & mask)) when cnt >= 0
 //                  (d == 0: popc(x & mask)), w * (-1)^popc(x & mask) when cnt < 0.
+//                  Packed (pad == 1): cnt ZZ terms of weight w, value(x) = w * (cnt - 2 popc64(W(x))),
+//                  W(x) = XOR of the 64-bit column words of x's set positions, held by the
+//                  N records that follow (pad == 2, word = (mask << 32) | d).
 //  Flip group f:   h_f(x) = sum_t w_t * i^{ny_t} * (-1)^popc(x & sm_t), and
 //                  (P psi)_y = h_f(y ^ f) psi_{y ^ f}.
 struct DevHDiag {

@@ -617,6 +617,19 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
               }
             if (!placed) ents.push_back({d, m});
           }
+          if (!dg.sign_mode && ents.size() >= 2 && it.members.size() <= 64) {
+            // several pair distances: one 64-bit column word per position
+            // (term k = member k), counted by XOR walk and popcount
+            std::vector<uint64_t> col(N, 0);
+            for (size_t k = 0; k < it.members.size(); ++k) {
+              const HGate& g = gates[it.members[k]];
+              col[g.p0] |= 1ull << k;
+              if (g.p1 >= 0) col[g.p1] |= 1ull << k;
+            }
+            ents.clear();
+            for (int p = 0; p < N; ++p) ents.push_back({(uint32_t)(col[p] & 0xffffffffu), (uint32_t)(col[p] >> 32)});
+            dg.packed = 1;
+          }
           for (auto& e : ents) A.dents.push_back(e);
           dg.n_ent = (int)ents.size();
           dg.tab = dg.sign_mode ? -1 : add_mat(g0.quarter ? MT_QUARTER : MT_DIAGTAB, g0, dg.T + 1);
@@ -803,6 +816,40 @@ bool build_hamiltonian(int n_user, int N, int k, const uint8_t* structures, cons
       d.w = w;
       diag.push_back(d);
     }
+  }
+  // ZZ terms of one weight at several distances: one 64-bit column word per
+  // position instead (term k sets bit k at both of its positions), so that
+  // the count of odd terms is one XOR walk and a popcount per amplitude
+  std::map<double, std::vector<std::pair<uint32_t, uint32_t>>> by_w;  // w -> (d, lower-position bit)
+  for (auto& kv : zz)
+    for (uint32_t m : kv.second) by_w[kv.first.first].push_back({kv.first.second, m});
+  for (auto& kv : by_w) {
+    std::map<uint32_t, int> dists;
+    for (auto& t : kv.second) dists[t.first]++;
+    if (dists.size() < 3) continue;
+    for (size_t c0 = 0; c0 < kv.second.size(); c0 += 64) {
+      const size_t c1 = std::min(kv.second.size(), c0 + 64);
+      std::vector<uint64_t> col(N, 0);
+      for (size_t t = c0; t < c1; ++t) {
+        const int a = __builtin_ctz(kv.second[t].second);
+        col[a] |= 1ull << (t - c0);
+        col[a + (int)kv.second[t].first] |= 1ull << (t - c0);
+      }
+      DevHDiag h{};
+      h.cnt = (int32_t)(c1 - c0);
+      h.pad = 1;  // packed header; the N column records follow
+      h.w = kv.first;
+      diag.push_back(h);
+      for (int q = 0; q < N; ++q) {
+        DevHDiag cr{};
+        cr.d = (uint32_t)(col[q] & 0xffffffffu);
+        cr.mask = (uint32_t)(col[q] >> 32);
+        cr.pad = 2;
+        diag.push_back(cr);
+      }
+      H.packed_groups++;
+    }
+    for (auto it = zz.begin(); it != zz.end();) it = it->first.first == kv.first ? zz.erase(it) : std::next(it);
   }
   for (auto& kv : zz) {
     std::vector<DevHDiag> ents;

@@ -69,6 +69,7 @@ struct HamPlan {
   std::vector<DevHTerm> hterms;
   std::vector<DevHFlip> hflips;
   int k = 0;
+  int packed_groups = 0;  // packed diagonal groups (DevHDiag.pad == 1)
 };
 
 // Normalise and validate ops; returns false and sets err on bad input.

@@ -638,9 +638,36 @@ __device__ __forceinline__ uint32_t diag_op_lin(uint32_t g, uint32_t o, const De
 
 // m(x) of an XOR-type diagonal group for every register amplitude: per entry
 // the count is popc(v(g) ^ v(o_i)), walked in Gray-code order.
+template <class Ents>
+__device__ __forceinline__ uint64_t diag_col(const Ents& ents, const DevDiag& dg, int p) {
+  const DevDiagEnt c = ents[dg.ent_off + p];
+  return ((uint64_t)c.mask << 32) | c.d;
+}
+// term parities of index x for a packed group: XOR of the columns of x's set bits
+template <class Ents>
+__device__ __forceinline__ uint64_t diag_word(uint32_t x, const DevDiag& dg, const Ents& ents) {
+  uint64_t w = 0;
+  for (int p = 0; p < dg.n_ent; ++p)
+    if ((x >> p) & 1u) w ^= diag_col(ents, dg, p);
+  return w;
+}
+
 template <int RB, class Ents>
 __device__ __forceinline__ void diag_counts_lin(int (&cnt)[1 << RB], const Map<RB>& m, const DevDiag& dg,
                                                 const Ents& ents) {
+  if (dg.packed) {
+    // one word per amplitude, walked in Gray-code order over the register bits
+    uint64_t w = diag_word(m.g, dg, ents);
+    uint64_t wr[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) wr[r] = diag_col(ents, dg, __ffs((int)m.ro[r]) - 1);
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) {
+      if (j) w ^= wr[low_bit(j)];
+      cnt[j ^ (j >> 1)] = __popcll(w);
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < (1 << RB); ++i) cnt[i] = 0;
   for (int e = 0; e < dg.n_ent; ++e) {
@@ -660,6 +687,7 @@ __device__ __forceinline__ void diag_counts_lin(int (&cnt)[1 << RB], const Map<R
 // m(x) of a diagonal group for one amplitude index
 template <class Ents>
 __device__ __forceinline__ int diag_count(uint32_t x, const DevDiag& dg, const Ents& ents) {
+  if (dg.packed) return __popcll(diag_word(x, dg, ents));
   int c = 0;
   for (int e = 0; e < dg.n_ent; ++e) {
     const DevDiagEnt en = ents[dg.ent_off + e];

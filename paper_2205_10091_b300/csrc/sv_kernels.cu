@@ -410,11 +410,33 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
       T eacc = 0;
       {
         // diagonal terms: the count (or parity) is XOR-linear in the index, so
-        // it is walked in Gray-code order over the registers
-        V e2 = mk<V>((T)0, (T)0);
+        // it is walked in Gray-code order over the registers; the terms'
+        // values h(x) are summed first and applied to the amplitude once
+        T hsum[R];
+  #pragma unroll
+        for (int i = 0; i < R; ++i) hsum[i] = 0;
         for (int e = 0; e < n_diag_here; ++e) {
           const DevHDiag hd = hds[e];
           const T w = (T)hd.w;
+          if (hd.pad == 1) {
+            // packed ZZ terms: column words of the N positions follow
+            const DevHDiag* cols = hds + e + 1;
+            auto colw = [&](int p) { return ((uint64_t)cols[p].mask << 32) | cols[p].d; };
+            uint64_t W = 0;
+            for (int p = 0; p < a.N; ++p)
+              if ((m.g >> p) & 1u) W ^= colw(p);
+            uint64_t wr[RB];
+  #pragma unroll
+            for (int r = 0; r < RB; ++r) wr[r] = colw(__ffs((int)m.ro[r]) - 1);
+  #pragma unroll
+            for (int j = 0; j < R; ++j) {
+              if (j) W ^= wr[low_bit(j)];
+              const int i = j ^ (j >> 1);
+              hsum[i] = fma(w, (T)(hd.cnt - 2 * __popcll(W)), hsum[i]);
+            }
+            e += a.N;
+            continue;
+          }
           const uint32_t dd = hd.cnt < 0 ? 0u : hd.d;
           auto op = [&](uint32_t x) { return (dd == 0 ? x : (x ^ (x >> dd))) & hd.mask; };
           uint32_t v = op(m.g);
@@ -426,24 +448,27 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
             for (int j = 0; j < R; ++j) {
               if (j) v ^= vr[low_bit(j)];
               const int i = j ^ (j >> 1);
-              const T h = (__popc(v) & 1) ? -w : w;
-              const V h2 = mk<V>(h, h);
-              L[i] = cfma2(h2, A[i], L[i]);
-              e2 = cfma2(cmul_re(h2, A[i]), A[i], e2);
+              hsum[i] += (__popc(v) & 1) ? -w : w;
             }
           } else {
   #pragma unroll
             for (int j = 0; j < R; ++j) {
               if (j) v ^= vr[low_bit(j)];
               const int i = j ^ (j >> 1);
-              const T h = w * (T)(hd.cnt - 2 * __popc(v));
-              const V h2 = mk<V>(h, h);
-              L[i] = cfma2(h2, A[i], L[i]);
-              e2 = cfma2(cmul_re(h2, A[i]), A[i], e2);
+              hsum[i] = fma(w, (T)(hd.cnt - 2 * __popc(v)), hsum[i]);
             }
           }
         }
-        eacc = e2.x + e2.y;
+        if (n_diag_here) {
+          V e2 = mk<V>((T)0, (T)0);
+  #pragma unroll
+          for (int i = 0; i < R; ++i) {
+            const V h2 = mk<V>(hsum[i], hsum[i]);
+            L[i] = cfma2(h2, A[i], L[i]);
+            e2 = cfma2(cmul_re(h2, A[i]), A[i], e2);
+          }
+          eacc = e2.x + e2.y;
+        }
       }
       for (int g = 0; g < g_hi - g_lo; ++g) {
         const DevHFlip fl = hfs[g];
@@ -787,32 +812,42 @@ cudaError_t launch_pass_specialised(cudaKernel_t kern, int mode, bool dbl, const
 // ---------------------------------------------------------------------------
 // Finalize: fixed-order sums (deterministic, independent of batch size)
 // ---------------------------------------------------------------------------
+// One block per (row, output): output 0 is the row's energy (sum of the
+// Pauli-sum passes' per-tile partials), output 1 + p the gradient of
+// parameter p (sum over its slots' per-tile partials).  Every thread of the
+// block sums a strided share; the order is fixed, so a row's result does not
+// depend on the other rows.
 __global__ void __launch_bounds__(256) k_finalize(const double* epart, int ne, const double* gpart, int gslots,
                                                   int tiles_b, const int* csr_off, const int* csr_slots,
                                                   int n_params, double* e_out, double* g_out) {
-  __shared__ double sh[256];
+  __shared__ double sh[32];
   const int row = blockIdx.x;
   const int tid = threadIdx.x;
-  if (e_out) {
+  for (int which = blockIdx.y; which <= n_params; which += gridDim.y) {
     double s = 0;
-    for (int i = tid; i < ne; i += blockDim.x) s += epart[(size_t)row * ne + i];
-    sh[tid] = s;
-    __syncthreads();
-    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
-      if (tid < w) sh[tid] += sh[tid + w];
-      __syncthreads();
-    }
-    if (tid == 0) e_out[row] = sh[0];
-  }
-  if (g_out) {
-    for (int p = tid; p < n_params; p += blockDim.x) {
-      double g = 0;
+    if (which == 0) {
+      if (!e_out) continue;
+      for (int i = tid; i < ne; i += blockDim.x) s += epart[(size_t)row * ne + i];
+    } else {
+      if (!g_out) break;
+      const int p = which - 1;
       for (int c = csr_off[p]; c < csr_off[p + 1]; ++c) {
         const double* src = gpart + ((size_t)row * gslots + csr_slots[c]) * tiles_b;
-        for (int t = 0; t < tiles_b; ++t) g += src[t];
+        for (int t = tid; t < tiles_b; t += blockDim.x) s += src[t];
       }
-      g_out[(size_t)row * n_params + p] = g;
     }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((tid & 31) == 0) sh[tid >> 5] = s;
+    __syncthreads();
+    if (tid < 32) {
+      s = tid < (int)(blockDim.x >> 5) ? sh[tid] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (tid == 0) {
+        if (which == 0) e_out[row] = s;
+        else g_out[(size_t)row * n_params + which - 1] = s;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -821,8 +856,9 @@ cudaError_t launch_finalize(const double* epart, int n_hpasses, int tiles_h, con
                             double* e_out, double* g_out, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
   prof_before(PK_FINALIZE, (double)rows * 8.0 * ((double)n_hpasses * tiles_h + (double)gslots * tiles_b), s);
-  k_finalize<<<rows, 256, 0, s>>>(epart, n_hpasses * tiles_h, gpart, gslots, tiles_b, csr_off, csr_slots,
-                                  n_params, e_out, g_out);
+  const unsigned outs = (unsigned)std::min(1 + (g_out ? n_params : 0), 65535);
+  k_finalize<<<dim3((unsigned)rows, outs), 256, 0, s>>>(epart, n_hpasses * tiles_h, gpart, gslots, tiles_b, csr_off,
+                                                        csr_slots, n_params, e_out, g_out);
   prof_after(s);
   return cudaGetLastError();
 }

@@ -70,13 +70,15 @@ class tc_plan_info(C.Structure):
         ("fwd_instrs", C.c_int32),
         ("bwd_instrs", C.c_int32),
         ("specialized_passes", C.c_int32),
-        ("reserved", C.c_int32 * 2),
+        ("packed_diag_groups", C.c_int32),
+        ("reserved", C.c_int32 * 1),
     ]
 
 
 class tc_pauli_sum_plan_info(C.Structure):
     _fields_ = [("passes", C.c_int32), ("paired_passes", C.c_int32), ("flip_groups", C.c_int32),
-                ("diag_entries", C.c_int32), ("tile_qubits", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("diag_entries", C.c_int32), ("tile_qubits", C.c_int32), ("packed_diag_groups", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class tc_grad_options(C.Structure):

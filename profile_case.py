@@ -7,6 +7,8 @@
                                                           # geometric tensor of the TFIM ansatz (10 layers)
     python profile_case.py --workload tn40 --rows 64 --precision 1
                                                           # whole 40-qubit testbed network, tensor-core steps
+    python profile_case.py --workload qaoa --qubits 26 --rows 1 --layers 3
+                                                          # MaxCut QAOA on a random 3-regular graph
 """
 import numpy as np
 import argparse
@@ -19,18 +21,29 @@ from paper_2205_10091_b300 import workloads as W
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="tfim20", choices=["tfim20", "noisy16", "hea10", "qgt", "tn40"])
+    ap.add_argument("--workload", default="tfim20", choices=["tfim20", "noisy16", "hea10", "qgt", "tn40", "qaoa"])
     ap.add_argument("--rows", type=int, default=32)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--qubits", type=int, default=16)
     ap.add_argument("--precision", type=int, default=1, help="tn40: 0 FP32, 1 TF32X3, 2 BF16X6")
-    ap.add_argument("--specialize", action="store_true", help="tfim20: pass kernels compiled for the circuit")
+    ap.add_argument("--layers", type=int, default=3, help="qaoa: layers p")
+    ap.add_argument("--specialize", action="store_true", help="tfim20, qaoa: pass kernels compiled for the circuit")
     args = ap.parse_args()
     if args.workload == "tfim20":
         circ, theta, ham = W.tfim_workload(20, 10, args.rows)
         c = nt.Circuit(circ, specialize=args.specialize)
         H = nt.Hamiltonian(ham)
         d = torch.as_tensor(theta, device="cuda")
+        for _ in range(args.steps):
+            e, g = c.expect_grad(d, H)
+        torch.cuda.synchronize()
+        print("rows", args.rows, "plan", c.info(), "E[0]", float(e[0]))
+    elif args.workload == "qaoa":
+        rng = np.random.default_rng(args.qubits)
+        edges = W.random_regular3(args.qubits, rng)
+        c = nt.Circuit(W.qaoa_circuit(args.qubits, edges, args.layers), specialize=args.specialize)
+        H = nt.Hamiltonian(W.zz_on_edges(args.qubits, edges))
+        d = torch.as_tensor(rng.uniform(0, np.pi, size=(args.rows, 2 * args.layers)), device="cuda")
         for _ in range(args.steps):
             e, g = c.expect_grad(d, H)
         torch.cuda.synchronize()

@@ -178,3 +178,34 @@ def test_specialised_passes_compile_for_every_instruction_kind(dtype):
     info = c.info()
     assert info["specialized_passes"] == info["fwd_passes"] + info["bwd_passes"] > 0
     assert nt.Circuit(circ, dtype=dtype).info()["specialized_passes"] == 0
+
+
+def test_qaoa_layers_use_packed_diag_groups():
+    """A QAOA cost layer on a 3-regular graph has ZZ pairs at many distances;
+    the planner evaluates such a group as one linear map per amplitude.  A
+    nearest-neighbour layer (one distance) keeps the entry form."""
+    rng = np.random.default_rng(5)
+    edges = W.random_regular3(16, rng)
+    info = nt.Circuit(W.qaoa_circuit(16, edges, 3)).info()
+    assert info["packed_diag_groups"] >= 3
+    assert nt.Circuit(W.tfim_circuit(16, 3)).info()["packed_diag_groups"] == 0
+
+
+def test_specialised_passes_compile_with_packed_groups():
+    rng = np.random.default_rng(6)
+    c = nt.Circuit(W.qaoa_circuit(14, W.random_regular3(14, rng), 2), specialize=True)
+    info = c.info()
+    assert info["packed_diag_groups"] >= 2
+    assert info["specialized_passes"] == info["fwd_passes"] + info["bwd_passes"]
+
+
+def test_pauli_sum_packs_zz_terms_of_one_weight():
+    rng = np.random.default_rng(8)
+    n = 16
+    edges = W.random_regular3(n, rng)
+    c = nt.Circuit(W.OpBuilder(n).build())
+    i = c.pauli_sum_info(nt.Hamiltonian(W.zz_on_edges(n, edges)))
+    assert i["packed_diag_groups"] == 1 and i["diag_entries"] == 1 + n
+    # nearest-neighbour bonds (one distance) keep the entry form
+    nn = W.pauli_sum(n, [(1.0, {q: 3, q + 1: 3}) for q in range(n - 1)])
+    assert c.pauli_sum_info(nt.Hamiltonian(nn))["packed_diag_groups"] == 0
