@@ -237,12 +237,25 @@ TC_API tc_status tc_apply_layers(const tc_circuit* c, const double* d_params, in
 TC_API tc_status tc_expect_pauli_sum(tc_circuit* c, const void* d_states, int B, const uint8_t* structures,
                               const double* weights, int T, double* d_energy_out, void* stream);
 
-typedef enum { TC_GRAD_UNCOMPUTE = 0 } tc_grad_mode;
+/*
+ * Gradient memory modes.
+ *   TC_GRAD_UNCOMPUTE:  two states per row; the adjoint sweep un-applies
+ *                       every gate from psi (no stored states).
+ *   TC_GRAD_CHECKPOINT: the op list is cut into segments of checkpoint_ops
+ *                       ops (0 = four segments), each planned as a circuit
+ *                       of its own; the forward sweep keeps the state after
+ *                       every segment (segments + 1 states per row), and the
+ *                       adjoint sweep of each segment starts from its stored
+ *                       state, so psi is un-applied across one segment at
+ *                       most.  Circuits with noise events: TC_E_UNSUPPORTED.
+ */
+typedef enum { TC_GRAD_UNCOMPUTE = 0, TC_GRAD_CHECKPOINT = 1 } tc_grad_mode;
 
 typedef struct {
-  int32_t mode;        /* tc_grad_mode */
-  int32_t max_rows;    /* rows per device chunk (0 = as many as the budget allows) */
-  int32_t reserved[6];
+  int32_t mode;           /* tc_grad_mode */
+  int32_t max_rows;       /* rows per device chunk (0 = as many as the budget allows) */
+  int32_t checkpoint_ops; /* TC_GRAD_CHECKPOINT: ops per segment (0 = a quarter of the circuit) */
+  int32_t reserved[5];
 } tc_grad_options;
 
 /*
@@ -556,17 +569,23 @@ TC_API tc_status tc_tn_circuit_expect(tc_tn* t, int B, const float* d_params, tc
  *
  * A request is one energy + gradient evaluation: an op list, its parameters
  * and a Pauli sum (the arguments of tc_expect_grad with B = 1; complex64).
- * tc_submit queues it and returns at once.  A scheduler thread admits queued
+ * tc_submit queues it and returns at once; planner threads compile its plan
+ * and Pauli sum on the host meanwhile.  A scheduler thread admits queued
  * requests in arrival order whenever a stream slot and enough of the memory
- * budget are free; each admitted request takes one stream-ordered block from
- * the server's own memory pool (plan, Pauli sum, parameters, two states,
- * outputs) and runs on its own CUDA stream, so requests that arrive while
- * others run overlap with them on the device.  The block returns to the pool
- * when the request completes and the next request is admitted.  A request's
- * arithmetic is exactly tc_expect_grad's: its result does not depend on what
- * else is in flight.  The paper has no serving layer; this realises the
- * batched evaluation of Section "Batched VQE" for a stream of independent
- * circuits.
+ * budget are free.  Queued requests of at most 20 qubits whose plans differ
+ * only in the values of their diagonal-group entries and Pauli-sum diagonal
+ * records (QAOA instances of one width and depth on different graphs, say)
+ * are admitted together, up to max_group_rows of them, as the rows of one
+ * evaluation: one launch per pass for the group.  Each admitted group takes
+ * one stream-ordered block from the server's own memory pool (plan, per-row
+ * diagonal entries, Pauli sum, parameters, two states per row, outputs) and
+ * runs on its own CUDA stream, so groups that arrive while others run
+ * overlap with them on the device.  The block returns to the pool when the
+ * group completes and the next request is admitted.  A row's arithmetic is
+ * exactly tc_expect_grad's on that request alone: a result does not depend
+ * on what it was grouped or overlapped with.  The paper has no serving
+ * layer; this realises the batched evaluation of Section "Batched VQE" for
+ * a stream of independent circuits.
  *
  * Errors: a malformed request is refused by tc_submit (TC_E_INVALID); a full
  * queue returns TC_E_BUSY; a request larger than the whole budget completes
@@ -582,8 +601,11 @@ typedef struct {
   int32_t max_inflight;     /* concurrent requests = CUDA streams (0 = 16, at most 256) */
   int32_t max_queue;        /* queued requests before tc_submit returns TC_E_BUSY (0 = unbounded) */
   int32_t timeout_ms;       /* queued longer than this -> TC_E_TIMEOUT (0 = never) */
-  int32_t start_paused;     /* 1 = admit nothing (and touch no GPU) until tc_server_resume */
-  int32_t reserved[6];
+  int32_t start_paused;     /* 1 = admit nothing (and touch no GPU) until tc_server_resume; requests are
+                               still planned on the host */
+  int32_t max_group_rows;   /* requests one admission may group as rows (0 = 32, 1 = no grouping) */
+  int32_t planner_threads;  /* host threads compiling request plans (0 = 2) */
+  int32_t reserved[4];
 } tc_server_options;
 typedef struct {
   int32_t n_qubits;
@@ -607,8 +629,13 @@ typedef struct {
 } tc_result;
 typedef struct {
   int64_t submitted, completed, cancelled, timed_out, failed, rejected;
-  int32_t pending, inflight, peak_inflight, pad;
+  int32_t pending;        /* queued, not admitted */
+  int32_t inflight;       /* admitted requests (rows) on the device */
+  int32_t peak_inflight;
+  int32_t planned;        /* queued requests whose plan is ready */
   int64_t bytes_in_use, peak_bytes;
+  int64_t groups;           /* admissions (launch sequences) so far */
+  int64_t grouped_requests; /* requests that ran as a row of a group of two or more */
 } tc_server_stats;
 TC_API tc_status tc_server_create(const tc_server_options* opt, tc_server** out);
 TC_API tc_status tc_submit(tc_server* s, const tc_request* req, uint64_t* id_out);

@@ -84,6 +84,7 @@ tc_circuit::~tc_circuit() {
   dev_free(d_qgt_off);
   dev_free(d_qgt_occ);
   dev_free(qgt_ws);
+  for (auto* sg : ckpt_segs) delete sg;
 }
 
 namespace {
@@ -216,8 +217,9 @@ tc_status run_schedule(tc_circuit* c, int mode, const Schedule& sc, const PlanAr
   a.tables = tables;
   a.table_stride = sc.table_total;
   TC_CHECK_CUDA(launch_tables(is_dbl(c), a, sc.first_mat, sc.n_mats, rows, s), "gate tables");
-  // the circuit's specialised kernels run its own schedules (not the unfused baseline's)
-  const bool spec = &A == &c->A && !c->jit_kern.empty();
+  // the circuit's specialised kernels run its own schedules (not the unfused
+  // baseline's) with the plan's own diagonal entries compiled in
+  const bool spec = &A == &c->A && !c->jit_kern.empty() && a.dent_row_stride == 0;
   for (int p = 0; p < sc.n_passes; ++p) {
     a.pass = sc.first_pass + p;
     if (spec)
@@ -265,7 +267,7 @@ size_t grad_ws_bytes(const tc_circuit* c, int chunk) {
 }
 
 tc_status expect_grad_run(tc_circuit* c, const double* d_params, int B, uint64_t seed, double* d_energy_out,
-                          double* d_grad_out, int chunk, char* w, cudaStream_t s) {
+                          double* d_grad_out, int chunk, char* w, cudaStream_t s, const RowDiag* rd) {
   const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
   const int nh = (int)c->H.passes.size();
   const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
@@ -289,6 +291,12 @@ tc_status expect_grad_run(tc_circuit* c, const double* d_params, int B, uint64_t
     a.theta = d_params ? d_params + (size_t)r0 * c->n_params : nullptr;
     a.seed = seed;
     a.row_offset = r0;
+    if (rd) {
+      a.dents = rd->dents + (size_t)r0 * rd->dent_stride;
+      a.dent_row_stride = rd->dent_stride;
+      a.hdiag = rd->hdiag + (size_t)r0 * rd->hdiag_stride;
+      a.hdiag_row_stride = rd->hdiag_stride;
+    }
     if ((st = run_schedule(c, KM_FWD, c->fwd, c->A, a, w + o_tf, rows, s)) != TC_OK) return st;
     if ((st = run_ham(c, a, rows, true, s)) != TC_OK) return st;
     if ((st = run_schedule(c, KM_BWD, c->bwd, c->A, a, w + o_tb, rows, s)) != TC_OK) return st;
@@ -642,17 +650,149 @@ tc_status tc_expect_pauli_sum(tc_circuit* c, const void* d_states, int B, const 
   return TC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Segments of `ops` ops each, planned as circuits of their own (built on
+// first use and kept while the segment length stays the same).
+tc_status ensure_segments(tc_circuit* c, int ops) {
+  if (c->ckpt_ops == ops && !c->ckpt_segs.empty()) return TC_OK;
+  for (auto* sg : c->ckpt_segs) delete sg;
+  c->ckpt_segs.clear();
+  c->ckpt_ops = 0;
+  tc_options o = c->opt;
+  o.specialize = 0;
+  for (int from = 0; from < c->n_ops; from += ops) {
+    tc_circuit* sg = nullptr;
+    const int cnt = std::min(ops, c->n_ops - from);
+    tc_status st = tc_circuit_create(c->n, c->dtype, c->init, c->ops_in.data() + from, cnt, c->n_params,
+                                     c->pool.empty() ? nullptr : c->pool.data(), (int)(c->pool.size() / 2), &o, &sg);
+    if (st == TC_OK) st = ensure_device(sg);
+    if (st != TC_OK) {
+      delete sg;
+      for (auto* q : c->ckpt_segs) delete q;
+      c->ckpt_segs.clear();
+      return st;
+    }
+    c->ckpt_segs.push_back(sg);
+  }
+  c->ckpt_ops = ops;
+  return TC_OK;
+}
+
+// Workspace of one row: the state after every segment, lambda, the
+// Pauli-sum partials, the largest segment's gradient partials and tables.
+size_t ckpt_row_bytes(const tc_circuit* c) {
+  const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
+  const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
+  size_t gp = 8, tab = 0;
+  for (const tc_circuit* sg : c->ckpt_segs) {
+    gp = std::max(gp, (size_t)std::max(sg->bwd.n_gslots, 1) * ((size_t)1 << (sg->N - sg->k_bwd)) * 8);
+    tab = std::max(tab, (size_t)std::max(sg->fwd.table_total, sg->bwd.table_total) * amp_bytes(c));
+  }
+  return (c->ckpt_segs.size() + 1) * per + c->H.passes.size() * tiles_h * 8 + gp + tab + 64 * 8;
+}
+
+// Checkpointed energy + gradient: forward segment by segment, keeping the
+// state after each; lambda = H psi; then the adjoint of each segment from
+// last to first, starting from that segment's stored state (so the
+// uncompute of psi never runs across a segment boundary) and adding its
+// gradient partials to the rows' gradients.
+tc_status expect_grad_ckpt_run(tc_circuit* c, const double* d_params, int B, uint64_t seed, double* d_e,
+                               double* d_g, int chunk, char* w, cudaStream_t s) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int S = (int)c->ckpt_segs.size();
+  const size_t per = ((size_t)1 << c->N) * amp_bytes(c);
+  const int nh = (int)c->H.passes.size();
+  const size_t tiles_h = (size_t)1 << (c->N - c->k_ham);
+  size_t gp = 8, tab = 0;
+  for (const tc_circuit* sg : c->ckpt_segs) {
+    gp = std::max(gp, (size_t)std::max(sg->bwd.n_gslots, 1) * ((size_t)1 << (sg->N - sg->k_bwd)) * 8);
+    tab = std::max(tab, (size_t)std::max(sg->fwd.table_total, sg->bwd.table_total) * amp_bytes(c));
+  }
+  const size_t o_lam = (size_t)S * al(per * chunk);
+  const size_t o_ep = o_lam + al(per * chunk);
+  const size_t o_gp = o_ep + al((size_t)chunk * nh * tiles_h * 8);
+  const size_t o_tab = o_gp + al(gp * chunk);
+  auto ckpt = [&](int k) { return w + (size_t)(k - 1) * al(per * chunk); };  // state after segment k-1 (k >= 1)
+  tc_status st;
+  for (int r0 = 0; r0 < B; r0 += chunk) {
+    const int rows = std::min(chunk, B - r0);
+    const double* th = d_params ? d_params + (size_t)r0 * c->n_params : nullptr;
+    for (int k = 0; k < S; ++k) {
+      tc_circuit* sg = c->ckpt_segs[k];
+      KArgs a = base_args(sg, sg->dplan);
+      a.psi = ckpt(k + 1);
+      a.theta = th;
+      a.seed = seed;
+      a.row_offset = r0;
+      if (k > 0) {
+        TC_CHECK_CUDA(cudaMemcpyAsync(ckpt(k + 1), ckpt(k), per * rows, cudaMemcpyDeviceToDevice, s), "checkpoint copy");
+        a.synth_init = 0;
+      }
+      if ((st = run_schedule(sg, KM_FWD, sg->fwd, sg->A, a, w + o_tab, rows, s)) != TC_OK) return st;
+    }
+    {
+      KArgs a = base_args(c, c->dplan);
+      a.psi = ckpt(S);
+      a.lam = w + o_lam;
+      a.epart = (double*)(w + o_ep);
+      if ((st = run_ham(c, a, rows, true, s)) != TC_OK) return st;
+    }
+    for (int k = S - 1; k >= 0; --k) {
+      tc_circuit* sg = c->ckpt_segs[k];
+      KArgs a = base_args(sg, sg->dplan);
+      a.psi = ckpt(k + 1);
+      a.lam = w + o_lam;
+      a.gpart = (double*)(w + o_gp);
+      a.gslots_total = sg->bwd.n_gslots;
+      a.theta = th;
+      a.seed = seed;
+      a.row_offset = r0;
+      if ((st = run_schedule(sg, KM_BWD, sg->bwd, sg->A, a, w + o_tab, rows, s)) != TC_OK) return st;
+      const size_t tiles_b = (size_t)1 << (sg->N - sg->k_bwd);
+      TC_CHECK_CUDA(launch_finalize((double*)(w + o_ep), nh, (int)tiles_h, (double*)(w + o_gp), sg->bwd.n_gslots,
+                                    (int)tiles_b, sg->d_csr_off, sg->d_csr_slots, c->n_params, rows,
+                                    k == S - 1 ? d_e + r0 : nullptr,
+                                    c->n_params ? d_g + (size_t)r0 * c->n_params : nullptr, s, k != S - 1),
+                    "finalize");
+    }
+  }
+  return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 tc_status tc_expect_grad(tc_circuit* c, const double* d_params, int B, const uint8_t* structures,
                          const double* weights, int T, uint64_t seed, double* d_energy_out, double* d_grad_out,
                          const tc_grad_options* gopt, void* stream) {
   if (!c || !d_energy_out) return fail(TC_E_INVALID, "NULL argument");
   if (B < 0) return fail(TC_E_INVALID, "B < 0");
   if (c->n_params > 0 && (!d_params || !d_grad_out) && B > 0) return fail(TC_E_INVALID, "d_params/d_grad_out NULL");
-  if (gopt && gopt->mode != TC_GRAD_UNCOMPUTE) return fail(TC_E_UNSUPPORTED, "unknown gradient mode");
+  if (gopt && gopt->mode != TC_GRAD_UNCOMPUTE && gopt->mode != TC_GRAD_CHECKPOINT)
+    return fail(TC_E_UNSUPPORTED, "unknown gradient mode");
+  const bool ck = gopt && gopt->mode == TC_GRAD_CHECKPOINT;
+  if (ck && c->n_noise > 0) return fail(TC_E_UNSUPPORTED, "checkpointed gradients of circuits with noise events");
+  if (ck && gopt->checkpoint_ops < 0) return fail(TC_E_INVALID, "checkpoint_ops < 0");
   if (B == 0) return TC_OK;
   tc_status st = ensure_device(c);
   if (st != TC_OK) return st;
   if ((st = ensure_ham(c, structures, weights, T)) != TC_OK) return st;
+  if (ck) {
+    const int ops = gopt->checkpoint_ops > 0 ? gopt->checkpoint_ops : std::max(1, (c->n_ops + 3) / 4);
+    if (c->n_ops == 0) return fail(TC_E_UNSUPPORTED, "checkpointed gradients of an empty circuit");
+    if ((st = ensure_segments(c, ops)) != TC_OK) return st;
+    int64_t cap = budget(c) / (int64_t)ckpt_row_bytes(c);
+    if (gopt->max_rows > 0) cap = std::min<int64_t>(cap, gopt->max_rows);
+    if (cap < 1) return fail(TC_E_NOMEM, "one row of checkpoints does not fit the memory budget");
+    const int chunk = (int)std::min<int64_t>(B, cap);
+    if ((st = ensure_ws(c, ckpt_row_bytes(c) * chunk + 4096)) != TC_OK) return st;
+    return expect_grad_ckpt_run(c, d_params, B, seed, d_energy_out, d_grad_out, chunk, (char*)c->ws,
+                                (cudaStream_t)stream);
+  }
   int64_t cap = budget(c) / (int64_t)grad_row_bytes(c);
   if (gopt && gopt->max_rows > 0) cap = std::min<int64_t>(cap, gopt->max_rows);
   if (cap < 1) return fail(TC_E_NOMEM, "one row of states does not fit the memory budget");

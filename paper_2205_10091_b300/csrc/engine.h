@@ -54,8 +54,17 @@ namespace tcb {
 // caller-provided workspace (used by the serving loop).
 size_t grad_row_bytes(const tc_circuit* c);
 size_t grad_ws_bytes(const tc_circuit* c, int chunk);
+// Per-row copies of the plan's diagonal entries and Pauli-sum diagonal
+// records (device, row-major, `*_stride` entries a row): rows of one plan
+// that differ only in those (serving-loop groups).
+struct RowDiag {
+  const DevDiagEnt* dents;
+  int dent_stride;
+  const DevHDiag* hdiag;
+  int hdiag_stride;
+};
 tc_status expect_grad_run(tc_circuit* c, const double* d_params, int B, uint64_t seed, double* d_energy_out,
-                          double* d_grad_out, int chunk, char* ws, cudaStream_t s);
+                          double* d_grad_out, int chunk, char* ws, cudaStream_t s, const RowDiag* rd = nullptr);
 // Plan + compiled Pauli sum placed in caller-provided device memory.
 size_t plan_dev_bytes(const tc_circuit* c);
 size_t ham_dev_bytes(const HamPlan& H);
@@ -144,6 +153,11 @@ struct tc_circuit {
   uint32_t* d_qgt_pauli = nullptr; // [occ][3] generator: flip mask, sign mask, number of Y
   void* qgt_ws = nullptr;
   size_t qgt_ws_bytes = 0;
+
+  // checkpointed gradients (TC_GRAD_CHECKPOINT): the op list cut into
+  // segments of ckpt_ops ops, each planned as a circuit of its own
+  std::vector<tc_circuit*> ckpt_segs;
+  int ckpt_ops = 0;
 
   ~tc_circuit();
 };

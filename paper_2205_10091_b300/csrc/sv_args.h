@@ -48,6 +48,12 @@ struct KArgs {
   // split over hchunks blocks per tile (blockIdx.y), each writing its own
   // energy partial; 0 or 1 = one block per tile (required when lambda is kept)
   int hchunks;
+  // grouped rows (serving): > 0 = `dents` (`hdiag`) hold one copy of the
+  // plan's diagonal entries (Pauli-sum diagonal records) per row, this many
+  // entries apart, so rows of one plan may differ in the column words of
+  // packed groups and in diagonal weights; 0 = one copy shared by all rows
+  int dent_row_stride;
+  int hdiag_row_stride;
 };
 
 // The pass descriptor and its first stage, passed by value as a kernel

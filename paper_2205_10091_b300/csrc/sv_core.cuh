@@ -849,7 +849,8 @@ __device__ __forceinline__ void gate_pass(const KArgs& a, const PassArgs& pa) {
         for (int i = tid; i < words; i += blockDim.x) dst[i] = src[i];
       }
       for (int i = tid; i < sp.n_diag; i += blockDim.x) const_cast<DevDiag*>(dgs)[i] = a.diags[sp.diag_off + i];
-      for (int i = tid; i < sp.n_dent; i += blockDim.x) const_cast<DevDiagEnt*>(des)[i] = a.dents[sp.dent_off + i];
+      const DevDiagEnt* drow = a.dents + (size_t)row * a.dent_row_stride + sp.dent_off;
+      for (int i = tid; i < sp.n_dent; i += blockDim.x) const_cast<DevDiagEnt*>(des)[i] = drow[i];
     }
     if (MODE == KM_BWD)
       for (int i = tid; i < sp.n_gslots * nwarps; i += blockDim.x) red[i] = 0.0;

@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? (RB <= 3 ? 4 : 2) : (RB
       auto stage = [&](void* dst, const void* src, int bytes) {
         for (int i = tid; i < bytes / 4; i += blockDim.x) ((uint32_t*)dst)[i] = ((const uint32_t*)src)[i];
       };
-      stage(hds, a.hdiag + sp.hdiag_off, n_diag_here * (int)sizeof(DevHDiag));
+      stage(hds, a.hdiag + (size_t)row * a.hdiag_row_stride + sp.hdiag_off, n_diag_here * (int)sizeof(DevHDiag));
       stage(hfs, a.hflips + sp.hflip_off + g_lo, (g_hi - g_lo) * (int)sizeof(DevHFlip));
       stage(hts, a.hterms + term_lo, (term_hi - term_lo) * (int)sizeof(DevHTerm));
     }
@@ -817,9 +817,9 @@ cudaError_t launch_pass_specialised(cudaKernel_t kern, int mode, bool dbl, const
 // parameter p (sum over its slots' per-tile partials).  Every thread of the
 // block sums a strided share; the order is fixed, so a row's result does not
 // depend on the other rows.
-__global__ void __launch_bounds__(256) k_finalize(const double* epart, int ne, const double* gpart, int gslots,
+__global__ void __launch_bounds__(512) k_finalize(const double* epart, int ne, const double* gpart, int gslots,
                                                   int tiles_b, const int* csr_off, const int* csr_slots,
-                                                  int n_params, double* e_out, double* g_out) {
+                                                  int n_params, double* e_out, double* g_out, int accumulate) {
   __shared__ double sh[32];
   const int row = blockIdx.x;
   const int tid = threadIdx.x;
@@ -831,10 +831,18 @@ __global__ void __launch_bounds__(256) k_finalize(const double* epart, int ne, c
     } else {
       if (!g_out) break;
       const int p = which - 1;
+      // four independent partial sums keep several loads in flight per thread
+      double s4[4] = {0, 0, 0, 0};
       for (int c = csr_off[p]; c < csr_off[p + 1]; ++c) {
         const double* src = gpart + ((size_t)row * gslots + csr_slots[c]) * tiles_b;
-        for (int t = tid; t < tiles_b; t += blockDim.x) s += src[t];
+        int t = tid;
+        for (; t + 3 * (int)blockDim.x < tiles_b; t += 4 * blockDim.x) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) s4[u] += src[t + u * blockDim.x];
+        }
+        for (; t < tiles_b; t += blockDim.x) s4[0] += src[t];
       }
+      s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((tid & 31) == 0) sh[tid >> 5] = s;
@@ -844,6 +852,7 @@ __global__ void __launch_bounds__(256) k_finalize(const double* epart, int ne, c
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (tid == 0) {
         if (which == 0) e_out[row] = s;
+        else if (accumulate) g_out[(size_t)row * n_params + which - 1] += s;
         else g_out[(size_t)row * n_params + which - 1] = s;
       }
     }
@@ -853,12 +862,12 @@ __global__ void __launch_bounds__(256) k_finalize(const double* epart, int ne, c
 
 cudaError_t launch_finalize(const double* epart, int n_hpasses, int tiles_h, const double* gpart, int gslots,
                             int tiles_b, const int* csr_off, const int* csr_slots, int n_params, int rows,
-                            double* e_out, double* g_out, cudaStream_t s) {
+                            double* e_out, double* g_out, cudaStream_t s, bool accumulate) {
   if (rows <= 0) return cudaSuccess;
   prof_before(PK_FINALIZE, (double)rows * 8.0 * ((double)n_hpasses * tiles_h + (double)gslots * tiles_b), s);
   const unsigned outs = (unsigned)std::min(1 + (g_out ? n_params : 0), 65535);
-  k_finalize<<<dim3((unsigned)rows, outs), 256, 0, s>>>(epart, n_hpasses * tiles_h, gpart, gslots, tiles_b, csr_off,
-                                                        csr_slots, n_params, e_out, g_out);
+  k_finalize<<<dim3((unsigned)rows, outs), 512, 0, s>>>(epart, n_hpasses * tiles_h, gpart, gslots, tiles_b, csr_off,
+                                                        csr_slots, n_params, e_out, g_out, accumulate ? 1 : 0);
   prof_after(s);
   return cudaGetLastError();
 }

@@ -25,9 +25,10 @@ cudaError_t launch_pass_specialised(cudaKernel_t kern, int mode, bool dbl, const
 cudaError_t launch_tables(bool dbl, const KArgs& a, int first_mat, int n_mats, int rows, cudaStream_t s);
 
 // E[b] = sum of energy partials; grad[b][p] = sum over slots of p and tiles.
+// accumulate: the gradients are added to g_out instead of written
 cudaError_t launch_finalize(const double* epart, int n_hpasses, int tiles_h, const double* gpart, int gslots,
                             int tiles_b, const int* csr_off, const int* csr_slots, int n_params, int rows,
-                            double* e_out, double* g_out, cudaStream_t s);
+                            double* e_out, double* g_out, cudaStream_t s, bool accumulate = false);
 
 // Copy a narrow (n < 9) state batch in or out of the padded internal layout.
 cudaError_t launch_pad_states(bool dbl, const void* src, void* dst, int n_user, int N, int rows, bool to_padded,

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libtc_b300.so")
 TC_OK, TC_E_INVALID, TC_E_NOMEM, TC_E_CUDA, TC_E_TIMEOUT, TC_E_UNSUPPORTED, TC_E_BUSY, TC_E_CANCELLED = range(8)
 TC_C64, TC_C128 = 0, 1
 TC_TN_FP32, TC_TN_TF32X3, TC_TN_BF16X6 = 0, 1, 2  # tc_tn_precision
+TC_GRAD_UNCOMPUTE, TC_GRAD_CHECKPOINT = 0, 1  # tc_grad_mode
 
 
 class TcError(RuntimeError):
@@ -82,7 +83,8 @@ class tc_pauli_sum_plan_info(C.Structure):
 
 
 class tc_grad_options(C.Structure):
-    _fields_ = [("mode", C.c_int32), ("max_rows", C.c_int32), ("reserved", C.c_int32 * 6)]
+    _fields_ = [("mode", C.c_int32), ("max_rows", C.c_int32), ("checkpoint_ops", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
 
 
 class tc_path_info(C.Structure):
@@ -95,7 +97,8 @@ class tc_path_info(C.Structure):
 
 class tc_server_options(C.Structure):
     _fields_ = [("mem_budget_bytes", C.c_int64), ("max_inflight", C.c_int32), ("max_queue", C.c_int32),
-                ("timeout_ms", C.c_int32), ("start_paused", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("timeout_ms", C.c_int32), ("start_paused", C.c_int32), ("max_group_rows", C.c_int32),
+                ("planner_threads", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class tc_request(C.Structure):
@@ -112,8 +115,9 @@ class tc_result(C.Structure):
 class tc_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("cancelled", C.c_int64),
                 ("timed_out", C.c_int64), ("failed", C.c_int64), ("rejected", C.c_int64), ("pending", C.c_int32),
-                ("inflight", C.c_int32), ("peak_inflight", C.c_int32), ("pad", C.c_int32),
-                ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64)]
+                ("inflight", C.c_int32), ("peak_inflight", C.c_int32), ("planned", C.c_int32),
+                ("bytes_in_use", C.c_int64), ("peak_bytes", C.c_int64), ("groups", C.c_int64),
+                ("grouped_requests", C.c_int64)]
 
 
 class tc_kernel_stat(C.Structure):
@@ -349,7 +353,10 @@ class Circuit:
         return out
 
     def expect_grad(self, params, ham: Hamiltonian, seed: int = 0, energy=None, grad=None, max_rows: int = 0,
-                    stream=None):
+                    stream=None, checkpoint_ops=None):
+        """Energies and gradients of every row (tc_expect_grad).  checkpoint_ops:
+        None = uncompute mode; an int = TC_GRAD_CHECKPOINT with that many ops
+        per segment (0 = four segments)."""
         import torch
 
         B = params.shape[0]
@@ -358,7 +365,8 @@ class Circuit:
         if grad is None:
             grad = torch.empty((B, self.n_params), dtype=torch.float64, device="cuda")
         s, w, T = ham.args()
-        go = tc_grad_options(0, max_rows)
+        go = tc_grad_options(TC_GRAD_UNCOMPUTE if checkpoint_ops is None else TC_GRAD_CHECKPOINT, max_rows,
+                             0 if checkpoint_ops is None else int(checkpoint_ops))
         _check(lib().tc_expect_grad(self.h, _ptr(params), B, s, w, T, C.c_uint64(seed), _ptr(energy), _ptr(grad),
                                     C.byref(go), _stream(stream)))
         return energy, grad
@@ -544,8 +552,9 @@ class Server:
     """Continuous-batching request server (tc_server_*)."""
 
     def __init__(self, mem_budget_bytes: int = 0, max_inflight: int = 0, max_queue: int = 0, timeout_ms: int = 0,
-                 start_paused: bool = False):
-        o = tc_server_options(mem_budget_bytes, max_inflight, max_queue, timeout_ms, int(start_paused))
+                 start_paused: bool = False, max_group_rows: int = 0, planner_threads: int = 0):
+        o = tc_server_options(mem_budget_bytes, max_inflight, max_queue, timeout_ms, int(start_paused),
+                              max_group_rows, planner_threads)
         h = C.c_void_p()
         _check(lib().tc_server_create(C.byref(o), C.byref(h)))
         self.h = h
@@ -593,7 +602,7 @@ class Server:
     def stats(self) -> dict:
         o = tc_server_stats()
         _check(lib().tc_server_get_stats(self.h, C.byref(o)))
-        return {f: getattr(o, f) for f, _ in tc_server_stats._fields_ if f != "pad"}
+        return {f: getattr(o, f) for f, _ in tc_server_stats._fields_}
 
     def wait(self, rid: int, timeout_s: float = 60.0, sleep_s: float = 0.0002):
         import time

@@ -209,3 +209,22 @@ def test_pauli_sum_packs_zz_terms_of_one_weight():
     # nearest-neighbour bonds (one distance) keep the entry form
     nn = W.pauli_sum(n, [(1.0, {q: 3, q + 1: 3}) for q in range(n - 1)])
     assert c.pauli_sum_info(nt.Hamiltonian(nn))["packed_diag_groups"] == 0
+
+
+def test_grad_options_validated_before_any_device_work():
+    """Bad gradient options fail on the host (no GPU needed): an unknown
+    mode, a negative segment length, checkpoints of a noisy circuit."""
+    import ctypes as C
+
+    L = nt.lib()
+    c = nt.Circuit(W.OpBuilder(10).build())
+    s, w, T = nt.Hamiltonian(W.pauli_sum(10, [(1.0, {0: 3})])).args()
+    fake = C.c_void_p(16)  # never dereferenced: validation fails first
+    for mode, ops, want in [(7, 0, nt.TC_E_UNSUPPORTED), (nt.TC_GRAD_CHECKPOINT, -1, nt.TC_E_INVALID)]:
+        go = nt.tc_grad_options(mode, 0, ops)
+        assert L.tc_expect_grad(c.h, None, 1, s, w, T, C.c_uint64(0), fake, None, C.byref(go), None) == want
+    circ = W.noisy_su2_cz_circuit(10, 1, 0.1, np.random.default_rng(1))
+    cn = nt.Circuit(circ)
+    go = nt.tc_grad_options(nt.TC_GRAD_CHECKPOINT, 0, 3)
+    assert L.tc_expect_grad(cn.h, None, 1, s, w, T, C.c_uint64(0), fake, None, C.byref(go), None) == \
+        nt.TC_E_UNSUPPORTED

@@ -69,3 +69,62 @@ def test_request_larger_than_budget_fails_with_nomem():
     r = s.wait(rid)
     assert r["status"] == nt.TC_E_NOMEM
     s.close()
+
+
+def _wait_planned(s, n, limit_s=30.0):
+    import time
+
+    t0 = time.monotonic()
+    while s.stats()["planned"] < n and time.monotonic() - t0 < limit_s:
+        time.sleep(0.01)
+    assert s.stats()["planned"] == n
+
+
+def test_same_shape_requests_run_as_rows_of_one_group():
+    """QAOA instances of one width and depth on different graphs share a plan
+    shape (their packed column words differ): queued together they run as the
+    rows of one launch sequence, bitwise equal to each request run alone, and
+    requests of another shape queued in between form their own group."""
+    rng = np.random.default_rng(11)
+    reqs = []
+    for k in range(12):
+        n, p = (10, 2) if k % 2 == 0 else (12, 1)
+        edges = W.random_regular3(n, rng)
+        reqs.append((W.qaoa_circuit(n, edges, p), rng.uniform(0, np.pi, 2 * p), W.zz_on_edges(n, edges)))
+    solo = nt.Server(max_group_rows=1)
+    alone = [solo.wait(solo.submit(*r)) for r in reqs]
+    assert solo.stats()["grouped_requests"] == 0
+    solo.close()
+    s = nt.Server(start_paused=True)
+    ids = [s.submit(*r) for r in reqs]
+    _wait_planned(s, len(ids))
+    s.resume()
+    got = [s.wait(i) for i in ids]
+    st = s.stats()
+    assert st["groups"] == 2 and st["grouped_requests"] == 12 and st["peak_inflight"] == 12
+    for a, g in zip(alone, got):
+        assert a["status"] == g["status"] == nt.TC_OK, g["error"]
+        assert a["energy"] == g["energy"] and np.array_equal(a["grad"], g["grad"])
+    for k in (0, 5, 10):
+        circ, th, ham = reqs[k]
+        assert_energy_close([got[k]["energy"]], [sv.energy(sv.run_circuit(circ, th), circ.n, ham)[0]])
+        assert_grad_close(got[k]["grad"], G.parameter_shift(circ, th, ham))
+    s.close()
+
+
+def test_group_is_cut_to_the_memory_budget():
+    rng = np.random.default_rng(12)
+    edges = W.random_regular3(18, rng)
+    reqs = [(W.qaoa_circuit(18, edges, 1), rng.uniform(0, np.pi, 2), W.zz_on_edges(18, edges)) for _ in range(8)]
+    budget = 24 << 20  # room for about four rows of two 2 MiB states
+    s = nt.Server(mem_budget_bytes=budget, start_paused=True)
+    ids = [s.submit(*r) for r in reqs]
+    _wait_planned(s, len(ids))
+    s.resume()
+    got = [s.wait(i) for i in ids]
+    st = s.stats()
+    assert all(g["status"] == nt.TC_OK for g in got)
+    assert st["peak_bytes"] <= budget and st["groups"] >= 2
+    circ, th, ham = reqs[7]
+    assert_energy_close([got[7]["energy"]], [sv.energy(sv.run_circuit(circ, th), circ.n, ham)[0]])
+    s.close()

@@ -78,3 +78,34 @@ def test_destroy_with_pending_requests_does_not_hang():
     t0 = time.monotonic()
     s.close()
     assert time.monotonic() - t0 < 5
+
+
+def test_requests_are_planned_while_paused():
+    """Planner threads compile queued plans on the host before admission."""
+    s = nt.Server(start_paused=True, planner_threads=3)
+    ids = [s.submit(*_qaoa(n=8 + 2 * (i % 4), p=1 + i % 3, seed=i)) for i in range(12)]
+    t0 = time.monotonic()
+    while s.stats()["planned"] < len(ids) and time.monotonic() - t0 < 10:
+        time.sleep(0.01)
+    st = s.stats()
+    assert st["planned"] == st["pending"] == len(ids)
+    assert st["groups"] == 0 and st["inflight"] == 0
+    s.cancel(ids[3])
+    assert s.stats()["planned"] == len(ids) - 1
+    s.close()
+
+
+def test_bad_pauli_sum_fails_in_planning_not_at_submit():
+    """A Pauli sum that passes tc_submit's checks but not the planner's (a
+    non-finite weight) completes with TC_E_INVALID once admitted; while the
+    server is paused it stays pending, planned as failed."""
+    s = nt.Server(start_paused=True)
+    circ, th, ham = _qaoa()
+    w = ham.weights.copy()
+    w[0] = np.nan
+    rid = s.submit(circ, th, W.PauliSum(ham.structures, w))
+    time.sleep(0.2)
+    st = s.stats()
+    assert st["pending"] == 1 and st["planned"] == 0
+    assert s.poll(rid) is None
+    s.close()
