@@ -463,36 +463,53 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
     d_th = torch.as_tensor(theta, device="cuda")
     st = torch.empty((1, 1 << 10), dtype=torch.complex128, device="cuda")
     Hs = [nt.Hamiltonian(o) for o in obs]
+    O2 = nt.Observables(obs)
+    vals = torch.empty((1, 2), dtype=torch.float64, device="cuda")
     e_out = [torch.empty(1, dtype=torch.float64, device="cuda") for _ in Hs]
 
-    def one():
+    def one():  # the state and both observables in one call (one launch)
+        c.apply_expect(d_th, O2, 1, states=st, values=vals)
+
+    def one_tile():  # the same through the tile passes: state, then one Pauli-sum call per observable
         c.apply(d_th, 1, out=st)
         for H, e in zip(Hs, e_out):
             c.expect(st, H, out=e)
 
+    def median_us(fn, n=1000):
+        # per-call latency: CUDA events around each call, median
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for e0, e1 in ev:
+            e0.record()
+            fn()
+            e1.record()
+        torch.cuda.synchronize()
+        return float(np.median([e0.elapsed_time(e1) for e0, e1 in ev])) * 1e3
+
+    one_tile()
+    med_tile = median_us(one_tile)
+    zz_tile, x5_tile = float(e_out[0].item()), float(e_out[1].item())
     ms1 = _time_cuda(one, 200)
-    # per-call latency: CUDA events around each call, median of 1000
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(1000)]
-    for e0, e1 in ev:
-        e0.record()
-        one()
-        e1.record()
-    torch.cuda.synchronize()
-    med1 = float(np.median([e0.elapsed_time(e1) for e0, e1 in ev]))
+    med1 = median_us(one)
     Bb = 65536
     d_thb = torch.as_tensor(np.tile(theta, (Bb, 1)), device="cuda")
     stb = torch.empty((Bb, 1 << 10), dtype=torch.complex128, device="cuda")
+    valb = torch.empty((Bb, 2), dtype=torch.float64, device="cuda")
     msb = _time_cuda(lambda: c.apply(d_thb, Bb, out=stb), 5, warm=2)
+    msb1 = _time_cuda(lambda: c.apply_expect(d_thb, O2, Bb, states=stb, values=valb), 5, warm=2)
+    v = vals.cpu().numpy()[0]
     out["hea10_c128"] = {"us_per_circuit_state_and_2_observables": ms1 * 1e3,
-                         "us_median_of_1000": med1 * 1e3,
-                         "batched_states_per_s": Bb / (msb / 1e3), "batch": Bb,
-                         "zz01": float(e_out[0].item()), "x5": float(e_out[1].item())}
+                         "us_median_of_1000": med1, "path": "tc_apply_expect, one cluster launch",
+                         "us_median_of_1000_tile_passes": med_tile,
+                         "batched_states_per_s": Bb / (msb / 1e3),
+                         "batched_states_and_2_observables_per_s": Bb / (msb1 / 1e3), "batch": Bb,
+                         "zz01": float(v[0]), "x5": float(v[1])}
     if check:
         ref = sv.run_circuit(circ, theta[0])
         got = st[0].cpu().numpy()
         out["hea10_c128"]["err_vs_oracle"] = {
             "amp_max_abs": float(np.abs(got - ref).max()), "amp_tol": 1e-12,
-            "obs_max_abs": max(abs(float(e_out[i].item()) - sv.energy(ref, 10, o)[0]) for i, o in enumerate(obs)),
+            "obs_max_abs": max(abs(float(v[i]) - sv.energy(ref, 10, o)[0]) for i, o in enumerate(obs)),
+            "obs_tile_path_max_abs": max(abs(x - sv.energy(ref, 10, o)[0]) for x, o in zip((zz_tile, x5_tile), obs)),
             "batched_amp_max_abs": float(np.abs(stb[Bb - 1].cpu().numpy() - ref).max())}
     del stb, d_thb
     # ---- light-cone TN, 200-qubit brickwork depth 8, <Z99 Z100> -----------

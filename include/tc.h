@@ -216,6 +216,30 @@ TC_API tc_status tc_apply_layers(const tc_circuit* c, const double* d_params, in
                           void* stream);
 
 /*
+ * tc_apply_expect — the state of every row and K Pauli-sum expectations of it
+ * in one call: the "Plain method" of Section "Basic circuits and outputs"
+ * (state, then c.expectation_ps per observable), equal to tc_apply_layers
+ * (circuit's tc_init state, no noise) followed by K tc_expect_pauli_sum calls.
+ *   T             host [K]: terms of observable k
+ *   structures    host [sum T][n] bytes 0..3 (I, X, Y, Z), observables in order
+ *   weights       host [sum T] doubles
+ *   d_states_out  device [B][2^n] complex of the circuit's dtype, or NULL
+ *   d_values_out  device [B][K] doubles (written; may be NULL if K == 0)
+ * Circuits of 5..10 qubits without noise events run as one launch per call:
+ * one thread-block cluster per row (up to 8 CTAs of 128 amplitudes) holds
+ * the state in shared memory; gates exchange partner amplitudes by warp
+ * shuffles, shared memory or distributed shared memory; consecutive one-qubit
+ * ops on a qubit are fused; each observable is reduced in FP64.  Up to 16
+ * observables and 256 terms take that path; other circuits run the tile
+ * passes and one Pauli-sum call per observable (scratch from the stream's
+ * memory pool when d_states_out is NULL).  Errors: TC_E_INVALID for bad
+ * sizes or structure entries, TC_E_UNSUPPORTED for density-matrix circuits.
+ */
+TC_API tc_status tc_apply_expect(tc_circuit* c, const double* d_params, int B, int K, const int* T,
+                                 const uint8_t* structures, const double* weights, void* d_states_out,
+                                 double* d_values_out, void* stream);
+
+/*
  * tc_expect_pauli_sum — E_b = sum_j w_j Re<psi_b|P_j|psi_b> for every row
  * (Eq. H-pauli; the "vmap over Pauli structures" evaluation of Section
  * "vmap over Pauli structures", fused: terms are grouped by their X/Y flip
@@ -379,7 +403,8 @@ TC_API tc_status tc_expect_pauli_sum_noalloc(const tc_circuit* c, const void* d_
  * summed algorithmic HBM bytes (each amplitude a launch must read or write,
  * counted once).  Kinds: 0 forward tile pass, 1 adjoint tile pass,
  * 2 Pauli-sum pass, 3 finalize reduction, 4 narrow-state padding,
- * 5 unfused per-term reduction, 6 per-row gate-table build.  `out` may be
+ * 5 unfused per-term reduction, 6 per-row gate-table build, 7 one-launch
+ * small-circuit kernel (tc_apply_expect).  `out` may be
  * NULL to count kinds only.
  */
 typedef struct {

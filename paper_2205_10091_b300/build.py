@@ -16,7 +16,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtc_b300.so")
 
 SOURCES = ["sv_kernels.cu", "planner.cpp", "abi.cpp", "jit.cpp", "noalloc.cu", "tn.cpp", "tn_kernels.cu", "tn_tc.cu", "qgt.cu", "server.cpp", "dm.cpp",
-           "dm_kernels.cu"]
+           "dm_kernels.cu", "small.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I", os.path.join(ROOT, "include"),

@@ -85,6 +85,7 @@ tc_circuit::~tc_circuit() {
   dev_free(d_qgt_occ);
   dev_free(qgt_ws);
   for (auto* sg : ckpt_segs) delete sg;
+  small_free(small);
 }
 
 namespace {
@@ -245,6 +246,8 @@ tc_status run_ham(tc_circuit* c, KArgs a, int rows, bool store_lambda, cudaStrea
 }  // namespace
 
 namespace tcb {
+
+tc_status circuit_upload(tc_circuit* c) { return ensure_device(c); }
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 

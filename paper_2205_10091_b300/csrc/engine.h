@@ -50,6 +50,10 @@ struct DevHam {
 struct tc_circuit;
 
 namespace tcb {
+struct SmallPlan;
+void small_free(SmallPlan* p);
+tc_status circuit_upload(tc_circuit* c);  // plan and matrix pool on the device (first compute call)
+bool small_eligible(tc_circuit* c);
 // Workspace of tc_expect_grad per row / for `chunk` rows, and its body with a
 // caller-provided workspace (used by the serving loop).
 size_t grad_row_bytes(const tc_circuit* c);
@@ -153,6 +157,11 @@ struct tc_circuit {
   uint32_t* d_qgt_pauli = nullptr; // [occ][3] generator: flip mask, sign mask, number of Y
   void* qgt_ws = nullptr;
   size_t qgt_ws_bytes = 0;
+
+  // the one-launch path of tc_apply_expect (small.cu; built on first use)
+  tcb::SmallPlan* small = nullptr;
+  bool small_tried = false;
+  std::string small_why;
 
   // checkpointed gradients (TC_GRAD_CHECKPOINT): the op list cut into
   // segments of ckpt_ops ops, each planned as a circuit of its own

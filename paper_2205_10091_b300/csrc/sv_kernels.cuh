@@ -47,7 +47,7 @@ cudaError_t launch_norm2(bool dbl, const void* psi, int n_qubits, int rows, int 
 cudaError_t launch_mean_stderr(const double* x, int n, double* out, cudaStream_t s);
 
 // Optional event timing of every launch (enabled by tc_profile_begin).
-enum ProfKind : int { PK_FWD = 0, PK_BWD = 1, PK_HAM = 2, PK_FINALIZE = 3, PK_PAD = 4, PK_PLAIN = 5, PK_TABLES = 6, PK_COUNT = 7 };
+enum ProfKind : int { PK_FWD = 0, PK_BWD = 1, PK_HAM = 2, PK_FINALIZE = 3, PK_PAD = 4, PK_PLAIN = 5, PK_TABLES = 6, PK_SMALL = 7, PK_COUNT = 8 };
 void prof_begin();
 bool prof_enabled();
 void prof_before(int kind, double algo_bytes, cudaStream_t s);

@@ -125,7 +125,7 @@ class tc_kernel_stat(C.Structure):
 
 
 KERNEL_KINDS = ["tile_pass_forward", "tile_pass_adjoint", "pauli_sum_pass", "finalize", "pad", "plain_term",
-                "gate_tables"]
+                "gate_tables", "one_launch_small"]
 
 assert C.sizeof(tc_op) == W.OP_DTYPE.itemsize == 56
 
@@ -147,6 +147,8 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p]),
     "tc_expect_pauli_sum": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                       C.c_void_p]),
+    "tc_apply_expect": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_expect_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_uint64,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tc_expect_plain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
@@ -261,6 +263,23 @@ class Hamiltonian:
         return (self.structures.ctypes.data_as(C.c_void_p), self.weights.ctypes.data_as(C.c_void_p), self.T)
 
 
+class Observables:
+    """K Pauli sums in tc_apply_expect's layout (term counts, concatenated
+    structures and weights), marshalled once."""
+
+    def __init__(self, sums):
+        hs = [s if isinstance(s, Hamiltonian) else Hamiltonian(s) for s in sums]
+        self.K = len(hs)
+        self.T = (C.c_int * max(self.K, 1))(*[h.T for h in hs])
+        n = hs[0].structures.shape[1] if hs else 0
+        self.structures = np.ascontiguousarray(
+            np.concatenate([h.structures.reshape(-1, n) for h in hs]) if hs else np.zeros((0, 0)), dtype=np.uint8)
+        self.weights = np.ascontiguousarray(np.concatenate([h.weights for h in hs]) if hs else np.zeros(0),
+                                            dtype=np.float64)
+        self._args = (C.cast(self.T, C.c_void_p), self.structures.ctypes.data_as(C.c_void_p),
+                      self.weights.ctypes.data_as(C.c_void_p))
+
+
 class Circuit:
     """Owns a tc_circuit handle compiled from a workloads.Circuit."""
 
@@ -312,6 +331,21 @@ class Circuit:
         _check(lib().tc_apply_layers(self.h, _ptr(params), B, _ptr(init), C.c_uint64(seed), _ptr(status),
                                      C.c_int64(row_offset), _ptr(out), _stream(stream)))
         return out
+
+    def apply_expect(self, params, obs: Observables, B: int, states=None, values=None, store_state: bool = True,
+                     stream=None):
+        """States and K expectations in one call (tc_apply_expect): (states or
+        None, values [B][K] float64)."""
+        import torch
+
+        if states is None and store_state:
+            states = torch.empty((B, 1 << self.n), dtype=self.state_dtype, device="cuda")
+        if values is None:
+            values = torch.empty((B, obs.K), dtype=torch.float64, device="cuda")
+        t, s, w = obs._args
+        _check(lib().tc_apply_expect(self.h, _ptr(params), B, obs.K, t, s, w, _ptr(states), _ptr(values),
+                                     _stream(stream)))
+        return states, values
 
     def expect(self, states, ham: Hamiltonian, out=None, stream=None):
         import torch

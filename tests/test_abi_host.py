@@ -228,3 +228,16 @@ def test_grad_options_validated_before_any_device_work():
     go = nt.tc_grad_options(nt.TC_GRAD_CHECKPOINT, 0, 3)
     assert L.tc_expect_grad(cn.h, None, 1, s, w, T, C.c_uint64(0), fake, None, C.byref(go), None) == \
         nt.TC_E_UNSUPPORTED
+
+
+def test_apply_expect_validates_on_the_host():
+    import ctypes as C
+
+    L = nt.lib()
+    c = nt.Circuit(W.hea10_workload()[0], dtype=nt.TC_C128)
+    fake = C.c_void_p(16)  # never dereferenced: validation fails first
+    T = (C.c_int * 1)(-1)
+    assert L.tc_apply_expect(c.h, fake, 1, 1, None, None, None, None, fake, None) == nt.TC_E_INVALID
+    assert L.tc_apply_expect(c.h, fake, 1, 1, C.cast(T, C.c_void_p), None, None, None, fake, None) == nt.TC_E_INVALID
+    assert L.tc_apply_expect(c.h, fake, -1, 0, None, None, None, None, None, None) == nt.TC_E_INVALID
+    assert L.tc_apply_expect(c.h, fake, 0, 0, None, None, None, None, None, None) == nt.TC_OK
