@@ -213,8 +213,9 @@ KArgs base_args(const tc_circuit* c, const DevPlan& dp) {
     if (_e != cudaSuccess) return cuda_fail(_e, where); \
   } while (0)
 
+// keep_lambda: the adjoint sweep's lambda is read afterwards (checkpoint segments)
 tc_status run_schedule(tc_circuit* c, int mode, const Schedule& sc, const PlanArrays& A, KArgs a, void* tables,
-                       int rows, cudaStream_t s) {
+                       int rows, cudaStream_t s, bool keep_lambda = false) {
   a.tables = tables;
   a.table_stride = sc.table_total;
   TC_CHECK_CUDA(launch_tables(is_dbl(c), a, sc.first_mat, sc.n_mats, rows, s), "gate tables");
@@ -226,9 +227,12 @@ tc_status run_schedule(tc_circuit* c, int mode, const Schedule& sc, const PlanAr
     if (spec)
       TC_CHECK_CUDA(launch_pass_specialised(c->jit_kern[a.pass], mode, is_dbl(c), a, A.passes[a.pass], rows, s),
                     mode == KM_FWD ? "forward pass (specialised)" : "adjoint pass (specialised)");
-    else
-      TC_CHECK_CUDA(launch_pass(mode, is_dbl(c), a, A.passes[a.pass], &A.stages[A.passes[a.pass].stage_off], rows, s),
+    else {
+      DevPass hp = A.passes[a.pass];
+      if (keep_lambda) hp.flags &= ~PF_SKIP_LAM;
+      TC_CHECK_CUDA(launch_pass(mode, is_dbl(c), a, hp, &A.stages[hp.stage_off], rows, s),
                     mode == KM_FWD ? "forward pass" : "adjoint pass");
+    }
   }
   return TC_OK;
 }
@@ -753,7 +757,7 @@ tc_status expect_grad_ckpt_run(tc_circuit* c, const double* d_params, int B, uin
       a.theta = th;
       a.seed = seed;
       a.row_offset = r0;
-      if ((st = run_schedule(sg, KM_BWD, sg->bwd, sg->A, a, w + o_tab, rows, s)) != TC_OK) return st;
+      if ((st = run_schedule(sg, KM_BWD, sg->bwd, sg->A, a, w + o_tab, rows, s, k > 0)) != TC_OK) return st;
       const size_t tiles_b = (size_t)1 << (sg->N - sg->k_bwd);
       TC_CHECK_CUDA(launch_finalize((double*)(w + o_ep), nh, (int)tiles_h, (double*)(w + o_gp), sg->bwd.n_gslots,
                                     (int)tiles_b, sg->d_csr_off, sg->d_csr_slots, c->n_params, rows,

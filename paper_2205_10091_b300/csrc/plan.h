@@ -190,6 +190,8 @@ enum : int32_t {
   PF_FULL = 8,       // the pass needs the full instruction set (CNOT, 4x4, multi-entry groups)
   PF_LEAN = 16,      // the pass needs more than rotation layers (RX, H, X, noise, 2x2, CZ groups)
   PF_MULTI = 32,     // the pass has an XOR-type diagonal group with several entries
+  PF_SKIP_PSI = 64,  // adjoint pass: psi is not written back (the last pass of an adjoint sweep)
+  PF_SKIP_LAM = 128, // adjoint pass: lambda is not written back (cleared at launch when lambda is still needed)
 };
 
 struct DevPass {

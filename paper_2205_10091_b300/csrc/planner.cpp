@@ -745,6 +745,8 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
   }
   sc.n_passes = (int)A.passes.size() - sc.first_pass;
   sc.n_mats = (int)A.mats.size() - sc.first_mat;
+  // the states after an adjoint sweep's last pass are not needed
+  if (adjoint && sc.n_passes > 0) A.passes.back().flags |= PF_SKIP_PSI | PF_SKIP_LAM;
   return sc;
 }
 

@@ -1196,7 +1196,9 @@ __device__ __forceinline__ void gate_pass(const KArgs& a, const PassArgs& pa) {
       for (int q = 0; q < n_instr; ++q) exec(ins[instr_off + q]);
     }
   }
-  if (sc != (T)1 || sl != (T)0) {
+  const bool skip_psi = MODE == KM_BWD && (sp.flags & PF_SKIP_PSI);
+  const bool skip_lam = MODE == KM_BWD && (sp.flags & PF_SKIP_LAM);
+  if ((sc != (T)1 || sl != (T)0) && !(skip_psi && skip_lam)) {
     const T se = sc + sl;
     const V s2 = mk<V>(se, se);
 #pragma unroll
@@ -1205,9 +1207,9 @@ __device__ __forceinline__ void gate_pass(const KArgs& a, const PassArgs& pa) {
       if (MODE == KM_BWD) L[i] = cmul_re(s2, L[i]);
     }
   }
-  store_regs<RB>(A, psi, m);
+  if (!skip_psi) store_regs<RB>(A, psi, m);
   if (MODE == KM_BWD) {
-    store_regs<RB>(L, lam, m);
+    if (!skip_lam) store_regs<RB>(L, lam, m);
 #pragma unroll
     for (int g = 0; g < kLocalSlots; ++g) {
       if (g >= sp.n_gslots) break;

@@ -740,7 +740,8 @@ bool prof_end(int* launches, double* ms, double* bytes) {
 static double pass_bytes(int mode, bool dbl, const DevPass& hp, const KArgs& a, int rows) {
   const double amps = (double)rows * (double)(1ull << a.N) * (dbl ? 16.0 : 8.0);
   if (mode == KM_FWD) return amps * (((hp.flags & PF_INIT) && a.synth_init) ? 1.0 : 2.0);
-  if (mode == KM_BWD) return amps * 4.0;
+  if (mode == KM_BWD)
+    return amps * (2.0 + ((hp.flags & PF_SKIP_PSI) ? 0.0 : 1.0) + ((hp.flags & PF_SKIP_LAM) ? 0.0 : 1.0));
   double t = 1.0;  // psi read
   if ((hp.flags & PF_LAM_LOAD) && a.lam) t += 1.0;
   if ((hp.flags & PF_LAM_STORE) && a.lam && a.store_lambda) t += 1.0;
