@@ -394,7 +394,7 @@ def run_gpu(args):
                     for k, v in prof.items()},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "peak_source": f"{peak_src} hbm_gbs",
-                     "traffic": traffic},
+                     "traffic": traffic, "binding": _binding(kname)},
         "plain_path": {"value": 1e3 / plain_ms, "unit": "forward+energy evals/s", "rows": 1,
                        "ms_per_eval": plain_ms, "what": "unfused: one HBM sweep per gate, one per Pauli term"},
         "clocks": clk,
@@ -771,6 +771,36 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
         out["qaoa_serving"]["err_vs_oracle"] = {"energy_max_abs": max(de), "grad_max_abs": max(dg),
                                                 "requests": len(sampled), "qubits": [p[0][0].n for p in sampled],
                                                 "grad_ref": "central differences, h = 1e-5"}
+    return out
+
+
+def _profile_kv(kernel: str):
+    """'key: value' lines of the committed ncu summary of `kernel`
+    (profiles/traffic_<kernel>.txt), or None when the file is absent or the
+    tile-pass sources changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    return kv if kv.get("source_hash") == _source_hash() else None
+
+
+def _binding(kernel: str):
+    """The roof that binds `kernel`, from the same ncu capture as its traffic."""
+    kv = _profile_kv(kernel)
+    if not kv or "binding" not in kv:
+        return None
+    out = {"roof": kv["binding"], "source": f"profiles/traffic_{kernel}.txt (ncu, same source hash)"}
+    for k in ("issue_active", "fp32_tflops", "fp32_peak_tflops"):
+        if k in kv:
+            out[k] = float(kv[k])
+    if "fp32_tflops" in out and "fp32_peak_tflops" in out:
+        out["fp32_frac"] = out["fp32_tflops"] / out["fp32_peak_tflops"]
     return out
 
 
