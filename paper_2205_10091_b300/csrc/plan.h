@@ -88,7 +88,8 @@ enum : int8_t {
 struct DevInstr {  // 16 bytes
   int8_t kind;
   int8_t j0, j1;   // register-bit indices
-  int8_t jc;       // CNOT: register bit of the control, or -1 (control from the thread base)
+  int8_t jc;       // CNOT: register bit of the control, or -1 (control from the thread base);
+                   // gradient instructions: 1 = the last of its gradient slot in the pass
   int16_t pos;     // CNOT: global position of the control
   int16_t gslot;   // local gradient slot (-1 = none)
   int32_t slot;    // table entry (or diagonal-group index for IK_DIAG / IK_GRADDIAG)
@@ -192,6 +193,8 @@ enum : int32_t {
   PF_MULTI = 32,     // the pass has an XOR-type diagonal group with several entries
   PF_SKIP_PSI = 64,  // adjoint pass: psi is not written back (the last pass of an adjoint sweep)
   PF_SKIP_LAM = 128, // adjoint pass: lambda is not written back (cleared at launch when lambda is still needed)
+  PF_GFLUSH = 256,   // adjoint pass: each gradient slot's last instruction is marked (jc = 1); compiled passes
+                     // reduce the slot there instead of at the end of the pass
 };
 
 struct DevPass {

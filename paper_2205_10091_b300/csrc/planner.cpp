@@ -739,6 +739,23 @@ Schedule build_schedule(const std::vector<HGate>& gates, int N, int k, int rb, b
     P.n_gslots = (int)local_slot.size();
     sc.n_gslots += P.n_gslots;
     sc.n_stages += P.n_stages;
+    if (adjoint && P.n_gslots > 0) {
+      // mark each gradient slot's last instruction in execution order (stage
+      // by stage): the kernel reduces the slot there, so its accumulator is
+      // live over the slot's own gates only
+      std::vector<int> last(P.n_gslots, -1);
+      for (int si = 0; si < P.n_stages; ++si) {
+        const DevStage& S = A.stages[P.stage_off + si];
+        for (int q = 0; q < S.n_instr; ++q) {
+          const int ii = P.instr_off + S.instr_off + q;
+          const DevInstr& in = A.instrs[ii];
+          if (in.kind != IK_CNOT && in.gslot >= 0 && in.gslot < P.n_gslots) last[in.gslot] = ii;
+        }
+      }
+      for (int ii : last)
+        if (ii >= 0) A.instrs[ii].jc = 1;
+      P.flags |= PF_GFLUSH;
+    }
     A.passes.push_back(P);
     remaining = deferred;
     first = false;

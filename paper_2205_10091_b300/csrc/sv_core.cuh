@@ -1174,6 +1174,18 @@ __device__ __forceinline__ void gate_pass(const KArgs& a, const PassArgs& pa) {
         default:
           break;
       }
+      // the last instruction of its gradient slot in this pass: reduce the
+      // slot now (the same sum as at the end of the pass, one reduction).  In
+      // a compiled pass this ends the accumulator's register live range; the
+      // interpreter keeps its accumulators in local memory and reduces at the end
+      if (Src::kConst && MODE == KM_BWD && in.kind != IK_CNOT && in.jc == 1 && in.gslot >= 0 &&
+          in.gslot < kLocalSlots) {
+        T v = gl[in.gslot];
+        gl[in.gslot] = 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[in.gslot * nwarps + warp] += (double)v;
+      }
   };
   if constexpr (Src::kConst) {
     // a generated program: every stage and instruction a compile-time constant
@@ -1212,7 +1224,7 @@ __device__ __forceinline__ void gate_pass(const KArgs& a, const PassArgs& pa) {
     if (!skip_lam) store_regs<RB>(L, lam, m);
 #pragma unroll
     for (int g = 0; g < kLocalSlots; ++g) {
-      if (g >= sp.n_gslots) break;
+      if (g >= sp.n_gslots || (Src::kConst && (sp.flags & PF_GFLUSH))) break;
       T v = gl[g];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
