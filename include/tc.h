@@ -365,6 +365,21 @@ TC_API tc_status tc_state_norms(tc_circuit* c, const void* d_states, int B, doub
 TC_API tc_status tc_mean_stderr(const double* d_x, int n, double* d_out, void* stream);
 
 /*
+ * Trajectories split over ranks (one process per GPU, each with its own
+ * trajectory rows).  tc_shard_moments writes a shard's (count, mean, M2 =
+ * sum of squared deviations from the mean) of d_x[0..n) to device d_out[0..2]
+ * in FP64 (fixed-order reduction).  tc_merge_moments (host only) combines R
+ * shards' triples, parts [R][3] in rank order, by the pairwise update of
+ * sample variances (Chan, Golub and LeVeque) into out[0] = mean and out[1] =
+ * standard error (ddof = 1): the same triples in the same order give the same
+ * bits on every rank.  The exchange of the triples (an all-gather of 3 doubles
+ * per rank) is the caller's.  TC_E_INVALID for NULL arguments, n < 1, negative
+ * counts or M2, or no samples at all.
+ */
+TC_API tc_status tc_shard_moments(const double* d_x, int n, double* d_out, void* stream);
+TC_API tc_status tc_merge_moments(const double* parts, int R, double* out);
+
+/*
  * tc_expect_pauli_sum_noalloc — the energies of tc_expect_pauli_sum, for
  * callers that cannot allocate device memory at the call site (a fixed
  * memory reservation, an allocator callback, a latency-critical loop where

@@ -1,4 +1,5 @@
 // C-ABI entry points of libtc_b300.so (declared in include/tc.h).
+#include <cmath>
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -881,6 +882,32 @@ tc_status tc_state_norms(tc_circuit* c, const void* d_states, int B, double* d_n
 tc_status tc_mean_stderr(const double* d_x, int n, double* d_out, void* stream) {
   if (!d_x || !d_out || n < 1) return fail(TC_E_INVALID, "NULL argument or n < 1");
   TC_CHECK_CUDA(launch_mean_stderr(d_x, n, d_out, (cudaStream_t)stream), "mean/stderr");
+  return TC_OK;
+}
+
+tc_status tc_shard_moments(const double* d_x, int n, double* d_out, void* stream) {
+  if (!d_x || !d_out || n < 1) return fail(TC_E_INVALID, "NULL argument or n < 1");
+  TC_CHECK_CUDA(launch_mean_stderr(d_x, n, d_out, (cudaStream_t)stream, true), "shard moments");
+  return TC_OK;
+}
+
+tc_status tc_merge_moments(const double* parts, int R, double* out) {
+  if (!parts || !out || R < 1) return fail(TC_E_INVALID, "NULL argument or R < 1");
+  // pairwise update of (count, mean, M2) in the given order (Chan, Golub and
+  // LeVeque's combination of sample variances)
+  double n = 0, mean = 0, m2 = 0;
+  for (int r = 0; r < R; ++r) {
+    const double nb = parts[3 * r], mb = parts[3 * r + 1], m2b = parts[3 * r + 2];
+    if (!(nb >= 0) || !std::isfinite(mb) || !(m2b >= 0)) return fail(TC_E_INVALID, "bad shard moments");
+    if (nb == 0) continue;
+    const double t = n + nb, d = mb - mean;
+    mean += d * (nb / t);
+    m2 += m2b + d * d * (n * nb / t);
+    n = t;
+  }
+  if (n < 1) return fail(TC_E_INVALID, "no samples in any shard");
+  out[0] = mean;
+  out[1] = n > 1 ? std::sqrt(m2 / (n - 1) / n) : 0.0;
   return TC_OK;
 }
 

@@ -226,8 +226,10 @@ __device__ void build_mat(const DevMat& m, V* tab, const double* th, const doubl
 }
 
 // Mean and standard error (sample std, ddof = 1, over sqrt(n)) of n doubles,
-// FP64, fixed-order reduction (one block).
-__global__ void __launch_bounds__(256) k_mean_stderr(const double* x, int n, double* out) {
+// FP64, fixed-order reduction (one block); moments = 1: out = (n, mean, M2)
+// with M2 the sum of squared deviations from the mean (one shard's share of a
+// split estimate).
+__global__ void __launch_bounds__(256) k_mean_stderr(const double* x, int n, double* out, int moments) {
   __shared__ double s1[256], s2[256];
   double a = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) a += x[i];
@@ -247,13 +249,19 @@ __global__ void __launch_bounds__(256) k_mean_stderr(const double* x, int n, dou
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[0] = mean;
-    out[1] = n > 1 ? sqrt(s2[0] / (n - 1) / n) : 0.0;
+    if (moments) {
+      out[0] = n;
+      out[1] = mean;
+      out[2] = s2[0];
+    } else {
+      out[0] = mean;
+      out[1] = n > 1 ? sqrt(s2[0] / (n - 1) / n) : 0.0;
+    }
   }
 }
 
-cudaError_t launch_mean_stderr(const double* x, int n, double* out, cudaStream_t s) {
-  k_mean_stderr<<<1, 256, 0, s>>>(x, n, out);
+cudaError_t launch_mean_stderr(const double* x, int n, double* out, cudaStream_t s, bool moments) {
+  k_mean_stderr<<<1, 256, 0, s>>>(x, n, out, moments ? 1 : 0);
   return cudaGetLastError();
 }
 

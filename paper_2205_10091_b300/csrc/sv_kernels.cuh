@@ -44,7 +44,7 @@ cudaError_t launch_plain_term(bool dbl, const void* psi, int N, int rows, uint32
 cudaError_t launch_norm2(bool dbl, const void* psi, int n_qubits, int rows, int nblk, double* part, cudaStream_t s);
 
 // Mean and standard error of n doubles into out[0], out[1].
-cudaError_t launch_mean_stderr(const double* x, int n, double* out, cudaStream_t s);
+cudaError_t launch_mean_stderr(const double* x, int n, double* out, cudaStream_t s, bool moments = false);
 
 // Optional event timing of every launch (enabled by tc_profile_begin).
 enum ProfKind : int { PK_FWD = 0, PK_BWD = 1, PK_HAM = 2, PK_FINALIZE = 3, PK_PAD = 4, PK_PLAIN = 5, PK_TABLES = 6, PK_SMALL = 7, PK_COUNT = 8 };

@@ -169,6 +169,8 @@ SIGNATURES = {
                                        C.POINTER(C.c_void_p)]),
     "tc_tn_circuit_expect": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tc_mean_stderr": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "tc_shard_moments": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "tc_merge_moments": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "tc_state_norms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tc_server_create": (C.c_int, [C.POINTER(tc_server_options), C.POINTER(C.c_void_p)]),
     "tc_submit": (C.c_int, [C.c_void_p, C.POINTER(tc_request), C.POINTER(C.c_uint64)]),
@@ -249,6 +251,40 @@ def mean_stderr(x, out=None, stream=None):
         out = torch.empty(2, dtype=torch.float64, device="cuda")
     _check(lib().tc_mean_stderr(_ptr(x), x.numel(), _ptr(out), _stream(stream)))
     return out
+
+
+def shard_moments(x, out=None, stream=None):
+    """(count, mean, M2) of this rank's CUDA float64 values (tc_shard_moments)."""
+    import torch
+
+    if out is None:
+        out = torch.empty(3, dtype=torch.float64, device="cuda")
+    _check(lib().tc_shard_moments(_ptr(x), x.numel(), _ptr(out), _stream(stream)))
+    return out
+
+
+def merge_moments(parts) -> tuple:
+    """(mean, standard error) from the ranks' (count, mean, M2) triples, in
+    rank order (tc_merge_moments, host)."""
+    p = np.ascontiguousarray(np.asarray(parts, dtype=np.float64).reshape(-1, 3))
+    out = np.zeros(2)
+    _check(lib().tc_merge_moments(p.ctypes.data_as(C.c_void_p), p.shape[0], out.ctypes.data_as(C.c_void_p)))
+    return float(out[0]), float(out[1])
+
+
+def mean_stderr_across_ranks(x, group=None):
+    """Monte Carlo estimate over trajectories split across torch.distributed
+    ranks: each rank's triple on its GPU, an all-gather of the triples, the
+    same rank-ordered merge on every rank."""
+    import torch
+    import torch.distributed as dist
+
+    m = shard_moments(x)
+    if dist.get_backend(group) != "nccl":
+        m = m.cpu()
+    parts = [torch.empty_like(m) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(parts, m, group=group)
+    return merge_moments(torch.stack(parts).cpu().numpy())
 
 
 class Hamiltonian:

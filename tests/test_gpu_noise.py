@@ -120,3 +120,22 @@ def test_folded_noise_gradients_per_trajectory(dtype):
         else:
             assert_energy_close(e[r:r + 1], [e_ref])
             assert_grad_close(g[r], g_ref)
+
+
+def test_shard_moments_merge_to_mean_stderr():
+    """Trajectory values split in three shards: each shard's (count, mean, M2)
+    from tc_shard_moments, merged on the host, equals tc_mean_stderr of the
+    whole set and numpy's estimate."""
+    import torch
+
+    rng = np.random.default_rng(12)
+    x = rng.normal(0.3, 1.0, size=10_000)
+    xd = torch.as_tensor(x, device="cuda")
+    parts = [nt.shard_moments(xd[a:b]).cpu().numpy() for a, b in [(0, 3000), (3000, 3001), (3001, 10_000)]]
+    for (a, b), p in zip([(0, 3000), (3000, 3001), (3001, 10_000)], parts):
+        s = x[a:b]
+        assert p[0] == len(s) and abs(p[1] - s.mean()) <= 1e-14 and abs(p[2] - ((s - s.mean()) ** 2).sum()) <= 1e-9
+    m, se = nt.merge_moments(parts)
+    whole = nt.mean_stderr(xd).cpu().numpy()
+    assert abs(m - whole[0]) <= 1e-14 and abs(se - whole[1]) <= 1e-15
+    assert abs(m - x.mean()) <= 1e-14 and abs(se - x.std(ddof=1) / np.sqrt(len(x))) <= 1e-15
