@@ -35,7 +35,7 @@ namespace {
 
 constexpr int kGramTile = 64;    // states per tile side
 constexpr int kGramX = 16;       // amplitudes per shared-memory stage
-constexpr int kGramChunk = 2048; // amplitudes summed in the state's precision before the FP64 atomics
+constexpr int kGramChunk = 2048; // amplitudes summed in the state's precision per chunk partial
 
 template <typename R>
 struct Cplx;
@@ -90,6 +90,16 @@ __global__ void k_qgt_pauli(const C2* __restrict__ phi, int R, int64_t L, const 
 
 // M[r][k][l] += sum_x conj(psi_{r,k}[x]) psi_{r,l}[x] over one amplitude
 // chunk, for the tile pair (kt <= lt) of blockIdx.x; 4 x 4 outputs a thread.
+// The Gram partials of the amplitude chunks, summed in chunk order.
+__global__ void __launch_bounds__(256) k_gram_sum(const double* __restrict__ Mp, int nchunk, size_t per,
+                                                  double* __restrict__ M) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < per; i += (size_t)gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int y = 0; y < nchunk; ++y) s += Mp[(size_t)y * per + i];
+    M[i] = s;
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_gram(const typename Cplx<R>::T* __restrict__ states, int S, int64_t L,
                                               int64_t kstride, int ntile, double* __restrict__ M) {
@@ -150,10 +160,10 @@ __global__ void __launch_bounds__(256) k_gram(const typename Cplx<R>::T* __restr
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int k = kt * kGramTile + ty * 4 + i, l = lt * kGramTile + tx * 4 + j;
-      if (k < S && l < S) {
-        double* m = M + (((size_t)r * S + k) * S + l) * 2;
-        atomicAdd(m, (double)ar[i][j]);
-        atomicAdd(m + 1, (double)ai[i][j]);
+      if (k < S && l < S) {  // this chunk's partial (summed over chunks in fixed order later)
+        double* m = M + ((((size_t)blockIdx.y * gridDim.z + r) * S + k) * S + l) * 2;
+        m[0] = (double)ar[i][j];
+        m[1] = (double)ai[i][j];
       }
     }
 }
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(256) k_gram(const typename Cplx<R>::T* __restr
 // (its error grows with the chain length: measured 3e-3 on G over 4096
 // amplitudes, 3e-5 over 64), so each stage's MMAs start a fresh TMEM
 // accumulator and every thread adds its 64 accumulator values into FP32
-// registers (round-to-nearest) after the stage; FP64 atomics combine the
+// registers (round-to-nearest) after the stage; per-chunk FP64 partials combine the
 // CTAs.  One CTA: 128 x 128 outputs (state rows k of tile kt by rows l of
 // tile lt), Re and Im in TMEM columns [0, 128) and [128, 256), over kTcChunk
 // amplitudes.  The raw amplitudes of stage s + 1 (16 per row of the 256 rows)
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const float2* __restr
     if (k < S) {
 #pragma unroll
       for (int j = 0; j < 64; ++j)
-        if (l0 + j < S) atomicAdd(M + (((size_t)r * S + k) * S + l0 + j) * 2 + comp, (double)acc[j]);
+        if (l0 + j < S) M[((((size_t)blockIdx.y * gridDim.z + r) * S + k) * S + l0 + j) * 2 + comp] = (double)acc[j];
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -650,8 +660,12 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
   int maxc = 0;
   for (const auto& g : c->qgt_groups) maxc = std::max(maxc, g.count + 1);
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const bool tcg = !dbl;  // complex64: tensor-core Gram
+  const int64_t nchunk = (L + (tcg ? kTcChunk : kGramChunk) - 1) / (tcg ? kTcChunk : kGramChunk);
   // per row: S states, the prefix state, replicated parameters, the Gram matrix
-  const size_t row_bytes = al((size_t)S * L * amp) + al((size_t)L * amp) + al((size_t)maxc * P * 8) + al((size_t)S * S * 16);
+  // and its per-chunk partials (summed in a fixed order: reproducible bits)
+  const size_t row_bytes = al((size_t)S * L * amp) + al((size_t)L * amp) + al((size_t)maxc * P * 8) +
+                           al((size_t)S * S * 16) + al((size_t)nchunk * S * S * 16);
   int64_t cap = c->opt.mem_budget_bytes;
   if (cap <= 0) {
     size_t fr = 0, tot = 0;
@@ -676,6 +690,7 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
   char* phi = states + al((size_t)S * L * amp) * chunk;         // [R][L]
   double* th = (double*)(phi + al((size_t)L * amp) * chunk);   // [count][R][P]
   double* M = (double*)((char*)th + al((size_t)maxc * P * 8) * chunk);
+  double* Mp = (double*)((char*)M + al((size_t)S * S * 16) * chunk);  // [nchunk][R][S][S][2]
   int* d_err = (int*)(w + row_bytes * chunk);                  // in the workspace's slack
   // complex64: tensor-core Gram (128-row tiles); complex128: FP64 CUDA-core Gram
   const bool tc = !dbl;
@@ -685,7 +700,6 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
   const int skip_mma = (skip_env && skip_env[0] == '1') ? 1 : 0;
   const int tile = tc ? kTcTile : kGramTile;
   const int ntile = (S + tile - 1) / tile;
-  const int64_t nchunk = (L + (tc ? kTcChunk : kGramChunk) - 1) / (tc ? kTcChunk : kGramChunk);
   if (nchunk > 65535) return fail(TC_E_UNSUPPORTED, "too many qubits for the Gram kernel");
   if (tc) {
     if ((e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem)) != cudaSuccess)
@@ -723,14 +737,17 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
         if ((st = tc_apply_layers(g.suffix, th, cnt * R, dst, 0, nullptr, 0, dst, s)) != TC_OK) return st;
       }
     }
-    if ((e = cudaMemsetAsync(M, 0, (size_t)R * S * S * 16, s)) != cudaSuccess) return cuda_fail(e, "memset");
+    const size_t per = (size_t)R * S * S * 2;  // doubles of one chunk's partial
+    if ((e = cudaMemsetAsync(Mp, 0, (size_t)nchunk * per * 8, s)) != cudaSuccess) return cuda_fail(e, "memset");
     dim3 grid((unsigned)(ntile * (ntile + 1) / 2), (unsigned)nchunk, (unsigned)R);
     if (tc)
-      k_gram_tc<<<grid, kTcThreads, kTcSmem, s>>>((const float2*)states, S, L, (int64_t)R * L, ntile, M, d_err,
+      k_gram_tc<<<grid, kTcThreads, kTcSmem, s>>>((const float2*)states, S, L, (int64_t)R * L, ntile, Mp, d_err,
                                                   skip_mma);
     else
-      k_gram<double><<<grid, 256, 0, s>>>((const double2*)states, S, L, (int64_t)R * L, ntile, M);
+      k_gram<double><<<grid, 256, 0, s>>>((const double2*)states, S, L, (int64_t)R * L, ntile, Mp);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gram");
+    k_gram_sum<<<grid_for((int64_t)per), 256, 0, s>>>(Mp, (int)nchunk, per, M);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "gram chunk sum");
     k_qgt_fold<<<grid_for((int64_t)R * P * P), 256, 0, s>>>(M, S, tile, c->d_qgt_off, c->d_qgt_occ, c->d_qgt_occ_c,
                                                              P, R, d_out + (size_t)r0 * P * P * 2);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "geometric tensor fold");

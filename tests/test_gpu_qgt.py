@@ -193,3 +193,17 @@ def test_gram_bounded_wait_reports_timeout_and_recovers(monkeypatch):
     monkeypatch.delenv("TC_TEST_GRAM_SKIP_MMA")
     g = c.qgt(d).cpu().numpy()[0]
     assert np.abs(g - G.quantum_geometric_tensor(circ, theta[0])).max() <= _tol(circ, nt.TC_C64)
+
+
+@pytest.mark.parametrize("dtype", [nt.TC_C64, nt.TC_C128])
+def test_qgt_bitwise_reproducible(dtype):
+    """The Gram's amplitude chunks are summed in a fixed order (no atomics):
+    two calls on the same rows give the same bits."""
+    import torch
+
+    circ, theta, _ = W.tfim_workload(n=14, layers=4, batch=3, seed=9)
+    c = nt.Circuit(circ, dtype=dtype)
+    d = torch.as_tensor(theta, device="cuda")
+    g1 = c.qgt(d).cpu().numpy()
+    g2 = c.qgt(d).cpu().numpy()
+    assert np.array_equal(g1, g2)
