@@ -679,6 +679,8 @@ void tn_release(tc_tn* t) {
   if (t->d_fblob) cudaFree(t->d_fblob);
   if (t->d_in_soff) cudaFree(t->d_in_soff);
   if (t->d_arena) cudaFree(t->d_arena);
+  if (t->d_lsteps) cudaFree(t->d_lsteps);
+  if (t->d_lstart) cudaFree(t->d_lstart);
 }
 }  // namespace
 
@@ -832,17 +834,68 @@ tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, int prec, v
   if (!t->graph || t->graph_B != B || t->graph_gates != d_src || t->graph_out != d_out || t->graph_prec != prec) {
     if (t->graph) cudaGraphExecDestroy(t->graph);
     t->graph = nullptr;
+    // steps grouped by level of the contraction tree (one more than their
+    // operands'): the steps of a level are independent and every step writes
+    // its own arena region, so a level's CUDA-core steps run as one launch and
+    // its tensor-core steps one launch each.  lstart holds, per level, the first
+    // output tile of each of its CUDA-core steps and the level's tile count.
+    std::vector<int> lev(t->steps.size());
+    int maxl = 0;
+    {
+      std::vector<int> tlev;  // level of each tensor id (inputs 0)
+      for (size_t i = 0; i < t->steps.size(); ++i) {
+        const TnStep& st = t->steps[i];
+        const int hi = std::max(std::max(st.a, st.b), st.c);
+        if ((int)tlev.size() <= hi) tlev.resize(hi + 1, 0);
+        lev[i] = 1 + std::max(tlev[st.a], tlev[st.b]);
+        tlev[st.c] = lev[i];
+        maxl = std::max(maxl, lev[i]);
+      }
+    }
+    std::vector<TnStep> ls;
+    std::vector<int> lstart, lfirst(maxl + 2, 0), lso(maxl + 2, 0);  // per level: first step, first lstart entry
+    std::vector<std::vector<size_t>> tcs(maxl + 1);
+    for (int l = 1; l <= maxl; ++l) {
+      lfirst[l] = (int)ls.size();
+      lso[l] = (int)lstart.size();
+      int tiles = 0;
+      for (size_t i = 0; i < t->steps.size(); ++i) {
+        if (lev[i] != l) continue;
+        const TnStep& st = t->steps[i];
+        if (prec != TN_FP32 && tn_step_tc_eligible(st, t->tc_min_cmacs)) {
+          tcs[l].push_back(i);
+          continue;
+        }
+        ls.push_back(st);
+        lstart.push_back(tiles);
+        tiles += ((st.M + kTnGemmTile - 1) / kTnGemmTile) * ((st.N + kTnGemmTile - 1) / kTnGemmTile);
+      }
+      lstart.push_back(tiles);
+    }
+    lfirst[maxl + 1] = (int)ls.size();
+    if (t->d_lsteps) cudaFree(t->d_lsteps);
+    if (t->d_lstart) cudaFree(t->d_lstart);
+    t->d_lsteps = nullptr;
+    t->d_lstart = nullptr;
+    if (!ls.empty()) {
+      if ((e = cudaMalloc(&t->d_lsteps, ls.size() * sizeof(TnStep))) != cudaSuccess) return cuda_fail(e, "tn level steps");
+      if ((e = cudaMalloc(&t->d_lstart, lstart.size() * sizeof(int))) != cudaSuccess) return cuda_fail(e, "tn levels");
+      if ((e = cudaMemcpy(t->d_lsteps, ls.data(), ls.size() * sizeof(TnStep), cudaMemcpyHostToDevice)) != cudaSuccess ||
+          (e = cudaMemcpy(t->d_lstart, lstart.data(), lstart.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
+              cudaSuccess)
+        return cuda_fail(e, "tn level copy");
+    }
     cudaStream_t cap;
     if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) return cuda_fail(e, "stream");
     cudaGraph_t g;
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = tn_launch_assemble(*t, B, d_src, arena, cap);
-    for (size_t i = 0; e == cudaSuccess && i < t->steps.size(); ++i) {
-      const TnStep& st = t->steps[i];
-      if (prec != TN_FP32 && tn_step_tc_eligible(st, t->tc_min_cmacs))
-        e = tn_launch_step_tc(*t, st, B, arena, prec, t->d_err, cap);
-      else
-        e = tn_launch_step(*t, st, B, arena, cap);
+    for (int l = 1; e == cudaSuccess && l <= maxl; ++l) {
+      const int n_l = lfirst[l + 1] - lfirst[l];
+      if (n_l > 0)
+        e = tn_launch_level(*t, t->d_lsteps + lfirst[l], t->d_lstart + lso[l], n_l, lstart[lso[l] + n_l], B, arena, cap);
+      for (size_t q = 0; e == cudaSuccess && q < tcs[l].size(); ++q)
+        e = tn_launch_step_tc(*t, t->steps[tcs[l][q]], B, arena, prec, t->d_err, cap);
     }
     if (e == cudaSuccess) e = tn_launch_result(*t, B, arena, d_out, cap);
     cudaError_t e2 = cudaStreamEndCapture(cap, &g);

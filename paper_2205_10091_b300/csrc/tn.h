@@ -128,6 +128,10 @@ struct TnPlan {
   cudaGraphExec_t graph = nullptr;
   int graph_B = -1;
   int graph_prec = -1;
+  // the CUDA-core steps of the captured graph grouped by tree level (device;
+  // rebuilt with the graph)
+  TnStep* d_lsteps = nullptr;
+  int* d_lstart = nullptr;
   // split-precision tensor-core steps: eligibility threshold and the
   // device error word of their bounded waits, read back after each call
   // (pinned h_err, event err_ev) and reported by the next call
@@ -150,7 +154,12 @@ bool tn_build_circuit(int n_qubits, int init, const tc_op* ops, int n_ops, int n
 // d_src: [B][n_gates][16] complex64 gates (light-cone plans) or [B][n_params]
 // float parameters (circuit networks)
 cudaError_t tn_launch_assemble(const TnPlan& P, int B, const float* d_src, float2* arena, cudaStream_t s);
+constexpr int kTnGemmTile = 32;  // output tile (rows and columns) of the CUDA-core step kernel
 cudaError_t tn_launch_step(const TnPlan& P, const TnStep& st, int B, float2* arena, cudaStream_t s);
+// the CUDA-core steps of one tree level in one launch: d_steps [n], d_tile_start [n + 1] (device), tiles output
+// tiles in all
+cudaError_t tn_launch_level(const TnPlan& P, const TnStep* d_steps, const int* d_tile_start, int n, int tiles, int B,
+                            float2* arena, cudaStream_t s);
 // The whole contraction of B instances in one launch (one CTA per instance,
 // grid-stride) with every live tensor in shared memory; taken when the
 // plan's layout fits (else one GEMM launch per step, replayed as a graph).

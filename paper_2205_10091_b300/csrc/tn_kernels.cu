@@ -112,20 +112,20 @@ __global__ void k_tn_assemble_circuit(const TnInput* inputs, const TnOp* ops, co
 }
 
 // C[i][j] = sum_k A[fa[i] + sa[k]] * B[sb[k] + fb[j]]  (complex, FP32 accumulate)
-constexpr int TM = 32, TN = 32, TK = 16;
+constexpr int TM = kTnGemmTile, TN = kTnGemmTile, TK = 16;
 
-__global__ void __launch_bounds__(256) k_tn_gemm(const int32_t* tables, TnStep st, int64_t arena_total, float2* arena) {
+// One TM x TN output tile (rows i0.., columns j0..) of step `st` of one
+// instance (`inst` = that instance's arena); 256 threads.
+__device__ __forceinline__ void tn_gemm_tile(const int32_t* tables, const TnStep& st, float2* inst, int i0, int j0) {
   __shared__ float2 As[TK][TM + 1];
   __shared__ float2 Bs[TK][TN + 1];
-  const size_t inst = (size_t)blockIdx.z * arena_total;
-  const float2* A = arena + inst + st.a_off;
-  const float2* Bm = arena + inst + st.b_off;
-  float2* C = arena + inst + st.c_off;
+  const float2* A = inst + st.a_off;
+  const float2* Bm = inst + st.b_off;
+  float2* C = inst + st.c_off;
   const int32_t* fa = tables + st.fa;
   const int32_t* sa = tables + st.sa;
   const int32_t* sb = tables + st.sb;
   const int32_t* fb = tables + st.fb;
-  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float2 acc[2][2] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};
   for (int k0 = 0; k0 < st.K; k0 += TK) {
@@ -162,6 +162,28 @@ __global__ void __launch_bounds__(256) k_tn_gemm(const int32_t* tables, TnStep s
       const int i = i0 + 2 * ty + r, j = j0 + 2 * tx + c;
       if (i < st.M && j < st.N) C[(size_t)i * st.N + j] = acc[r][c];
     }
+}
+
+__global__ void __launch_bounds__(256) k_tn_gemm(const int32_t* tables, TnStep st, int64_t arena_total, float2* arena) {
+  tn_gemm_tile(tables, st, arena + (size_t)blockIdx.z * arena_total, blockIdx.y * TM, blockIdx.x * TN);
+}
+
+// Every step of one level of the contraction tree (independent of each
+// other) in one launch: block x is output tile x of the level, counted over
+// its steps in order (tile_start[s] = first tile of step s, n + 1 entries).
+__global__ void __launch_bounds__(256) k_tn_gemm_level(const int32_t* tables, const TnStep* __restrict__ steps,
+                                                       const int* __restrict__ tile_start, int n, int64_t arena_total,
+                                                       float2* arena) {
+  const int x = (int)blockIdx.x;
+  int lo = 0, hi = n - 1;  // the last step whose first tile is <= x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_start[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  const TnStep st = steps[lo];
+  const int local = x - tile_start[lo], nj = (st.N + TN - 1) / TN;
+  tn_gemm_tile(tables, st, arena + (size_t)blockIdx.z * arena_total, (local / nj) * TM, (local % nj) * TN);
 }
 
 __global__ void k_tn_result(const float2* arena, int64_t arena_total, int64_t off, int B, double* out) {
@@ -333,6 +355,14 @@ cudaError_t tn_launch_assemble(const TnPlan& P, int B, const float* d_src, float
   else
     k_tn_assemble<<<grid, 32, 0, s>>>(P.d_inputs, (int)P.inputs.size(), d_src, P.n_gates, P.in_total, P.arena_total,
                                       arena);
+  return cudaGetLastError();
+}
+
+cudaError_t tn_launch_level(const TnPlan& P, const TnStep* d_steps, const int* d_tile_start, int n, int tiles, int B,
+                            float2* arena, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_tn_gemm_level<<<dim3((unsigned)tiles, 1, (unsigned)B), 256, 0, s>>>(P.d_tables, d_steps, d_tile_start, n,
+                                                                        P.arena_total, arena);
   return cudaGetLastError();
 }
 
