@@ -403,6 +403,9 @@ TC_API tc_status tc_merge_moments(const double* parts, int R, double* out);
  *     any fixed reservation or allocator callback, and before any stream
  *     capture.  The address is cached per device index: do not use the
  *     library on a device after a cudaDeviceReset there.
+ *   - Not under stream capture: the plan copy reads host memory that is
+ *     freed when the call returns, so a call on a capturing stream returns
+ *     TC_E_UNSUPPORTED (a B = 0 call is still accepted).
  *   - Every call shares the array and overwrites what it uses; calls that
  *     overlap on the GPU (other streams, other host threads) race.
  */

@@ -65,6 +65,14 @@ extern "C" tc_status tc_expect_pauli_sum_noalloc(const tc_circuit* c, const void
   tc_status st = scratch_for_device(dev, &base);
   if (st != TC_OK) return st;
   if (B == 0) return TC_OK;
+  // the plan is copied from host memory that is freed when the call returns:
+  // a captured copy node would read it later, so capture is refused
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing((cudaStream_t)stream, &cs)) != cudaSuccess) return cuda_fail(e, "capture query");
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(TC_E_UNSUPPORTED, "the allocation-free entry point cannot be captured into a graph");
+  }
 
   // compile the Pauli sum on the host (host memory only)
   HamPlan H;

@@ -82,3 +82,23 @@ def test_noalloc_rejects_oversize_request():
     with pytest.raises(nt.TcError) as e:
         c.expect_noalloc(states, nt.Hamiltonian(ham), out)
     assert e.value.status == nt.TC_E_INVALID and "limit" in str(e.value)
+
+
+def test_refused_under_stream_capture():
+    """The plan copy reads host memory freed at return: a capturing stream is refused."""
+    import torch
+
+    circ, theta, ham = W.tfim_workload(n=12, layers=2, batch=2, seed=3)
+    c = nt.Circuit(circ)
+    st = c.apply(torch.as_tensor(theta, device="cuda"), 2)
+    H = nt.Hamiltonian(ham)
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    c.expect_noalloc(st, H, out=out)  # warm-up outside capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    sw, w, T = H.args()
+    code = None
+    with torch.cuda.graph(g, stream=s):
+        code = nt.lib().tc_expect_pauli_sum_noalloc(c.h, nt._ptr(st), 2, sw, w, T, nt._ptr(out), nt._stream(s))
+    assert code == nt.TC_E_UNSUPPORTED
