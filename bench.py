@@ -608,7 +608,9 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
     del net40, whole
     # ---- noisy 16-qubit trajectories ---------------------------------------
     circ, n_traj, seed, obs = W.noisy16_workload()
-    c = nt.Circuit(circ)
+    t_nz = time.monotonic()
+    c = nt.Circuit(circ, specialize=True)  # pass kernels compiled for the circuit (outside the timed region)
+    t_nz = time.monotonic() - t_nz
     sts = torch.empty((n_traj, 1 << 16), dtype=torch.complex64, device="cuda")
     Hs = [nt.Hamiltonian(o) for o in obs]
     vals = [torch.empty(n_traj, dtype=torch.float64, device="cuda") for _ in Hs]
@@ -638,6 +640,7 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
         "trajectories_per_s": n_traj / (ms_tr / 1e3), "ms_per_run": ms_tr, "trajectories": n_traj,
         "ms_forward": ms_ap, "forward_tflops": flop / (ms_ap / 1e3) / 1e12,
         "fp32_frac": flop / (ms_ap / 1e3) / 1e12 / FP32_TFLOPS_PROBE,
+        "pass_kernels": "compiled for the circuit at plan time", "plan_seconds": t_nz,
         "z0": [float(x) for x in ests[0].tolist()], "sum_zz": [float(x) for x in ests[1].tolist()]}
     del sts
     torch.cuda.synchronize()
