@@ -538,6 +538,10 @@ typedef struct {
   int32_t fused_groups;     /* barriers of the fused launch: groups of independent steps */
   int32_t tc_steps;         /* steps the split-precision modes run on tensor cores (current threshold) */
   double tc_cmacs;          /* complex multiply-adds of those steps per instance */
+  int32_t max_cluster;      /* fused launch with few instances: CTAs (a thread-block cluster) per instance */
+  int32_t split_min_items;  /* groups of at least this many work items are split over the cluster */
+  int32_t split_groups;     /* groups of the fused launch that are split */
+  int32_t reserved;
 } tc_path_info;
 
 /*
@@ -567,6 +571,19 @@ TC_API tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, tc_tn_p
  * every step with K >= 2 there).  Host only.
  */
 TC_API tc_status tc_tn_set_tc_threshold(tc_tn* t, double min_cmacs);
+/*
+ * tc_tn_set_cluster — the fused executor with few instances.  While B
+ * clusters of max_cluster CTAs fit on the GPU at once (B x max_cluster <= the
+ * SM count) and the cluster is schedulable, each instance runs on a
+ * thread-block cluster: every CTA holds all live tensors, groups of fewer
+ * than split_min_items work items run in every CTA, and larger groups are
+ * split over the cluster with outputs written into every CTA's shared memory
+ * (distributed shared memory).  Each output is computed by the same code
+ * either way, so results are bitwise those of the one-CTA launch.
+ * max_cluster: 1 (off), 2, 4 or 8 (default 8); split_min_items >= 1 (default
+ * 2048).  TC_E_INVALID otherwise.  Host-only; takes effect at the next call.
+ */
+TC_API tc_status tc_tn_set_cluster(tc_tn* t, int max_cluster, int split_min_items);
 TC_API void tc_tn_destroy(tc_tn* t);
 
 /*

@@ -731,6 +731,24 @@ tc_status tc_tn_info(const tc_tn* t, tc_path_info* o) {
       o->tc_steps++;
       o->tc_cmacs += (double)st.M * st.N * st.K;
     }
+  o->max_cluster = t->max_cluster;
+  o->split_min_items = t->split_min;
+  if (tn_fused_ok(*t))
+    for (size_t off = 0, gi = 0; gi < (size_t)t->n_groups && off + 2 < t->fblob.size(); ++gi) {
+      if (t->fblob[off + 1] >= t->split_min) o->split_groups++;
+      off += (size_t)t->fblob[off + 2];
+    }
+  return TC_OK;
+}
+
+tc_status tc_tn_set_cluster(tc_tn* t, int max_cluster, int split_min_items) {
+  if (!t) return fail(TC_E_INVALID, "NULL plan");
+  if (max_cluster < 1 || max_cluster > kTnMaxCluster || (max_cluster & (max_cluster - 1)))
+    return fail(TC_E_INVALID, "max_cluster must be 1, 2, 4 or 8");
+  if (split_min_items < 1) return fail(TC_E_INVALID, "split_min_items must be >= 1");
+  t->max_cluster = max_cluster;
+  t->split_min = split_min_items;
+  t->fused_B = -1;  // the next call recomputes the launch shape
   return TC_OK;
 }
 
@@ -815,9 +833,14 @@ tc_status tn_run(tc_tn* t, int B, const float* d_src, double* d_out, int prec, v
       return cuda_fail(e, "tn status event");
   }
   if (tn_fused_ok(*t) && !use_tc) {
-    const int grid = tn_fused_grid(*t, B);
-    if (grid < 1) return fail(TC_E_CUDA, "tn fused launch: no valid grid");
-    if ((e = tn_launch_fused(*t, B, d_src, d_out, grid, s)) != cudaSuccess) return cuda_fail(e, "tn fused launch");
+    if (t->fused_B != B) {
+      t->fused_cl = tn_fused_cluster(*t, B);
+      t->fused_grid = tn_fused_grid(*t, B, t->fused_cl);
+      t->fused_B = B;
+    }
+    if (t->fused_grid < 1) return fail(TC_E_CUDA, "tn fused launch: no valid grid");
+    if ((e = tn_launch_fused(*t, B, d_src, d_out, t->fused_grid, t->fused_cl, s)) != cudaSuccess)
+      return cuda_fail(e, "tn fused launch");
     return TC_OK;
   }
   if (B > t->arena_B) {

@@ -69,6 +69,11 @@ constexpr int kTnGHdr = 8;
 constexpr int kTnFullTabBits = 8;
 // Threads of a fused-executor CTA (work items of a group are spread over them).
 constexpr int kTnFusedThreads = 1024;
+// Fused executor, few instances: up to kTnMaxCluster CTAs (a portable cluster)
+// share an instance while B x cluster fits on the GPU's SMs; groups of at
+// least kTnSplitMinItems work items are split over the cluster.
+constexpr int kTnMaxCluster = 8;
+constexpr int kTnSplitMinItems = 2048;
 constexpr int kTnSRec = 12;
 // Longest group block staged in shared memory (ints).
 constexpr int kTnBlobMax = 3072;
@@ -136,6 +141,11 @@ struct TnPlan {
   // device error word of their bounded waits, read back after each call
   // (pinned h_err, event err_ev) and reported by the next call
   double tc_min_cmacs = kTnTcMinCmacs;
+  // fused executor with few instances: cluster size per instance (1 = one
+  // CTA) and the group size (work items) from which a group is split over it
+  int max_cluster = kTnMaxCluster;
+  int split_min = kTnSplitMinItems;
+  int fused_B = -1, fused_cl = 1, fused_grid = 0;  // launch shape cached for the last B
   int* d_err = nullptr;
   int* h_err = nullptr;
   cudaEvent_t err_ev = nullptr;
@@ -164,8 +174,12 @@ cudaError_t tn_launch_level(const TnPlan& P, const TnStep* d_steps, const int* d
 // grid-stride) with every live tensor in shared memory; taken when the
 // plan's layout fits (else one GEMM launch per step, replayed as a graph).
 bool tn_fused_ok(const TnPlan& P);
-int tn_fused_grid(const TnPlan& P, int B);
-cudaError_t tn_launch_fused(const TnPlan& P, int B, const float* d_src, double* d_out, int grid, cudaStream_t s);
+// CTAs per instance of the fused launch for B instances (1, or a cluster when
+// B clusters fit on the GPU at once and the plan allows it)
+int tn_fused_cluster(const TnPlan& P, int B);
+int tn_fused_grid(const TnPlan& P, int B, int cl);
+cudaError_t tn_launch_fused(const TnPlan& P, int B, const float* d_src, double* d_out, int grid, int cl,
+                            cudaStream_t s);
 cudaError_t tn_launch_result(const TnPlan& P, int B, const float2* arena, double* d_out, cudaStream_t s);
 // Tensor-core step (tn_tc.cu): TF32X3 or BF16X6; the larger free side on the
 // MMA's 128 rows.  Eligible: K >= 2 and M N K >= min_cmacs.

@@ -4,7 +4,11 @@
 // indices is a permutation of address bits; the host precomputes, per step,
 // the addresses of A's rows/columns and B's rows/columns (fa, sa, sb, fb) so
 // the GEMM reads operands in place with no separate permute kernel.
+#include <cooperative_groups.h>
+
 #include "tn.h"
+
+namespace cg = cooperative_groups;
 
 namespace tcb {
 
@@ -198,7 +202,14 @@ __global__ void k_tn_result(const float2* arena, int64_t arena_total, int64_t of
 // Fused executor: one CTA per instance (grid-stride over instances) runs the
 // assembly and the whole path with all live tensors in shared memory.  The path runs group by group (independent
 // steps of one tree level, see tn.h), one barrier per group; the group's work
-// items are spread over the CTA's threads.  A step computes
+// items are spread over the CTA's threads.  With few instances (CL) a
+// thread-block cluster runs each instance: every CTA holds all live tensors,
+// groups below split_min items run redundantly in every CTA (no exchange),
+// and a larger group's 32-item units are dealt over the cluster's warps, each
+// output written into every CTA's shared memory (distributed shared memory)
+// between two cluster barriers: the first keeps those writes from landing in
+// regions a slower CTA still reads, the second publishes them.  Each output is
+// computed by the same code in either case, so results do not depend on CL.  A step computes
 // C[e] = sum_k A[fa(i) + sa(k)] B[sb(k) + fb(j)], e = i N + j, with tpo
 // items per output (a power of two <= 32: small results with long sums
 // spread the sum over lanes and reduce by shuffles).  Group blocks are staged
@@ -219,21 +230,37 @@ __device__ __forceinline__ int tn_tab_len(int lg) {
   return (1 << lo) + (1 << (lg - lo));
 }
 
-template <bool CIRCUIT>
+template <bool CIRCUIT, bool CL>
 __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __restrict__ inputs,
                                                             const int32_t* __restrict__ in_soff, int n_inputs,
-                                                            const int32_t* __restrict__ blob, int n_groups,
-                                                            const float* __restrict__ src, int n_src,
+                                                            const int32_t* __restrict__ blob, int blob_ints,
+                                                            int n_groups, const float* __restrict__ src, int n_src,
                                                             const TnOp* __restrict__ ops,
                                                             const float* __restrict__ mats, int result_soff, int B,
-                                                            double* __restrict__ out) {
+                                                            int split_min, double* __restrict__ out) {
   extern __shared__ float2 sm[];
   __shared__ int32_t tb[2][kTnBlobMax];
   const int tid = threadIdx.x;
-  for (int b = blockIdx.x; b < B; b += gridDim.x) {
+  const int warp = tid >> 5, lane = tid & 31;
+  // instances and this CTA's rank: a cluster shares one instance
+  int crank = 0, csize = 1;
+  if constexpr (CL) {
+    crank = (int)cg::this_cluster().block_rank();
+    csize = (int)cg::this_cluster().num_blocks();
+  }
+  const int inst0 = (int)blockIdx.x / csize, istride = (int)gridDim.x / csize;
+  // a path whose group blocks fit both slots is staged once, whole; a longer
+  // one streams through the two slots, the next block loaded during a group
+  const bool whole = blob_ints <= 2 * kTnBlobMax;
+  int32_t* tbw = &tb[0][0];
+  if (whole)
+    for (int i = tid; i < blob_ints; i += kFusedThreads) tbw[i] = __ldg(blob + i);
+  for (int b = inst0; b < B; b += istride) {
     // ---- group 0's block, and the inputs: one warp per tensor, a lane per entry
-    const int len0 = n_groups > 0 ? __ldg(blob + 2) : 0;
-    for (int i = tid; i < len0; i += kFusedThreads) tb[0][i] = __ldg(blob + i);
+    if (!whole) {
+      const int len0 = n_groups > 0 ? __ldg(blob + 2) : 0;
+      for (int i = tid; i < len0; i += kFusedThreads) tb[0][i] = __ldg(blob + i);
+    }
     for (int t = tid >> 5; t < n_inputs; t += kFusedThreads / 32) {
       const TnInput in = inputs[t];
       const int e = tid & 31;
@@ -257,9 +284,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
     // ---- path, group by group ------------------------------------------------
     int off = 0;
     for (int gi = 0; gi < n_groups; ++gi) {
-      const int32_t* g = tb[gi & 1];
+      const int32_t* g = whole ? tbw + off : tb[gi & 1];
       const int n_st = g[0], n_items = g[1], len = g[2];
-      const int nlen = gi + 1 < n_groups ? g[3] : 0;
+      const int nlen = (!whole && gi + 1 < n_groups) ? g[3] : 0;
       int32_t pf[kFusedPf];
 #pragma unroll
       for (int r = 0; r < kFusedPf; ++r) {
@@ -267,8 +294,15 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
         pf[r] = i < nlen ? __ldg(blob + off + len + i) : 0;
       }
       const int32_t* recs = g + kTnGHdr;
-      for (int base = 0; base < n_items; base += kFusedThreads) {
-        const int w = base + tid;
+      // uniform over the cluster: every CTA reads the same group header
+      const bool split = CL && csize > 1 && n_items >= split_min;
+      if constexpr (CL) {
+        if (split) cg::this_cluster().sync();
+      }
+      const int nunits = (n_items + 31) >> 5;
+      const int ustride = split ? csize * (kFusedThreads / 32) : kFusedThreads / 32;
+      for (int u = (split ? crank * (kFusedThreads / 32) : 0) + warp; u < nunits; u += ustride) {
+        const int w = (u << 5) + lane;
         int lo = 0, hi = n_st - 1;  // last step whose first item is <= w
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
@@ -287,6 +321,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
         if (valid) {
           const float2* Ar = sm + r[8] + tn_tab(fa, lgM, e >> lgN);
           const float2* Bc = sm + r[9] + tn_tab(fb, lgN, e & (N - 1));
+#pragma unroll 4
           for (int k = part; k < K; k += tpo) {
             const float2 a = Ar[tn_tab(sa, lgK, k)];
             const float2 c = Bc[tn_tab(sb, lgK, k)];
@@ -299,7 +334,18 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
           acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
           acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
         }
-        if (valid && part == 0) sm[r[10] + e] = acc;
+        if (valid && part == 0) {
+          sm[r[10] + e] = acc;
+          if constexpr (CL) {
+            if (split) {
+              cg::cluster_group cl = cg::this_cluster();
+              for (int q = 1; q < csize; ++q) {
+                const int dst = crank + q < csize ? crank + q : crank + q - csize;
+                *cl.map_shared_rank(sm + r[10] + e, dst) = acc;
+              }
+            }
+          }
+        }
       }
       // the other slot held the previous group's block, which no thread reads any more
       int32_t* nb = tb[(gi + 1) & 1];
@@ -309,15 +355,23 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
         if (i < nlen) nb[i] = pf[r];
       }
       off += len;
+      if constexpr (CL) {
+        if (split) {
+          cg::this_cluster().sync();
+          continue;
+        }
+      }
       __syncthreads();
     }
-    if (tid == 0) {
+    if (tid == 0 && crank == 0) {
       const float2 v = sm[result_soff];
       out[2 * b] = (double)v.x;
       out[2 * b + 1] = (double)v.y;
     }
     __syncthreads();
   }
+  // no CTA leaves while another may still write into its shared memory
+  if constexpr (CL) cg::this_cluster().sync();
 }
 
 bool tn_fused_ok(const TnPlan& P) {
@@ -325,25 +379,87 @@ bool tn_fused_ok(const TnPlan& P) {
          P.smem_entries * 8 <= kTnFusedSmemMax;
 }
 
-int tn_fused_grid(const TnPlan& P, int B) {
+namespace {
+template <bool CIRCUIT, bool CL>
+cudaError_t fused_attr(const TnPlan& P) {
+  return cudaFuncSetAttribute(k_tn_fused<CIRCUIT, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(P.smem_entries * 8));
+}
+void fused_cfg(cudaLaunchConfig_t& cfg, cudaLaunchAttribute* attr, const TnPlan& P, int grid, int cl,
+               cudaStream_t s) {
+  cfg = cudaLaunchConfig_t{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kFusedThreads);
+  cfg.dynamicSmemBytes = (size_t)(P.smem_entries * 8);
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = cl > 1 ? 1 : 0;
+}
+}  // namespace
+
+int tn_fused_cluster(const TnPlan& P, int B) {
+  int sms = 0, dev = 0;
+  if (P.max_cluster < 2 || B < 1) return 1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  int cl = 1;
+  while (cl * 2 <= P.max_cluster && cl * 2 <= kTnMaxCluster) cl *= 2;
+  if ((long long)B * cl > sms) return 1;
+  // the cluster must be schedulable with this shared-memory size
+  if ((P.circuit ? fused_attr<true, true>(P) : fused_attr<false, true>(P)) != cudaSuccess) return 1;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fused_cfg(cfg, attr, P, B * cl, cl, nullptr);
+  int n = 0;
+  const cudaError_t e = P.circuit ? cudaOccupancyMaxActiveClusters(&n, k_tn_fused<true, true>, &cfg)
+                                  : cudaOccupancyMaxActiveClusters(&n, k_tn_fused<false, true>, &cfg);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 1;
+  }
+  return n >= 1 ? cl : 1;
+}
+
+int tn_fused_grid(const TnPlan& P, int B, int cl) {
+  if (cl > 1) return B * cl;
   const int smem = (int)(P.smem_entries * 8);
   int per_sm = 0, sms = 0, dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  auto kern = P.circuit ? k_tn_fused<true> : k_tn_fused<false>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+  auto kern = P.circuit ? k_tn_fused<true, false> : k_tn_fused<false, false>;
+  if ((P.circuit ? fused_attr<true, false>(P) : fused_attr<false, false>(P)) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, smem) != cudaSuccess) return 0;
   if (per_sm < 1) return 0;
   return B < per_sm * sms ? B : per_sm * sms;
 }
 
-cudaError_t tn_launch_fused(const TnPlan& P, int B, const float* d_src, double* d_out, int grid, cudaStream_t s) {
-  if (!tn_fused_ok(P) || grid < 1) return cudaErrorInvalidConfiguration;
-  const int smem = (int)(P.smem_entries * 8);
-  auto kern = P.circuit ? k_tn_fused<true> : k_tn_fused<false>;
-  kern<<<grid, kFusedThreads, smem, s>>>(P.d_inputs, P.d_in_soff, (int)P.inputs.size(), P.d_fblob, P.n_groups,
-                                         d_src, P.circuit ? P.n_params : P.n_gates, P.d_ops, P.d_mats,
-                                         P.result_soff, B, d_out);
+cudaError_t tn_launch_fused(const TnPlan& P, int B, const float* d_src, double* d_out, int grid, int cl,
+                            cudaStream_t s) {
+  if (!tn_fused_ok(P) || grid < 1 || cl < 1 || cl > kTnMaxCluster) return cudaErrorInvalidConfiguration;
+  if (cl > 1 && grid != B * cl) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  fused_cfg(cfg, attr, P, grid, cl, s);
+  const int n_in = (int)P.inputs.size(), n_src = P.circuit ? P.n_params : P.n_gates;
+  const int n_blob = (int)P.fblob.size();
+  const TnInput* inp = P.d_inputs;
+  const int32_t* soff = P.d_in_soff;
+  const int32_t* fb = P.d_fblob;
+  const TnOp* ops = P.d_ops;
+  const float* mats = P.d_mats;
+  const int rs = (int)P.result_soff, sm = P.split_min;
+  if (cl > 1)
+    return P.circuit ? cudaLaunchKernelEx(&cfg, k_tn_fused<true, true>, inp, soff, n_in, fb, n_blob, P.n_groups, d_src,
+                                          n_src, ops, mats, rs, B, sm, d_out)
+                     : cudaLaunchKernelEx(&cfg, k_tn_fused<false, true>, inp, soff, n_in, fb, n_blob, P.n_groups, d_src,
+                                          n_src, ops, mats, rs, B, sm, d_out);
+  auto kern = P.circuit ? k_tn_fused<true, false> : k_tn_fused<false, false>;
+  kern<<<grid, kFusedThreads, cfg.dynamicSmemBytes, s>>>(inp, soff, n_in, fb, n_blob, P.n_groups, d_src, n_src, ops,
+                                                          mats, rs, B, sm, d_out);
   return cudaGetLastError();
 }
 

@@ -92,7 +92,8 @@ class tc_path_info(C.Structure):
                 ("n_steps", C.c_int32), ("max_rank", C.c_int32), ("n_cone_gates", C.c_int32), ("cone_lo", C.c_int32),
                 ("cone_hi", C.c_int32), ("n_inputs", C.c_int32), ("n_active", C.c_int32), ("fused", C.c_int32),
                 ("smem_bytes", C.c_int32), ("fused_groups", C.c_int32), ("tc_steps", C.c_int32),
-                ("tc_cmacs", C.c_double)]
+                ("tc_cmacs", C.c_double), ("max_cluster", C.c_int32), ("split_min_items", C.c_int32),
+                ("split_groups", C.c_int32), ("reserved", C.c_int32)]
 
 
 class tc_server_options(C.Structure):
@@ -160,6 +161,7 @@ SIGNATURES = {
     "tc_tn_info": (C.c_int, [C.c_void_p, C.POINTER(tc_path_info)]),
     "tc_contract_path": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tc_tn_set_tc_threshold": (C.c_int, [C.c_void_p, C.c_double]),
+    "tc_tn_set_cluster": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "tc_tn_destroy": (None, [C.c_void_p]),
     "tc_qgt": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "tc_natural_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p,
@@ -553,6 +555,11 @@ class LightCone:
         in the split-precision modes."""
         _check(lib().tc_tn_set_tc_threshold(self.h, C.c_double(min_cmacs)))
 
+    def set_cluster(self, max_cluster: int = 8, split_min_items: int = 2048):
+        """Fused launch with few instances: CTAs per instance (1 = off) and the
+        group size from which a group is split over them."""
+        _check(lib().tc_tn_set_cluster(self.h, int(max_cluster), int(split_min_items)))
+
     def contract(self, d_gates, out=None, stream=None, precision: int = TC_TN_FP32):
         """d_gates: CUDA complex64 tensor [B][n_gates][4][4]; returns CUDA float64 [B][2]."""
         import torch
@@ -605,6 +612,11 @@ class CircuitNetwork:
         """Steps of at least min_cmacs complex multiply-adds run on tensor cores
         in the split-precision modes."""
         _check(lib().tc_tn_set_tc_threshold(self.h, C.c_double(min_cmacs)))
+
+    def set_cluster(self, max_cluster: int = 8, split_min_items: int = 2048):
+        """Fused launch with few instances: CTAs per instance (1 = off) and the
+        group size from which a group is split over them."""
+        _check(lib().tc_tn_set_cluster(self.h, int(max_cluster), int(split_min_items)))
 
     def expect(self, d_params, B: int | None = None, out=None, stream=None, precision: int = TC_TN_FP32):
         """d_params: CUDA float32 [B][n_params]; returns CUDA float64 [B][2] (Re, Im)."""

@@ -123,3 +123,20 @@ def test_mixed_pauli_string_on_testbed():
     for b in range(2):
         ref = T.circuit_window_expectation(circ, theta[b], pauli, 19 - d - 1, 22 + d + 1)
         assert abs(out[b, 0] - ref.real) <= TOL_SMALL and abs(out[b, 1] - ref.imag) <= TOL_SMALL
+
+
+def test_circuit_network_cluster_bitwise_equals_one_cta():
+    # the fused launch of a circuit network (gate entries evaluated from the
+    # parameters in the kernel) on a cluster and on one CTA per instance
+    n, d, c = 40, 6, 20
+    circ = W.example_block_circuit(n, d)
+    theta = _testbed_rows(circ, 3, 11)
+    net = nt.CircuitNetwork(circ, {c: 3}, prune=2, split=True)
+    assert net.info()["fused"] == 1
+    net.set_cluster(8, 1)
+    a = net.expect(_params(theta)).cpu().numpy()
+    net.set_cluster(1)
+    b = net.expect(_params(theta)).cpu().numpy()
+    assert np.array_equal(a, b)
+    ref = T.circuit_window_expectation(circ, theta[2], {c: 3}, c - d - 1, c + d + 1)
+    assert abs(a[2, 0] - ref.real) <= TOL_SMALL

@@ -136,3 +136,18 @@ def test_executor_choice():
     assert whole["fused"] == 0 and whole["smem_bytes"] > 200 * 1024
     n, gates, obs = W.brick200_workload()
     assert nt.LightCone(n, [(a, b) for a, b, _ in gates], obs).info()["fused"] == 0
+
+
+def test_cluster_setting_validated_and_reported():
+    n, gates, obs = W.brick200_workload()
+    lc = nt.LightCone(n, [(a, b) for a, b, _ in gates], obs, greedy_trials=64)
+    info = lc.info()
+    assert info["max_cluster"] == 8 and info["split_min_items"] == 2048
+    assert 1 <= info["split_groups"] < info["fused_groups"]
+    for bad in ((0, 2048), (3, 2048), (16, 2048), (8, 0)):
+        with pytest.raises(RuntimeError):
+            lc.set_cluster(*bad)
+    lc.set_cluster(4, 1)
+    assert lc.info()["split_groups"] == lc.info()["fused_groups"]
+    lc.set_cluster(1, 4096)
+    assert lc.info()["max_cluster"] == 1
