@@ -286,6 +286,56 @@ void tn_layout_fused(TnPlan& P) {
   auto step_tabs = [&](const TnStep& st) {
     return tab_len(lg(st.M)) + 2 * tab_len(lg(st.K)) + tab_len(lg(st.N));
   };
+  // shared-memory swizzle of every tensor (tn_swz), chosen for the lanes of
+  // the one step that reads it: two sample warps (the step's first and middle
+  // one), two k-iterations each; cost = wavefronts of the warp's loads (the
+  // largest number of distinct entries on one bank pair)
+  std::vector<int> rot(n_ten, 0);
+  for (int s = 0; s < n_steps; ++s) {
+    const TnStep& st = P.steps[s];
+    const int tpo = tpo_of(st), lgN = lg(st.N);
+    const int64_t n_items = (int64_t)st.M * st.N * tpo;
+    for (int side = 0; side < 2; ++side) {
+      int best = 0;
+      int64_t best_cost = -1;
+      for (int r = 0; r < 4; ++r) {
+        int64_t cost = 0;
+        for (int64_t w0 : {(int64_t)0, (n_items / 64) * 32}) {
+          for (int it = 0; it < 2; ++it) {
+            int32_t words[32];
+            int nw = 0;
+            for (int l = 0; l < 32; ++l) {
+              const int64_t item = w0 + l;
+              const int64_t e = item / tpo;
+              const int k = (int)(item % tpo) + it * tpo;
+              if (e >= (int64_t)st.M * st.N || k >= st.K) continue;
+              const int64_t i = e >> lgN, j = e & (st.N - 1);
+              const int32_t x = side == 0 ? P.tables[st.fa + i] + P.tables[st.sa + k]
+                                          : P.tables[st.sb + k] + P.tables[st.fb + j];
+              words[nw++] = tn_swz(x, r);
+            }
+            int worst = 0;
+            for (int q = 0; q < nw; ++q) {  // distinct words on the bank pair of word q
+              int cnt = 0;
+              for (int u = 0; u < nw; ++u) {
+                if ((words[u] & 15) != (words[q] & 15)) continue;
+                bool first = true;
+                for (int v = 0; v < u; ++v) first = first && words[v] != words[u];
+                cnt += first ? 1 : 0;
+              }
+              worst = std::max(worst, cnt);
+            }
+            cost += worst;
+          }
+        }
+        if (best_cost < 0 || cost < best_cost) {
+          best_cost = cost;
+          best = r;
+        }
+      }
+      rot[side == 0 ? st.a : st.b] = best;
+    }
+  }
   for (int i = 0; i < n_inputs; ++i) place(i, pow2(P.inputs[i].rank));
   P.fblob.clear();
   P.fblob_ok = true;
@@ -298,7 +348,7 @@ void tn_layout_fused(TnPlan& P) {
     int len = kTnGHdr;
     while (g1 < order.size() && lvl[order[g1]] == lvl[order[g0]]) {
       const int add = kTnSRec + step_tabs(P.steps[order[g1]]);
-      if (g1 > g0 && len + add > kTnBlobMax) break;
+      if (g1 > g0 && len + add + 3 > kTnBlobMax) break;  // + the alignment padding
       len += add;
       ++g1;
     }
@@ -328,28 +378,36 @@ void tn_layout_fused(TnPlan& P) {
       rec[4] = lgM;
       rec[5] = lgK;
       rec[6] = lgN;
-      rec[7] = tpo;
+      rec[7] = tpo | (rot[st.c] << 8);
       rec[8] = (int32_t)off[st.a];
       rec[9] = (int32_t)off[st.b];
       rec[10] = (int32_t)off[st.c];
-      rec[11] = (int32_t)(P.fblob.size() - gstart);
-      auto split = [&](int32_t tab, int g) {
+      auto split = [&](int32_t tab, int g, int r) {
         if (g <= kTnFullTabBits) {
-          for (int v = 0; v < (1 << g); ++v) P.fblob.push_back(P.tables[tab + v]);
+          for (int v = 0; v < (1 << g); ++v) P.fblob.push_back(tn_swz(P.tables[tab + v], r));
           return;
         }
         const int lo = (g + 1) / 2, hi = g - lo;
-        for (int v = 0; v < (1 << lo); ++v) P.fblob.push_back(P.tables[tab + v]);
-        for (int v = 0; v < (1 << hi); ++v) P.fblob.push_back(P.tables[tab + ((int64_t)v << lo)]);
+        for (int v = 0; v < (1 << lo); ++v) P.fblob.push_back(tn_swz(P.tables[tab + v], r));
+        for (int v = 0; v < (1 << hi); ++v) P.fblob.push_back(tn_swz(P.tables[tab + ((int64_t)v << lo)], r));
       };
-      split(st.fa, lgM);
-      split(st.sa, lgK);
-      split(st.sb, lgK);
-      split(st.fb, lgN);
+      // (rec is re-taken after each push: the blob may reallocate)
+      auto mark = [&](int field) {
+        P.fblob[gstart + kTnGHdr + kTnSRec * q + field] = (int32_t)(P.fblob.size() - gstart);
+      };
+      mark(11);
+      split(st.fa, lgM, rot[st.a]);
+      mark(12);
+      split(st.sa, lgK, rot[st.a]);
+      mark(13);
+      split(st.sb, lgK, rot[st.b]);
+      mark(14);
+      split(st.fb, lgN, rot[st.b]);
       items += (int64_t)st.M * st.N * tpo;
       if ((int64_t)st.M * st.N * tpo > (1 << 26)) P.fblob_ok = false;
     }
     items = (items + 31) / 32 * 32;
+    while (P.fblob.size() % 4) P.fblob.push_back(0);  // the next group's records stay 16-byte aligned
     P.fblob[gstart + 0] = (int32_t)gs.size();
     P.fblob[gstart + 1] = (int32_t)std::min<int64_t>(items, INT32_MAX);
     for (int s : gs) {
@@ -367,7 +425,7 @@ void tn_layout_fused(TnPlan& P) {
     if (i > 0) P.fblob[starts[i - 1] + 3] = len;
   }
   P.in_soff.assign(n_inputs, 0);
-  for (int i = 0; i < n_inputs; ++i) P.in_soff[i] = (int32_t)off[i];
+  for (int i = 0; i < n_inputs; ++i) P.in_soff[i] = (int32_t)off[i] | (int32_t)(rot[i] << 28);
   P.smem_entries = peak;
   P.result_soff = n_steps == 0 ? 0 : (int32_t)off[P.steps.back().c];
 }

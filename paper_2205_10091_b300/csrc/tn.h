@@ -57,16 +57,38 @@ struct TnStep {
 // being independent; a level too large for one staged block is cut into
 // several groups run one after another.  Per group:
 //   header (kTnGHdr ints): {n_steps, n_items, len, next_len, 0...}
-//   per step (kTnSRec ints): {item0, M, K, N, lgM, lgK, lgN, tpo, a, b, c, tab}
+//   per step (kTnSRec ints, 16-byte aligned): {item0, M, K, N, lgM, lgK, lgN,
+//     tpo | rot_c << 8, a, b, c, fa, sa, sb, fb, 0}
 //     item0 = first work item of the step (work items: M N tpo, each run of
 //     equal tpo padded to a warp), a, b, c = live-tensor offsets (complex
-//     entries), tab = offset of the step's tables from the group start
-//   tables: per step fa, sa, sb, fb; an index set of g <= 8 bits as one full
-//     table, a wider one split in two levels: lo = the lowest (g + 1) / 2
-//     bits, table(v) = lo[v & (2^lo - 1)] + hi[v >> lo] (the bits scatter to
-//     disjoint positions, so the parts add)
+//     entries), rot_c = swizzle of the output tensor (tn_swz), fa..fb =
+//     offsets of the step's four tables from the group start; each group's
+//     block is padded to a multiple of four ints
+//   tables: per step fa, sa, sb, fb, each entry already swizzled with its
+//     operand's rotation; an index set of g <= 8 bits as one full table, a
+//     wider one split in two levels: lo = the lowest (g + 1) / 2 bits,
+//     table(v) = lo[v & (2^lo - 1)] ^ hi[v >> lo].  The swizzle is linear over
+//     XOR and the index sets of one operand scatter to disjoint bit positions,
+//     so an operand's address is its offset plus the XOR of its table entries.
+//   Shared memory holds entry x of a tensor at offset + tn_swz(x, rot): bits
+//   4.. of x are XOR-folded into bits 0..3 (rotated by rot), so lanes whose
+//   entries differ only in high bits fall on different bank pairs.  Each
+//   tensor's rot (0..3) is chosen on the host for the lanes of the one step
+//   that reads it; inputs carry theirs in bits 28..29 of their offset.
 constexpr int kTnGHdr = 8;
 constexpr int kTnFullTabBits = 8;
+#ifdef __CUDACC__
+#define TN_HD __host__ __device__
+#else
+#define TN_HD
+#endif
+// The fused executor's shared-memory swizzle of a tensor entry x (< 2^20).
+TN_HD inline int32_t tn_swz(int32_t x, int rot) {
+  const uint32_t u = (uint32_t)x;
+  uint32_t f = ((u >> 4) ^ (u >> 8) ^ (u >> 12) ^ (u >> 16)) & 15u;
+  f = ((f << rot) | (f >> ((4 - rot) & 3))) & 15u;
+  return (int32_t)(u ^ f);
+}
 // Threads of a fused-executor CTA (work items of a group are spread over them).
 constexpr int kTnFusedThreads = 1024;
 // Fused executor, few instances: up to kTnMaxCluster CTAs (a portable cluster)
@@ -74,7 +96,7 @@ constexpr int kTnFusedThreads = 1024;
 // least kTnSplitMinItems work items are split over the cluster.
 constexpr int kTnMaxCluster = 8;
 constexpr int kTnSplitMinItems = 2048;
-constexpr int kTnSRec = 12;
+constexpr int kTnSRec = 16;
 // Longest group block staged in shared memory (ints).
 constexpr int kTnBlobMax = 3072;
 

@@ -218,16 +218,11 @@ __global__ void k_tn_result(const float2* arena, int64_t arena_total, int64_t of
 constexpr int kFusedThreads = kTnFusedThreads;
 constexpr int kFusedPf = (kTnBlobMax + kFusedThreads - 1) / kFusedThreads;
 
+// an index set's swizzled entry offset (fused blob tables, see tn.h)
 __device__ __forceinline__ int tn_tab(const int32_t* t, int lg, int v) {
   if (lg <= kTnFullTabBits) return t[v];
   const int lo = (lg + 1) >> 1;
-  return t[v & ((1 << lo) - 1)] + t[(1 << lo) + (v >> lo)];
-}
-
-__device__ __forceinline__ int tn_tab_len(int lg) {
-  if (lg <= kTnFullTabBits) return 1 << lg;
-  const int lo = (lg + 1) >> 1;
-  return (1 << lo) + (1 << (lg - lo));
+  return t[v & ((1 << lo) - 1)] ^ t[(1 << lo) + (v >> lo)];
 }
 
 template <bool CIRCUIT, bool CL>
@@ -239,7 +234,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
                                                             const float* __restrict__ mats, int result_soff, int B,
                                                             int split_min, double* __restrict__ out) {
   extern __shared__ float2 sm[];
-  __shared__ int32_t tb[2][kTnBlobMax];
+  __shared__ __align__(16) int32_t tb[2][kTnBlobMax];
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   // instances and this CTA's rank: a cluster shares one instance
@@ -277,7 +272,8 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
         } else {  // TS_Z
           v = make_float2(e == 0 ? 1.f : (e == 3 ? -1.f : 0.f), 0.f);
         }
-        sm[in_soff[t] + e] = v;
+        const int32_t so = in_soff[t];
+        sm[(so & 0x0fffffff) + tn_swz(e, (so >> 28) & 3)] = v;
       }
     }
     __syncthreads();
@@ -308,25 +304,36 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
           const int mid = (lo + hi + 1) >> 1;
           if (recs[mid * kTnSRec] <= w) lo = mid; else hi = mid - 1;
         }
-        const int32_t* r = recs + lo * kTnSRec;
-        const int M = r[1], K = r[2], N = r[3], lgM = r[4], lgK = r[5], lgN = r[6], tpo = r[7];
-        const int local = w - r[0];
+        const int4* rv = reinterpret_cast<const int4*>(recs + lo * kTnSRec);
+        const int4 r0 = rv[0], r1 = rv[1], r2 = rv[2], r3 = rv[3];
+        const int M = r0.y, K = r0.z, N = r0.w, lgM = r1.x, lgK = r1.y, lgN = r1.z, tpo = r1.w & 255;
+        const int local = w - r0.x;
         const int e = local >> (__ffs(tpo) - 1), part = local & (tpo - 1);
-        const int32_t* fa = g + r[11];
-        const int32_t* sa = fa + tn_tab_len(lgM);
-        const int32_t* sb = sa + tn_tab_len(lgK);
-        const int32_t* fb = sb + tn_tab_len(lgK);
+        const int32_t* fa = g + r2.w;
+        const int32_t* sa = g + r3.x;
+        const int32_t* sb = g + r3.y;
+        const int32_t* fb = g + r3.z;
         float2 acc = make_float2(0.f, 0.f);
         const bool valid = e < M * N;
         if (valid) {
-          const float2* Ar = sm + r[8] + tn_tab(fa, lgM, e >> lgN);
-          const float2* Bc = sm + r[9] + tn_tab(fb, lgN, e & (N - 1));
-#pragma unroll 4
-          for (int k = part; k < K; k += tpo) {
-            const float2 a = Ar[tn_tab(sa, lgK, k)];
-            const float2 c = Bc[tn_tab(sb, lgK, k)];
+          const float2* As = sm + r2.x;
+          const float2* Bs = sm + r2.y;
+          const int ai = tn_tab(fa, lgM, e >> lgN), bj = tn_tab(fb, lgN, e & (N - 1));
+          auto mac = [&](int ka, int kb) {
+            const float2 a = As[ai ^ ka];
+            const float2 c = Bs[bj ^ kb];
             acc.x = fmaf(a.x, c.x, fmaf(-a.y, c.y, acc.x));
             acc.y = fmaf(a.x, c.y, fmaf(a.y, c.x, acc.y));
+          };
+          // the same sums in the same order; the loops differ in table form and stride only
+          if (lgK <= kTnFullTabBits && tpo == 1) {
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) mac(sa[k], sb[k]);
+          } else if (lgK <= kTnFullTabBits) {
+#pragma unroll 4
+            for (int k = part; k < K; k += tpo) mac(sa[k], sb[k]);
+          } else {
+            for (int k = part; k < K; k += tpo) mac(tn_tab(sa, lgK, k), tn_tab(sb, lgK, k));
           }
         }
         // tpo is uniform over a warp: runs of equal tpo are padded to 32 items
@@ -335,13 +342,14 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
           acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
         }
         if (valid && part == 0) {
-          sm[r[10] + e] = acc;
+          const int ce = r2.z + tn_swz(e, r1.w >> 8);
+          sm[ce] = acc;
           if constexpr (CL) {
             if (split) {
               cg::cluster_group cl = cg::this_cluster();
               for (int q = 1; q < csize; ++q) {
                 const int dst = crank + q < csize ? crank + q : crank + q - csize;
-                *cl.map_shared_rank(sm + r[10] + e, dst) = acc;
+                *cl.map_shared_rank(sm + ce, dst) = acc;
               }
             }
           }
