@@ -9,6 +9,8 @@
                                                           # whole 40-qubit testbed network, tensor-core steps
     python profile_case.py --workload qaoa --qubits 26 --rows 1 --layers 3
                                                           # MaxCut QAOA on a random 3-regular graph
+    python profile_case.py --workload cone200 --rows 1 --cluster 8
+                                                          # <Z99 Z100> light cone of the 200-qubit brickwork
 """
 import numpy as np
 import argparse
@@ -21,12 +23,13 @@ from paper_2205_10091_b300 import workloads as W
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="tfim20", choices=["tfim20", "noisy16", "hea10", "qgt", "tn40", "qaoa"])
+    ap.add_argument("--workload", default="tfim20", choices=["tfim20", "noisy16", "hea10", "qgt", "tn40", "qaoa", "cone200"])
     ap.add_argument("--rows", type=int, default=32)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--qubits", type=int, default=16)
     ap.add_argument("--precision", type=int, default=1, help="tn40: 0 FP32, 1 TF32X3, 2 BF16X6")
     ap.add_argument("--layers", type=int, default=3, help="qaoa: layers p")
+    ap.add_argument("--cluster", type=int, default=8, help="cone200: CTAs per instance of the fused launch (1 = off)")
     ap.add_argument("--specialize", action="store_true", help="tfim20, qaoa: pass kernels compiled for the circuit")
     args = ap.parse_args()
     if args.workload == "tfim20":
@@ -65,6 +68,17 @@ def main():
             out = net.expect(th, precision=args.precision)
         torch.cuda.synchronize()
         print("rows", args.rows, "info", net.info(), "<Z20>[0]", float(out[0, 0]))
+    elif args.workload == "cone200":
+        n, gates0, zq = W.brick200_workload()
+        lc = nt.LightCone(n, [(a, b) for a, b, _ in gates0], zq, greedy_trials=64)
+        lc.set_cluster(args.cluster)
+        gl = [gates0] + [W.brickwork_u4(n, 8, np.random.default_rng(s)) for s in range(1, args.rows)]
+        g = torch.as_tensor(np.stack([np.stack([u for (_, _, u) in x]) for x in gl]).astype(np.complex64),
+                            device="cuda")
+        for _ in range(args.steps):
+            out = lc.contract(g)
+        torch.cuda.synchronize()
+        print("rows", args.rows, "info", lc.info(), "<ZZ>[0]", float(out[0, 0]))
     elif args.workload == "qgt":
         circ, theta, _ = W.tfim_workload(args.qubits, 10, args.rows)
         c = nt.Circuit(circ)
