@@ -541,7 +541,8 @@ typedef struct {
   int32_t max_cluster;      /* fused launch with few instances: CTAs (a thread-block cluster) per instance */
   int32_t split_min_items;  /* groups of at least this many work items are split over the cluster */
   int32_t split_groups;     /* groups of the fused launch that are split */
-  int32_t reserved;
+  int32_t blob_ints;        /* fused launch: step records and tables (ints); up to 6144 are staged in shared
+                               memory once, whole, a longer path streams group by group */
 } tc_path_info;
 
 /*

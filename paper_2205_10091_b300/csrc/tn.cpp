@@ -789,6 +789,7 @@ tc_status tc_tn_info(const tc_tn* t, tc_path_info* o) {
       o->tc_steps++;
       o->tc_cmacs += (double)st.M * st.N * st.K;
     }
+  o->blob_ints = tn_fused_ok(*t) ? (int32_t)t->fblob.size() : 0;
   o->max_cluster = t->max_cluster;
   o->split_min_items = t->split_min;
   if (tn_fused_ok(*t))

@@ -93,7 +93,7 @@ class tc_path_info(C.Structure):
                 ("cone_hi", C.c_int32), ("n_inputs", C.c_int32), ("n_active", C.c_int32), ("fused", C.c_int32),
                 ("smem_bytes", C.c_int32), ("fused_groups", C.c_int32), ("tc_steps", C.c_int32),
                 ("tc_cmacs", C.c_double), ("max_cluster", C.c_int32), ("split_min_items", C.c_int32),
-                ("split_groups", C.c_int32), ("reserved", C.c_int32)]
+                ("split_groups", C.c_int32), ("blob_ints", C.c_int32)]
 
 
 class tc_server_options(C.Structure):

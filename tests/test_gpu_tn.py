@@ -83,6 +83,7 @@ def test_cluster_fused_bitwise_equals_one_cta(cluster, split_min):
     n, gates0, obs = W.brick200_workload()
     lc = nt.LightCone(n, [(a, b) for a, b, _ in gates0], obs, greedy_trials=64)
     assert lc.info()["fused"] == 1 and lc.info()["max_cluster"] == 8
+    assert 0 < lc.info()["blob_ints"] <= 6144  # group blocks staged once, whole
     gl = [gates0] + [W.brickwork_u4(n, 8, np.random.default_rng(s)) for s in (7, 8, 9)]
     g = _gates_tensor(gl)
     lc.set_cluster(cluster, split_min)

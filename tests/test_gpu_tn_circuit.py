@@ -133,6 +133,7 @@ def test_circuit_network_cluster_bitwise_equals_one_cta():
     theta = _testbed_rows(circ, 3, 11)
     net = nt.CircuitNetwork(circ, {c: 3}, prune=2, split=True)
     assert net.info()["fused"] == 1
+    assert net.info()["blob_ints"] > 6144  # group blocks streamed through the two shared slots
     net.set_cluster(8, 1)
     a = net.expect(_params(theta)).cpu().numpy()
     net.set_cluster(1)

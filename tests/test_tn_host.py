@@ -144,6 +144,7 @@ def test_cluster_setting_validated_and_reported():
     info = lc.info()
     assert info["max_cluster"] == 8 and info["split_min_items"] == 2048
     assert 1 <= info["split_groups"] < info["fused_groups"]
+    assert 0 < info["blob_ints"] <= 6144
     for bad in ((0, 2048), (3, 2048), (16, 2048), (8, 0)):
         with pytest.raises(RuntimeError):
             lc.set_cluster(*bad)
