@@ -200,21 +200,25 @@ __global__ void k_tn_result(const float2* arena, int64_t arena_total, int64_t of
 }
 
 // Fused executor: one CTA per instance (grid-stride over instances) runs the
-// assembly and the whole path with all live tensors in shared memory.  The path runs group by group (independent
-// steps of one tree level, see tn.h), one barrier per group; the group's work
-// items are spread over the CTA's threads.  With few instances (CL) a
-// thread-block cluster runs each instance: every CTA holds all live tensors,
-// groups below split_min items run redundantly in every CTA (no exchange),
-// and a larger group's 32-item units are dealt over the cluster's warps, each
-// output written into every CTA's shared memory (distributed shared memory)
-// between two cluster barriers: the first keeps those writes from landing in
-// regions a slower CTA still reads, the second publishes them.  Each output is
-// computed by the same code in either case, so results do not depend on CL.  A step computes
-// C[e] = sum_k A[fa(i) + sa(k)] B[sb(k) + fb(j)], e = i N + j, with tpo
-// items per output (a power of two <= 32: small results with long sums
-// spread the sum over lanes and reduce by shuffles).  Group blocks are staged
-// in a double-buffered shared slot: the next block is loaded into registers
-// before the current group computes and stored after it.
+// assembly and the whole path with all live tensors in shared memory.  The
+// path runs group by group (independent steps of one tree level, see tn.h),
+// one barrier per group; a group's work items are spread over the CTA's warps,
+// 32 items (one unit) per warp at a time.  A step computes
+//   C[e] = sum_k A[fa(i) ^ sa(k)] B[sb(k) ^ fb(j)],  e = i N + j,
+// where the tables hold swizzled entry offsets (tn_swz, tn.h) and C[e] is
+// stored at tn_swz(e, rot_c); tpo items per output (a power of two <= 32:
+// small results with long sums spread the sum over lanes and reduce by
+// shuffles).  Group blocks fitting both shared slots are staged once, whole;
+// a longer path's blocks stream through the two slots, the next block loaded
+// into registers before the current group computes and stored after it.
+// With few instances (CL) a thread-block cluster runs each instance: every
+// CTA holds all live tensors, groups below split_min items run redundantly in
+// every CTA (no exchange), and a larger group's units are dealt over the
+// cluster's warps, each output written into every CTA's shared memory
+// (distributed shared memory) between two cluster barriers: the first keeps
+// those writes from landing in regions a slower CTA still reads, the second
+// publishes them.  Each output is computed by the same code in either case, so
+// results do not depend on CL.
 constexpr int kFusedThreads = kTnFusedThreads;
 constexpr int kFusedPf = (kTnBlobMax + kFusedThreads - 1) / kFusedThreads;
 
