@@ -37,6 +37,13 @@
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
  * default stream).  Calls are asynchronous with respect to the host unless
  * stated otherwise; results are valid after the stream is synchronised.
+ *
+ * Host threads: an object returned by a create call (a circuit plan, a
+ * network, a Hamiltonian) builds device copies, captured graphs, launch
+ * shapes and scratch lazily on first use and keeps them; calls on one object
+ * must not overlap in time (the caller serialises them).  Distinct objects
+ * may be used from different threads at once.  A server is the exception:
+ * tc_submit and tc_poll may be called from any thread while it runs.
  */
 #ifndef TC_B300_H
 #define TC_B300_H
