@@ -286,6 +286,18 @@ void tn_layout_fused(TnPlan& P) {
   auto step_tabs = [&](const TnStep& st) {
     return tab_len(lg(st.M)) + 2 * tab_len(lg(st.K)) + tab_len(lg(st.N));
   };
+  // paired steps: one lane per output pair (j, j + 32) of a row, sharing the
+  // A entry and the k tables (one lane per output, rows of >= 64, full tables)
+  auto pair_of = [&](const TnStep& st) { return tpo_of(st) == 1 && st.N >= 64 && lg(st.K) <= kTnFullTabBits; };
+  auto items_of = [&](const TnStep& st) {
+    return (int64_t)st.M * st.N * tpo_of(st) / (pair_of(st) ? 2 : 1);
+  };
+  // output index of a work item: e = item / tpo, or for a paired step the
+  // first output of the pair (blocks of 64 outputs: lanes take j and j + 32)
+  auto out_of = [&](const TnStep& st, int64_t item) -> int64_t {
+    if (pair_of(st)) return ((item >> 5) << 6) | (item & 31);
+    return item / tpo_of(st);
+  };
   // shared-memory swizzle of every tensor (tn_swz), chosen for the lanes of
   // the one step that reads it: two sample warps (the step's first and middle
   // one), two k-iterations each; cost = wavefronts of the warp's loads (the
@@ -294,20 +306,22 @@ void tn_layout_fused(TnPlan& P) {
   for (int s = 0; s < n_steps; ++s) {
     const TnStep& st = P.steps[s];
     const int tpo = tpo_of(st), lgN = lg(st.N);
-    const int64_t n_items = (int64_t)st.M * st.N * tpo;
+    const int64_t n_items = items_of(st);
+    const bool paired = pair_of(st);
     for (int side = 0; side < 2; ++side) {
       int best = 0;
       int64_t best_cost = -1;
       for (int r = 0; r < 4; ++r) {
         int64_t cost = 0;
         for (int64_t w0 : {(int64_t)0, (n_items / 64) * 32}) {
-          for (int it = 0; it < 2; ++it) {
+          for (int it = 0; it < (paired && side == 1 ? 4 : 2); ++it) {
             int32_t words[32];
             int nw = 0;
             for (int l = 0; l < 32; ++l) {
               const int64_t item = w0 + l;
-              const int64_t e = item / tpo;
-              const int k = (int)(item % tpo) + it * tpo;
+              // a paired step's B side loads j (it even) and j + 32 (it odd)
+              const int64_t e = out_of(st, item) + (paired && side == 1 && (it & 1) ? 32 : 0);
+              const int k = paired ? (side == 1 ? it >> 1 : it) : (int)(item % tpo) + it * tpo;
               if (e >= (int64_t)st.M * st.N || k >= st.K) continue;
               const int64_t i = e >> lgN, j = e & (st.N - 1);
               const int32_t x = side == 0 ? P.tables[st.fa + i] + P.tables[st.sa + k]
@@ -355,19 +369,20 @@ void tn_layout_fused(TnPlan& P) {
     if (len > kTnBlobMax) P.fblob_ok = false;
     // steps of the group sorted by tpo so a warp never mixes tpo values
     std::vector<int> gs(order.begin() + g0, order.begin() + g1);
-    std::stable_sort(gs.begin(), gs.end(),
-                     [&](int x, int y) { return tpo_of(P.steps[x]) < tpo_of(P.steps[y]); });
+    auto run_key = [&](int x) { return 2 * tpo_of(P.steps[x]) + (pair_of(P.steps[x]) ? 1 : 0); };
+    std::stable_sort(gs.begin(), gs.end(), [&](int x, int y) { return run_key(x) < run_key(y); });
     for (int s : gs) place(P.steps[s].c, (int64_t)P.steps[s].M * P.steps[s].N);
     const size_t gstart = P.fblob.size();
     starts.push_back(gstart);
     P.fblob.resize(gstart + kTnGHdr + kTnSRec * gs.size(), 0);
     int64_t items = 0;
-    int prev_tpo = -1;
+    int prev_key = -1;
     for (size_t q = 0; q < gs.size(); ++q) {
       const TnStep& st = P.steps[gs[q]];
       const int tpo = tpo_of(st);
-      if (tpo != prev_tpo) items = (items + 31) / 32 * 32;  // a warp never spans two tpo values
-      prev_tpo = tpo;
+      const int key = run_key(gs[q]);
+      if (key != prev_key) items = (items + 31) / 32 * 32;  // a warp never spans two tpo values (or pairings)
+      prev_key = key;
       const int lgM = lg(st.M), lgK = lg(st.K), lgN = lg(st.N);
       if (lgM > 16 || lgK > 16 || lgN > 16) P.fblob_ok = false;
       int32_t* rec = P.fblob.data() + gstart + kTnGHdr + kTnSRec * q;
@@ -378,7 +393,7 @@ void tn_layout_fused(TnPlan& P) {
       rec[4] = lgM;
       rec[5] = lgK;
       rec[6] = lgN;
-      rec[7] = tpo | (rot[st.c] << 8);
+      rec[7] = tpo | (rot[st.c] << 8) | ((pair_of(st) ? 1 : 0) << 16);
       rec[8] = (int32_t)off[st.a];
       rec[9] = (int32_t)off[st.b];
       rec[10] = (int32_t)off[st.c];
@@ -403,8 +418,8 @@ void tn_layout_fused(TnPlan& P) {
       split(st.sb, lgK, rot[st.b]);
       mark(14);
       split(st.fb, lgN, rot[st.b]);
-      items += (int64_t)st.M * st.N * tpo;
-      if ((int64_t)st.M * st.N * tpo > (1 << 26)) P.fblob_ok = false;
+      items += items_of(st);
+      if (items_of(st) > (1 << 26)) P.fblob_ok = false;
     }
     items = (items + 31) / 32 * 32;
     while (P.fblob.size() % 4) P.fblob.push_back(0);  // the next group's records stay 16-byte aligned

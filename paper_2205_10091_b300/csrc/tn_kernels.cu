@@ -299,9 +299,12 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
       if constexpr (CL) {
         if (split) cg::this_cluster().sync();
       }
-      const int nunits = (n_items + 31) >> 5;
+      // a split group deals the two halves of a paired unit to different warps
+      // (one output per lane), keeping the cluster's warps busy
+      const int nunits = (n_items + 31) >> 5, nvirt = split ? 2 * nunits : nunits;
       const int ustride = split ? csize * (kFusedThreads / 32) : kFusedThreads / 32;
-      for (int u = (split ? crank * (kFusedThreads / 32) : 0) + warp; u < nunits; u += ustride) {
+      for (int uv = (split ? crank * (kFusedThreads / 32) : 0) + warp; uv < nvirt; uv += ustride) {
+        const int u = split ? uv >> 1 : uv, half = split ? uv & 1 : 0;
         const int w = (u << 5) + lane;
         int lo = 0, hi = n_st - 1;  // last step whose first item is <= w
         while (lo < hi) {
@@ -311,13 +314,18 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
         const int4* rv = reinterpret_cast<const int4*>(recs + lo * kTnSRec);
         const int4 r0 = rv[0], r1 = rv[1], r2 = rv[2], r3 = rv[3];
         const int M = r0.y, K = r0.z, N = r0.w, lgM = r1.x, lgK = r1.y, lgN = r1.z, tpo = r1.w & 255;
+        const bool pstep = (r1.w >> 16) & 1;  // outputs e and e + 32 of one row (tpo 1, full tables)
+        // a unit never mixes paired and other steps, so both flags are warp-uniform
+        if (half && !pstep) continue;
+        const bool paired = pstep && !split;
         const int local = w - r0.x;
-        const int e = local >> (__ffs(tpo) - 1), part = local & (tpo - 1);
+        const int e = pstep ? (((local >> 5) << 6) | (local & 31)) + 32 * half : local >> (__ffs(tpo) - 1);
+        const int part = pstep ? 0 : local & (tpo - 1);
         const int32_t* fa = g + r2.w;
         const int32_t* sa = g + r3.x;
         const int32_t* sb = g + r3.y;
         const int32_t* fb = g + r3.z;
-        float2 acc = make_float2(0.f, 0.f);
+        float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
         const bool valid = e < M * N;
         if (valid) {
           const float2* As = sm + r2.x;
@@ -330,7 +338,19 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
             acc.y = fmaf(a.x, c.y, fmaf(a.y, c.x, acc.y));
           };
           // the same sums in the same order; the loops differ in table form and stride only
-          if (lgK <= kTnFullTabBits && tpo == 1) {
+          if (paired) {
+            const int bj1 = tn_tab(fb, lgN, (e + 32) & (N - 1));
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) {
+              const float2 a = As[ai ^ sa[k]];
+              const int kb = sb[k];
+              const float2 c = Bs[bj ^ kb], c1 = Bs[bj1 ^ kb];
+              acc.x = fmaf(a.x, c.x, fmaf(-a.y, c.y, acc.x));
+              acc.y = fmaf(a.x, c.y, fmaf(a.y, c.x, acc.y));
+              acc1.x = fmaf(a.x, c1.x, fmaf(-a.y, c1.y, acc1.x));
+              acc1.y = fmaf(a.x, c1.y, fmaf(a.y, c1.x, acc1.y));
+            }
+          } else if (lgK <= kTnFullTabBits && tpo == 1) {
 #pragma unroll 4
             for (int k = 0; k < K; ++k) mac(sa[k], sb[k]);
           } else if (lgK <= kTnFullTabBits) {
@@ -346,14 +366,17 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
           acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
         }
         if (valid && part == 0) {
-          const int ce = r2.z + tn_swz(e, r1.w >> 8);
+          const int rot = (r1.w >> 8) & 3;
+          const int ce = r2.z + tn_swz(e, rot), ce1 = r2.z + tn_swz(e + 32, rot);
           sm[ce] = acc;
+          if (paired) sm[ce1] = acc1;
           if constexpr (CL) {
             if (split) {
               cg::cluster_group cl = cg::this_cluster();
               for (int q = 1; q < csize; ++q) {
                 const int dst = crank + q < csize ? crank + q : crank + q - csize;
                 *cl.map_shared_rank(sm + ce, dst) = acc;
+                if (paired) *cl.map_shared_rank(sm + ce1, dst) = acc1;
               }
             }
           }
