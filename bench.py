@@ -546,7 +546,11 @@ def extra_workloads(serve_rates=(250.0, 500.0, 1000.0, 2000.0), serve_seconds: f
         "zz": float(o1[0, 0].item()), "us_per_contraction": ms_tn * 1e3,
         "batched_contractions_per_s": Bt / (ms_tnb / 1e3), "batch_seeds": Bt,
         "log10_flops": float(np.log10(info["flops"])), "log2_size": float(np.log2(info["size"])),
-        "log2_write": float(np.log2(info["write"])), "steps": info["n_steps"], "cone_gates": info["n_cone_gates"]}
+        "log2_write": float(np.log2(info["write"])), "steps": info["n_steps"], "cone_gates": info["n_cone_gates"],
+        "executor": {"fused": info["fused"], "level_groups": info["fused_groups"],
+                     "live_kib": info["smem_bytes"] / 1024, "b1": f"{info['max_cluster']}-CTA cluster",
+                     "split_groups_b1": info["split_groups"], "batched": "one CTA per seed"},
+        "timing": "CUDA events around back-to-back calls (B = 1: 200 calls; batched: 20)"}
     del gb, ob
     # ---- contraction testbed: 40 qubits, 6 layers of ZZ + RX, <Z_20> -------
     cb40 = W.example_block_circuit(40, 6)
