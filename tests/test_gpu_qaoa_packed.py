@@ -17,6 +17,7 @@ from paper_2205_10091_b300 import native as nt
 from paper_2205_10091_b300 import workloads as W
 
 from gpu_util import TOL_AMP_C64, TOL_AMP_C128, assert_energy_close, assert_grad_close, cuda_params
+from qaoa_cone import edge_cone
 
 pytestmark = pytest.mark.gpu
 
@@ -106,6 +107,36 @@ def test_packed_pauli_sum_terms_next_to_other_terms(dtype):
         if dtype == nt.TC_C128:
             assert abs(e[b] - e_ref) <= 1e-11 * max(1, abs(e_ref))
             assert np.abs(g[b] - g_ref).max() <= 1e-10 * max(1, np.abs(g_ref).max())
+        else:
+            assert_energy_close(e[b:b + 1], [e_ref])
+            assert_grad_close(g[b], g_ref)
+
+
+@pytest.mark.parametrize("p,dtype,specialize", [(1, nt.TC_C64, False), (1, nt.TC_C64, True), (1, nt.TC_C128, False),
+                                                (2, nt.TC_C64, False)])
+def test_qaoa26_full_width_against_edge_light_cones(p, dtype, specialize):
+    """The serving stream's widest request: MaxCut QAOA on a random 3-regular
+    graph of 26 qubits (H = sum over edges of Z_u Z_v).  The oracle evaluates
+    each edge's term and its parameter-shift gradient on that edge's light cone
+    (at most 6 qubits for p = 1, 14 for p = 2) in FP64; the sums are the exact
+    26-qubit energy and gradient."""
+    n = 26
+    rng = np.random.default_rng(2600 + p)
+    edges = W.random_regular3(n, rng)
+    circ = W.qaoa_circuit(n, edges, p)
+    ham = W.zz_on_edges(n, edges)
+    theta = rng.uniform(0.0, np.pi, size=(2, 2 * p))
+    c = nt.Circuit(circ, dtype=dtype, specialize=specialize)
+    e, g = c.expect_grad(cuda_params(theta), nt.Hamiltonian(ham))
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    cones = [edge_cone(circ, u, v) for (u, v) in edges]
+    assert max(cc.n for cc, _ in cones) <= (6 if p == 1 else 14)
+    for b in range(2):
+        e_ref = sum(sv.energy(sv.run_circuit(cc, theta[b]), cc.n, hh)[0] for cc, hh in cones)
+        g_ref = sum(G.parameter_shift(cc, theta[b], hh) for cc, hh in cones)
+        if dtype == nt.TC_C128:
+            assert abs(e[b] - e_ref) <= 1e-10 * max(1, abs(e_ref))
+            assert np.abs(g[b] - g_ref).max() <= 1e-9 * max(1, np.abs(g_ref).max())
         else:
             assert_energy_close(e[b:b + 1], [e_ref])
             assert_grad_close(g[b], g_ref)
