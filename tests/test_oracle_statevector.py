@@ -5,6 +5,7 @@ import os
 import numpy as np
 import pytest
 
+from oracle import gradients as G
 from oracle import statevector as sv
 from paper_2205_10091_b300 import workloads as W
 
@@ -260,3 +261,26 @@ def test_norm_preserved_large():
     circ = W.random_circuit(12, 80, rng)
     psi = sv.run_circuit(circ, rng.uniform(-3, 3, circ.n_params))
     assert abs(np.linalg.norm(psi) - 1) < 1e-13
+
+
+@pytest.mark.parametrize("n", [3, 6])
+def test_ghz_type_state_closed_forms(n):
+    """RY(theta) on qubit 0 and a CNOT chain give cos(theta/2)|0..0> +
+    sin(theta/2)|1..1>: <X^(x)n> = sin(theta), <Y Y X..X> = -sin(theta),
+    <Z_0> = cos(theta), <Z_0 Z_{n-1}> = 1 (the closed forms of the 30-qubit GPU
+    test), and their parameter-shift derivatives."""
+    b = W.OpBuilder(n, W.INIT_ZERO)
+    b.ry(0, 0)
+    for q in range(n - 1):
+        b.cnot(q, q + 1)
+    circ = b.build(1)
+    ystr = {0: 2, 1: 2}
+    ystr.update({q: 1 for q in range(2, n)})
+    terms = [{q: 1 for q in range(n)}, {0: 3}, {0: 3, n - 1: 3}, ystr]
+    for theta in (0.37, 2.9, -1.3):
+        psi = sv.run_circuit(circ, [theta])
+        assert abs(psi[0] - np.cos(theta / 2)) < 1e-14 and abs(psi[-1] - np.sin(theta / 2)) < 1e-14
+        vals = [sv.energy(psi, n, W.pauli_sum(n, [(1.0, t)]))[0] for t in terms]
+        assert np.allclose(vals, [np.sin(theta), np.cos(theta), 1.0, -np.sin(theta)], atol=1e-14)
+        ders = [G.parameter_shift(circ, [theta], W.pauli_sum(n, [(1.0, t)]))[0] for t in terms]
+        assert np.allclose(ders, [np.cos(theta), -np.sin(theta), 0.0, -np.cos(theta)], atol=1e-13)
