@@ -29,7 +29,10 @@
  * Host arrays passed to a create call are copied before it returns.
  *
  * Errors: every entry point returns a tc_status.  Argument errors are found
- * on the host before any launch and leave device memory untouched.  A CUDA
+ * on the host before any launch and leave device memory untouched.  B = 0 (no
+ * rows or instances) is a valid call on every batched entry point: after the
+ * checks of its other arguments it returns TC_OK without a launch, and its
+ * device buffer pointers may then be NULL.  A CUDA
  * launch or runtime error returns TC_E_CUDA.  tc_last_error() returns a
  * thread-local message for the last non-TC_OK status.  No exception crosses
  * the ABI and no device code traps.

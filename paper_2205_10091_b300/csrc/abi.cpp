@@ -486,7 +486,7 @@ tc_status tc_dm_circuit_create(int n_qubits, tc_dtype dtype, tc_init init, const
 
 tc_status tc_dm_expect_pauli_sum(tc_circuit* c, const void* d_rho, int B, const uint8_t* structures,
                                  const double* weights, int T, double* d_out, void* stream) {
-  if (!c || !d_rho || !d_out) return fail(TC_E_INVALID, "NULL argument");
+  if (!c || (B != 0 && (!d_rho || !d_out))) return fail(TC_E_INVALID, "NULL argument");
   if (c->dm_n <= 0) return fail(TC_E_INVALID, "not a density-matrix circuit (tc_dm_circuit_create)");
   if (B < 0 || T < 0 || (T > 0 && (!structures || !weights))) return fail(TC_E_INVALID, "bad Pauli sum or B");
   if (B == 0) return TC_OK;
@@ -567,7 +567,7 @@ tc_status tc_pauli_sum_info(const tc_circuit* c, const uint8_t* structures, cons
 tc_status tc_apply_layers(const tc_circuit* cc, const double* d_params, int B, const void* d_init, uint64_t seed,
                           const float* d_status, int64_t row_offset, void* d_states_out, void* stream) {
   tc_circuit* c = const_cast<tc_circuit*>(cc);
-  if (!c || !d_states_out) return fail(TC_E_INVALID, "NULL circuit or output");
+  if (!c || (B != 0 && !d_states_out)) return fail(TC_E_INVALID, "NULL circuit or output");
   if (B < 0) return fail(TC_E_INVALID, "B < 0");
   if (c->n_params > 0 && !d_params && B > 0) return fail(TC_E_INVALID, "d_params is NULL");
   if (B == 0) return TC_OK;
@@ -610,7 +610,7 @@ tc_status tc_apply_layers(const tc_circuit* cc, const double* d_params, int B, c
 
 tc_status tc_expect_pauli_sum(tc_circuit* c, const void* d_states, int B, const uint8_t* structures,
                               const double* weights, int T, double* d_energy_out, void* stream) {
-  if (!c || !d_states || !d_energy_out) return fail(TC_E_INVALID, "NULL argument");
+  if (!c || (B != 0 && (!d_states || !d_energy_out))) return fail(TC_E_INVALID, "NULL argument");
   if (B < 0) return fail(TC_E_INVALID, "B < 0");
   if (B == 0) return TC_OK;
   tc_status st = ensure_device(c);
@@ -777,7 +777,7 @@ extern "C" {
 tc_status tc_expect_grad(tc_circuit* c, const double* d_params, int B, const uint8_t* structures,
                          const double* weights, int T, uint64_t seed, double* d_energy_out, double* d_grad_out,
                          const tc_grad_options* gopt, void* stream) {
-  if (!c || !d_energy_out) return fail(TC_E_INVALID, "NULL argument");
+  if (!c || (B != 0 && !d_energy_out)) return fail(TC_E_INVALID, "NULL argument");
   if (B < 0) return fail(TC_E_INVALID, "B < 0");
   if (c->n_params > 0 && (!d_params || !d_grad_out) && B > 0) return fail(TC_E_INVALID, "d_params/d_grad_out NULL");
   if (gopt && gopt->mode != TC_GRAD_UNCOMPUTE && gopt->mode != TC_GRAD_CHECKPOINT)
@@ -811,7 +811,7 @@ tc_status tc_expect_grad(tc_circuit* c, const double* d_params, int B, const uin
 
 tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, const uint8_t* structures,
                           const double* weights, int T, void* d_states_work, double* d_energy_out, void* stream) {
-  if (!c || !d_states_work || !d_energy_out) return fail(TC_E_INVALID, "NULL argument");
+  if (!c || (B != 0 && (!d_states_work || !d_energy_out))) return fail(TC_E_INVALID, "NULL argument");
   if (B < 0 || T < 0) return fail(TC_E_INVALID, "B < 0 or T < 0");
   if (T > 0 && (!structures || !weights)) return fail(TC_E_INVALID, "structures/weights NULL");
   if (c->N != c->n) return fail(TC_E_UNSUPPORTED, "the unfused baseline needs n >= 9");
@@ -853,7 +853,7 @@ tc_status tc_expect_plain(tc_circuit* c, const double* d_params, int B, const ui
 }
 
 tc_status tc_state_norms(tc_circuit* c, const void* d_states, int B, double* d_norm2_out, void* stream) {
-  if (!c || !d_states || !d_norm2_out) return fail(TC_E_INVALID, "NULL argument");
+  if (!c || (B != 0 && (!d_states || !d_norm2_out))) return fail(TC_E_INVALID, "NULL argument");
   if (B < 0) return fail(TC_E_INVALID, "B < 0");
   if (B == 0) return TC_OK;
   const bool dbl = is_dbl(c);

@@ -49,7 +49,7 @@ using namespace tcb;
 extern "C" tc_status tc_expect_pauli_sum_noalloc(const tc_circuit* c, const void* d_states, int B,
                                                  const uint8_t* structures, const double* weights, int T,
                                                  double* d_energy_out, void* stream) {
-  if (!c || !d_states || !d_energy_out) return fail(TC_E_INVALID, "NULL argument");
+  if (!c || (B != 0 && (!d_states || !d_energy_out))) return fail(TC_E_INVALID, "NULL argument");
   if (B < 0 || T < 0) return fail(TC_E_INVALID, "B < 0 or T < 0");
   if (T > 0 && (!structures || !weights)) return fail(TC_E_INVALID, "structures/weights are NULL");
   if (c->N != c->n) return fail(TC_E_UNSUPPORTED, "the allocation-free entry point needs n >= 10");

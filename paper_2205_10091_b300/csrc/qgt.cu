@@ -640,7 +640,7 @@ int grid_for(int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>
 extern "C" {
 
 tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, void* stream) {
-  if (!c || !d_out) return fail(TC_E_INVALID, "NULL circuit or output");
+  if (!c || (B != 0 && !d_out)) return fail(TC_E_INVALID, "NULL circuit or output");
   if (B < 0) return fail(TC_E_INVALID, "B < 0");
   if (c->n_params > 0 && !d_params && B > 0) return fail(TC_E_INVALID, "d_params is NULL");
   if (c->dm_n > 0) return fail(TC_E_UNSUPPORTED, "geometric tensor of a density-matrix circuit");
@@ -764,7 +764,7 @@ tc_status tc_qgt(tc_circuit* c, const double* d_params, int B, double* d_out, vo
 
 tc_status tc_natural_gradient(const double* d_qgt, const double* d_grad, int B, int P, double eps, double* d_out,
                               void* stream) {
-  if (!d_qgt || !d_grad || !d_out) return fail(TC_E_INVALID, "NULL argument");
+  if (B != 0 && (!d_qgt || !d_grad || !d_out)) return fail(TC_E_INVALID, "NULL argument");
   if (B < 0 || P < 1) return fail(TC_E_INVALID, "B < 0 or P < 1");
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(TC_E_INVALID, "eps must be positive and finite");
   if (P > kNgMaxP) return fail(TC_E_UNSUPPORTED, "natural gradient for more than 128 parameters");

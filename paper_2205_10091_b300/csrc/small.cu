@@ -713,7 +713,7 @@ tc_status tc_apply_expect(tc_circuit* c, const double* d_params, int B, int K, c
                           double* d_values_out, void* stream) {
   if (!c) return fail(TC_E_INVALID, "NULL circuit");
   if (B < 0 || K < 0) return fail(TC_E_INVALID, "B < 0 or K < 0");
-  if (K > 0 && (!T || !d_values_out)) return fail(TC_E_INVALID, "T or d_values_out is NULL");
+  if (K > 0 && (!T || (B != 0 && !d_values_out))) return fail(TC_E_INVALID, "T or d_values_out is NULL");
   if (c->n_params > 0 && !d_params && B > 0) return fail(TC_E_INVALID, "d_params is NULL");
   if (c->dm_n > 0) return fail(TC_E_UNSUPPORTED, "density-matrix circuits: use tc_dm_expect_pauli_sum");
   int total = 0;

@@ -1027,8 +1027,10 @@ extern "C" {
 
 tc_status tc_contract_path(tc_tn* t, int B, const float* d_gates, tc_tn_precision precision, double* d_out,
                            void* stream) {
-  if (!t || !d_gates || !d_out) return fail(TC_E_INVALID, "NULL argument");
+  if (!t || (B != 0 && (!d_gates || !d_out))) return fail(TC_E_INVALID, "NULL argument");
   if (t->circuit) return fail(TC_E_INVALID, "plan was built from a circuit: use tc_tn_circuit_expect");
+  if (precision != TC_TN_FP32 && precision != TC_TN_TF32X3 && precision != TC_TN_BF16X6)
+    return fail(TC_E_INVALID, "unknown precision");
   if (B <= 0) return B == 0 ? TC_OK : fail(TC_E_INVALID, "B < 0");
   return tn_run(t, B, d_gates, d_out, (int)precision, stream);
 }
@@ -1060,9 +1062,11 @@ tc_status tc_tn_circuit_create(int n_qubits, tc_init init, const tc_op* ops, int
 
 tc_status tc_tn_circuit_expect(tc_tn* t, int B, const float* d_params, tc_tn_precision precision, double* d_out,
                                void* stream) {
-  if (!t || !d_out) return fail(TC_E_INVALID, "NULL argument");
+  if (!t || (B != 0 && !d_out)) return fail(TC_E_INVALID, "NULL argument");
   if (!t->circuit) return fail(TC_E_INVALID, "plan is a light-cone gate network: use tc_contract_path");
-  if (t->n_params > 0 && !d_params) return fail(TC_E_INVALID, "d_params is NULL");
+  if (precision != TC_TN_FP32 && precision != TC_TN_TF32X3 && precision != TC_TN_BF16X6)
+    return fail(TC_E_INVALID, "unknown precision");
+  if (t->n_params > 0 && B != 0 && !d_params) return fail(TC_E_INVALID, "d_params is NULL");
   if (B <= 0) return B == 0 ? TC_OK : fail(TC_E_INVALID, "B < 0");
   return tn_run(t, B, d_params, d_out, (int)precision, stream);
 }

@@ -241,3 +241,47 @@ def test_apply_expect_validates_on_the_host():
     assert L.tc_apply_expect(c.h, fake, 1, 1, C.cast(T, C.c_void_p), None, None, None, fake, None) == nt.TC_E_INVALID
     assert L.tc_apply_expect(c.h, fake, -1, 0, None, None, None, None, None, None) == nt.TC_E_INVALID
     assert L.tc_apply_expect(c.h, fake, 0, 0, None, None, None, None, None, None) == nt.TC_OK
+
+
+def test_zero_rows_accept_null_buffers_and_one_row_refuses_them():
+    """B = 0 is a valid call on every batched entry point: it returns TC_OK
+    after the argument checks, before any launch, with NULL device buffers.
+    The same NULL buffers with B = 1 are refused (TC_E_INVALID).  No GPU is
+    touched either way."""
+    import ctypes as C
+
+    n = 12
+    b = W.OpBuilder(n, W.INIT_PLUS)
+    for q in range(n):
+        b.rx(q, 0)
+    b.rzz(0, 1, 1)
+    c = nt.Circuit(b.build(2))
+    L = nt.lib()
+    s = np.zeros((1, n), np.uint8)
+    s[0, 0] = 3
+    w = np.ones(1)
+    sp, wp = s.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p)
+    T = (C.c_int * 1)(1)
+    calls = {
+        "apply_layers": lambda B: L.tc_apply_layers(c.h, None, B, None, 0, None, 0, None, None),
+        "expect_pauli_sum": lambda B: L.tc_expect_pauli_sum(c.h, None, B, sp, wp, 1, None, None),
+        "expect_grad": lambda B: L.tc_expect_grad(c.h, None, B, sp, wp, 1, 0, None, None, None, None),
+        "expect_plain": lambda B: L.tc_expect_plain(c.h, None, B, sp, wp, 1, None, None, None),
+        "state_norms": lambda B: L.tc_state_norms(c.h, None, B, None, None),
+        "qgt": lambda B: L.tc_qgt(c.h, None, B, None, None),
+        "natural_gradient": lambda B: L.tc_natural_gradient(None, None, B, 2, C.c_double(1e-3), None, None),
+        "apply_expect": lambda B: L.tc_apply_expect(c.h, None, B, 1, T, sp, wp, None, None, None),
+    }
+    n_lc, gates, zq = W.brick200_workload()
+    lc = nt.LightCone(n_lc, [(a, q) for a, q, _ in gates], zq)
+    net = nt.CircuitNetwork(W.example_block_circuit(40, 6), {20: 3}, prune=2)
+    calls["contract_path"] = lambda B: L.tc_contract_path(lc.h, B, None, nt.TC_TN_FP32, None, None)
+    calls["tn_circuit_expect"] = lambda B: L.tc_tn_circuit_expect(net.h, B, None, nt.TC_TN_FP32, None, None)
+    for name, call in calls.items():
+        assert call(0) == nt.TC_OK, name
+        assert call(1) == nt.TC_E_INVALID, name
+    # the other arguments are still checked with no rows
+    assert L.tc_contract_path(lc.h, 0, None, 7, None, None) == nt.TC_E_INVALID
+    assert L.tc_tn_circuit_expect(net.h, 0, None, 7, None, None) == nt.TC_E_INVALID
+    assert L.tc_natural_gradient(None, None, 0, 2, C.c_double(-1.0), None, None) == nt.TC_E_INVALID
+    assert L.tc_expect_grad(c.h, None, -1, sp, wp, 1, 0, None, None, None, None) == nt.TC_E_INVALID
