@@ -277,10 +277,13 @@ void tn_layout_fused(TnPlan& P) {
   std::vector<int> order(n_steps);
   for (int s = 0; s < n_steps; ++s) order[s] = s;
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lvl[x] < lvl[y]; });
+  // lanes per output: enough to fill the CTA with a small result, but each
+  // lane keeps at least four terms of the sum (a shorter share costs more in
+  // shuffles and work units than it saves)
   auto tpo_of = [](const TnStep& st) {
     int t = kTnFusedThreads / std::max(1, st.M * st.N);
     t = std::max(1, std::min(32, t));
-    while (t > st.K) t >>= 1;
+    while (t > 1 && 4 * t > st.K) t >>= 1;
     return t;
   };
   auto step_tabs = [&](const TnStep& st) {
