@@ -289,9 +289,14 @@ void tn_layout_fused(TnPlan& P) {
   auto step_tabs = [&](const TnStep& st) {
     return tab_len(lg(st.M)) + 2 * tab_len(lg(st.K)) + tab_len(lg(st.N));
   };
-  // paired steps: one lane per output pair (j, j + 32) of a row, sharing the
-  // A entry and the k tables (one lane per output, rows of >= 64, full tables)
-  auto pair_of = [&](const TnStep& st) { return tpo_of(st) == 1 && st.N >= 64 && lg(st.K) <= kTnFullTabBits; };
+  // paired steps (one lane per output, >= 64 outputs, full tables): a lane
+  // computes outputs e and e + 32, which share A's row when rows hold >= 64
+  // outputs (mode 1) and B's column otherwise (mode 2: e + 32 is row i + 32 / N)
+  auto pair_mode = [&](const TnStep& st) {
+    if (tpo_of(st) != 1 || (int64_t)st.M * st.N < 64 || lg(st.K) > kTnFullTabBits) return 0;
+    return st.N >= 64 ? 1 : 2;
+  };
+  auto pair_of = [&](const TnStep& st) { return pair_mode(st) != 0; };
   auto items_of = [&](const TnStep& st) {
     return (int64_t)st.M * st.N * tpo_of(st) / (pair_of(st) ? 2 : 1);
   };
@@ -317,14 +322,14 @@ void tn_layout_fused(TnPlan& P) {
       for (int r = 0; r < 4; ++r) {
         int64_t cost = 0;
         for (int64_t w0 : {(int64_t)0, (n_items / 64) * 32}) {
-          for (int it = 0; it < (paired && side == 1 ? 4 : 2); ++it) {
+          for (int it = 0; it < (paired ? 4 : 2); ++it) {
             int32_t words[32];
             int nw = 0;
             for (int l = 0; l < 32; ++l) {
               const int64_t item = w0 + l;
-              // a paired step's B side loads j (it even) and j + 32 (it odd)
-              const int64_t e = out_of(st, item) + (paired && side == 1 && (it & 1) ? 32 : 0);
-              const int k = paired ? (side == 1 ? it >> 1 : it) : (int)(item % tpo) + it * tpo;
+              // a paired step loads for outputs e (it even) and e + 32 (it odd)
+              const int64_t e = out_of(st, item) + (paired && (it & 1) ? 32 : 0);
+              const int k = paired ? it >> 1 : (int)(item % tpo) + it * tpo;
               if (e >= (int64_t)st.M * st.N || k >= st.K) continue;
               const int64_t i = e >> lgN, j = e & (st.N - 1);
               const int32_t x = side == 0 ? P.tables[st.fa + i] + P.tables[st.sa + k]
@@ -396,7 +401,7 @@ void tn_layout_fused(TnPlan& P) {
       rec[4] = lgM;
       rec[5] = lgK;
       rec[6] = lgN;
-      rec[7] = tpo | (rot[st.c] << 8) | ((pair_of(st) ? 1 : 0) << 16);
+      rec[7] = tpo | (rot[st.c] << 8) | (pair_mode(st) << 16);
       rec[8] = (int32_t)off[st.a];
       rec[9] = (int32_t)off[st.b];
       rec[10] = (int32_t)off[st.c];

@@ -314,7 +314,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
         const int4* rv = reinterpret_cast<const int4*>(recs + lo * kTnSRec);
         const int4 r0 = rv[0], r1 = rv[1], r2 = rv[2], r3 = rv[3];
         const int M = r0.y, K = r0.z, N = r0.w, lgM = r1.x, lgK = r1.y, lgN = r1.z, tpo = r1.w & 255;
-        const bool pstep = (r1.w >> 16) & 1;  // outputs e and e + 32 of one row (tpo 1, full tables)
+        // outputs e and e + 32 (tpo 1, full tables): pmode 1 shares A's row, 2 B's column
+        const int pmode = (r1.w >> 16) & 3;
+        const bool pstep = pmode != 0;
         // a unit never mixes paired and other steps, so both flags are warp-uniform
         if (half && !pstep) continue;
         const bool paired = pstep && !split;
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
             acc.y = fmaf(a.x, c.y, fmaf(a.y, c.x, acc.y));
           };
           // the same sums in the same order; the loops differ in table form and stride only
-          if (paired) {
+          if (paired && pmode == 1) {
             const int bj1 = tn_tab(fb, lgN, (e + 32) & (N - 1));
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
@@ -349,6 +351,18 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
               acc.y = fmaf(a.x, c.y, fmaf(a.y, c.x, acc.y));
               acc1.x = fmaf(a.x, c1.x, fmaf(-a.y, c1.y, acc1.x));
               acc1.y = fmaf(a.x, c1.y, fmaf(a.y, c1.x, acc1.y));
+            }
+          } else if (paired) {
+            const int ai1 = tn_tab(fa, lgM, (e + 32) >> lgN);
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) {
+              const int ka = sa[k];
+              const float2 a = As[ai ^ ka], a1 = As[ai1 ^ ka];
+              const float2 c = Bs[bj ^ sb[k]];
+              acc.x = fmaf(a.x, c.x, fmaf(-a.y, c.y, acc.x));
+              acc.y = fmaf(a.x, c.y, fmaf(a.y, c.x, acc.y));
+              acc1.x = fmaf(a1.x, c.x, fmaf(-a1.y, c.y, acc1.x));
+              acc1.y = fmaf(a1.x, c.y, fmaf(a1.y, c.x, acc1.y));
             }
           } else if (lgK <= kTnFullTabBits && tpo == 1) {
 #pragma unroll 4
