@@ -286,8 +286,8 @@ void tn_layout_fused(TnPlan& P) {
     while (t > 1 && 4 * t > st.K) t >>= 1;
     return t;
   };
-  auto step_tabs = [&](const TnStep& st) {
-    return tab_len(lg(st.M)) + 2 * tab_len(lg(st.K)) + tab_len(lg(st.N));
+  auto step_tabs = [&](const TnStep& st) {  // + 1: the pair table's alignment word
+    return tab_len(lg(st.M)) + 2 * tab_len(lg(st.K)) + tab_len(lg(st.N)) + 1;
   };
   // paired steps (one lane per output, >= 64 outputs, full tables): a lane
   // computes outputs e and e + 32, which share A's row when rows hold >= 64
@@ -420,10 +420,22 @@ void tn_layout_fused(TnPlan& P) {
       };
       mark(11);
       split(st.fa, lgM, rot[st.a]);
-      mark(12);
-      split(st.sa, lgK, rot[st.a]);
-      mark(13);
-      split(st.sb, lgK, rot[st.b]);
+      if (lgK <= kTnFullTabBits) {
+        // full k tables interleaved as (sa[k], sb[k]) pairs at an even offset:
+        // one 8-byte load per k (the group block starts 16-byte aligned)
+        if ((P.fblob.size() - gstart) & 1) P.fblob.push_back(0);
+        mark(12);
+        for (int v = 0; v < (1 << lgK); ++v) {
+          P.fblob.push_back(tn_swz(P.tables[st.sa + v], rot[st.a]));
+          P.fblob.push_back(tn_swz(P.tables[st.sb + v], rot[st.b]));
+        }
+        P.fblob[gstart + kTnGHdr + kTnSRec * q + 13] = P.fblob[gstart + kTnGHdr + kTnSRec * q + 12] + 1;
+      } else {
+        mark(12);
+        split(st.sa, lgK, rot[st.a]);
+        mark(13);
+        split(st.sb, lgK, rot[st.b]);
+      }
       mark(14);
       split(st.fb, lgN, rot[st.b]);
       items += items_of(st);

@@ -65,7 +65,9 @@ struct TnStep {
 //     offsets of the step's four tables from the group start; each group's
 //     block is padded to a multiple of four ints
 //   tables: per step fa, sa, sb, fb, each entry already swizzled with its
-//     operand's rotation; an index set of g <= 8 bits as one full table, a
+//     operand's rotation (a full k table, K <= 256, is stored as (sa[k], sb[k])
+//     pairs at an even offset, sb = sa + 1 with stride 2); an index set of
+//     g <= 8 bits as one full table, a
 //     wider one split in two levels: lo = the lowest (g + 1) / 2 bits,
 //     table(v) = lo[v & (2^lo - 1)] ^ hi[v >> lo].  The swizzle is linear over
 //     XOR and the index sets of one operand scatter to disjoint bit positions,

@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
         const int32_t* fa = g + r2.w;
         const int32_t* sa = g + r3.x;
         const int32_t* sb = g + r3.y;
+        const int2* sab = reinterpret_cast<const int2*>(sa);  // full k tables: (sa[k], sb[k]) pairs
         const int32_t* fb = g + r3.z;
         float2 acc = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
         const bool valid = e < M * N;
@@ -344,8 +345,9 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
             const int bj1 = tn_tab(fb, lgN, (e + 32) & (N - 1));
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
-              const float2 a = As[ai ^ sa[k]];
-              const int kb = sb[k];
+              const int2 kk = sab[k];
+              const float2 a = As[ai ^ kk.x];
+              const int kb = kk.y;
               const float2 c = Bs[bj ^ kb], c1 = Bs[bj1 ^ kb];
               acc.x = fmaf(a.x, c.x, fmaf(-a.y, c.y, acc.x));
               acc.y = fmaf(a.x, c.y, fmaf(a.y, c.x, acc.y));
@@ -356,9 +358,10 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
             const int ai1 = tn_tab(fa, lgM, (e + 32) >> lgN);
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
-              const int ka = sa[k];
+              const int2 kk = sab[k];
+              const int ka = kk.x;
               const float2 a = As[ai ^ ka], a1 = As[ai1 ^ ka];
-              const float2 c = Bs[bj ^ sb[k]];
+              const float2 c = Bs[bj ^ kk.y];
               acc.x = fmaf(a.x, c.x, fmaf(-a.y, c.y, acc.x));
               acc.y = fmaf(a.x, c.y, fmaf(a.y, c.x, acc.y));
               acc1.x = fmaf(a1.x, c.x, fmaf(-a1.y, c.y, acc1.x));
@@ -366,10 +369,16 @@ __global__ void __launch_bounds__(kFusedThreads) k_tn_fused(const TnInput* __res
             }
           } else if (lgK <= kTnFullTabBits && tpo == 1) {
 #pragma unroll 4
-            for (int k = 0; k < K; ++k) mac(sa[k], sb[k]);
+            for (int k = 0; k < K; ++k) {
+              const int2 kk = sab[k];
+              mac(kk.x, kk.y);
+            }
           } else if (lgK <= kTnFullTabBits) {
 #pragma unroll 4
-            for (int k = part; k < K; k += tpo) mac(sa[k], sb[k]);
+            for (int k = part; k < K; k += tpo) {
+              const int2 kk = sab[k];
+              mac(kk.x, kk.y);
+            }
           } else {
             for (int k = part; k < K; k += tpo) mac(tn_tab(sa, lgK, k), tn_tab(sb, lgK, k));
           }
