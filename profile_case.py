@@ -11,6 +11,8 @@
                                                           # MaxCut QAOA on a random 3-regular graph
     python profile_case.py --workload cone200 --rows 1 --cluster 8
                                                           # <Z99 Z100> light cone of the 200-qubit brickwork
+    python profile_case.py --workload hea10_one --steps 4
+                                                          # the 10-qubit ansatz, state and observables in one launch
 """
 import numpy as np
 import argparse
@@ -23,7 +25,7 @@ from paper_2205_10091_b300 import workloads as W
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="tfim20", choices=["tfim20", "noisy16", "hea10", "qgt", "tn40", "qaoa", "cone200"])
+    ap.add_argument("--workload", default="tfim20", choices=["tfim20", "noisy16", "hea10", "hea10_one", "qgt", "tn40", "qaoa", "cone200"])
     ap.add_argument("--rows", type=int, default=32)
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--qubits", type=int, default=16)
@@ -79,6 +81,15 @@ def main():
             out = lc.contract(g)
         torch.cuda.synchronize()
         print("rows", args.rows, "info", lc.info(), "<ZZ>[0]", float(out[0, 0]))
+    elif args.workload == "hea10_one":
+        circ, theta, obs = W.hea10_workload()
+        c = nt.Circuit(circ, dtype=nt.TC_C128)
+        d = torch.as_tensor(theta, device="cuda")
+        o = nt.Observables(obs)
+        for _ in range(args.steps):
+            st, vals = c.apply_expect(d, o, 1)
+        torch.cuda.synchronize()
+        print("one launch", vals.cpu().numpy())
     elif args.workload == "qgt":
         circ, theta, _ = W.tfim_workload(args.qubits, 10, args.rows)
         c = nt.Circuit(circ)
