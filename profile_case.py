@@ -32,7 +32,7 @@ def main():
     ap.add_argument("--precision", type=int, default=1, help="tn40: 0 FP32, 1 TF32X3, 2 BF16X6")
     ap.add_argument("--layers", type=int, default=3, help="qaoa: layers p")
     ap.add_argument("--cluster", type=int, default=8, help="cone200: CTAs per instance of the fused launch (1 = off)")
-    ap.add_argument("--specialize", action="store_true", help="tfim20, qaoa: pass kernels compiled for the circuit")
+    ap.add_argument("--specialize", action="store_true", help="tfim20, qaoa, noisy16: pass kernels compiled for the circuit")
     args = ap.parse_args()
     if args.workload == "tfim20":
         circ, theta, ham = W.tfim_workload(20, 10, args.rows)
@@ -55,7 +55,7 @@ def main():
         print("rows", args.rows, "plan", c.info(), "E[0]", float(e[0]))
     elif args.workload == "noisy16":
         circ, n_traj, seed, obs = W.noisy16_workload()
-        c = nt.Circuit(circ)
+        c = nt.Circuit(circ, specialize=args.specialize)
         for _ in range(args.steps):
             st = c.apply(None, n_traj, seed=seed)
             vals = [c.expect(st, nt.Hamiltonian(o)) for o in obs]
